@@ -1,0 +1,576 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+None of these re-types an oracle formula: each checks a property the paper
+states (conservation, fixed points, the entropy identities of Section 4, the
+ELBM root of Section 3), a closed form (Couette flow, shear-wave decay, the
+Lallemand-Luo polynomials behind M_1), an independent high-precision or
+brute-force evaluation (mpmath, pure-Python sorting), or a value the paper
+prints (tests/golden).
+"""
+import itertools
+import math
+import os
+
+import mpmath as mp
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1110_0270_gb300 import workloads as WL
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+mp.mp.dps = 50
+
+
+def _golden_int_matrix(name):
+    rows = [l.split() for l in open(os.path.join(GOLDEN, name)) if l.strip() and not l.startswith("#")]
+    return np.array([[int(v) for v in r] for r in rows])
+
+
+def near_eq_state(name, seed, amp, kind="poly", u_amp=0.08):
+    """A positive site state: equilibrium of random moments times lognormal
+    noise (the oracle's f* of the perturbed state is recomputed inside)."""
+    rng = np.random.default_rng(seed)
+    rho = 1.0 + 0.2 * rng.uniform(-1, 1)
+    ux, uy = u_amp * rng.uniform(-1, 1, 2)
+    if name == "D1Q3":
+        uy = 0.0
+    feq = O.equilibrium(name, kind, rho, ux, uy)
+    return feq * WL.lognormal_factors(feq.shape, seed + 1000, amp)
+
+
+def feq_of(name, kind, f):
+    rho, ux, uy = O.moments(name, f)
+    return O.equilibrium(name, kind, rho, ux, uy)
+
+
+# ----------------------------------------------------------------------------- lattice
+def test_d2q9_numbering_matches_paper_array():
+    grid = _golden_int_matrix("d2q9_numbering.txt")
+    cx, cy, W = O.lattice("D2Q9")
+    for r in range(3):
+        for c in range(3):
+            i = grid[r, c] - 1
+            assert (cx[i], cy[i]) == (c - 1, 1 - r)
+    # weights are the rest values of the product of the 1D polynomial equilibria
+    assert np.allclose(W.sum(), 1.0, atol=0, rtol=1e-15)
+    for i in range(9):
+        assert cx[O.opposite("D2Q9", i)] == -cx[i] and cy[O.opposite("D2Q9", i)] == -cy[i]
+
+
+def test_m1_matches_printed_matrix_and_lallemand_luo_polynomials():
+    M = O.mrt_basis("D2Q9")
+    assert np.array_equal(M, _golden_int_matrix("m1_matrix.txt"))
+    cx, cy, _ = O.lattice("D2Q9")
+    c2 = cx ** 2 + cy ** 2
+    polys = np.array([np.ones(9), -4 + 3 * c2, 4 - 10.5 * c2 + 4.5 * c2 ** 2, cx,
+                      (-5 + 3 * c2) * cx, cy, (-5 + 3 * c2) * cy, cx ** 2 - cy ** 2, cx * cy])
+    assert np.array_equal(M, polys)
+    G = M @ M.T
+    assert np.array_equal(G, np.diag([9, 36, 36, 6, 12, 6, 12, 4, 4]))
+
+
+# ----------------------------------------------------------------------------- equilibria
+@pytest.mark.parametrize("kind", ["poly", "entropic", "poly_std"])
+def test_equilibrium_conserves_mass_and_momentum(kind):
+    rng = np.random.default_rng(1)
+    cx, cy, _ = O.lattice("D2Q9")
+    for _ in range(50):
+        rho, ux, uy = 1 + 0.3 * rng.uniform(-1, 1), *(0.2 * rng.uniform(-1, 1, 2))
+        f = O.equilibrium("D2Q9", kind, rho, ux, uy)
+        assert abs(f.sum() - rho) < 1e-15 * 4
+        assert abs((f * cx).sum() - rho * ux) < 1e-15 * 4
+        assert abs((f * cy).sum() - rho * uy) < 1e-15 * 4
+        if kind != "entropic":
+            # second moments of the Maxwellian, rho (c_s^2 delta + u u), c_s^2 = 1/3
+            assert abs((f * cx * cx).sum() - rho * (1 / 3 + ux * ux)) < 1e-14
+            assert abs((f * cy * cy).sum() - rho * (1 / 3 + uy * uy)) < 1e-14
+            assert abs((f * cx * cy).sum() - rho * ux * uy) < 1e-14
+
+
+def test_d1q3_entropic_equilibrium_is_the_entropy_maximum():
+    """Section 6: the entropic equilibria maximise Eq. (ELBMEntropy) at fixed
+    rho and rho u.  With mass and momentum fixed, f = (a, rho - 2a - rho u... )
+    has one free parameter; maximise it in mpmath."""
+    for rho, u in [(1.0, 0.0), (0.7, 0.3), (1.3, -0.55)]:
+        fe = O.equilibrium("D1Q3", "entropic", rho, u)
+
+        # fm = f_-; f_+ = fm + rho u; f_0 = rho - f_- - f_+.  The derivative
+        # of -fm ln fm - f0 ln(f0/4) - fp ln fp along this line vanishes at
+        # the maximum: -ln fm - ln fp + 2 ln(f0/4) = 0.
+        def dS(fm):
+            fp = fm + mp.mpf(rho) * mp.mpf(u)
+            f0 = mp.mpf(rho) - fm - fp
+            return -mp.log(fm) - mp.log(fp) + 2 * mp.log(f0 / 4)
+
+        lo = max(mp.mpf(0), -mp.mpf(rho) * mp.mpf(u)) + mp.mpf(10) ** -30
+        hi = (mp.mpf(rho) - mp.mpf(rho) * mp.mpf(u)) / 2 - mp.mpf(10) ** -30
+        fm_star = mp.findroot(dS, (lo, hi), solver="bisect")
+        assert abs(float(fm_star) - fe[0]) < 1e-15
+
+
+def test_d2q9_entropic_equilibrium_satisfies_lagrange_condition():
+    """Section 4: ln f*_k = sum_j mu_j m_jk for the perfect entropy, i.e.
+    ln(f*_i / W_i) is affine in (1, v_x, v_y).  Also checks the closed form of
+    the 2D entropic equilibrium written as W_i rho prod (2 - s)((2u+s)/(1-u))^c."""
+    cx, cy, W = O.lattice("D2Q9")
+    A = np.stack([np.ones(9), cx, cy], 1).astype(float)
+    for rho, ux, uy in [(1.0, 0.1, -0.05), (0.8, -0.3, 0.2), (1.2, 0.0, 0.4)]:
+        f = O.equilibrium("D2Q9", "entropic", rho, ux, uy)
+        y = np.log(f / W)
+        coef, res, *_ = np.linalg.lstsq(A, y, rcond=None)
+        assert np.max(np.abs(A @ coef - y)) < 5e-15
+        sx, sy = math.sqrt(1 + 3 * ux * ux), math.sqrt(1 + 3 * uy * uy)
+        alt = W * rho * (2 - sx) * (2 - sy) * ((2 * ux + sx) / (1 - ux)) ** cx * ((2 * uy + sy) / (1 - uy)) ** cy
+        assert np.allclose(f, alt, rtol=2e-15, atol=0)
+
+
+def test_d1q3_paper_entropy_is_perfect_entropy_plus_rho_ln6():
+    for s in range(10):
+        f = near_eq_state("D1Q3", s, 0.3)
+        assert abs(O.entropy_d1q3_paper(f) - (O.entropy("D1Q3", f) + f.sum() * math.log(6))) < 1e-14
+
+
+# ----------------------------------------------------------------------------- entropy
+def _g_mp(x):
+    x = mp.mpf(x)
+    return (1 + x) * mp.log1p(x) - x
+
+
+@pytest.mark.parametrize("x", [1e-12, -3e-9, 1e-6, -1e-4, 0.01, -0.2, 0.249, -0.2501, 0.5, -0.9, 3.0])
+def test_gfun_against_high_precision(x):
+    """Below |x| = 1/4 the series must be good to a few ulp; above it the
+    closed form loses at most log2(|x| / g(x)) < 3 bits to cancellation."""
+    ref = _g_mp(x)
+    tol = 4e-16 if abs(x) < 0.25 else 2e-15
+    assert abs(O.gfun(x) - float(ref)) <= tol * abs(float(ref))
+
+
+def _ds_mp(f, feq):
+    return sum(mp.mpf(a) * mp.log(mp.mpf(a) / mp.mpf(b)) for a, b in zip(f, feq))
+
+
+@pytest.mark.parametrize("amp", [1e-7, 1e-4, 1e-2, 0.3])
+@pytest.mark.parametrize("kind", ["poly", "entropic"])
+def test_delta_s_is_the_kullback_distance(amp, kind):
+    """Eq. (DelS): Delta S = sum f ln(f / f*), evaluated here in 50 digits.
+    The rounded f* carries the density of f only to rounding, r = sum (f - f*);
+    the cancellation-free form equals sum f ln(f/f*) - r exactly, so it is
+    checked against that to 1e-13 and against the bare sum to within |r|."""
+    for s in range(5):
+        f = near_eq_state("D2Q9", s, amp, kind)
+        feq = feq_of("D2Q9", kind, f)
+        r = sum(mp.mpf(a) - mp.mpf(b) for a, b in zip(f, feq))
+        ref = float(_ds_mp(f, feq))
+        assert ref > 0
+        assert abs(O.delta_s(f, feq) - float(_ds_mp(f, feq) - r)) <= 1e-13 * ref
+        assert abs(O.delta_s(f, feq) - ref) <= 1e-13 * ref + abs(float(r))
+        if amp >= 1e-2:
+            assert abs(O.delta_s_direct(f, feq) - ref) <= 1e-10 * ref
+
+
+def test_delta_s_is_zero_only_at_equilibrium_and_infinite_for_negative():
+    f = O.equilibrium("D2Q9", "poly", 1.0, 0.05, 0.02)
+    assert O.delta_s(f, f) == 0.0
+    g = f.copy()
+    g[3] = -1e-3
+    assert O.delta_s(g, f) == math.inf
+
+
+def test_delta_s_equals_entropy_gap_for_entropic_equilibria():
+    """Section 4: for entropic quasi-equilibria Delta S = S(f*) - S(f)."""
+    for s in range(5):
+        f = near_eq_state("D2Q9", s, 0.05, "entropic")
+        feq = feq_of("D2Q9", "entropic", f)
+        gap = O.entropy("D2Q9", feq) - O.entropy("D2Q9", f)
+        assert abs(O.delta_s(f, feq) - gap) < 1e-12 * abs(gap) + 1e-15
+
+
+def test_delta_s_quadratic_scaling_and_half_factor():
+    """Section 4.1: Delta S(f* + x (f - f*)) ~ x^2 Delta S(f); and the
+    quadratic form is (1/2) sum (f - f*)^2 / f* (Taylor), the paper's
+    Eq. (KulSq) without the 1/2 being the leading-order proportionality."""
+    f = near_eq_state("D2Q9", 3, 1e-3)
+    feq = feq_of("D2Q9", "poly", f)
+    d = O.delta_s(f, feq)
+    for x in [0.1, 0.5, 2.0]:
+        assert abs(O.delta_s(feq + x * (f - feq), feq) / (x * x * d) - 1) < 5e-3
+    quad = 0.5 * np.sum((f - feq) ** 2 / feq)
+    assert abs(d / quad - 1) < 5e-3
+
+
+# ----------------------------------------------------------------------------- collisions
+def cfg_site(name, collision, **kw):
+    c = dict(lattice=name, nx=1, ny=1, collision=collision, beta=0.93,
+             s_e=1.64, s_eps=1.54, s_q=1.2, elbm_fallback="positivity")
+    c.update(kw)
+    return O.OracleConfig.from_dict(c)
+
+
+@pytest.mark.parametrize("name", ["D1Q3", "D2Q9"])
+@pytest.mark.parametrize("collision", ["lbgk", "elbm", "positivity", "mrt"])
+@pytest.mark.parametrize("eq", ["poly", "entropic"])
+def test_local_collisions_conserve_moments_and_fix_equilibrium(name, collision, eq):
+    """Section 2: collisions conserve rho and rho u; f* is a fixed point."""
+    cfg = cfg_site(name, collision, equilibrium=eq)
+    ekind = "entropic" if collision == "elbm" else eq
+    cx, cy, _ = O.lattice(name)
+    for s in range(20):
+        f = near_eq_state(name, s, 0.2 if s % 2 else 0.02, ekind)
+        F = O.collide_site(cfg, f)
+        assert abs(F.sum() - f.sum()) < 1e-14
+        assert abs(F @ cx - f @ cx) < 1e-14
+        assert abs(F @ cy - f @ cy) < 1e-14
+        fe = feq_of(name, ekind, f)
+        assert np.allclose(O.collide_site(cfg, fe), fe, rtol=0, atol=1e-15)
+
+
+def test_lbgk_entropy_production_matches_section_4_2():
+    """delta_LBGK S ~ [1 - (2 beta - 1)^2] Delta S per site near equilibrium."""
+    for beta in [0.6, 0.8, 0.97]:
+        cfg = cfg_site("D2Q9", "lbgk", beta=beta, equilibrium="entropic")
+        f = near_eq_state("D2Q9", 11, 1e-4, "entropic")
+        feq = feq_of("D2Q9", "entropic", f)
+        F = O.collide_site(cfg, f)
+        prod = float(-_ds_mp(F, feq) + _ds_mp(f, feq))  # S(F) - S(f) = dS(f) - dS(F)
+        assert abs(prod / ((1 - (2 * beta - 1) ** 2) * O.delta_s(f, feq)) - 1) < 1e-3
+
+
+def test_mrt_equal_rates_is_lbgk_and_d1q3_mrt_is_lbgk():
+    """Section 5: A = M^-1 C M; with every non-conserved rate equal to s, A
+    acts as s I on every vector with zero conserved moments (the C_1 entries of
+    rho, j_x, j_y do not matter, as the paper notes), which is LBGK with
+    s = 2 beta.  D1Q3 has a single non-conserved moment."""
+    beta = 0.87
+    cfg = cfg_site("D2Q9", "mrt", beta=beta, s_e=2 * beta, s_eps=2 * beta, s_q=2 * beta)
+    lb = cfg_site("D2Q9", "lbgk", beta=beta)
+    for s in range(5):
+        f = near_eq_state("D2Q9", s, 0.1)
+        assert np.allclose(O.collide_site(cfg, f), O.collide_site(lb, f), atol=2e-15)
+    cfg1 = cfg_site("D1Q3", "mrt", beta=beta)
+    cfgl = cfg_site("D1Q3", "lbgk", beta=beta)
+    for s in range(5):
+        f = near_eq_state("D1Q3", s, 0.1)
+        assert np.allclose(O.collide_site(cfg1, f), O.collide_site(cfgl, f), atol=1e-15)
+
+
+def test_mrt_relaxes_each_moment_at_its_rate():
+    """M (F - f) = C M (f* - f): each moment of Section 5 relaxes at its own
+    C_1 rate (s_e, s_eps, s_q, s_nu = 2 beta)."""
+    cfg = cfg_site("D2Q9", "mrt", beta=0.9, s_e=1.64, s_eps=1.54, s_q=1.2)
+    rates = np.array([1, 1.64, 1.54, 1, 1.2, 1, 1.2, 1.8, 1.8])
+    M = _golden_int_matrix("m1_matrix.txt").astype(float)
+    f = near_eq_state("D2Q9", 4, 0.1)
+    feq = feq_of("D2Q9", "poly", f)
+    F = O.collide_site(cfg, f)
+    assert np.allclose(M @ (F - f), rates * (M @ (feq - f)), atol=1e-14)
+
+
+def test_positivity_rule_lands_on_the_boundary_along_the_line():
+    """Section 4 (Eq. StrLine): a negative post-collision state moves along
+    the line through f* to the nearest nonnegative point."""
+    cfg = cfg_site("D2Q9", "positivity", beta=0.99)
+    lb = cfg_site("D2Q9", "lbgk", beta=0.99)
+    hits = 0
+    for s in range(40):
+        f = near_eq_state("D2Q9", s, 1.2)
+        feq = feq_of("D2Q9", "poly", f)
+        Fl = O.collide_site(lb, f)
+        F = O.collide_site(cfg, f)
+        if Fl.min() >= 0:
+            assert np.array_equal(F, Fl)
+            continue
+        hits += 1
+        assert abs(F.min()) < 1e-15 and F.min() >= -1e-15
+        lam = (F - feq) / (Fl - feq)
+        assert np.allclose(lam, lam[0], atol=1e-12) and 0 < lam[0] < 1
+        assert abs(F.sum() - f.sum()) < 1e-14
+    assert hits >= 3
+
+
+# ----------------------------------------------------------------------------- ELBM
+def _S_mp(f, W):
+    return -sum(mp.mpf(a) * mp.log(mp.mpf(a) / mp.mpf(w)) for a, w in zip(f, W) if a != 0)
+
+
+def _entropic_eq_mp(name, f):
+    """Exact entropic equilibrium of the moments of f, in 50 digits, from the
+    closed form W_i rho prod_a (2 - s_a) ((2 u_a + s_a)/(1 - u_a))^{c_ia}."""
+    cx, cy, W = O.lattice(name)
+    fm = [mp.mpf(v) for v in f]
+    rho = sum(fm)
+    ux = sum(a * int(c) for a, c in zip(fm, cx)) / rho
+    uy = sum(a * int(c) for a, c in zip(fm, cy)) / rho
+    sx, sy = mp.sqrt(1 + 3 * ux * ux), mp.sqrt(1 + 3 * uy * uy)
+    bx, by = (2 * ux + sx) / (1 - ux), (2 * uy + sy) / (1 - uy)
+    Wm = [mp.mpf(1) / 6, mp.mpf(2) / 3, mp.mpf(1) / 6] if name == "D1Q3" else [
+        mp.mpf(4) / 9 if (a == 0 and b == 0) else (mp.mpf(1) / 9 if a * a + b * b == 1 else mp.mpf(1) / 36)
+        for a, b in zip(cx, cy)]
+    return [w * rho * (2 - sx) * (2 - sy) * bx ** int(a) * by ** int(b)
+            for w, a, b in zip(Wm, cx, cy)]
+
+
+def _root_mp(f, feq, W, amax):
+    """Non-trivial root of S(f + a (f* - f)) = S(f) on (1, amax), by bisection
+    in 50-digit arithmetic (independent of the oracle's parabola iteration).
+    feq is the exact (50-digit) equilibrium."""
+    f = [mp.mpf(v) for v in f]
+    D = [mp.mpf(b) - a for a, b in zip(f, feq)]
+    amax = min(-a / d for a, d in zip(f, D) if d < 0)
+    S0 = _S_mp(f, W)
+    h = lambda a: _S_mp([x + a * d for x, d in zip(f, D)], W) - S0
+    lo, hi = mp.mpf(1), mp.mpf(amax) * (1 - mp.mpf(10) ** -40)
+    if h(hi) > 0:
+        return None
+    for _ in range(200):
+        m = (lo + hi) / 2
+        lo, hi = (m, hi) if h(m) > 0 else (lo, m)
+    return lo
+
+
+@pytest.mark.parametrize("name", ["D1Q3", "D2Q9"])
+@pytest.mark.parametrize("amp", [1e-3, 3e-2, 0.3])
+def test_elbm_alpha_is_the_entropy_root_from_below(name, amp):
+    """Eq. (ELBMCondition): S(f + alpha (f* - f)) = S(f), alpha the non-trivial
+    root, approached from below (Section 3.3); the collision then does not
+    lower the entropy (Section 3.1's H-theorem)."""
+    cfg = cfg_site(name, "elbm")
+    _, _, W = O.lattice(name)
+    for s in range(4):
+        f = near_eq_state(name, s, amp, "entropic")
+        feq = feq_of(name, "entropic", f)
+        D = feq - f
+        amax = min(-f[i] / D[i] for i in range(len(f)) if D[i] < 0)
+        alpha, code, iters, corr = O.elbm_alpha(cfg, f, feq)
+        feq_x = _entropic_eq_mp(name, f)
+        ref = _root_mp(f, feq_x, W, amax)
+        assert code == 0 and ref is not None
+        # the rounded f* moves the root by O(eps / Delta S) relative to the
+        # exact one; the estimate is from below up to that rounding
+        tol = 1e-12 + 1e-17 / O.delta_s(f, feq)
+        assert float(ref) - tol <= alpha <= float(ref) + tol, (alpha, float(ref), tol)
+        Sf = _S_mp([mp.mpf(a) + mp.mpf(alpha) * (b - mp.mpf(a)) for a, b in zip(f, feq_x)], W) - _S_mp(f, W)
+        slack = 4 * O.delta_s(f, feq) * tol  # |S_f'| ~ 2 Delta S near the root
+        assert Sf >= -slack
+        F = O.collide_site(cfg, f)
+        assert _S_mp(F, W) >= _S_mp(f, W) - mp.mpf(1e-30)
+        if name == "D1Q3":  # the paper's own D1Q3 entropy gives the same root
+            Sp = lambda y: (-y[0] * mp.log(y[0]) - y[1] * mp.log(y[1] / 4) - y[2] * mp.log(y[2]))
+            fm = [mp.mpf(v) for v in f]
+            ym = [a + mp.mpf(alpha) * (b - a) for a, b in zip(fm, feq_x)]
+            assert abs(Sp(ym) - Sp(fm)) < slack
+
+
+def test_elbm_alpha_tends_to_two_linearly():
+    """Section 3.3 starts from the LBGK estimate alpha = 2, the root for
+    f -> f*; the gap closes linearly in the nonequilibrium amplitude."""
+    cfg = cfg_site("D2Q9", "elbm")
+    gaps = []
+    amps = [1e-2, 1e-3, 1e-4]
+    for amp in amps:
+        f = near_eq_state("D2Q9", 7, amp, "entropic")
+        feq = feq_of("D2Q9", "entropic", f)
+        a, code, *_ = O.elbm_alpha(cfg, f, feq)
+        assert code == 0
+        gaps.append(abs(a - 2))
+    slopes = np.diff(np.log(gaps)) / np.diff(np.log(amps))
+    assert np.all(np.abs(slopes - 1) < 0.1), slopes
+
+
+def test_elbm_near_equilibrium_skip_and_no_root_fallbacks():
+    cfg = cfg_site("D2Q9", "elbm")
+    f = O.equilibrium("D2Q9", "entropic", 1.0, 0.05, 0.0)
+    g = f * (1 + 1e-9 * np.array([1, -1, 1, -1, 1, -1, 1, -1, 0.5]))
+    feq = feq_of("D2Q9", "entropic", g)
+    a, code, *_ = O.elbm_alpha(cfg, g, feq)
+    assert code == 1 and a == 2.0  # Delta S < 1e-15: plain LBGK
+    # a state whose mirror line leaves the positive cone before the entropy
+    # returns to S(f): one tiny population with a large equilibrium value
+    _, _, W = O.lattice("D2Q9")
+    bad = np.array([0.9, 0.001, 0.001, 0.001, 1e-12, 0.001, 0.001, 0.001, 0.2])
+    feq = feq_of("D2Q9", "entropic", bad)
+    D = feq - bad
+    amax = min(-bad[i] / D[i] for i in range(9) if D[i] < 0)
+    if _root_mp(bad, feq, W, amax) is None:
+        a, code, *_ = O.elbm_alpha(cfg, bad, feq)
+        assert code == 2 and a == pytest.approx(amax, rel=1e-15)
+        assert (bad + a * D).min() >= -1e-15
+        cfg_e = cfg_site("D2Q9", "elbm", elbm_fallback="ehrenfest")
+        a2, code2, *_ = O.elbm_alpha(cfg_e, bad, feq)
+        assert code2 == 2 and a2 == 1.0
+    else:  # pragma: no cover - the construction above always lacks a root
+        pytest.fail("expected a state without a non-trivial root")
+
+
+# ----------------------------------------------------------------------------- selection
+def test_topk_selection_matches_brute_force_with_ties():
+    rng = np.random.default_rng(5)
+    for trial in range(30):
+        n = int(rng.integers(1, 70))
+        vals = rng.choice([0.0, 1e-4, 2e-3, 2e-3, 5e-3, 1e-2, 0.1, math.inf], size=n)
+        vals = vals * (1 + (rng.uniform(size=n) < 0.5) * 0)  # many exact ties
+        k = int(rng.integers(0, 12))
+        delta = 1e-3
+        mask, nc = O.select_topk(vals, k, delta)
+        cand = [x for x in range(n) if vals[x] > delta]
+        best = sorted(cand, key=lambda x: (-vals[x], x))[:k]
+        assert nc == len(cand)
+        assert set(np.flatnonzero(mask)) == set(best)
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_median_field_matches_brute_force(periodic):
+    rng = np.random.default_rng(9)
+    ny, nx = 5, 7
+    dS = rng.choice([0.0, 1.0, 2.0, 3.0, 5.0], size=(ny, nx)) * rng.uniform(0.5, 1, (ny, nx))
+    med = O.median_field("D2Q9", dS, periodic, periodic)
+    for y in range(ny):
+        for x in range(nx):
+            w = []
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    yy, xx = y + dy, x + dx
+                    if periodic:
+                        yy, xx = yy % ny, xx % nx
+                    if 0 <= yy < ny and 0 <= xx < nx:
+                        w.append(dS[yy, xx])
+            assert med[y, x] == sorted(w)[(len(w) - 1) // 2]
+    # the 1D window of three: the middle value
+    line = rng.uniform(size=9)
+    m1 = O.median_field("D1Q3", line)
+    assert m1[4] == sorted(line[3:6])[1] and m1[0] == sorted(line[0:2])[0]
+
+
+# ----------------------------------------------------------------------------- streaming
+def test_pure_advection_and_bounce_back_with_moving_lid():
+    """With beta = 0 the collision is the identity, so a step is Section 2's
+    free flight plus the wall rule, which is affine: a pulse added to a rest
+    background moves by v_i per step and reflects at the walls, while the
+    moving top wall adds the Ladd term -6 W_i (v_i . u_wall) to every
+    population it reflects."""
+    U = 0.1
+    ny, nx = 4, 5
+    cfg = dict(lattice="D2Q9", nx=nx, ny=ny, collision="lbgk", beta=0.0, bc="cavity", lid_u=U)
+    _, _, W = O.lattice("D2Q9")
+    bg = np.broadcast_to(W[:, None, None], (9, ny, nx)).copy()
+    NE, SW, E, W_, SE, NW, S = 8, 4, 1, 5, 2, 6, 3
+    p = np.zeros((9, ny, nx))
+    p[NE, 1, 2] = 1.0
+    p[E, 0, 4] = 0.5  # east wall, at rest
+    run = lambda f, n: O.step(cfg, f, n)
+    d1 = run(bg + p, 1) - run(bg, 1)
+    assert abs(d1[NE, 2, 3] - 1.0) < 1e-15 and abs(d1[W_, 0, 4] - 0.5) < 1e-15
+    assert abs(abs(d1).sum() - 1.5) < 1e-14
+    d3 = run(bg + p, 3) - run(bg, 3)
+    # (2,1) -> (3,2) -> (4,3) -> through the top-right corner: back as SW at (4,3)
+    assert abs(d3[SW, 3, 4] - 1.0) < 1e-15
+    b = run(bg, 1)
+    assert np.allclose(b[SW, ny - 1], W[NE] - 6 * W[NE] * U, atol=1e-16)
+    assert np.allclose(b[SE, ny - 1], W[NW] + 6 * W[NW] * U, atol=1e-16)
+    assert np.allclose(b[S, ny - 1], W[7], atol=1e-16)
+    assert np.allclose(b[:, : ny - 1], bg[:, : ny - 1], atol=1e-16)
+
+
+def test_cavity_conserves_mass_exactly():
+    cfg, init = WL.cavity(24, 400.0, 0.1)
+    cfg.update(collision="lbgk")
+    f = O.init_equilibrium(cfg, init["rho"], init["ux"], init["uy"])
+    m0 = f.sum()
+    f = O.step(cfg, f, 300)
+    assert abs(f.sum() - m0) < 1e-12 * m0
+    rho, ux, uy = O.macros(cfg, f)
+    assert ux[-1].mean() > 0.01  # the lid drags the top row along +x
+
+
+def test_couette_flow_is_linear_between_walls():
+    """Channel periodic in x, bottom wall at rest, top wall moving with U.
+    The steady Navier-Stokes solution is u_x = U (y + 1/2) / ny with the walls
+    half a link outside the first and last rows."""
+    ny, U = 12, 0.01
+    cfg = dict(lattice="D2Q9", nx=4, ny=ny, collision="lbgk", beta=1 / (6 * 0.5 + 1),
+               bc="channel", lid_u=U)
+    f = O.init_equilibrium(cfg, np.ones((ny, 4)), np.zeros((ny, 4)), np.zeros((ny, 4)))
+    f = O.step(cfg, f, 4000)
+    rho, ux, uy = O.macros(cfg, f)
+    exact = U * (np.arange(ny) + 0.5) / ny
+    assert np.allclose(ux[:, 0], exact, rtol=1e-6, atol=1e-9)
+    assert np.max(np.abs(uy)) < 1e-12
+
+
+@pytest.mark.parametrize("collision", ["lbgk", "mrt"])
+def test_shear_wave_decays_at_the_lattice_viscosity(collision):
+    """Section 7: u_y = u0 exp(-nu k^2 t) sin(k x), k = 2 pi / L, with
+    nu = c_s^2 (1/beta - 1)/2 = (1/beta - 1)/6 (the MRT shear rate s_nu = 2 beta)."""
+    L, nu = 64, 0.02
+    cfg, init = WL.shear_wave(L, 0.01, nu)
+    cfg.update(collision=collision, s_e=1.64, s_eps=1.54, s_q=1.2)
+    f = O.init_equilibrium(cfg, init["rho"], init["ux"], init["uy"])
+    k = 2 * np.pi / L
+    sinx = np.sin(k * np.arange(L))
+    amp = lambda f: (O.macros(cfg, f)[2].mean(0) @ sinx) / (sinx @ sinx)
+    f = O.step(cfg, f, 100)  # skip the start-up transient of the equilibrium start
+    a0 = amp(f)
+    T = 800
+    f = O.step(cfg, f, T)
+    nu_fit = -np.log(amp(f) / a0) / (k * k * T)
+    assert abs(nu_fit / nu - 1) < 0.01
+
+
+def test_limiters_conserve_mass_and_momentum_on_a_periodic_lattice():
+    ny, nx = 9, 11
+    base = O.init_equilibrium(dict(lattice="D2Q9", nx=nx, ny=ny),
+                              **WL.random_fields(ny, nx, 3, 0.05, 0.05))
+    f = base * WL.lognormal_factors(base.shape, 4, 0.02) * (
+        1 + WL.hot_spots(ny, nx, 5, 6, 0.5)[None])
+    cx, cy, _ = O.lattice("D2Q9")
+    for collision in ["ehrenfest", "median"]:
+        cfg = dict(lattice="D2Q9", nx=nx, ny=ny, collision=collision, beta=0.95, bc="periodic",
+                   topk=4, delta=1e-4)
+        g, st = O.step(cfg, f, 3, stats=True)
+        assert st["limited_sites"] > 0
+        assert abs(g.sum() - f.sum()) < 1e-12
+        assert abs(np.einsum("iyx,i->", g, cx) - np.einsum("iyx,i->", f, cx)) < 1e-12
+        assert abs(np.einsum("iyx,i->", g, cy) - np.einsum("iyx,i->", f, cy)) < 1e-12
+
+
+def test_ehrenfest_sends_selected_sites_to_equilibrium():
+    """Section 4: the k sites of largest Delta S above delta jump to f*; all
+    other sites take the LBGK step.  Checked on one step without streaming
+    effects by comparing with the LBGK step site by site."""
+    ny, nx = 6, 6
+    base = O.init_equilibrium(dict(lattice="D2Q9", nx=nx, ny=ny),
+                              **WL.random_fields(ny, nx, 8, 0.05, 0.05))
+    f = base * WL.lognormal_factors(base.shape, 9, 0.05)
+    common = dict(lattice="D2Q9", nx=nx, ny=ny, beta=0.9, bc="periodic", delta=1e-5, topk=3)
+    dS = O.delta_s_field(common, f)
+    mask, nc = O.select_topk(dS, 3, 1e-5)
+    assert nc > 3
+    g = O.step(dict(common, collision="ehrenfest"), f, 1)
+    h = O.step(dict(common, collision="lbgk"), f, 1)
+    # undo the streaming: the post-collision value of site s in direction i
+    # sits at s + v_i (periodic)
+    cx, cy, _ = O.lattice("D2Q9")
+    for s in np.flatnonzero(mask.ravel()):
+        y, x = divmod(s, nx)
+        fe = feq_of("D2Q9", "poly", f[:, y, x])
+        for i in range(9):
+            assert abs(g[i, (y + cy[i]) % ny, (x + cx[i]) % nx] - fe[i]) < 1e-15
+    diff = np.abs(g - h).sum(0)
+    assert np.count_nonzero(diff > 0) <= 9 * 3
+
+
+def test_shock_tube_runs_and_conserves_mass():
+    """Section 6 set-up; LBGK at nu = 1e-9 shows the post-shock oscillations
+    the paper reports, and the Ehrenfest limiter damps them."""
+    cfg, init = WL.shock_tube(800, 1e-9)
+    out = {}
+    for collision in ["lbgk", "ehrenfest", "elbm"]:
+        c = dict(cfg, collision=collision, topk=4, delta=1e-3)
+        f = O.init_equilibrium(c, init["rho"], init["ux"])
+        m0 = f.sum()
+        f = O.step(c, f, 400)
+        assert abs(f.sum() - m0) < 1e-10
+        rho = O.macros(c, f)[0][0]
+        out[collision] = np.abs(np.diff(rho)).sum()  # total variation
+    assert out["lbgk"] > 0.6  # oscillations: well above the 0.5 jump
+    assert out["ehrenfest"] < out["lbgk"]
