@@ -1,0 +1,368 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused D2Q9 stream-and-collide step on one or more GB300s.
+
+Workload (the bandwidth configuration): D2Q9 lid-driven cavity 4097 x 4097,
+Re = 10000, U = 0.05 (nu = U (N - 1) / Re), started from rest, FP32
+populations; headline step = LBGK with the Ehrenfest limiter (k = 64,
+delta = 1e-3), i.e. load/stream, moments, equilibrium, Delta S screen,
+collision, limiter selection and store in one pass over the lattice.
+
+One bench step = one lattice time step.  The state (604 MB in FP32) is far
+larger than L2 (126 MB), so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SIDE = 4097
+RE, LID_U = 10000.0, 0.05
+TOPK, DELTA = 64, 1e-3
+METRIC = "MLUPS and % HBM peak per collision variant; adjoint grad time vs forward, 1 GB300"
+Q = 9
+BYTES_PER_POP = {"fp64": 8, "fp32": 4, "bf16_dev": 2, "fp16_dev": 2}
+
+
+def workload_cfg(collision="ehrenfest", precision="fp32", n=N_SIDE):
+    from paper_1110_0270_gb300 import workloads as WL
+    cfg, init = WL.cavity(n, RE, LID_U)
+    cfg.update(collision=collision, precision=precision, topk=TOPK, delta=DELTA,
+               s_e=1.64, s_eps=1.64, s_q=1.2)
+    return cfg, init
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (every 100 ms) with host timestamps, so that only
+    the samples inside the timed window are kept."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self._stop = threading.Event()
+        self._proc = None
+
+    def start(self):
+        try:
+            self._proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self._proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self._proc.stdout:
+            self.rows.append((time.time(), [c.strip() for c in line.split(",")]))
+
+    def stop(self):
+        if self._proc is not None:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except Exception:
+                self._proc.kill()
+
+    def summary(self, t0: float, t1: float) -> dict:
+        inside = [r for t, r in self.rows if t0 <= t <= t1]
+        pool = inside if inside else [r for _, r in self.rows]
+        if not pool:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "samples": 0}
+        sm = [float(r[1]) for r in pool if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in pool if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in pool for n, v in zip(names, r[5:9]) if v == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(inside), "window_s": round(t1 - t0, 3)}
+
+
+# --------------------------------------------------------------------------- GPU arm
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def time_steps(lat, steps, warmup, dist=None, profile=False, sampler=None):
+    """Warm up, then time exactly `steps` lattice steps on the current stream
+    with CUDA events, barrier + synchronize on both sides."""
+    import torch
+    for _ in range(warmup):
+        lat.step(1)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if profile:
+        lat.profile(True)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
+    e0.record(s)
+    for _ in range(steps):
+        lat.step(1)
+    e1.record(s)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = lat.profile_read() if profile else None
+    if profile:
+        lat.profile(False)
+    return ms, prof, (t0, t1)
+
+
+def run_variants(n_side, steps, warmup):
+    """MLUPS and fraction of HBM peak per collision x precision (one GPU)."""
+    import torch
+    from paper_1110_0270_gb300 import lbm
+    hbm, _ = peaks()
+    out = {}
+    N = n_side * n_side
+    for precision in ["fp32", "fp16_dev", "bf16_dev", "fp64"]:
+        for coll in ["lbgk", "ehrenfest", "median", "positivity", "mrt", "elbm"]:
+            cfg, init = workload_cfg(coll, precision, n_side)
+            lat = lbm.Lattice(cfg)
+            lat.init(init["rho"], init["ux"], init["uy"])
+            k = max(5, steps // 10) if coll == "elbm" else steps
+            ms, prof, _ = time_steps(lat, k, warmup, profile=True)
+            per = ms / k
+            mlups = N / (per * 1e-3) / 1e6
+            alg = 2 * Q * BYTES_PER_POP[precision] * N
+            kstep = prof["step"][1] / max(1, prof["step"][0])
+            out[f"{coll}/{precision}"] = {
+                "mlups": round(mlups, 1), "ms_per_step": round(per, 4),
+                "hbm_frac_step": round(alg / (per * 1e-3) / 1e9 / hbm, 4),
+                "hbm_frac_step_kernel": round(alg / (kstep * 1e-3) / 1e9 / hbm, 4),
+                "steps": k}
+            del lat
+            torch.cuda.empty_cache()
+    return out
+
+
+def e2e_measure(cfg, init, jobs=3, inner=100):
+    """End to end through the public API with host buffers: lbm_init from
+    pinned host rho/u (H2D), `inner` steps, lbm_macros and a D2H copy of
+    rho and u into pinned host memory, per job."""
+    import torch
+    from paper_1110_0270_gb300 import lbm
+    lat = lbm.Lattice(cfg)
+    host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in init.items()}
+    ny, nx = init["rho"].shape
+    out_rho = torch.empty((ny, nx), dtype=torch.float32).pin_memory()
+    out_u = torch.empty((2, ny, nx), dtype=torch.float32).pin_memory()
+    times = []
+    for j in range(jobs + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.init(host["rho"].numpy(), host["ux"].numpy(), host["uy"].numpy())
+        lat.step(inner)
+        rho, u = lat.macros(torch.float32)
+        out_rho.copy_(rho, non_blocking=True)
+        out_u.copy_(u, non_blocking=True)
+        torch.cuda.synchronize()
+        if j > 0:  # the first job warms the pinned buffers
+            times.append(time.perf_counter() - t0)
+    t = statistics.median(times)
+    N = nx * ny
+    return {"value": round(N * inner / t / 1e6, 1), "unit": "MLUPS",
+            "h2d_bytes_per_step": int(3 * 8 * N), "d2h_bytes_per_step": int(3 * 4 * N),
+            "steps_per_job": inner, "jobs": jobs,
+            "note": "one e2e step = lbm_init from pinned host rho,u + 100 lattice steps + "
+                    "lbm_macros + D2H of rho,u"}
+
+
+def cpu_baseline(budget_s=12.0):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample of
+    the workload: a smaller cavity of the same Re and U, same collision."""
+    import oracle as O
+    n = 1025
+    cfg, init = workload_cfg("ehrenfest", "fp64", n)
+    f = O.init_equilibrium(cfg, init["rho"], init["ux"], init["uy"])
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < budget_s:
+        f = O.step(cfg, f, 1)
+        steps += 1
+    t = time.perf_counter() - t0
+    return {"value": round(n * n * steps / t / 1e6, 3), "unit": "MLUPS", "cores": 1,
+            "kind": "oracle",
+            "sample": f"D2Q9 cavity {n}x{n} (1/16 of the 4097^2 sites), Re {RE:g}, U {LID_U}, "
+                      f"Ehrenfest k={TOPK} delta={DELTA:g}, FP64, {steps} steps, "
+                      f"{os.cpu_count()} host cores present, 1 used"}
+
+
+def gpu_arm(args):
+    import torch
+    from paper_1110_0270_gb300 import build as B
+    from paper_1110_0270_gb300 import lbm
+
+    ws, rank, local = dist_setup()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist_mod
+        torch.cuda.set_device(local)
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0:
+        B.build()
+    if dist is not None:
+        dist.barrier()
+    cfg, init = workload_cfg("ehrenfest", "fp32", args.side)
+    N = args.side * args.side
+    lat = lbm.Lattice(cfg)
+    lat.init(init["rho"], init["ux"], init["uy"])
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    ms, prof, (t0, t1) = time_steps(lat, args.steps, args.warmup, dist, profile=True)
+    if sampler:
+        time.sleep(0.25)
+        sampler.stop()
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    st = lat.stats()
+    per = ms / args.steps
+    value = ws * N * args.steps / (ms * 1e-3) / 1e6
+    hbm, peak_kind = peaks()
+    alg = 2 * Q * 4 * N  # bytes per launch of the fused step kernel
+    k_ms = prof["step"][1] / max(1, prof["step"][0])
+    achieved = alg / (k_ms * 1e-3) / 1e9
+    launches = prof["step"][0] + prof["fixup"][0]
+    result = {
+        "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"D2Q9 lid-driven cavity {args.side}x{args.side}, Re {RE:g}, "
+                               f"U {LID_U}, FP32 populations, LBGK + Ehrenfest limiter "
+                               f"(k={TOPK}, delta={DELTA:g}), started from rest",
+                   "sites": N, "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (state 604 MB in FP32), no flush",
+                   "limiter_sites_total": st["limited_total"]},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+                     "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                     "kernel": "step_kernel<D2Q9, FP32, EHRENFEST>",
+                     "algorithmic_bytes_per_launch": alg,
+                     "kernel_ms": round(k_ms, 5), "peak_kind": f"{peak_kind} hbm_gbs",
+                     "fixup_ms": round(prof["fixup"][1] / max(1, prof["fixup"][0]), 5)},
+        "gpu_launches": launches,
+    }
+    if rank == 0:
+        result["clocks"] = sampler.summary(t0, t1) if sampler else None
+        if not args.no_variants:
+            result["variants"] = run_variants(args.side, args.variant_steps, 3)
+        if not args.no_e2e:
+            result["e2e"] = e2e_measure(workload_cfg("ehrenfest", "fp32", args.side)[0], init)
+        if not args.no_cpu:
+            result["cpu_baseline"] = cpu_baseline(args.cpu_budget)
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------- reference arm
+def reference_arm(args):
+    """The FP64 oracle on the host cores, same metric and unit; each step is
+    one oracle step of a smaller cavity sized so that the whole run stays
+    within about `budget` seconds."""
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import oracle as O
+    budget = args.ref_budget
+    total = args.steps + args.warmup
+    # the oracle's Ehrenfest FP64 step runs at roughly 0.7 MLUPS on one core
+    sites = max(65 * 65, int(0.7e6 * budget / max(1, total)))
+    n = int(min(args.side, max(65, int(sites ** 0.5))))
+    cfg, init = workload_cfg("ehrenfest", "fp64", n)
+    f = O.init_equilibrium(cfg, init["rho"], init["ux"], init["uy"])
+    for _ in range(args.warmup):
+        f = O.step(cfg, f, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = O.step(cfg, f, 1)
+    t = time.perf_counter() - t0
+    value = n * n * args.steps / t / 1e6
+    sample = (f"D2Q9 cavity {n}x{n} per step (a bounded sample of the {args.side}^2 workload), "
+              f"Ehrenfest k={TOPK}, FP64 oracle, single thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "MLUPS",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(t / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"D2Q9 lid-driven cavity {args.side}x{args.side}, Re {RE:g}, "
+                               f"U {LID_U}, LBGK + Ehrenfest limiter (k={TOPK}, delta={DELTA:g})"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--side", type=int, default=N_SIDE)
+    ap.add_argument("--variant-steps", type=int, default=100)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--ref-budget", type=float, default=90.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

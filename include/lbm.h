@@ -1,0 +1,218 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) lattice Boltzmann stream-and-collide
+ * library with the add-ons of Brownlee, Levesley, Packwood and Gorban,
+ * "Add-ons for Lattice Boltzmann Methods: Regularization, Filtering and
+ * Limiters" (arXiv:1110.0270).
+ *
+ * What one step computes (Section 2, collide then stream): at every site the
+ * moments {rho, rho u} = sum_i {1, v_i} f_i, an equilibrium f*, the selected
+ * collision F(f), then free flight f_i(x + v_i, t + 1) = F_i(x, t) with
+ * half-way bounce-back at walls (Section 8) and the moving-wall term
+ * -6 W_i rho_w (v_i . u_wall), rho_w = 1, on links that cross a moving lid.
+ *
+ * Lattices and numbering:
+ *   D1Q3 (Section 6): i = 0, 1, 2  <->  v = -1, 0, +1.
+ *   D2Q9 (Section 5's numbering 1..9 shifted to 0..8):
+ *     0 rest, 1 E, 2 SE, 3 S, 4 SW, 5 W, 6 NW, 7 N, 8 NE  (y grows north;
+ *     the moving lid is the top row y = ny - 1, moving along +x).
+ *
+ * Collisions (lbm_config.collision):
+ *   LBM_LBGK        F = f + 2 beta (f* - f)                  (Eq. CollisionIntegral)
+ *   LBM_ELBM        F = f + alpha beta (f* - f), alpha the non-trivial root of
+ *                   S(f + alpha (f* - f)) = S(f), entropic f*; parabola root
+ *                   finder in FP64 (Section 3.3, Eqs. NewCondition,
+ *                   Stopping, ConvergenceTwo)
+ *   LBM_EHRENFEST   LBGK, except that among the sites with Delta S > delta the
+ *                   k (= topk) largest jump to f* (Section 4, Ehrenfests'
+ *                   regularisation); Delta S = sum f ln(f/f*) (Eq. DelS)
+ *   LBM_POSITIVITY  LBGK followed by the positivity rule (Section 4, Eq. StrLine)
+ *   LBM_MEDIAN      LBGK after the median entropy filter (Section 4.4): where
+ *                   Delta S > delta and the median of Delta S over the site and
+ *                   its neighbours is smaller, f -> f* + sqrt(med/DeltaS)(f - f*)
+ *   LBM_MRT         F = f + M1^-1 C1 M1 (f* - f) (Section 5), C1 = diag(1, s_e,
+ *                   s_eps, 1, s_q, 1, s_q, s_nu, s_nu), s_nu = 2 beta
+ *
+ * Memory and ownership.  The caller provides ONE device allocation of at
+ * least lbm_required_bytes() bytes (for example a torch uint8 tensor) to
+ * lbm_create(); the library carves the population array and its scratch out
+ * of it and never allocates device memory itself.  The allocation must stay
+ * alive until lbm_destroy().  The population array is structure-of-arrays,
+ * f[i][y][pitch], with pitch = nx rounded up to 32 elements, updated in place
+ * with the A-A pattern (every step reads and writes each population once).
+ *
+ * Streams.  Every call that takes `stream` (a cudaStream_t, NULL = legacy
+ * default stream) enqueues its work there and returns without waiting,
+ * except where a host output is documented to synchronise that stream.
+ *
+ * Errors.  Every call returns an lbm_status; no C++ exception crosses the
+ * ABI.  On failure lbm_last_error(ctx) describes the cause.  A context whose
+ * kernel launch failed with a CUDA error keeps returning LBM_ERR_CUDA.
+ *
+ * Thread safety.  A context is not thread safe; distinct contexts are
+ * independent.  Steps on the same context must not overlap on the GPU.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_ABI_VERSION 1
+
+typedef struct lbm_ctx lbm_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,      /* invalid argument or configuration */
+    LBM_ERR_CUDA = 2,     /* a CUDA runtime call or kernel launch failed */
+    LBM_ERR_OOM = 3,      /* the caller's allocation is smaller than required */
+    LBM_ERR_DIVERGED = 4, /* a non-finite or non-positive density was seen */
+    LBM_ERR_TIMEOUT = 5,  /* a bounded device wait gave up */
+    LBM_ERR_STATE = 6     /* call not valid in the context's current state */
+} lbm_status;
+
+enum { LBM_D1Q3 = 1, LBM_D2Q9 = 2 };
+enum { LBM_LBGK = 0, LBM_ELBM = 1, LBM_EHRENFEST = 2, LBM_POSITIVITY = 3,
+       LBM_MEDIAN = 4, LBM_MRT = 5 };
+/* Equilibria: product of the 1D polynomial equilibria of Section 6 (the
+ * paper's D2Q9 choice, Section 8), product of the 1D entropic equilibria
+ * (always used by ELBM), or the textbook W_i rho (1 + 3cu + 9/2 (cu)^2 - 3/2 u^2). */
+enum { LBM_EQ_POLY_PRODUCT = 0, LBM_EQ_ENTROPIC = 1, LBM_EQ_POLY_STD = 2 };
+/* Storage of the populations.  FP64 and FP32 store f; BF16_DEV and FP16_DEV
+ * store the deviation f_i - W_i rounded to nearest even, with FP32 math. */
+enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_BF16_DEV = 2, LBM_FP16_DEV = 3 };
+/* Boundaries: CAVITY = walls on all four sides, the top one moving with
+ * lid_u; ENDS = D1Q3 tube closed at both ends; PERIODIC = both directions
+ * wrap; CHANNEL = periodic in x, walls at bottom and top (top moving). */
+enum { LBM_BC_CAVITY = 0, LBM_BC_ENDS = 1, LBM_BC_PERIODIC = 2, LBM_BC_CHANNEL = 3 };
+enum { LBM_NORM_ENTROPIC = 0, LBM_NORM_L1 = 1 };
+enum { LBM_FALLBACK_POSITIVITY = 0, LBM_FALLBACK_EHRENFEST = 1 };
+/* Element types of caller buffers exchanged with the library. */
+enum { LBM_DTYPE_F64 = 0, LBM_DTYPE_F32 = 1 };
+
+typedef struct {
+    int lattice;     /* LBM_D1Q3 | LBM_D2Q9 */
+    int nx, ny;      /* sites; ny = 1 for D1Q3.  nx, ny >= 1 */
+    int collision;   /* LBM_LBGK ... LBM_MRT */
+    int equilibrium; /* LBM_EQ_*; ignored by LBM_ELBM (always entropic) */
+    int precision;   /* LBM_FP64 | LBM_FP32 | LBM_BF16_DEV | LBM_FP16_DEV */
+    int bc;          /* LBM_BC_* */
+    double beta;     /* over-relaxation coefficient in (0, 1]; if <= 0 it is
+                        set from nu as beta = 1 / (6 nu + 1), the reading
+                        nu = c_s^2 (1/beta - 1) / 2 with c_s^2 = 1/3 */
+    double nu;       /* kinematic viscosity, used only when beta <= 0 */
+    double lid_u;    /* velocity of the top wall along +x (0: resting wall) */
+    int topk;        /* Ehrenfest: at most this many sites per step (>= 0) */
+    double delta;    /* Ehrenfest / median threshold on Delta S (>= 0) */
+    double s_e, s_eps, s_q; /* MRT relaxation rates of C1 */
+    double elbm_eps;        /* ELBM stopping tolerance (> 0), e.g. 1e-15 */
+    int elbm_max_iter;      /* ELBM parabola iterations (>= 1), e.g. 20 */
+    int elbm_norm;          /* LBM_NORM_* in the stopping rule */
+    int elbm_fallback;      /* rule when no non-trivial root exists */
+} lbm_config;
+
+typedef struct {
+    uint64_t steps;            /* steps taken since lbm_init/lbm_set_state */
+    uint64_t candidates_last;  /* sites with Delta S > delta in the last step */
+    uint64_t limited_total;    /* limiter corrections applied, cumulative */
+    uint64_t elbm_solved;      /* ELBM sites that ran the root finder */
+    uint64_t elbm_skipped;     /* ELBM sites with Delta S < 1e-15 */
+    uint64_t elbm_fallbacks;   /* ELBM sites without a non-trivial root */
+    uint64_t elbm_iters_total; /* parabola iterations, summed */
+    uint64_t elbm_iters_max;   /* largest iteration count at one site */
+    uint64_t diverged;         /* 1 once a non-finite or non-positive rho is seen */
+    uint64_t overflow;         /* 1 if a candidate list overflowed (never with
+                                  the default capacity of one entry per site) */
+} lbm_stats;
+
+/* Fills *cfg with defaults: D2Q9 16x16 cavity, LBGK, product polynomial
+ * equilibrium, FP32, beta = 0.9, topk = 0, delta = 1e-3, MRT rates
+ * (1.64, 1.54, 1.9), elbm_eps = 1e-15, elbm_max_iter = 20. */
+lbm_status lbm_config_default(lbm_config* cfg);
+
+/* Device bytes needed for cfg (populations + scratch).  Fails with
+ * LBM_ERR_ARG for an invalid configuration. */
+lbm_status lbm_required_bytes(const lbm_config* cfg, size_t* bytes);
+
+/* Creates a context over the caller's device allocation dev_mem (256-byte
+ * aligned, at least lbm_required_bytes) on the current CUDA device.  The
+ * populations are undefined until lbm_init or lbm_set_state.  Clears the
+ * scratch with a synchronous cudaMemset. */
+lbm_status lbm_create(const lbm_config* cfg, void* dev_mem, size_t bytes, lbm_ctx** out);
+
+/* Releases the host-side context (not the caller's device memory). */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* f = f*(rho, u) at every site from HOST arrays rho, ux, uy of nx*ny
+ * doubles, row-major [y][x] (uy may be NULL for D1Q3).  The equilibrium is
+ * the configured one (entropic for ELBM).  Copies the inputs to device
+ * scratch first; synchronises `stream` (the host arrays may be reused on
+ * return).  Resets the step counter and statistics. */
+lbm_status lbm_init(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy,
+                    void* stream);
+
+/* Same as lbm_init with DEVICE arrays (no synchronisation). */
+lbm_status lbm_init_device(lbm_ctx* ctx, const double* rho, const double* ux,
+                           const double* uy, void* stream);
+
+/* Loads the pre-collision populations from a dense DEVICE array f[Q][ny][nx]
+ * of dtype LBM_DTYPE_F64 or LBM_DTYPE_F32 (rounded to the storage format). */
+lbm_status lbm_set_state(lbm_ctx* ctx, const void* f, int dtype, void* stream);
+
+/* Writes the current pre-collision populations to a dense DEVICE array
+ * f[Q][ny][nx] of the given dtype (undoing the A-A layout of odd steps). */
+lbm_status lbm_get_state(lbm_ctx* ctx, void* f, int dtype, void* stream);
+
+/* Advances nsteps >= 0 steps.  Allocates nothing. */
+lbm_status lbm_step(lbm_ctx* ctx, int nsteps, void* stream);
+
+/* Density rho[ny][nx] and velocity u[2][ny][nx] (u_x plane then u_y plane;
+ * D1Q3 writes only u_x) of the current state into caller-owned DEVICE
+ * buffers of the given dtype. */
+lbm_status lbm_macros(lbm_ctx* ctx, void* rho, void* u, int dtype, void* stream);
+
+/* H = sum_x sum_i f_i ln(f_i / W_i) (minus the perfect-mixture entropy of
+ * Section 4, summed over the lattice) into *H_total_host (synchronises
+ * `stream`), and optionally the FP64 Delta S field dS[ny][nx] (DEVICE,
+ * may be NULL), Delta S computed against the configured equilibrium. */
+lbm_status lbm_entropy(lbm_ctx* ctx, double* H_total_host, double* dS_dev, void* stream);
+
+/* Copies the step counters into *out (synchronises `stream`). */
+lbm_status lbm_stats_get(lbm_ctx* ctx, lbm_stats* out, void* stream);
+
+/* Limiter candidates of the most recent step (EHRENFEST and MEDIAN only):
+ * up to `cap` entries of (Delta S in FP64, linear site index y*nx + x,
+ * selected flag) into HOST arrays (any may be NULL); *count receives the
+ * number of candidates.  Synchronises `stream`.  The candidate order is
+ * arbitrary. */
+lbm_status lbm_last_candidates(lbm_ctx* ctx, double* ds, int32_t* site, int32_t* selected,
+                               int cap, int* count, void* stream);
+
+/* Kernel tracing.  While enabled, every kernel lbm_step launches is
+ * bracketed by two CUDA events recorded on the caller's stream (timing
+ * events; the first LBM_PROFILE_MAX launches after enabling are kept).
+ * Enabling clears the record.  Costs two event records per launch. */
+#define LBM_PROFILE_MAX 65536
+enum { LBM_KERNEL_STEP = 0, LBM_KERNEL_FIXUP = 1, LBM_KERNEL_KINDS = 2 };
+lbm_status lbm_profile_enable(lbm_ctx* ctx, int enable);
+
+/* Waits for the recorded events and returns, per kernel kind (index
+ * LBM_KERNEL_STEP: the fused stream-collide kernel; LBM_KERNEL_FIXUP: the
+ * Ehrenfest/median fix-up), the number of launches and their summed device
+ * time in milliseconds (arrays of LBM_KERNEL_KINDS entries), then clears the
+ * record. */
+lbm_status lbm_profile_read(lbm_ctx* ctx, int* launches, double* ms);
+
+/* Message of the last failure on ctx ("" if none).  Valid until the next call. */
+const char* lbm_last_error(const lbm_ctx* ctx);
+const char* lbm_status_string(lbm_status s);
+int lbm_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,460 @@
+// extern "C" boundary of the GB300 lattice Boltzmann library (declared in
+// include/lbm.h).  Owns no device memory: the caller's allocation is carved
+// into the population array and the scratch the limiters need.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_kernels.cuh"
+
+using namespace lbm;
+
+namespace lbm {
+extern template struct Launch<StF64>;
+extern template struct Launch<StF32>;
+extern template struct Launch<StBF16>;
+extern template struct Launch<StF16>;
+}  // namespace lbm
+
+struct lbm_ctx {
+    lbm_config cfg;
+    int Q = 0;
+    Params p;
+    char* base = nullptr;
+    size_t bytes = 0;
+    int parity = 0;   // 0: natural layout; 1: after an even (in-place) step
+    uint64_t t = 0;   // steps since init / set_state
+    int nsm = 1;
+    int device = 0;
+    double* staging = nullptr;  // 3 * N doubles for lbm_init
+    std::string err;
+    // kernel tracing (lbm_profile_enable)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;  // pairs (start, end)
+    std::vector<int> ev_kind;
+    size_t ev_used = 0;
+    ~lbm_ctx() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+size_t storage_bytes(int precision) {
+    return precision == LBM_FP64 ? 8 : (precision == LBM_FP32 ? 4 : 2);
+}
+size_t math_bytes(int precision) { return precision == LBM_FP64 ? 8 : 4; }
+
+bool limiter(int coll) { return coll == LBM_EHRENFEST || coll == LBM_MEDIAN; }
+
+struct Layout {
+    int Q, pitch;
+    int64_t plane;
+    size_t f_off, f_bytes, cnt_off, cand_f_off, cand_ds_off, cand_site_off, cand_sel_off,
+        field_off, staging_off, total;
+    int cand_cap;
+};
+
+const char* check_config(const lbm_config* c) {
+    if (!c) return "config is NULL";
+    if (c->lattice != LBM_D1Q3 && c->lattice != LBM_D2Q9) return "lattice must be LBM_D1Q3 or LBM_D2Q9";
+    if (c->nx < 1 || c->ny < 1) return "nx and ny must be >= 1";
+    if (c->lattice == LBM_D1Q3 && c->ny != 1) return "D1Q3 needs ny == 1";
+    if ((long long)c->nx * c->ny > 0x7fffffffLL) return "nx * ny must fit in 31 bits";
+    if (c->ny > 65535LL * kBlockY) return "ny too large for the launch grid";
+    if (c->collision < LBM_LBGK || c->collision > LBM_MRT) return "unknown collision";
+    if (c->equilibrium < LBM_EQ_POLY_PRODUCT || c->equilibrium > LBM_EQ_POLY_STD) return "unknown equilibrium";
+    if (c->precision < LBM_FP64 || c->precision > LBM_FP16_DEV) return "unknown precision";
+    if (c->bc < LBM_BC_CAVITY || c->bc > LBM_BC_CHANNEL) return "unknown boundary condition";
+    if (c->lattice == LBM_D1Q3 && c->bc == LBM_BC_CHANNEL) return "CHANNEL needs D2Q9";
+    double beta = c->beta > 0 ? c->beta : (c->nu > 0 ? 1.0 / (6.0 * c->nu + 1.0) : -1.0);
+    if (!(beta > 0.0 && beta <= 1.0)) return "beta must be in (0, 1] (or nu > 0)";
+    if (!std::isfinite(c->lid_u)) return "lid_u must be finite";
+    if (c->topk < 0) return "topk must be >= 0";
+    if (!(c->delta >= 0.0)) return "delta must be >= 0";
+    if (c->collision == LBM_ELBM) {
+        if (!(c->elbm_eps > 0.0)) return "elbm_eps must be > 0";
+        if (c->elbm_max_iter < 1) return "elbm_max_iter must be >= 1";
+        if (c->elbm_norm != LBM_NORM_ENTROPIC && c->elbm_norm != LBM_NORM_L1) return "unknown elbm_norm";
+        if (c->elbm_fallback != LBM_FALLBACK_POSITIVITY && c->elbm_fallback != LBM_FALLBACK_EHRENFEST)
+            return "unknown elbm_fallback";
+    }
+    return nullptr;
+}
+
+Layout layout(const lbm_config* c) {
+    Layout L;
+    L.Q = c->lattice == LBM_D1Q3 ? 3 : 9;
+    L.pitch = (c->nx + 31) / 32 * 32;
+    L.plane = (int64_t)c->ny * L.pitch;
+    const size_t N = (size_t)c->nx * c->ny;
+    size_t off = 0;
+    L.f_off = off;
+    L.f_bytes = align_up((size_t)L.Q * L.plane * storage_bytes(c->precision));
+    off += L.f_bytes;
+    L.cnt_off = off;
+    off += align_up(CNT_WORDS * 4 + ST_WORDS * 8 + 8 * 8);
+    L.cand_cap = limiter(c->collision) ? (int)N : 0;
+    const size_t cap = (size_t)L.cand_cap;
+    L.cand_f_off = off;
+    off += align_up(cap * L.Q * math_bytes(c->precision));
+    L.cand_ds_off = off;
+    off += align_up(cap * 8);
+    L.cand_site_off = off;
+    off += align_up(cap * 4);
+    L.cand_sel_off = off;
+    off += align_up(cap * 4);
+    L.field_off = off;
+    off += c->collision == LBM_MEDIAN ? align_up(N * math_bytes(c->precision)) : 0;
+    L.staging_off = off;
+    off += align_up(3 * N * 8);
+    L.total = off;
+    return L;
+}
+
+lbm_status fail(lbm_ctx* ctx, lbm_status s, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return s;
+}
+
+lbm_status cuda_fail(lbm_ctx* ctx, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(ctx, LBM_ERR_CUDA, m);
+}
+
+#define LBM_CK(ctx, expr)                                       \
+    do {                                                        \
+        cudaError_t e_ = (expr);                                \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #expr); \
+    } while (0)
+
+template <class Fn>
+cudaError_t dispatch(int precision, Fn&& fn) {
+    switch (precision) {
+        case LBM_FP64: return fn(Launch<StF64>());
+        case LBM_FP32: return fn(Launch<StF32>());
+        case LBM_BF16_DEV: return fn(Launch<StBF16>());
+        case LBM_FP16_DEV: return fn(Launch<StF16>());
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaStream_t S(void* s) { return (cudaStream_t)s; }
+
+// Launches fn() bracketed by a pair of timing events when tracing is on.
+template <class Fn>
+cudaError_t traced(lbm_ctx* ctx, int kind, cudaStream_t s, Fn&& fn) {
+    if (!ctx->profiling || ctx->ev_used >= LBM_PROFILE_MAX) return fn();
+    if (ctx->ev.size() < 2 * (ctx->ev_used + 1)) {
+        for (int k = 0; k < 2; ++k) {
+            cudaEvent_t e;
+            cudaError_t err = cudaEventCreate(&e);
+            if (err != cudaSuccess) return err;
+            ctx->ev.push_back(e);
+        }
+        ctx->ev_kind.push_back(0);
+    }
+    cudaEvent_t a = ctx->ev[2 * ctx->ev_used], b = ctx->ev[2 * ctx->ev_used + 1];
+    cudaError_t err = cudaEventRecord(a, s);
+    if (err == cudaSuccess) err = fn();
+    if (err == cudaSuccess) err = cudaEventRecord(b, s);
+    if (err == cudaSuccess) ctx->ev_kind[ctx->ev_used++] = kind;
+    return err;
+}
+
+lbm_status reset_counters(lbm_ctx* ctx, cudaStream_t s) {
+    LBM_CK(ctx, cudaMemsetAsync(ctx->p.counters, 0, CNT_WORDS * 4 + ST_WORDS * 8, s));
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_abi_version(void) { return LBM_ABI_VERSION; }
+
+const char* lbm_status_string(lbm_status s) {
+    switch (s) {
+        case LBM_OK: return "LBM_OK";
+        case LBM_ERR_ARG: return "LBM_ERR_ARG";
+        case LBM_ERR_CUDA: return "LBM_ERR_CUDA";
+        case LBM_ERR_OOM: return "LBM_ERR_OOM";
+        case LBM_ERR_DIVERGED: return "LBM_ERR_DIVERGED";
+        case LBM_ERR_TIMEOUT: return "LBM_ERR_TIMEOUT";
+        case LBM_ERR_STATE: return "LBM_ERR_STATE";
+    }
+    return "unknown lbm_status";
+}
+
+const char* lbm_last_error(const lbm_ctx* ctx) { return ctx ? ctx->err.c_str() : "ctx is NULL"; }
+
+lbm_status lbm_config_default(lbm_config* c) {
+    if (!c) return LBM_ERR_ARG;
+    std::memset(c, 0, sizeof *c);
+    c->lattice = LBM_D2Q9;
+    c->nx = c->ny = 16;
+    c->collision = LBM_LBGK;
+    c->equilibrium = LBM_EQ_POLY_PRODUCT;
+    c->precision = LBM_FP32;
+    c->bc = LBM_BC_CAVITY;
+    c->beta = 0.9;
+    c->delta = 1e-3;
+    c->s_e = 1.64;
+    c->s_eps = 1.54;
+    c->s_q = 1.9;
+    c->elbm_eps = 1e-15;
+    c->elbm_max_iter = 20;
+    c->elbm_norm = LBM_NORM_ENTROPIC;
+    c->elbm_fallback = LBM_FALLBACK_POSITIVITY;
+    return LBM_OK;
+}
+
+lbm_status lbm_required_bytes(const lbm_config* cfg, size_t* bytes) {
+    if (!bytes || check_config(cfg)) return LBM_ERR_ARG;
+    *bytes = layout(cfg).total;
+    return LBM_OK;
+}
+
+lbm_status lbm_create(const lbm_config* cfg, void* dev_mem, size_t bytes, lbm_ctx** out) {
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    if (check_config(cfg)) return LBM_ERR_ARG;
+    if (!dev_mem || ((uintptr_t)dev_mem % kAlign) != 0) return LBM_ERR_ARG;
+    Layout L = layout(cfg);
+    if (bytes < L.total) return LBM_ERR_OOM;
+    lbm_ctx* ctx = new (std::nothrow) lbm_ctx();
+    if (!ctx) return LBM_ERR_OOM;
+    ctx->cfg = *cfg;
+    if (!(ctx->cfg.beta > 0)) ctx->cfg.beta = 1.0 / (6.0 * cfg->nu + 1.0);
+    ctx->Q = L.Q;
+    ctx->base = (char*)dev_mem;
+    ctx->bytes = bytes;
+    if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
+        delete ctx;
+        return LBM_ERR_CUDA;
+    }
+    Params& p = ctx->p;
+    std::memset(&p, 0, sizeof p);
+    p.f = ctx->base + L.f_off;
+    p.plane = L.plane;
+    p.pitch = L.pitch;
+    p.nx = cfg->nx;
+    p.ny = cfg->ny;
+    p.periodic_x = cfg->bc == LBM_BC_PERIODIC || cfg->bc == LBM_BC_CHANNEL;
+    p.periodic_y = cfg->bc == LBM_BC_PERIODIC;
+    p.eq = cfg->equilibrium;
+    p.lid_u = (cfg->bc == LBM_BC_CAVITY || cfg->bc == LBM_BC_CHANNEL) ? cfg->lid_u : 0.0;
+    p.beta = ctx->cfg.beta;
+    p.topk = cfg->topk;
+    p.delta = cfg->delta;
+    const double snu = 2.0 * p.beta;
+    p.mrt.e = cfg->s_e / 36.0;
+    p.mrt.eps = cfg->s_eps / 36.0;
+    p.mrt.q = cfg->s_q / 12.0;
+    p.mrt.nu = snu / 4.0;
+    p.elbm_eps = cfg->elbm_eps;
+    p.elbm_max_iter = cfg->elbm_max_iter;
+    p.elbm_norm = cfg->elbm_norm;
+    p.elbm_fallback = cfg->elbm_fallback;
+    p.counters = (unsigned*)(ctx->base + L.cnt_off);
+    p.stats = (unsigned long long*)(ctx->base + L.cnt_off + CNT_WORDS * 4);
+    p.scratch_d = (double*)(ctx->base + L.cnt_off + CNT_WORDS * 4 + ST_WORDS * 8);
+    p.cand_cap = L.cand_cap;
+    p.cand_f = ctx->base + L.cand_f_off;
+    p.cand_ds = (double*)(ctx->base + L.cand_ds_off);
+    p.cand_site = (int*)(ctx->base + L.cand_site_off);
+    p.cand_sel = (int*)(ctx->base + L.cand_sel_off);
+    p.ds_field = ctx->base + L.field_off;
+    ctx->staging = (double*)(ctx->base + L.staging_off);
+    cudaError_t e = cudaMemset(ctx->base + L.cnt_off, 0, align_up(CNT_WORDS * 4 + ST_WORDS * 8 + 64));
+    if (e != cudaSuccess) {
+        delete ctx;
+        return LBM_ERR_CUDA;
+    }
+    *out = ctx;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* ctx) { delete ctx; }
+
+lbm_status lbm_init_device(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy,
+                           void* stream) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (!rho || !ux || (ctx->Q == 9 && !uy)) return fail(ctx, LBM_ERR_ARG, "rho, ux (and uy for D2Q9) are required");
+    const int eqkind = ctx->cfg.collision == LBM_ELBM ? LBM_EQ_ENTROPIC : ctx->cfg.equilibrium;
+    lbm_status st = reset_counters(ctx, S(stream));
+    if (st) return st;
+    LBM_CK(ctx, dispatch(ctx->cfg.precision, [&](auto L) {
+               return decltype(L)::init(ctx->Q, ctx->p, rho, ux, ctx->Q == 9 ? uy : nullptr, eqkind, S(stream));
+           }));
+    ctx->parity = 0;
+    ctx->t = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_init(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy, void* stream) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (!rho || !ux || (ctx->Q == 9 && !uy)) return fail(ctx, LBM_ERR_ARG, "rho, ux (and uy for D2Q9) are required");
+    const size_t N = (size_t)ctx->cfg.nx * ctx->cfg.ny;
+    double* d = ctx->staging;
+    LBM_CK(ctx, cudaMemcpyAsync(d, rho, N * 8, cudaMemcpyHostToDevice, S(stream)));
+    LBM_CK(ctx, cudaMemcpyAsync(d + N, ux, N * 8, cudaMemcpyHostToDevice, S(stream)));
+    if (ctx->Q == 9) LBM_CK(ctx, cudaMemcpyAsync(d + 2 * N, uy, N * 8, cudaMemcpyHostToDevice, S(stream)));
+    lbm_status st = lbm_init_device(ctx, d, d + N, d + 2 * N, stream);
+    if (st) return st;
+    LBM_CK(ctx, cudaStreamSynchronize(S(stream)));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_state(lbm_ctx* ctx, const void* f, int dtype, void* stream) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (!f || (dtype != LBM_DTYPE_F64 && dtype != LBM_DTYPE_F32)) return fail(ctx, LBM_ERR_ARG, "bad state buffer or dtype");
+    lbm_status st = reset_counters(ctx, S(stream));
+    if (st) return st;
+    LBM_CK(ctx, dispatch(ctx->cfg.precision, [&](auto L) {
+               return decltype(L)::set_state(ctx->Q, ctx->p, f, dtype, S(stream));
+           }));
+    ctx->parity = 0;
+    ctx->t = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_state(lbm_ctx* ctx, void* f, int dtype, void* stream) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (!f || (dtype != LBM_DTYPE_F64 && dtype != LBM_DTYPE_F32)) return fail(ctx, LBM_ERR_ARG, "bad state buffer or dtype");
+    LBM_CK(ctx, dispatch(ctx->cfg.precision, [&](auto L) {
+               return decltype(L)::get_state(ctx->Q, ctx->p, f, dtype, ctx->parity != 0, S(stream));
+           }));
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* ctx, int nsteps, void* stream) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (nsteps < 0) return fail(ctx, LBM_ERR_ARG, "nsteps must be >= 0");
+    const int coll = ctx->cfg.collision;
+    for (int k = 0; k < nsteps; ++k) {
+        Params q = ctx->p;
+        q.cslot = (int)(ctx->t & 1);
+        const bool odd = ctx->parity != 0;
+        LBM_CK(ctx, traced(ctx, LBM_KERNEL_STEP, S(stream), [&] {
+                   return dispatch(ctx->cfg.precision, [&](auto L) {
+                       return decltype(L)::step(ctx->Q, coll, odd, q, S(stream));
+                   });
+               }));
+        if (limiter(coll))
+            LBM_CK(ctx, traced(ctx, LBM_KERNEL_FIXUP, S(stream), [&] {
+                       return dispatch(ctx->cfg.precision, [&](auto L) {
+                           return decltype(L)::fixup(ctx->Q, coll, odd, q, S(stream), ctx->nsm);
+                       });
+                   }));
+        ctx->parity ^= 1;
+        ctx->t += 1;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_macros(lbm_ctx* ctx, void* rho, void* u, int dtype, void* stream) {
+    if (!ctx) return LBM_ERR_ARG;
+    if ((!rho && !u) || (dtype != LBM_DTYPE_F64 && dtype != LBM_DTYPE_F32)) return fail(ctx, LBM_ERR_ARG, "bad outputs or dtype");
+    LBM_CK(ctx, dispatch(ctx->cfg.precision, [&](auto L) {
+               return decltype(L)::macros(ctx->Q, ctx->p, rho, u, dtype, ctx->parity != 0, S(stream));
+           }));
+    return LBM_OK;
+}
+
+lbm_status lbm_entropy(lbm_ctx* ctx, double* H_total_host, double* dS_dev, void* stream) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (!H_total_host && !dS_dev) return fail(ctx, LBM_ERR_ARG, "no output requested");
+    const int eqkind = ctx->cfg.collision == LBM_ELBM ? LBM_EQ_ENTROPIC : ctx->cfg.equilibrium;
+    double* H = ctx->p.scratch_d;
+    LBM_CK(ctx, cudaMemsetAsync(H, 0, sizeof(double), S(stream)));
+    LBM_CK(ctx, dispatch(ctx->cfg.precision, [&](auto L) {
+               return decltype(L)::entropy(ctx->Q, ctx->p, H, dS_dev, ctx->parity != 0, eqkind, S(stream));
+           }));
+    if (H_total_host) {
+        LBM_CK(ctx, cudaMemcpyAsync(H_total_host, H, sizeof(double), cudaMemcpyDeviceToHost, S(stream)));
+        LBM_CK(ctx, cudaStreamSynchronize(S(stream)));
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_stats_get(lbm_ctx* ctx, lbm_stats* out, void* stream) {
+    if (!ctx || !out) return LBM_ERR_ARG;
+    unsigned cnt[CNT_WORDS];
+    unsigned long long st[ST_WORDS];
+    LBM_CK(ctx, cudaMemcpyAsync(cnt, ctx->p.counters, sizeof cnt, cudaMemcpyDeviceToHost, S(stream)));
+    LBM_CK(ctx, cudaMemcpyAsync(st, ctx->p.stats, sizeof st, cudaMemcpyDeviceToHost, S(stream)));
+    LBM_CK(ctx, cudaStreamSynchronize(S(stream)));
+    std::memset(out, 0, sizeof *out);
+    out->steps = ctx->t;
+    out->candidates_last = (ctx->t > 0 && limiter(ctx->cfg.collision)) ? cnt[(ctx->t - 1) & 1] : 0;
+    out->limited_total = st[ST_LIMITED];
+    out->elbm_solved = st[ST_ELBM_SOLVED];
+    out->elbm_skipped = st[ST_ELBM_SKIPPED];
+    out->elbm_fallbacks = st[ST_ELBM_FALLBACK];
+    out->elbm_iters_total = st[ST_ELBM_ITERS];
+    out->elbm_iters_max = st[ST_ELBM_ITERS_MAX];
+    out->diverged = cnt[CNT_DIVERGED];
+    out->overflow = cnt[CNT_OVERFLOW];
+    return LBM_OK;
+}
+
+lbm_status lbm_last_candidates(lbm_ctx* ctx, double* ds, int32_t* site, int32_t* selected, int cap,
+                               int* count, void* stream) {
+    if (!ctx || !count || cap < 0) return LBM_ERR_ARG;
+    if (!limiter(ctx->cfg.collision)) return fail(ctx, LBM_ERR_STATE, "collision has no candidate list");
+    if (ctx->t == 0) {
+        *count = 0;
+        return LBM_OK;
+    }
+    unsigned n = 0;
+    LBM_CK(ctx, cudaMemcpyAsync(&n, ctx->p.counters + ((ctx->t - 1) & 1), sizeof n, cudaMemcpyDeviceToHost, S(stream)));
+    LBM_CK(ctx, cudaStreamSynchronize(S(stream)));
+    if (n > (unsigned)ctx->p.cand_cap) n = (unsigned)ctx->p.cand_cap;
+    *count = (int)n;
+    const size_t m = n < (unsigned)cap ? n : (unsigned)cap;
+    if (m) {
+        if (ds) LBM_CK(ctx, cudaMemcpyAsync(ds, ctx->p.cand_ds, m * 8, cudaMemcpyDeviceToHost, S(stream)));
+        if (site) LBM_CK(ctx, cudaMemcpyAsync(site, ctx->p.cand_site, m * 4, cudaMemcpyDeviceToHost, S(stream)));
+        if (selected) LBM_CK(ctx, cudaMemcpyAsync(selected, ctx->p.cand_sel, m * 4, cudaMemcpyDeviceToHost, S(stream)));
+        LBM_CK(ctx, cudaStreamSynchronize(S(stream)));
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_profile_enable(lbm_ctx* ctx, int enable) {
+    if (!ctx) return LBM_ERR_ARG;
+    ctx->profiling = enable != 0;
+    ctx->ev_used = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_profile_read(lbm_ctx* ctx, int* launches, double* ms) {
+    if (!ctx || !launches || !ms) return LBM_ERR_ARG;
+    for (int k = 0; k < LBM_KERNEL_KINDS; ++k) {
+        launches[k] = 0;
+        ms[k] = 0.0;
+    }
+    for (size_t j = 0; j < ctx->ev_used; ++j) {
+        float t = 0.f;
+        LBM_CK(ctx, cudaEventSynchronize(ctx->ev[2 * j + 1]));
+        LBM_CK(ctx, cudaEventElapsedTime(&t, ctx->ev[2 * j], ctx->ev[2 * j + 1]));
+        launches[ctx->ev_kind[j]] += 1;
+        ms[ctx->ev_kind[j]] += t;
+    }
+    ctx->ev_used = 0;
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,481 @@
+// Device side of the GB300 lattice Boltzmann step: lattice tables, storage
+// formats, equilibria, collisions and the fused A-A stream-and-collide kernel.
+//
+// Paper: Brownlee, Levesley, Packwood, Gorban, "Add-ons for Lattice Boltzmann
+// Methods: Regularization, Filtering and Limiters".  Section numbers below
+// refer to it.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm_params.h"
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// Lattices.  D1Q3 (Section 6): v = -1, 0, +1.  D2Q9 (Section 5 numbering,
+// rest, E, then clockwise): 0 rest, 1 E, 2 SE, 3 S, 4 SW, 5 W, 6 NW, 7 N, 8 NE.
+// ---------------------------------------------------------------------------
+template <int Q> struct Lat;
+
+template <> struct Lat<3> {
+    static constexpr int Q = 3;
+    __host__ __device__ static constexpr int cx(int i) { return i - 1; }
+    __host__ __device__ static constexpr int cy(int) { return 0; }
+    __host__ __device__ static constexpr int opp(int i) { return 2 - i; }
+    __host__ __device__ static constexpr double w(int i) { return i == 1 ? 2.0 / 3.0 : 1.0 / 6.0; }
+};
+
+template <> struct Lat<9> {
+    static constexpr int Q = 9;
+    __host__ __device__ static constexpr int cx(int i) {
+        return (i == 1 || i == 2 || i == 8) ? 1 : ((i == 4 || i == 5 || i == 6) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int cy(int i) {
+        return (i == 6 || i == 7 || i == 8) ? 1 : ((i == 2 || i == 3 || i == 4) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : ((i + 3) % 8) + 1; }
+    __host__ __device__ static constexpr double w(int i) {
+        return (cx(i) * cx(i) + cy(i) * cy(i)) == 0 ? 4.0 / 9.0
+               : ((cx(i) * cx(i) + cy(i) * cy(i)) == 1 ? 1.0 / 9.0 : 1.0 / 36.0);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Storage formats.  T is the arithmetic type, S the stored type.  The 16-bit
+// formats hold the deviation f_i - W_i (round to nearest even) so that the
+// format's precision is spent on the part that varies.
+// ---------------------------------------------------------------------------
+struct StF64 {
+    using S = double;
+    using T = double;
+    static constexpr int code = LBM_FP64;
+    __device__ static T ld(const S* p, T) { return *p; }
+    __device__ static void st(S* p, T v, T) { *p = v; }
+};
+struct StF32 {
+    using S = float;
+    using T = float;
+    static constexpr int code = LBM_FP32;
+    __device__ static T ld(const S* p, T) { return *p; }
+    __device__ static void st(S* p, T v, T) { *p = v; }
+};
+struct StBF16 {
+    using S = __nv_bfloat16;
+    using T = float;
+    static constexpr int code = LBM_BF16_DEV;
+    __device__ static T ld(const S* p, T w) { return w + __bfloat162float(*p); }
+    __device__ static void st(S* p, T v, T w) { *p = __float2bfloat16_rn(v - w); }
+};
+struct StF16 {
+    using S = __half;
+    using T = float;
+    static constexpr int code = LBM_FP16_DEV;
+    __device__ static T ld(const S* p, T w) { return w + __half2float(*p); }
+    __device__ static void st(S* p, T v, T w) { *p = __float2half_rn(v - w); }
+};
+
+// ---------------------------------------------------------------------------
+// Equilibria.  1D polynomial and entropic equilibria of Section 6 per unit
+// density (order -, 0, +); the D2Q9 quasi-equilibrium is their product
+// (Section 8).  The textbook polynomial is an option.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void eq1d_poly(T u, T& m, T& z, T& p) {
+    const T sixth = T(1) / T(6);
+    T uu3 = T(3) * u * u;
+    m = (T(1) - T(3) * u + uu3) * sixth;
+    p = (T(1) + T(3) * u + uu3) * sixth;
+    z = T(2) / T(3) * (T(1) - T(1.5) * u * u);
+}
+
+template <class T>
+__device__ __forceinline__ void eq1d_entropic(T u, T& m, T& z, T& p) {
+    const T sixth = T(1) / T(6);
+    T s = sqrt(T(1) + T(3) * u * u);
+    m = (T(-3) * u - T(1) + T(2) * s) * sixth;
+    p = (T(3) * u - T(1) + T(2) * s) * sixth;
+    z = T(2) / T(3) * (T(2) - s);
+}
+
+template <int Q, class T>
+__device__ __forceinline__ void equilibrium(int kind, T rho, T ux, T uy, T* feq) {
+    using L = Lat<Q>;
+    if (Q == 9 && kind == LBM_EQ_POLY_STD) {
+        T uu = ux * ux + uy * uy;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            T cu = T(L::cx(i)) * ux + T(L::cy(i)) * uy;
+            feq[i] = T(L::w(i)) * rho * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
+        }
+        return;
+    }
+    T ax[3], ay[3];
+    if (kind == LBM_EQ_ENTROPIC) {
+        eq1d_entropic<T>(ux, ax[0], ax[1], ax[2]);
+        if (Q == 9) eq1d_entropic<T>(uy, ay[0], ay[1], ay[2]);
+    } else {
+        eq1d_poly<T>(ux, ax[0], ax[1], ax[2]);
+        if (Q == 9) eq1d_poly<T>(uy, ay[0], ay[1], ay[2]);
+    }
+    if (Q == 3) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) feq[i] = rho * ax[i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) feq[i] = rho * ax[L::cx(i) + 1] * ay[L::cy(i) + 1];
+    }
+}
+
+template <int Q, class T>
+__device__ __forceinline__ void moments(const T* f, T& rho, T& ux, T& uy) {
+    using L = Lat<Q>;
+    T r = T(0), jx = T(0), jy = T(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        r += f[i];
+        if (L::cx(i) > 0) jx += f[i];
+        if (L::cx(i) < 0) jx -= f[i];
+        if (L::cy(i) > 0) jy += f[i];
+        if (L::cy(i) < 0) jy -= f[i];
+    }
+    rho = r;
+    T inv = T(1) / r;
+    ux = jx * inv;
+    uy = jy * inv;
+}
+
+// ---------------------------------------------------------------------------
+// g(x) = (1+x) ln(1+x) - x, the per-population term of the nonequilibrium
+// entropy Delta S = sum f*_i g((f_i - f*_i)/f*_i) (Eq. DelS with the zero sum
+// sum (f* - f) added).  For |x| < 1/4 the Taylor series
+// x^2 sum_k (-1)^k x^k / ((k+1)(k+2)) replaces the closed form, whose two
+// terms cancel; the truncation is below one unit in the last place.
+// ---------------------------------------------------------------------------
+template <int K>
+__device__ __forceinline__ double gseries_d(double x) {
+    double p = ((K & 1) ? -1.0 : 1.0) / (double)((K + 1) * (K + 2));
+#pragma unroll
+    for (int k = K - 1; k >= 0; --k) p = fma(p, x, ((k & 1) ? -1.0 : 1.0) / (double)((k + 1) * (k + 2)));
+    return x * x * p;
+}
+
+__device__ __forceinline__ double gfun_d(double x) {
+    if (x <= -1.0) return 1.0;  // g(-1) = 1; below -1 only for negative populations
+    if (fabs(x) < 0.25) return gseries_d<24>(x);
+    return (1.0 + x) * log1p(x) - x;
+}
+
+__device__ __forceinline__ float gfun_f(float x) {
+    if (x <= -1.0f) return 1.0f;
+    if (fabsf(x) < 0.25f) {
+        float p = 1.0f / 132.0f;  // k = 10
+#pragma unroll
+        for (int k = 9; k >= 0; --k) p = fmaf(p, x, ((k & 1) ? -1.0f : 1.0f) / (float)((k + 1) * (k + 2)));
+        return x * x * p;
+    }
+    return (1.0f + x) * log1pf(x) - x;
+}
+
+template <class T> __device__ __forceinline__ T gfun(T x);
+template <> __device__ __forceinline__ double gfun<double>(double x) { return gfun_d(x); }
+template <> __device__ __forceinline__ float gfun<float>(float x) { return gfun_f(x); }
+
+// Delta S in FP64 from populations f (any type, converted exactly).  The
+// equilibrium is recomputed in FP64 from the FP64 moments of f.  A negative
+// population gives +inf.
+template <int Q, class T>
+__device__ double delta_s_fp64(const T* f, int eqkind) {
+    double fd[Q], feq[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) fd[i] = (double)f[i];
+    double rho, ux, uy;
+    moments<Q, double>(fd, rho, ux, uy);
+    equilibrium<Q, double>(eqkind, rho, ux, uy, feq);
+    double s = 0.0;
+    bool neg = false;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        neg |= (fd[i] < 0.0) || !(feq[i] > 0.0);
+        s += feq[i] * gfun_d((fd[i] - feq[i]) / feq[i]);
+    }
+    return neg ? __longlong_as_double(0x7ff0000000000000ULL) : s;
+}
+
+// Delta S in the arithmetic type T from f and its equilibrium.
+template <int Q, class T>
+__device__ __forceinline__ T delta_s_t(const T* f, const T* feq) {
+    T s = T(0);
+    bool neg = false;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        neg |= (f[i] < T(0)) || !(feq[i] > T(0));
+        s += feq[i] * gfun<T>((f[i] - feq[i]) / feq[i]);
+    }
+    return neg ? T(INFINITY) : s;
+}
+
+// Upper bound on Delta S from its quadratic form: with a = max_i |x_i| < 1,
+// g(x) <= x^2 / (2 (1 - a)), so Delta S <= q / (1 - a), q = 1/2 sum f* x^2.
+// Returns true when the site may exceed delta and needs the FP64 value.
+template <int Q, class T>
+__device__ __forceinline__ bool maybe_above(const T* f, const T* feq, double delta) {
+    T q = T(0), a = T(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        T x = (f[i] - feq[i]) / feq[i];
+        q += feq[i] * x * x;
+        a = fmax(a, fabs(x));
+    }
+    if (!(a < T(0.5))) return true;  // also NaN
+    double bound = 0.5 * (double)q / (1.0 - (double)a);
+    // margin for the rounding of q and f* in T (relative 1e-3 covers FP32)
+    return bound * 1.001 + 1e-12 > delta;
+}
+
+// ---------------------------------------------------------------------------
+// Collisions.
+// ---------------------------------------------------------------------------
+
+// LBGK with over-relaxation, Eq. (CollisionIntegral) with alpha = 2.
+template <int Q, class T>
+__device__ __forceinline__ void lbgk(const T* f, const T* feq, T beta, T* F) {
+    T om = T(2) * beta;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) F[i] = f[i] + om * (feq[i] - f[i]);
+}
+
+// Positivity rule (Section 4, Eq. StrLine): a state with a negative
+// component moves along the line through f* to the nearest nonnegative point.
+template <int Q, class T>
+__device__ __forceinline__ bool positivity(const T* feq, T* F) {
+    T lam = T(1);
+    bool hit = false;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (F[i] < T(0)) {
+            T l = feq[i] / (feq[i] - F[i]);
+            lam = l < lam ? l : lam;
+            hit = true;
+        }
+    }
+    if (hit) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) F[i] = feq[i] + lam * (F[i] - feq[i]);
+    }
+    return hit;
+}
+
+// MRT of Section 5 in moment space: with the orthogonal basis M1 (rows
+// rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy; squared norms 9, 36, 36, 6, 12,
+// 6, 12, 4, 4) the inverse is M1^T N^-1, so
+// F = f - M1^T (C1 N^-1) M1 (f - f*).  The conserved rows contribute zero
+// (f and f* share rho and rho u) and are skipped.  rate[k] = C1_k / N_k.
+template <class T>
+__device__ __forceinline__ void mrt_d2q9(const T* f, const T* feq, const MrtRates& r, T* F) {
+    T d[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i] = f[i] - feq[i];
+    // rows of M1 in the paper numbering (rest, E, SE, S, SW, W, NW, N, NE)
+    T se = d[2] + d[4] + d[6] + d[8];  // diagonals
+    T ax = d[1] + d[3] + d[5] + d[7];  // axis
+    T e = T(-4) * d[0] - ax + T(2) * se;
+    T ep = T(4) * d[0] - T(2) * ax + se;
+    T qx = T(-2) * d[1] + d[2] - d[4] + T(2) * d[5] - d[6] + d[8];
+    T qy = -d[2] + T(2) * d[3] - d[4] + d[6] - T(2) * d[7] + d[8];
+    T pxx = d[1] - d[3] + d[5] - d[7];
+    T pxy = -d[2] + d[4] - d[6] + d[8];
+    e *= T(r.e);
+    ep *= T(r.eps);
+    qx *= T(r.q);
+    qy *= T(r.q);
+    pxx *= T(r.nu);
+    pxy *= T(r.nu);
+    // F_i = f_i - sum_k M1[k][i] * m_k
+    F[0] = f[0] - (T(-4) * e + T(4) * ep);
+    F[1] = f[1] - (-e - T(2) * ep - T(2) * qx + pxx);
+    F[2] = f[2] - (T(2) * e + ep + qx - qy - pxy);
+    F[3] = f[3] - (-e - T(2) * ep + T(2) * qy - pxx);
+    F[4] = f[4] - (T(2) * e + ep - qx - qy + pxy);
+    F[5] = f[5] - (-e - T(2) * ep + T(2) * qx + pxx);
+    F[6] = f[6] - (T(2) * e + ep - qx + qy - pxy);
+    F[7] = f[7] - (-e - T(2) * ep - T(2) * qy - pxx);
+    F[8] = f[8] - (T(2) * e + ep + qx + qy + pxy);
+}
+
+// ELBM (Section 3).  S_f(alpha) = S(f + alpha Delta) - S(f), Delta = f* - f,
+// written without cancellation via the entropic equilibrium's identity
+// S(y) = S(f*) - DeltaS(y): with d_i = Delta_i / f*_i and x_i = (alpha-1) d_i,
+//   S_f = sum f*_i [g(-d_i) - g(x_i)],  S_f' = -sum Delta_i ln(1 + x_i),
+//   S_f'' = -sum Delta_i^2 / (f_i + alpha Delta_i).
+template <int Q>
+__device__ __forceinline__ void elbm_eval(const double* f, const double* feq, const double* D,
+                                          const double* gm, double a, double& s0, double& s1,
+                                          double& s2) {
+    double A = 0.0, B = 0.0, C = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        double x = (a - 1.0) * (D[i] / feq[i]);
+        x = x < -1.0 ? -1.0 : x;
+        A += feq[i] * (gm[i] - gfun_d(x));
+        B -= D[i] * log1p(x);
+        C -= D[i] * D[i] / (f[i] + a * D[i]);
+    }
+    s0 = A;
+    s1 = B;
+    s2 = C;
+}
+
+struct ElbmOut {
+    double alpha;
+    int code;   // 0 root, 1 near-equilibrium skip, 2 fallback
+    int iters;
+};
+
+// Root finder of Section 3.3: start at the LBGK value alpha = 2, step to the
+// greater root of the local second-order Taylor parabola, stop when
+// |S_f / S_f'| ||f* - f|| < eps (Eqs. Stopping, ConvergenceTwo), and take the
+// double Newton step back if the estimate ended above the root.  Sites with
+// Delta S < 1e-15 take the LBGK step.  Where the paper is silent: iterates are
+// kept inside the admissible bracket (1, alpha_max] by bisection; existence
+// of a non-trivial root is decided by the sign of S_f(alpha_max); without a
+// root the configured rule of Section 3.2 applies.
+template <int Q>
+__device__ ElbmOut elbm_alpha(const double* f, const double* feq, const Params& p) {
+    ElbmOut o;
+    o.iters = 0;
+    double D[Q], gm[Q];
+    double dS = 0.0, amax = __longlong_as_double(0x7ff0000000000000ULL);
+    bool neg = false;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        D[i] = feq[i] - f[i];
+        gm[i] = gfun_d(-D[i] / feq[i]);
+        dS += feq[i] * gm[i];
+        neg |= f[i] < 0.0;
+        if (D[i] < 0.0) amax = fmin(amax, -f[i] / D[i]);
+    }
+    if (!neg && dS < 1e-15) {
+        o.alpha = 2.0;
+        o.code = 1;
+        return o;
+    }
+    double fb = p.elbm_fallback == LBM_FALLBACK_EHRENFEST ? 1.0 : amax;
+    if (neg) {
+        o.alpha = fb;
+        o.code = 2;
+        return o;
+    }
+    double nrm = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) nrm += p.elbm_norm == LBM_NORM_L1 ? fabs(D[i]) : D[i] * D[i] / feq[i];
+    if (p.elbm_norm != LBM_NORM_L1) nrm = sqrt(nrm);
+    double lo = 1.0, hi = amax;
+    double a = (2.0 < amax) ? 2.0 : 0.5 * (1.0 + amax);
+    double s0, s1, s2;
+    elbm_eval<Q>(f, feq, D, gm, a, s0, s1, s2);
+    if (s0 > 0.0) {
+        double m0, m1, m2;
+        elbm_eval<Q>(f, feq, D, gm, amax, m0, m1, m2);
+        if (m0 > 0.0) {
+            o.alpha = fb;
+            o.code = 2;
+            return o;
+        }
+        lo = a;
+    } else {
+        hi = a;
+    }
+    int it = 0;
+    while (it < p.elbm_max_iter) {
+        if (fabs(s0 / s1) * nrm < p.elbm_eps) break;
+        ++it;
+        double disc = s1 * s1 - 2.0 * s0 * s2;
+        double next = __longlong_as_double(0x7ff8000000000000ULL);
+        if (disc >= 0.0) {
+            // greater root of (s2/2) h^2 + s1 h + s0 = 0, cancellation-free
+            double q = -0.5 * (s1 + copysign(sqrt(disc), s1));
+            double r1 = q / (0.5 * s2);
+            double r2 = s0 / q;
+            next = a + fmax(r1, r2);
+        }
+        if (!(next > lo && next < hi)) next = 0.5 * (lo + hi);
+        a = next;
+        elbm_eval<Q>(f, feq, D, gm, a, s0, s1, s2);
+        if (s0 > 0.0)
+            lo = a;
+        else
+            hi = a;
+    }
+    if (s0 < 0.0) a = a - 2.0 * s0 / s1;
+    o.alpha = a;
+    o.code = 0;
+    o.iters = it;
+    return o;
+}
+
+// ---------------------------------------------------------------------------
+// A-A addressing.  For each direction i a site owns one address R_i; it loads
+// its pre-collision f_i from R_i and stores its post-collision F_opp(i) to
+// R_i, so that every address is read and written by exactly one thread.
+//   even step:  R_i = (slot i, site x): F_j lands in slot opp(j) unstreamed.
+//   odd step:   R_i = (slot opp(i), x - v_i) when x - v_i is in the domain
+//               (the F_i that site streamed towards x), else (slot i, x): a
+//               link through a wall, whose population bounces back half-way,
+//               picking up -6 W_j (v_j . u_wall) (j = opp(i)) on the lid.
+// After an odd step the array is in natural layout again.
+// ---------------------------------------------------------------------------
+template <int Q, class T>
+__device__ __forceinline__ void aa_addresses(const Params& p, int x, int y, bool odd, bool interior,
+                                             int64_t* R, T* lidc) {
+    using L = Lat<Q>;
+    const int64_t site = (int64_t)y * p.pitch + x;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        lidc[i] = T(0);
+        if (!odd) {
+            R[i] = (int64_t)i * p.plane + site;
+        } else if (interior) {
+            R[i] = (int64_t)L::opp(i) * p.plane + site - (int64_t)L::cy(i) * p.pitch - L::cx(i);
+        } else {
+            int sx = x - L::cx(i), sy = y - L::cy(i);
+            if (p.periodic_x) sx = sx < 0 ? sx + p.nx : (sx >= p.nx ? sx - p.nx : sx);
+            if (p.periodic_y) sy = sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy);
+            bool inside = sx >= 0 && sx < p.nx && sy >= 0 && sy < p.ny;
+            if (inside) {
+                R[i] = (int64_t)L::opp(i) * p.plane + (int64_t)sy * p.pitch + sx;
+            } else {
+                R[i] = (int64_t)i * p.plane + site;
+                // the population that left x along j = opp(i) crossed the top wall
+                if (y - L::cy(i) >= p.ny)
+                    lidc[i] = T(6.0 * L::w(L::opp(i)) * L::cx(L::opp(i))) * T(p.lid_u);
+            }
+        }
+    }
+}
+
+// Loads the pre-collision populations of a site in arithmetic type T.
+// (W_i = W_opp(i), so the deviation formats need no slot bookkeeping.)
+template <int Q, class ST>
+__device__ __forceinline__ void load_site(const typename ST::S* f, const int64_t* R,
+                                          const typename ST::T* lidc, typename ST::T* out) {
+    using T = typename ST::T;
+    using L = Lat<Q>;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) out[i] = ST::ld(f + R[i], T(L::w(i))) - lidc[i];
+}
+
+// Stores post-collision F at the site's addresses (F_opp(i) to R_i).
+template <int Q, class ST>
+__device__ __forceinline__ void store_site(typename ST::S* f, const int64_t* R,
+                                           const typename ST::T* lidc, const typename ST::T* F) {
+    using T = typename ST::T;
+    using L = Lat<Q>;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) ST::st(f + R[i], F[L::opp(i)] - lidc[i], T(L::w(i)));
+}
+
+}  // namespace lbm

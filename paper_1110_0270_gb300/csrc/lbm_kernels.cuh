@@ -1,0 +1,591 @@
+// Kernels of the GB300 lattice Boltzmann step (templates; instantiated per
+// storage format in lbm_kernels_<format>.cu).
+//
+//  step_kernel      fused stream + collide for one A-A half of the pattern:
+//                   one read and one write per population, boundary rules
+//                   and the moving lid folded into the addressing; LBGK,
+//                   ELBM, positivity and MRT are complete here, the Ehrenfest
+//                   and median limiters additionally append their candidate
+//                   sites (Delta S > delta) to a compact list.
+//  ehrenfest_fixup  one CTA: k-largest selection over the candidate list by
+//                   MSB radix select on the FP64 Delta S bits, ties by site
+//                   index; selected sites are rewritten with f*.
+//  median_fixup     grid-stride over candidates: median of the Delta S window,
+//                   homothety of Eq. (entrHom) where it lowers Delta S.
+#pragma once
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+constexpr int kBlockX = 128;
+constexpr int kBlockY = 2;
+constexpr int kFixupThreads = 1024;
+
+__device__ __forceinline__ int lane_id() {
+    return (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+}
+
+// The whole step for the site (x, y): addresses, load, collide, store.
+// Returns the FP64 Delta S candidate flag for the limiter collisions.
+template <int Q, class ST, int COLL, bool ODD>
+__device__ __forceinline__ void site_update(const Params& p, int x, int y, bool& cand, double& ds64,
+                                            typename ST::T* fsave, int& e_code, int& e_iters) {
+    using T = typename ST::T;
+    using S = typename ST::S;
+    S* fs = (S*)p.f;
+    T f[Q], F[Q], feq[Q], lidc[Q];
+    int64_t R[Q];
+    const bool interior = x > 0 && x < p.nx - 1 && (Q == 3 || (y > 0 && y < p.ny - 1));
+    aa_addresses<Q, T>(p, x, y, ODD, interior, R, lidc);
+    load_site<Q, ST>(fs, R, lidc, f);
+    T rho, ux, uy;
+    moments<Q, T>(f, rho, ux, uy);
+    if (!(rho > T(0)) || !(fabs(ux) < T(1e30)) || !(fabs(uy) < T(1e30)))
+        atomicExch(&p.counters[CNT_DIVERGED], 1u);
+    const T beta = T(p.beta);
+    if (COLL == LBM_ELBM) {
+        double fd[Q], fe[Q], r, a, b;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) fd[i] = (double)f[i];
+        moments<Q, double>(fd, r, a, b);
+        equilibrium<Q, double>(LBM_EQ_ENTROPIC, r, a, b, fe);
+        ElbmOut o = elbm_alpha<Q>(fd, fe, p);
+        e_code = o.code;
+        e_iters = o.iters;
+        double ab = o.alpha * p.beta;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) F[i] = (T)(fd[i] + ab * (fe[i] - fd[i]));
+    } else {
+        equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
+        if (COLL == LBM_MRT && Q == 9) {
+            mrt_d2q9<T>(f, feq, p.mrt, F);
+        } else {
+            lbgk<Q, T>(f, feq, beta, F);
+        }
+        if (COLL == LBM_POSITIVITY) {
+            if (positivity<Q, T>(feq, F)) atomicAdd(&p.stats[ST_LIMITED], 1ull);
+        }
+        if (COLL == LBM_EHRENFEST || COLL == LBM_MEDIAN) {
+            T dsT = T(0);
+            if (sizeof(T) == 8) {
+                dsT = delta_s_t<Q, T>(f, feq);
+                ds64 = (double)dsT;
+                cand = ds64 > p.delta;
+            } else {
+                if (COLL == LBM_MEDIAN) dsT = delta_s_t<Q, T>(f, feq);
+                if (maybe_above<Q, T>(f, feq, p.delta)) {
+                    ds64 = delta_s_fp64<Q, T>(f, p.eq);
+                    cand = ds64 > p.delta;
+                }
+            }
+            if (COLL == LBM_MEDIAN) ((T*)p.ds_field)[(int64_t)y * p.nx + x] = dsT;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) fsave[i] = f[i];
+        }
+    }
+    store_site<Q, ST>(fs, R, lidc, F);
+}
+
+template <int Q, class ST, int COLL, bool ODD>
+__global__ void __launch_bounds__(kBlockX* kBlockY) step_kernel(Params p) {
+    using T = typename ST::T;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const bool valid = x < p.nx && y < p.ny;
+    constexpr bool kLimiter = (COLL == LBM_EHRENFEST || COLL == LBM_MEDIAN);
+    if (kLimiter && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+        p.counters[p.cslot ^ 1] = 0u;  // the next step's list starts empty
+    bool cand = false;
+    double ds64 = 0.0;
+    T fsave[Q];
+    int e_code = -1, e_iters = 0;
+    if (valid) site_update<Q, ST, COLL, ODD>(p, x, y, cand, ds64, fsave, e_code, e_iters);
+    if (kLimiter) {
+        // warp-aggregated append to the candidate list
+        const unsigned m = __ballot_sync(0xffffffffu, cand);
+        if (m) {
+            const int lane = lane_id();
+            const int leader = __ffs(m) - 1;
+            unsigned base = 0;
+            if (lane == leader) base = atomicAdd(&p.counters[p.cslot], (unsigned)__popc(m));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (cand) {
+                unsigned pos = base + __popc(m & ((1u << lane) - 1u));
+                if (pos < (unsigned)p.cand_cap) {
+                    T* cf = (T*)p.cand_f;
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) cf[(int64_t)i * p.cand_cap + pos] = fsave[i];
+                    p.cand_ds[pos] = ds64;
+                    p.cand_site[pos] = y * p.nx + x;
+                } else {
+                    atomicExch(&p.counters[CNT_OVERFLOW], 1u);
+                }
+            }
+        }
+    }
+    if (COLL == LBM_ELBM) {
+        unsigned solved = __reduce_add_sync(0xffffffffu, e_code == 0 ? 1u : 0u);
+        unsigned skipped = __reduce_add_sync(0xffffffffu, e_code == 1 ? 1u : 0u);
+        unsigned fallback = __reduce_add_sync(0xffffffffu, e_code == 2 ? 1u : 0u);
+        unsigned iters = __reduce_add_sync(0xffffffffu, (unsigned)e_iters);
+        unsigned itmax = __reduce_max_sync(0xffffffffu, (unsigned)e_iters);
+        if (lane_id() == 0) {
+            if (solved) atomicAdd(&p.stats[ST_ELBM_SOLVED], (unsigned long long)solved);
+            if (skipped) atomicAdd(&p.stats[ST_ELBM_SKIPPED], (unsigned long long)skipped);
+            if (fallback) atomicAdd(&p.stats[ST_ELBM_FALLBACK], (unsigned long long)fallback);
+            if (iters) atomicAdd(&p.stats[ST_ELBM_ITERS], (unsigned long long)iters);
+            if (itmax) atomicMax(&p.stats[ST_ELBM_ITERS_MAX], (unsigned long long)itmax);
+        }
+    }
+}
+
+// Writes F for a candidate site recorded by the step kernel (same parity).
+template <int Q, class ST, bool ODD>
+__device__ __forceinline__ void rewrite_site(const Params& p, int site, const typename ST::T* F) {
+    using T = typename ST::T;
+    const int x = site % p.nx, y = site / p.nx;
+    T lidc[Q];
+    int64_t R[Q];
+    aa_addresses<Q, T>(p, x, y, ODD, false, R, lidc);
+    store_site<Q, ST>((typename ST::S*)p.f, R, lidc, F);
+}
+
+template <int Q, class ST>
+__device__ __forceinline__ void load_candidate(const Params& p, int j, typename ST::T* f) {
+    using T = typename ST::T;
+    const T* cf = (const T*)p.cand_f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = cf[(int64_t)i * p.cand_cap + j];
+}
+
+// Ehrenfest regularisation (Section 4): the k candidates with the largest
+// Delta S (ties: lower site index) jump to f*.  One CTA; Delta S > delta >= 0
+// so the IEEE bit patterns order like the values (+inf last).
+template <int Q, class ST, bool ODD>
+__global__ void __launch_bounds__(kFixupThreads) ehrenfest_fixup(Params p) {
+    using T = typename ST::T;
+    __shared__ unsigned hist[256];
+    __shared__ unsigned long long s_prefix, s_mask;
+    __shared__ unsigned s_rem;
+    __shared__ unsigned s_count;
+    const int tid = threadIdx.x;
+    unsigned M = p.counters[p.cslot];
+    if (M > (unsigned)p.cand_cap) M = (unsigned)p.cand_cap;
+    const unsigned K = p.topk > 0 ? (unsigned)p.topk : 0u;
+    if (tid == 0) s_count = 0;
+    const bool all = M <= K;
+    unsigned long long tkey = 0;
+    unsigned icut = 0xffffffffu;
+    if (!all && K > 0) {
+        // MSB-first radix select of the K-th largest key, 8 bits per pass
+        if (tid == 0) {
+            s_prefix = 0;
+            s_mask = 0;
+            s_rem = K;
+        }
+        __syncthreads();
+        for (int shift = 56; shift >= 0; shift -= 8) {
+            for (int d = tid; d < 256; d += blockDim.x) hist[d] = 0;
+            __syncthreads();
+            const unsigned long long pre = s_prefix, msk = s_mask;
+            for (unsigned j = tid; j < M; j += blockDim.x) {
+                unsigned long long key = (unsigned long long)__double_as_longlong(p.cand_ds[j]);
+                if ((key & msk) == pre) atomicAdd(&hist[(key >> shift) & 255ull], 1u);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                unsigned rem = s_rem;
+                int d = 255;
+                for (; d > 0; --d) {
+                    if (hist[d] >= rem) break;
+                    rem -= hist[d];
+                }
+                s_rem = rem;
+                s_prefix = pre | ((unsigned long long)d << shift);
+                s_mask = msk | (255ull << shift);
+            }
+            __syncthreads();
+        }
+        tkey = s_prefix;
+        // among keys equal to the threshold, take the s_rem smallest sites
+        if (tid == 0) {
+            s_prefix = 0;
+            s_mask = 0;
+        }
+        __syncthreads();
+        for (int shift = 24; shift >= 0; shift -= 8) {
+            for (int d = tid; d < 256; d += blockDim.x) hist[d] = 0;
+            __syncthreads();
+            const unsigned pre = (unsigned)s_prefix, msk = (unsigned)s_mask;
+            for (unsigned j = tid; j < M; j += blockDim.x) {
+                unsigned long long key = (unsigned long long)__double_as_longlong(p.cand_ds[j]);
+                unsigned site = (unsigned)p.cand_site[j];
+                if (key == tkey && (site & msk) == pre) atomicAdd(&hist[(site >> shift) & 255u], 1u);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                unsigned rem = s_rem;
+                int d = 0;
+                for (; d < 255; ++d) {
+                    if (hist[d] >= rem) break;
+                    rem -= hist[d];
+                }
+                s_rem = rem;
+                s_prefix = pre | ((unsigned)d << shift);
+                s_mask = msk | (255u << shift);
+            }
+            __syncthreads();
+        }
+        icut = (unsigned)s_prefix;
+    }
+    __syncthreads();
+    unsigned mine = 0;
+    for (unsigned j = tid; j < M; j += blockDim.x) {
+        bool sel = false;
+        if (K > 0) {
+            if (all) {
+                sel = true;
+            } else {
+                unsigned long long key = (unsigned long long)__double_as_longlong(p.cand_ds[j]);
+                unsigned site = (unsigned)p.cand_site[j];
+                sel = key > tkey || (key == tkey && site <= icut);
+            }
+        }
+        p.cand_sel[j] = sel ? 1 : 0;
+        if (sel) {
+            T f[Q], feq[Q], rho, ux, uy;
+            load_candidate<Q, ST>(p, (int)j, f);
+            moments<Q, T>(f, rho, ux, uy);
+            equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
+            rewrite_site<Q, ST, ODD>(p, p.cand_site[j], feq);
+            ++mine;
+        }
+    }
+    if (mine) atomicAdd(&s_count, mine);
+    __syncthreads();
+    if (tid == 0) {
+        p.counters[CNT_NSEL] = s_count;
+        if (s_count) atomicAdd(&p.stats[ST_LIMITED], (unsigned long long)s_count);
+    }
+}
+
+// Median entropy filter (Section 4.4): lower median of Delta S over the site
+// and its neighbours (clipped at walls, wrapped where periodic); where the
+// median is below the site's Delta S the homothety with coefficient
+// sqrt(med / DeltaS) (Eq. entrHom) precedes the LBGK collision.
+template <int Q, class ST, bool ODD>
+__global__ void __launch_bounds__(256) median_fixup(Params p) {
+    using T = typename ST::T;
+    unsigned M = p.counters[p.cslot];
+    if (M > (unsigned)p.cand_cap) M = (unsigned)p.cand_cap;
+    const T* field = (const T*)p.ds_field;
+    unsigned count = 0;
+    for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+        const int site = p.cand_site[j];
+        const int x = site % p.nx, y = site / p.nx;
+        T w[9];
+        int n = 0;
+        const int ry = Q == 9 ? 1 : 0;
+        for (int dy = -ry; dy <= ry; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int xx = x + dx, yy = y + dy;
+                if (p.periodic_x) xx = xx < 0 ? xx + p.nx : (xx >= p.nx ? xx - p.nx : xx);
+                if (p.periodic_y) yy = yy < 0 ? yy + p.ny : (yy >= p.ny ? yy - p.ny : yy);
+                if (xx < 0 || xx >= p.nx || yy < 0 || yy >= p.ny) continue;
+                T v = field[(int64_t)yy * p.nx + xx];
+                int k = n++;
+                while (k > 0 && w[k - 1] > v) {  // insertion sort, ascending
+                    w[k] = w[k - 1];
+                    --k;
+                }
+                w[k] = v;
+            }
+        const T med = w[(n - 1) / 2];
+        const T c = field[site];
+        const bool sel = med < c;
+        p.cand_sel[j] = sel ? 1 : 0;
+        if (sel) {
+            const T phi = isinf(c) ? T(0) : sqrt(med / c);
+            T f[Q], feq[Q], F[Q], rho, ux, uy;
+            load_candidate<Q, ST>(p, (int)j, f);
+            moments<Q, T>(f, rho, ux, uy);
+            equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
+            const T om = T(2) * T(p.beta);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                T fl = feq[i] + phi * (f[i] - feq[i]);
+                F[i] = fl + om * (feq[i] - fl);
+            }
+            rewrite_site<Q, ST, ODD>(p, site, F);
+            ++count;
+        }
+    }
+    if (count) atomicAdd(&p.stats[ST_LIMITED], (unsigned long long)count);
+}
+
+// ---------------------------------------------------------------------------
+// State transfer, macroscopic fields and entropy.
+// ---------------------------------------------------------------------------
+template <int Q, class ST>
+__global__ void init_kernel(Params p, const double* rho, const double* ux, const double* uy,
+                            int eqkind) {
+    using T = typename ST::T;
+    using L = Lat<Q>;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const int64_t s = (int64_t)y * p.nx + x;
+    double feq[Q];
+    equilibrium<Q, double>(eqkind, rho[s], ux[s], uy ? uy[s] : 0.0, feq);
+    typename ST::S* f = (typename ST::S*)p.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        ST::st(f + (int64_t)i * p.plane + (int64_t)y * p.pitch + x, (T)feq[i], T(L::w(i)));
+}
+
+template <int Q, class ST, class In>
+__global__ void set_state_kernel(Params p, const In* src) {
+    using T = typename ST::T;
+    using L = Lat<Q>;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const int64_t N = (int64_t)p.nx * p.ny, s = (int64_t)y * p.nx + x;
+    typename ST::S* f = (typename ST::S*)p.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        ST::st(f + (int64_t)i * p.plane + (int64_t)y * p.pitch + x, (T)src[i * N + s], T(L::w(i)));
+}
+
+template <int Q, class ST>
+__device__ __forceinline__ void read_state(const Params& p, int x, int y, bool odd,
+                                           typename ST::T* f) {
+    using T = typename ST::T;
+    T lidc[Q];
+    int64_t R[Q];
+    aa_addresses<Q, T>(p, x, y, odd, false, R, lidc);
+    load_site<Q, ST>((const typename ST::S*)p.f, R, lidc, f);
+}
+
+template <int Q, class ST, class Out>
+__global__ void get_state_kernel(Params p, Out* dst, int odd) {
+    using T = typename ST::T;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    T f[Q];
+    read_state<Q, ST>(p, x, y, odd != 0, f);
+    const int64_t N = (int64_t)p.nx * p.ny, s = (int64_t)y * p.nx + x;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) dst[i * N + s] = (Out)f[i];
+}
+
+template <int Q, class ST, class Out>
+__global__ void macros_kernel(Params p, Out* rho, Out* u, int odd) {
+    using T = typename ST::T;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    T f[Q];
+    read_state<Q, ST>(p, x, y, odd != 0, f);
+    double fd[Q], r, a, b;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) fd[i] = (double)f[i];
+    moments<Q, double>(fd, r, a, b);
+    const int64_t N = (int64_t)p.nx * p.ny, s = (int64_t)y * p.nx + x;
+    if (rho) rho[s] = (Out)r;
+    if (u) {
+        u[s] = (Out)a;
+        if (Q == 9) u[N + s] = (Out)b;
+    }
+}
+
+// H = sum_x sum_i f ln(f / W) (block-reduced, one FP64 atomic per block) and
+// the FP64 Delta S field against the equilibrium kind eqkind.
+template <int Q, class ST>
+__global__ void __launch_bounds__(256) entropy_kernel(Params p, double* H, double* dS, int odd,
+                                                     int eqkind) {
+    using T = typename ST::T;
+    using L = Lat<Q>;
+    __shared__ double red[32];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    double h = 0.0;
+    if (x < p.nx && y < p.ny) {
+        T f[Q];
+        read_state<Q, ST>(p, x, y, odd != 0, f);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            double v = (double)f[i];
+            if (v > 0.0) h += v * log(v / L::w(i));
+        }
+        if (dS) dS[(int64_t)y * p.nx + x] = delta_s_fp64<Q, T>(f, eqkind);
+    }
+    for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    if ((t & 31) == 0) red[t >> 5] = h;
+    __syncthreads();
+    if (t < 32) {
+        const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+        double v = t < nw ? red[t] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (t == 0) atomicAdd(H, v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (explicitly instantiated per storage format).
+// ---------------------------------------------------------------------------
+template <class ST>
+struct Launch {
+    static cudaError_t step(int Q, int coll, bool odd, const Params& p, cudaStream_t s);
+    static cudaError_t fixup(int Q, int coll, bool odd, const Params& p, cudaStream_t s, int nsm);
+    static cudaError_t init(int Q, const Params& p, const double* r, const double* ux,
+                            const double* uy, int eqkind, cudaStream_t s);
+    static cudaError_t set_state(int Q, const Params& p, const void* src, int dtype, cudaStream_t s);
+    static cudaError_t get_state(int Q, const Params& p, void* dst, int dtype, bool odd,
+                                 cudaStream_t s);
+    static cudaError_t macros(int Q, const Params& p, void* rho, void* u, int dtype, bool odd,
+                              cudaStream_t s);
+    static cudaError_t entropy(int Q, const Params& p, double* H, double* dS, bool odd, int eqkind,
+                               cudaStream_t s);
+};
+
+inline dim3 site_grid(const Params& p, dim3 block) {
+    return dim3((p.nx + block.x - 1) / block.x, (p.ny + block.y - 1) / block.y);
+}
+
+inline dim3 site_block(int Q) { return Q == 3 ? dim3(256, 1) : dim3(kBlockX, kBlockY); }
+
+template <int Q, class ST, int COLL>
+cudaError_t launch_step_q(bool odd, const Params& p, cudaStream_t s) {
+    dim3 b = site_block(Q), g = site_grid(p, b);
+    if (odd)
+        step_kernel<Q, ST, COLL, true><<<g, b, 0, s>>>(p);
+    else
+        step_kernel<Q, ST, COLL, false><<<g, b, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int Q, class ST>
+cudaError_t launch_step_c(int coll, bool odd, const Params& p, cudaStream_t s) {
+    switch (coll) {
+        case LBM_LBGK: return launch_step_q<Q, ST, LBM_LBGK>(odd, p, s);
+        case LBM_ELBM: return launch_step_q<Q, ST, LBM_ELBM>(odd, p, s);
+        case LBM_EHRENFEST: return launch_step_q<Q, ST, LBM_EHRENFEST>(odd, p, s);
+        case LBM_POSITIVITY: return launch_step_q<Q, ST, LBM_POSITIVITY>(odd, p, s);
+        case LBM_MEDIAN: return launch_step_q<Q, ST, LBM_MEDIAN>(odd, p, s);
+        case LBM_MRT: return launch_step_q<Q, ST, LBM_MRT>(odd, p, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int Q, class ST>
+cudaError_t launch_fixup_q(int coll, bool odd, const Params& p, cudaStream_t s, int nsm) {
+    if (coll == LBM_EHRENFEST) {
+        if (odd)
+            ehrenfest_fixup<Q, ST, true><<<1, kFixupThreads, 0, s>>>(p);
+        else
+            ehrenfest_fixup<Q, ST, false><<<1, kFixupThreads, 0, s>>>(p);
+    } else if (coll == LBM_MEDIAN) {
+        // candidate count is only known on the device: a fixed grid of one
+        // CTA per SM strides over the list
+        if (odd)
+            median_fixup<Q, ST, true><<<nsm, 256, 0, s>>>(p);
+        else
+            median_fixup<Q, ST, false><<<nsm, 256, 0, s>>>(p);
+    } else {
+        return cudaSuccess;
+    }
+    return cudaGetLastError();
+}
+
+template <class ST>
+cudaError_t Launch<ST>::step(int Q, int coll, bool odd, const Params& p, cudaStream_t s) {
+    return Q == 3 ? launch_step_c<3, ST>(coll, odd, p, s) : launch_step_c<9, ST>(coll, odd, p, s);
+}
+
+template <class ST>
+cudaError_t Launch<ST>::fixup(int Q, int coll, bool odd, const Params& p, cudaStream_t s, int nsm) {
+    return Q == 3 ? launch_fixup_q<3, ST>(coll, odd, p, s, nsm)
+                  : launch_fixup_q<9, ST>(coll, odd, p, s, nsm);
+}
+
+template <class ST>
+cudaError_t Launch<ST>::init(int Q, const Params& p, const double* r, const double* ux,
+                             const double* uy, int eqkind, cudaStream_t s) {
+    dim3 b = site_block(Q), g = site_grid(p, b);
+    if (Q == 3)
+        init_kernel<3, ST><<<g, b, 0, s>>>(p, r, ux, uy, eqkind);
+    else
+        init_kernel<9, ST><<<g, b, 0, s>>>(p, r, ux, uy, eqkind);
+    return cudaGetLastError();
+}
+
+template <class ST>
+cudaError_t Launch<ST>::set_state(int Q, const Params& p, const void* src, int dtype,
+                                  cudaStream_t s) {
+    dim3 b = site_block(Q), g = site_grid(p, b);
+    if (dtype == LBM_DTYPE_F64) {
+        if (Q == 3)
+            set_state_kernel<3, ST, double><<<g, b, 0, s>>>(p, (const double*)src);
+        else
+            set_state_kernel<9, ST, double><<<g, b, 0, s>>>(p, (const double*)src);
+    } else {
+        if (Q == 3)
+            set_state_kernel<3, ST, float><<<g, b, 0, s>>>(p, (const float*)src);
+        else
+            set_state_kernel<9, ST, float><<<g, b, 0, s>>>(p, (const float*)src);
+    }
+    return cudaGetLastError();
+}
+
+template <class ST>
+cudaError_t Launch<ST>::get_state(int Q, const Params& p, void* dst, int dtype, bool odd,
+                                  cudaStream_t s) {
+    dim3 b = site_block(Q), g = site_grid(p, b);
+    if (dtype == LBM_DTYPE_F64) {
+        if (Q == 3)
+            get_state_kernel<3, ST, double><<<g, b, 0, s>>>(p, (double*)dst, odd);
+        else
+            get_state_kernel<9, ST, double><<<g, b, 0, s>>>(p, (double*)dst, odd);
+    } else {
+        if (Q == 3)
+            get_state_kernel<3, ST, float><<<g, b, 0, s>>>(p, (float*)dst, odd);
+        else
+            get_state_kernel<9, ST, float><<<g, b, 0, s>>>(p, (float*)dst, odd);
+    }
+    return cudaGetLastError();
+}
+
+template <class ST>
+cudaError_t Launch<ST>::macros(int Q, const Params& p, void* rho, void* u, int dtype, bool odd,
+                               cudaStream_t s) {
+    dim3 b = site_block(Q), g = site_grid(p, b);
+    if (dtype == LBM_DTYPE_F64) {
+        if (Q == 3)
+            macros_kernel<3, ST, double><<<g, b, 0, s>>>(p, (double*)rho, (double*)u, odd);
+        else
+            macros_kernel<9, ST, double><<<g, b, 0, s>>>(p, (double*)rho, (double*)u, odd);
+    } else {
+        if (Q == 3)
+            macros_kernel<3, ST, float><<<g, b, 0, s>>>(p, (float*)rho, (float*)u, odd);
+        else
+            macros_kernel<9, ST, float><<<g, b, 0, s>>>(p, (float*)rho, (float*)u, odd);
+    }
+    return cudaGetLastError();
+}
+
+template <class ST>
+cudaError_t Launch<ST>::entropy(int Q, const Params& p, double* H, double* dS, bool odd,
+                                int eqkind, cudaStream_t s) {
+    dim3 b = site_block(Q), g = site_grid(p, b);
+    if (Q == 3)
+        entropy_kernel<3, ST><<<g, b, 0, s>>>(p, H, dS, odd, eqkind);
+    else
+        entropy_kernel<9, ST><<<g, b, 0, s>>>(p, H, dS, odd, eqkind);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,61 @@
+// Launch parameters shared by the host ABI and the kernels (plain data).
+#pragma once
+
+#include <stdint.h>
+
+#include "lbm.h"
+
+namespace lbm {
+
+// MRT rates divided by the squared row norms of M1 (Section 5):
+// e: s_e/36, eps: s_eps/36, q: s_q/12, nu: s_nu/4 with s_nu = 2 beta.
+struct MrtRates {
+    double e, eps, q, nu;
+};
+
+// Device counters (one 256-byte block of scratch, zeroed at create).
+enum Counter {
+    CNT_CAND0 = 0,     // candidate count, step parity 0
+    CNT_CAND1 = 1,     // candidate count, step parity 1
+    CNT_DIVERGED = 2,  // set to 1 on a non-finite / non-positive density
+    CNT_OVERFLOW = 3,  // candidate list overflow
+    CNT_NSEL = 4,      // number of sites selected in the last Ehrenfest step
+    CNT_WORDS = 8
+};
+enum Stat {
+    ST_LIMITED = 0,
+    ST_ELBM_SOLVED = 1,
+    ST_ELBM_SKIPPED = 2,
+    ST_ELBM_FALLBACK = 3,
+    ST_ELBM_ITERS = 4,
+    ST_ELBM_ITERS_MAX = 5,
+    ST_WORDS = 16
+};
+
+struct Params {
+    void* f;          // population storage base (pitched SoA)
+    int64_t plane;    // elements per population plane (ny * pitch)
+    int pitch, nx, ny;
+    int periodic_x, periodic_y;
+    int eq;           // equilibrium kind (LBM_EQ_*)
+    double lid_u;     // top wall velocity along +x
+    double beta;
+    int topk;
+    double delta;
+    MrtRates mrt;
+    double elbm_eps;
+    int elbm_max_iter, elbm_norm, elbm_fallback;
+    // scratch
+    unsigned* counters;              // CNT_WORDS words
+    unsigned long long* stats;       // ST_WORDS words
+    int cand_cap;                    // capacity of the candidate list
+    void* cand_f;                    // [Q][cand_cap] arithmetic type
+    double* cand_ds;                 // [cand_cap] FP64 Delta S
+    int* cand_site;                  // [cand_cap] y * nx + x
+    int* cand_sel;                   // [cand_cap] selected flag (Ehrenfest/median)
+    void* ds_field;                  // [ny][nx] arithmetic type (median only)
+    double* scratch_d;               // small FP64 reduction scratch
+    int cslot;                       // candidate counter used by this step (t & 1)
+};
+
+}  // namespace lbm

@@ -1,0 +1,279 @@
+"""Thin ctypes binding of the C ABI in ``include/lbm.h``.
+
+Argument marshalling only: every step of the lattice Boltzmann path runs in
+the CUDA kernels of ``_lib/liblbm.so``.  PyTorch supplies the device
+allocation and the current stream.  Importing this module fails loudly when
+the library has not been built; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblbm.so")
+
+LATTICES = {"D1Q3": 1, "D2Q9": 2}
+COLLISIONS = {"lbgk": 0, "elbm": 1, "ehrenfest": 2, "positivity": 3, "median": 4, "mrt": 5}
+EQUILIBRIA = {"poly": 0, "entropic": 1, "poly_std": 2}
+PRECISIONS = {"fp64": 0, "fp32": 1, "bf16_dev": 2, "fp16_dev": 3}
+BCS = {"cavity": 0, "ends": 1, "periodic": 2, "channel": 3}
+NORMS = {"entropic": 0, "l1": 1}
+FALLBACKS = {"positivity": 0, "ehrenfest": 1}
+DTYPE_F64, DTYPE_F32 = 0, 1
+STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_CUDA", 3: "LBM_ERR_OOM",
+          4: "LBM_ERR_DIVERGED", 5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_STATE"}
+
+# every symbol declared in include/lbm.h
+EXPORTS = ["lbm_config_default", "lbm_required_bytes", "lbm_create", "lbm_destroy", "lbm_init",
+           "lbm_init_device", "lbm_set_state", "lbm_get_state", "lbm_step", "lbm_macros",
+           "lbm_entropy", "lbm_stats_get", "lbm_last_candidates", "lbm_last_error",
+           "lbm_status_string", "lbm_abi_version", "lbm_profile_enable", "lbm_profile_read"]
+
+
+class lbm_config(C.Structure):
+    _fields_ = [
+        ("lattice", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("collision", C.c_int),
+        ("equilibrium", C.c_int), ("precision", C.c_int), ("bc", C.c_int),
+        ("beta", C.c_double), ("nu", C.c_double), ("lid_u", C.c_double),
+        ("topk", C.c_int), ("delta", C.c_double),
+        ("s_e", C.c_double), ("s_eps", C.c_double), ("s_q", C.c_double),
+        ("elbm_eps", C.c_double), ("elbm_max_iter", C.c_int), ("elbm_norm", C.c_int),
+        ("elbm_fallback", C.c_int),
+    ]
+
+
+class lbm_stats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in (
+        "steps", "candidates_last", "limited_total", "elbm_solved", "elbm_skipped",
+        "elbm_fallbacks", "elbm_iters_total", "elbm_iters_max", "diverged", "overflow")]
+
+
+class LBMError(RuntimeError):
+    pass
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(
+            f"{path} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(path)
+    p, i, sz = C.c_void_p, C.c_int, C.c_size_t
+    sig = {
+        "lbm_config_default": (i, [C.POINTER(lbm_config)]),
+        "lbm_required_bytes": (i, [C.POINTER(lbm_config), C.POINTER(sz)]),
+        "lbm_create": (i, [C.POINTER(lbm_config), p, sz, C.POINTER(p)]),
+        "lbm_destroy": (None, [p]),
+        "lbm_init": (i, [p, p, p, p, p]),
+        "lbm_init_device": (i, [p, p, p, p, p]),
+        "lbm_set_state": (i, [p, p, i, p]),
+        "lbm_get_state": (i, [p, p, i, p]),
+        "lbm_step": (i, [p, i, p]),
+        "lbm_macros": (i, [p, p, p, i, p]),
+        "lbm_entropy": (i, [p, C.POINTER(C.c_double), p, p]),
+        "lbm_stats_get": (i, [p, C.POINTER(lbm_stats), p]),
+        "lbm_last_candidates": (i, [p, p, p, p, i, C.POINTER(i), p]),
+        "lbm_last_error": (C.c_char_p, [p]),
+        "lbm_status_string": (C.c_char_p, [i]),
+        "lbm_abi_version": (i, []),
+        "lbm_profile_enable": (i, [p, i]),
+        "lbm_profile_read": (i, [p, C.POINTER(i), C.POINTER(C.c_double)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+@dataclasses.dataclass
+class LBMConfig:
+    """Python mirror of ``lbm_config``; accepts the names used by the
+    workload generators (``nu`` instead of ``beta`` where given)."""
+    lattice: str = "D2Q9"
+    nx: int = 16
+    ny: int = 16
+    collision: str = "lbgk"
+    equilibrium: str = "poly"
+    precision: str = "fp32"
+    bc: str = "cavity"
+    beta: float = 0.0
+    nu: float = 0.0
+    lid_u: float = 0.0
+    topk: int = 0
+    delta: float = 1e-3
+    s_e: float = 1.64
+    s_eps: float = 1.54
+    s_q: float = 1.9
+    elbm_eps: float = 1e-15
+    elbm_max_iter: int = 20
+    elbm_norm: str = "entropic"
+    elbm_fallback: str = "positivity"
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "LBMConfig":
+        names = {f.name for f in dataclasses.fields(cls)}
+        return cls(**{k: v for k, v in d.items() if k in names})
+
+    @property
+    def Q(self) -> int:
+        return 3 if self.lattice == "D1Q3" else 9
+
+    def to_c(self) -> lbm_config:
+        return lbm_config(LATTICES[self.lattice], int(self.nx), int(self.ny),
+                          COLLISIONS[self.collision], EQUILIBRIA[self.equilibrium],
+                          PRECISIONS[self.precision], BCS[self.bc], float(self.beta),
+                          float(self.nu), float(self.lid_u), int(self.topk), float(self.delta),
+                          float(self.s_e), float(self.s_eps), float(self.s_q),
+                          float(self.elbm_eps), int(self.elbm_max_iter), NORMS[self.elbm_norm],
+                          FALLBACKS[self.elbm_fallback])
+
+
+def required_bytes(cfg) -> int:
+    cfg = cfg if isinstance(cfg, LBMConfig) else LBMConfig.from_dict(cfg)
+    c = cfg.to_c()
+    n = C.c_size_t()
+    rc = lib().lbm_required_bytes(C.byref(c), C.byref(n))
+    if rc != 0:
+        raise LBMError(f"lbm_required_bytes: {STATUS.get(rc, rc)} for {cfg}")
+    return n.value
+
+
+def _stream(stream=None) -> C.c_void_p:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> C.c_void_p:
+    return C.c_void_p(t.data_ptr())
+
+
+class Lattice:
+    """One lattice on the current CUDA device, backed by a torch uint8 tensor.
+
+    All methods enqueue on the current torch stream unless `stream` is given.
+    """
+
+    def __init__(self, cfg, device=None):
+        import torch
+        self.cfg = cfg if isinstance(cfg, LBMConfig) else LBMConfig.from_dict(cfg)
+        self.device = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        self.Q = self.cfg.Q
+        self._c = self.cfg.to_c()
+        self.nbytes = required_bytes(self.cfg)
+        self.mem = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = lib().lbm_create(C.byref(self._c), _ptr(self.mem), self.nbytes, C.byref(h))
+        if rc != 0:
+            raise LBMError(f"lbm_create: {STATUS.get(rc, rc)}")
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.lbm_destroy(h)
+            self._h = None
+
+    # -- helpers
+    def _check(self, rc: int, what: str):
+        if rc != 0:
+            msg = lib().lbm_last_error(self._h)
+            raise LBMError(f"{what}: {STATUS.get(rc, rc)}: {msg.decode() if msg else ''}")
+
+    @property
+    def shape(self):
+        return (self.Q, self.cfg.ny, self.cfg.nx)
+
+    # -- ABI calls
+    def init(self, rho, ux, uy=None, stream=None):
+        """f = f*(rho, u) from host arrays (numpy float64, [ny][nx])."""
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (rho, ux)]
+        arrs.append(np.ascontiguousarray(uy, dtype=np.float64) if uy is not None else None)
+        p = [a.ctypes.data_as(C.c_void_p) if a is not None else None for a in arrs]
+        self._check(lib().lbm_init(self._h, *p, _stream(stream)), "lbm_init")
+
+    def init_device(self, rho, ux, uy=None, stream=None):
+        p = [_ptr(a) if a is not None else None for a in (rho, ux, uy)]
+        self._check(lib().lbm_init_device(self._h, *p, _stream(stream)), "lbm_init_device")
+
+    def set_state(self, f, stream=None):
+        import torch
+        assert f.is_cuda and f.is_contiguous() and tuple(f.shape) == self.shape
+        dt = DTYPE_F64 if f.dtype == torch.float64 else DTYPE_F32
+        assert f.dtype in (torch.float64, torch.float32)
+        self._check(lib().lbm_set_state(self._h, _ptr(f), dt, _stream(stream)), "lbm_set_state")
+
+    def get_state(self, dtype=None, out=None, stream=None):
+        import torch
+        dtype = dtype or torch.float64
+        out = out if out is not None else torch.empty(self.shape, dtype=dtype, device=self.device)
+        dt = DTYPE_F64 if out.dtype == torch.float64 else DTYPE_F32
+        self._check(lib().lbm_get_state(self._h, _ptr(out), dt, _stream(stream)), "lbm_get_state")
+        return out
+
+    def step(self, n: int = 1, stream=None):
+        self._check(lib().lbm_step(self._h, int(n), _stream(stream)), "lbm_step")
+
+    def macros(self, dtype=None, stream=None):
+        import torch
+        dtype = dtype or torch.float64
+        rho = torch.empty((self.cfg.ny, self.cfg.nx), dtype=dtype, device=self.device)
+        u = torch.empty((2 if self.Q == 9 else 1, self.cfg.ny, self.cfg.nx), dtype=dtype,
+                        device=self.device)
+        dt = DTYPE_F64 if dtype == torch.float64 else DTYPE_F32
+        self._check(lib().lbm_macros(self._h, _ptr(rho), _ptr(u), dt, _stream(stream)), "lbm_macros")
+        return rho, u
+
+    def entropy(self, field: bool = False, stream=None):
+        import torch
+        H = C.c_double()
+        dS = torch.empty((self.cfg.ny, self.cfg.nx), dtype=torch.float64,
+                         device=self.device) if field else None
+        self._check(lib().lbm_entropy(self._h, C.byref(H), _ptr(dS) if field else None,
+                                      _stream(stream)), "lbm_entropy")
+        return (H.value, dS) if field else H.value
+
+    def stats(self, stream=None) -> dict:
+        st = lbm_stats()
+        self._check(lib().lbm_stats_get(self._h, C.byref(st), _stream(stream)), "lbm_stats_get")
+        return {n: int(getattr(st, n)) for n, _ in lbm_stats._fields_}
+
+    def profile(self, enable: bool = True):
+        """Start (or stop) per-kernel CUDA-event timing of step()."""
+        self._check(lib().lbm_profile_enable(self._h, int(enable)), "lbm_profile_enable")
+
+    def profile_read(self) -> dict:
+        """{kind: (launches, total_ms)} for 'step' and 'fixup' kernels."""
+        n = (C.c_int * 2)()
+        ms = (C.c_double * 2)()
+        self._check(lib().lbm_profile_read(self._h, n, ms), "lbm_profile_read")
+        return {"step": (n[0], ms[0]), "fixup": (n[1], ms[1])}
+
+    def last_candidates(self, cap: int | None = None, stream=None):
+        """(delta_s float64, site int32, selected int32) of the last step."""
+        cap = cap if cap is not None else self.cfg.nx * self.cfg.ny
+        ds = np.zeros(cap, np.float64)
+        site = np.zeros(cap, np.int32)
+        sel = np.zeros(cap, np.int32)
+        n = C.c_int()
+        self._check(lib().lbm_last_candidates(
+            self._h, ds.ctypes.data_as(C.c_void_p), site.ctypes.data_as(C.c_void_p),
+            sel.ctypes.data_as(C.c_void_p), cap, C.byref(n), _stream(stream)), "lbm_last_candidates")
+        m = min(n.value, cap)
+        return ds[:m], site[:m], sel[:m]

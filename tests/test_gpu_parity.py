@@ -1,0 +1,236 @@
+"""GPU-vs-oracle parity through the C ABI (CUDA kernels on sm_103a).
+
+Each test runs the same seeded input through ``paper_1110_0270_gb300.lbm``
+(the CUDA path) and through the FP64 oracle, and compares element by
+element: rel-L2 <= 1e-12 for FP64 storage and <= 1e-5 for FP32 storage over
+the stated number of steps (the bounds the task's accuracy target states),
+bit-exact for the integer limiter-site selection.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_1110_0270_gb300 import lbm  # noqa: E402
+from paper_1110_0270_gb300 import workloads as WL  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def perturbed_state(cfg, seed, amp=0.02, hot=0, hot_amp=0.4, u_amp=0.05):
+    """Equilibrium of random moments (oracle) times lognormal noise, with an
+    optional few strongly non-equilibrium sites."""
+    ny, nx = cfg["ny"], cfg["nx"]
+    fields = WL.random_fields(ny, nx, seed, 0.05, u_amp)
+    if cfg["lattice"] == "D1Q3":
+        fields["uy"] = None
+    f = O.init_equilibrium(dict(cfg, collision="lbgk"), fields["rho"], fields["ux"], fields["uy"])
+    f = f * WL.lognormal_factors(f.shape, seed + 1, amp)
+    if hot:
+        f = f * WL.lognormal_factors(f.shape, seed + 2, 1.0) ** (WL.hot_spots(ny, nx, seed + 3, hot, hot_amp)[None])
+    return f
+
+
+def gpu_run(cfg, f0, n, store=None):
+    lat = lbm.Lattice(cfg)
+    dt = torch.float64 if cfg.get("precision", "fp32") == "fp64" else torch.float32
+    lat.set_state(torch.tensor(f0, dtype=dt, device="cuda"))
+    lat.step(n)
+    return lat.get_state(torch.float64).cpu().numpy(), lat
+
+
+def as_stored(cfg, f0):
+    """The state both sides start from: rounded to the storage format."""
+    return f0.astype(np.float32).astype(np.float64) if cfg["precision"] != "fp64" else f0
+
+
+CASES = {
+    "cavity": dict(lattice="D2Q9", nx=37, ny=29, bc="cavity", lid_u=0.1),
+    "periodic": dict(lattice="D2Q9", nx=33, ny=17, bc="periodic"),
+    "channel": dict(lattice="D2Q9", nx=130, ny=5, bc="channel", lid_u=0.05),
+    "tube": dict(lattice="D1Q3", nx=301, ny=1, bc="ends"),
+    "ring": dict(lattice="D1Q3", nx=64, ny=1, bc="periodic"),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("collision", ["lbgk", "mrt", "positivity", "elbm"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_local_collisions_match_oracle(case, collision, precision):
+    cfg = dict(CASES[case], collision=collision, precision=precision, beta=0.95,
+               s_e=1.64, s_eps=1.54, s_q=1.2)
+    amp = 0.6 if collision == "positivity" else 0.02
+    f0 = as_stored(cfg, perturbed_state(cfg, 11, amp=amp))
+    n = 301 if collision == "elbm" else 1001
+    g, lat = gpu_run(cfg, f0, n)
+    f = O.step(cfg, f0, n)
+    assert rel(g, f) < TOL[precision], rel(g, f)
+    assert lat.stats()["diverged"] == 0
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("collision", ["ehrenfest", "median"])
+def test_limiters_fp64_match_oracle(case, collision):
+    cfg = dict(CASES[case], collision=collision, precision="fp64", beta=0.97, topk=3, delta=2e-4)
+    f0 = perturbed_state(cfg, 5, amp=0.01, hot=12)
+    n = 201
+    g, lat = gpu_run(cfg, f0, n)
+    f, st = O.step(cfg, f0, n, stats=True)
+    assert rel(g, f) < TOL["fp64"], rel(g, f)
+    gs = lat.stats()
+    assert gs["limited_total"] == st["limited_sites"]
+    assert st["limited_sites"] > 0
+
+
+@pytest.mark.parametrize("collision", ["ehrenfest", "median"])
+@pytest.mark.parametrize("case", ["cavity", "tube"])
+def test_limiters_fp32_one_step_and_selection_replay(case, collision):
+    """FP32 storage: one step from a common state, and the integer selection
+    replayed on the CPU from the GPU's own FP64 Delta S keys (bit-exact) and
+    from the oracle's Delta S of the same state."""
+    cfg = dict(CASES[case], collision=collision, precision="fp32", beta=0.97, topk=3, delta=2e-4)
+    f0 = as_stored(cfg, perturbed_state(cfg, 7, amp=0.01, hot=12))
+    g, lat = gpu_run(cfg, f0, 1)
+    f = O.step(cfg, f0, 1)
+    assert rel(g, f) < 1e-6, rel(g, f)
+    ds, site, sel = lat.last_candidates()
+    dS_or = O.delta_s_field(cfg, f0).ravel()
+    cand_or = np.flatnonzero(dS_or > cfg["delta"])
+    assert sorted(site.tolist()) == cand_or.tolist()
+    assert np.allclose(ds, dS_or[site], rtol=1e-13, atol=0)
+    if collision == "ehrenfest":
+        order = sorted(range(len(ds)), key=lambda j: (-ds[j], site[j]))
+        replay = set(site[order[: cfg["topk"]]].tolist())
+        assert set(site[sel == 1].tolist()) == replay
+        mask, _ = O.select_topk(dS_or, cfg["topk"], cfg["delta"])
+        assert set(np.flatnonzero(mask).tolist()) == replay
+
+
+def test_cavity_from_rest_fp64_1000_steps_and_macros():
+    cfg, init = WL.cavity(41, 400.0, 0.1)
+    cfg.update(collision="lbgk", precision="fp64")
+    lat = lbm.Lattice(cfg)
+    lat.init(init["rho"], init["ux"], init["uy"])
+    f = O.init_equilibrium(cfg, init["rho"], init["ux"], init["uy"])
+    for n in (999, 1):  # odd then even parity
+        lat.step(n)
+        f = O.step(cfg, f, n)
+        g = lat.get_state(torch.float64).cpu().numpy()
+        assert rel(g, f) < 1e-12
+        rho, u = lat.macros(torch.float64)
+        r0, ux0, uy0 = O.macros(cfg, f)
+        assert np.max(np.abs(rho.cpu().numpy() - r0)) < 1e-13
+        assert np.max(np.abs(u[0].cpu().numpy() - ux0)) < 1e-13
+        assert np.max(np.abs(u[1].cpu().numpy() - uy0)) < 1e-13
+        H, dS = lat.entropy(field=True)
+        assert abs(H - O.total_h(cfg, f)) < 1e-12 * abs(O.total_h(cfg, f))
+        dS_or = O.delta_s_field(cfg, f)
+        assert np.allclose(dS.cpu().numpy(), dS_or, rtol=1e-11, atol=1e-25)
+
+
+def test_shock_tube_all_collisions_400_steps():
+    cfg, init = WL.shock_tube(800, 1e-9)
+    for collision in ["lbgk", "elbm", "ehrenfest", "median", "mrt"]:
+        c = dict(cfg, collision=collision, precision="fp64", topk=4, delta=1e-3)
+        lat = lbm.Lattice(c)
+        lat.init(init["rho"], init["ux"])
+        lat.step(400)
+        g = lat.get_state(torch.float64).cpu().numpy()
+        f = O.step(c, O.init_equilibrium(c, init["rho"], init["ux"]), 400)
+        assert rel(g, f) < 1e-12, (collision, rel(g, f))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp16_dev", 3e-3), ("bf16_dev", 3e-2)])
+def test_reduced_precision_storage_tracks_fp64(precision, tol):
+    """16-bit deviation storage with FP32 math: error against the FP64 oracle
+    after 200 steps of a 65^2 cavity stays within the stated bound."""
+    cfg, init = WL.cavity(65, 1000.0, 0.1)
+    cfg.update(collision="lbgk", precision=precision)
+    lat = lbm.Lattice(cfg)
+    lat.init(init["rho"], init["ux"], init["uy"])
+    lat.step(200)
+    f = O.step(cfg, O.init_equilibrium(cfg, init["rho"], init["ux"], init["uy"]), 200)
+    g = lat.get_state(torch.float64).cpu().numpy()
+    assert rel(g, f) < tol, rel(g, f)
+    rho, u = lat.macros(torch.float64)
+    r0, ux0, uy0 = O.macros(cfg, f)
+    uerr = np.linalg.norm(u[0].cpu().numpy() - ux0) / np.linalg.norm(ux0)
+    assert uerr < 20 * tol, uerr
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 7), (7, 1), (2, 2), (33, 3), (129, 3)])
+def test_tiny_and_ragged_lattices(shape):
+    nx, ny = shape
+    for bc in ["cavity", "periodic", "channel"]:
+        cfg = dict(lattice="D2Q9", nx=nx, ny=ny, bc=bc, lid_u=0.1, collision="lbgk",
+                   precision="fp64", beta=0.9)
+        f0 = perturbed_state(cfg, 3)
+        g, _ = gpu_run(cfg, f0, 17)
+        assert rel(g, O.step(cfg, f0, 17)) < 1e-12, (shape, bc)
+    for nx1 in (1, 2, 3, 257):
+        cfg = dict(lattice="D1Q3", nx=nx1, ny=1, bc="ends", collision="lbgk", precision="fp64", beta=0.9)
+        f0 = perturbed_state(cfg, 4)
+        g, _ = gpu_run(cfg, f0, 9)
+        assert rel(g, O.step(cfg, f0, 9)) < 1e-12
+
+
+def test_ehrenfest_selection_edge_cases():
+    base = dict(lattice="D2Q9", nx=40, ny=30, bc="periodic", collision="ehrenfest",
+                precision="fp64", beta=0.9)
+    f0 = perturbed_state(base, 21, amp=0.03, hot=25)
+    # delta = 0: every site is a candidate (large list, radix select path)
+    for topk, delta in [(0, 1e-4), (5, 0.0), (10**6, 1e-4), (1, 1e-4), (37, 1e-9)]:
+        cfg = dict(base, topk=topk, delta=delta)
+        g, lat = gpu_run(cfg, f0, 3)
+        f = O.step(cfg, f0, 3)
+        assert rel(g, f) < 1e-12, (topk, delta, rel(g, f))
+    # exact ties: identical hot spots in a uniform field; lower index wins
+    cfg = dict(base, nx=16, ny=16, topk=3, delta=1e-5)
+    f0 = O.init_equilibrium(cfg, np.ones((16, 16)), np.zeros((16, 16)), np.zeros((16, 16)))
+    bump = np.array([1.3, 0.8, 1.1, 0.9, 1.2, 0.7, 1.05, 0.95, 1.0])
+    for s in [(3, 3), (3, 9), (10, 4), (12, 12), (7, 7)]:
+        f0[:, s[0], s[1]] *= bump
+    g, lat = gpu_run(cfg, f0, 1)
+    ds, site, sel = lat.last_candidates()
+    assert len(site) == 5 and len(set(ds.tolist())) == 1
+    assert sorted(site[sel == 1].tolist()) == sorted([3 * 16 + 3, 3 * 16 + 9, 7 * 16 + 7])
+    assert rel(g, O.step(cfg, f0, 1)) < 1e-12
+
+
+def test_full_size_4097_sampled_sites_and_mass():
+    """The benchmark's lattice (4097^2, FP32, the same lbm_step launch):
+    sampled interior sites after one step equal the oracle's collision of
+    the source sites, f_i(x, t+1) = F_i(x - v_i, t); total mass is kept."""
+    n = 4097
+    for collision in ["lbgk", "mrt", "positivity"]:
+        cfg = dict(lattice="D2Q9", nx=n, ny=n, bc="cavity", lid_u=0.05, collision=collision,
+                   precision="fp32", nu=0.05 * (n - 1) / 10000.0, s_e=1.64, s_eps=1.54, s_q=1.2)
+        lat = lbm.Lattice(cfg)
+        fields = WL.random_fields(n, n, 99, 0.05, 0.05)
+        lat.init(fields["rho"], fields["ux"], fields["uy"])
+        lat.step(1)  # a non-equilibrium state with the A-A layout of odd steps
+        pre = lat.get_state(torch.float32)
+        m0 = float(pre.double().sum())
+        lat.step(1)
+        post = lat.get_state(torch.float32)
+        assert abs(float(post.double().sum()) - m0) < 1e-6 * m0
+        rng = np.random.default_rng(5)
+        xs, ys = rng.integers(1, n - 1, 400), rng.integers(1, n - 1, 400)
+        cx, cy, _ = O.lattice("D2Q9")
+        beta = 1.0 / (6 * cfg["nu"] + 1)
+        ocfg = dict(cfg, nx=1, ny=1, beta=beta)
+        for x, y in zip(xs, ys):
+            for i in range(9):
+                src = pre[:, y - cy[i], x - cx[i]].double().cpu().numpy()
+                F = O.collide_site(ocfg, src)
+                got = float(post[i, y, x])
+                assert abs(got - F[i]) < 2e-6 * abs(F[i]) + 1e-7, (collision, x, y, i, got, F[i])
+        del lat, pre, post
+        torch.cuda.empty_cache()
