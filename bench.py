@@ -246,7 +246,7 @@ def gpu_arm(args):
         B.build()
     if dist is not None:
         dist.barrier()
-    cfg, init = workload_cfg("ehrenfest", "fp32", args.side)
+    cfg, init = workload_cfg(args.collision, args.precision, args.side)
     N = args.side * args.side
     lat = lbm.Lattice(cfg)
     lat.init(init["rho"], init["ux"], init["uy"])
@@ -266,27 +266,29 @@ def gpu_arm(args):
     per = ms / args.steps
     value = ws * N * args.steps / (ms * 1e-3) / 1e6
     hbm, peak_kind = peaks()
-    alg = 2 * Q * 4 * N  # bytes per launch of the fused step kernel
+    alg = 2 * Q * BYTES_PER_POP[args.precision] * N  # bytes per launch of the fused step kernel
     k_ms = prof["step"][1] / max(1, prof["step"][0])
     achieved = alg / (k_ms * 1e-3) / 1e9
-    launches = prof["step"][0] + prof["fixup"][0]
+    launches = prof["step"][0] + prof["fixup"][0] + prof["eval"][0]
     result = {
         "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per, 5),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32", "bf16_dev": "bf16", "fp16_dev": "f16"}[args.precision],
         "data": "synthetic",
         "config": {"workload": f"D2Q9 lid-driven cavity {args.side}x{args.side}, Re {RE:g}, "
-                               f"U {LID_U}, FP32 populations, LBGK + Ehrenfest limiter "
-                               f"(k={TOPK}, delta={DELTA:g}), started from rest",
+                               f"U {LID_U}, {args.precision} populations, collision {args.collision}"
+                               f" (Ehrenfest/median: k={TOPK}, delta={DELTA:g}), started from rest",
                    "sites": N, "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "inputs larger than L2 (state 604 MB in FP32), no flush",
                    "limiter_sites_total": st["limited_total"]},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                      "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
-                     "kernel": "step_kernel<D2Q9, FP32, EHRENFEST>",
+                     "kernel": f"step_kernel<D2Q9, {args.precision}, {args.collision}>",
                      "algorithmic_bytes_per_launch": alg,
                      "kernel_ms": round(k_ms, 5), "peak_kind": f"{peak_kind} hbm_gbs",
-                     "fixup_ms": round(prof["fixup"][1] / max(1, prof["fixup"][0]), 5)},
+                     "fixup_ms": round(prof["fixup"][1] / max(1, prof["fixup"][0]), 5),
+                     "eval_ms": round(prof["eval"][1] / max(1, prof["eval"][0]), 5)},
         "gpu_launches": launches,
     }
     if rank == 0:
@@ -294,7 +296,7 @@ def gpu_arm(args):
         if not args.no_variants:
             result["variants"] = run_variants(args.side, args.variant_steps, 3)
         if not args.no_e2e:
-            result["e2e"] = e2e_measure(workload_cfg("ehrenfest", "fp32", args.side)[0], init)
+            result["e2e"] = e2e_measure(workload_cfg(args.collision, args.precision, args.side)[0], init)
         if not args.no_cpu:
             result["cpu_baseline"] = cpu_baseline(args.cpu_budget)
         print(json.dumps(result), flush=True)
@@ -349,6 +351,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--side", type=int, default=N_SIDE)
+    ap.add_argument("--collision", default="ehrenfest",
+                    choices=["lbgk", "elbm", "ehrenfest", "positivity", "median", "mrt"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16_dev", "bf16_dev"])
     ap.add_argument("--variant-steps", type=int, default=100)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

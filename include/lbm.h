@@ -184,11 +184,12 @@ lbm_status lbm_entropy(lbm_ctx* ctx, double* H_total_host, double* dS_dev, void*
 /* Copies the step counters into *out (synchronises `stream`). */
 lbm_status lbm_stats_get(lbm_ctx* ctx, lbm_stats* out, void* stream);
 
-/* Limiter candidates of the most recent step (EHRENFEST and MEDIAN only):
- * up to `cap` entries of (Delta S in FP64, linear site index y*nx + x,
- * selected flag) into HOST arrays (any may be NULL); *count receives the
- * number of candidates.  Synchronises `stream`.  The candidate order is
- * arbitrary. */
+/* Limiter candidates of the most recent step (EHRENFEST and MEDIAN only),
+ * i.e. the sites whose FP64 Delta S exceeds delta: up to `cap` entries of
+ * (Delta S, linear site index y*nx + x, selected flag) into HOST arrays
+ * (any may be NULL); *count receives the number of candidates.  Synchronises
+ * `stream`.  The candidate order is arbitrary.  Uses a host buffer of one
+ * entry per screened site. */
 lbm_status lbm_last_candidates(lbm_ctx* ctx, double* ds, int32_t* site, int32_t* selected,
                                int cap, int* count, void* stream);
 
@@ -197,12 +198,13 @@ lbm_status lbm_last_candidates(lbm_ctx* ctx, double* ds, int32_t* site, int32_t*
  * events; the first LBM_PROFILE_MAX launches after enabling are kept).
  * Enabling clears the record.  Costs two event records per launch. */
 #define LBM_PROFILE_MAX 65536
-enum { LBM_KERNEL_STEP = 0, LBM_KERNEL_FIXUP = 1, LBM_KERNEL_KINDS = 2 };
+enum { LBM_KERNEL_STEP = 0, LBM_KERNEL_FIXUP = 1, LBM_KERNEL_EVAL = 2, LBM_KERNEL_KINDS = 3 };
 lbm_status lbm_profile_enable(lbm_ctx* ctx, int enable);
 
 /* Waits for the recorded events and returns, per kernel kind (index
  * LBM_KERNEL_STEP: the fused stream-collide kernel; LBM_KERNEL_FIXUP: the
- * Ehrenfest/median fix-up), the number of launches and their summed device
+ * Ehrenfest selection or median filter fix-up; LBM_KERNEL_EVAL: the FP64
+ * Delta S of the screened sites), the number of launches and their summed device
  * time in milliseconds (arrays of LBM_KERNEL_KINDS entries), then clears the
  * record. */
 lbm_status lbm_profile_read(lbm_ctx* ctx, int* launches, double* ms);

@@ -72,6 +72,8 @@ const char* check_config(const lbm_config* c) {
     if (c->lattice == LBM_D1Q3 && c->ny != 1) return "D1Q3 needs ny == 1";
     if ((long long)c->nx * c->ny > 0x7fffffffLL) return "nx * ny must fit in 31 bits";
     if (c->ny > 65535LL * kBlockY) return "ny too large for the launch grid";
+    if ((long long)(c->lattice == LBM_D1Q3 ? 3 : 9) * c->ny * ((c->nx + 31) / 32 * 32) >= 0x7fffffffLL)
+        return "Q * ny * pitch must be below 2^31 elements";
     if (c->collision < LBM_LBGK || c->collision > LBM_MRT) return "unknown collision";
     if (c->equilibrium < LBM_EQ_POLY_PRODUCT || c->equilibrium > LBM_EQ_POLY_STD) return "unknown equilibrium";
     if (c->precision < LBM_FP64 || c->precision > LBM_FP16_DEV) return "unknown precision";
@@ -248,6 +250,7 @@ lbm_status lbm_create(const lbm_config* cfg, void* dev_mem, size_t bytes, lbm_ct
     std::memset(&p, 0, sizeof p);
     p.f = ctx->base + L.f_off;
     p.plane = L.plane;
+    p.plane32 = (int)L.plane;
     p.pitch = L.pitch;
     p.nx = cfg->nx;
     p.ny = cfg->ny;
@@ -258,11 +261,15 @@ lbm_status lbm_create(const lbm_config* cfg, void* dev_mem, size_t bytes, lbm_ct
     p.beta = ctx->cfg.beta;
     p.topk = cfg->topk;
     p.delta = cfg->delta;
+    p.beta_f = (float)p.beta;
+    p.lid_u_f = (float)p.lid_u;
+    p.delta_f = (float)cfg->delta;
     const double snu = 2.0 * p.beta;
     p.mrt.e = cfg->s_e / 36.0;
     p.mrt.eps = cfg->s_eps / 36.0;
     p.mrt.q = cfg->s_q / 12.0;
     p.mrt.nu = snu / 4.0;
+    p.mrt_f = {(float)p.mrt.e, (float)p.mrt.eps, (float)p.mrt.q, (float)p.mrt.nu};
     p.elbm_eps = cfg->elbm_eps;
     p.elbm_max_iter = cfg->elbm_max_iter;
     p.elbm_norm = cfg->elbm_norm;
@@ -352,6 +359,12 @@ lbm_status lbm_step(lbm_ctx* ctx, int nsteps, void* stream) {
                        return decltype(L)::step(ctx->Q, coll, odd, q, S(stream));
                    });
                }));
+        if (coll == LBM_EHRENFEST)
+            LBM_CK(ctx, traced(ctx, LBM_KERNEL_EVAL, S(stream), [&] {
+                       return dispatch(ctx->cfg.precision, [&](auto L) {
+                           return decltype(L)::eval(ctx->Q, q, S(stream), ctx->nsm);
+                       });
+                   }));
         if (limiter(coll))
             LBM_CK(ctx, traced(ctx, LBM_KERNEL_FIXUP, S(stream), [&] {
                        return dispatch(ctx->cfg.precision, [&](auto L) {
@@ -398,7 +411,7 @@ lbm_status lbm_stats_get(lbm_ctx* ctx, lbm_stats* out, void* stream) {
     LBM_CK(ctx, cudaStreamSynchronize(S(stream)));
     std::memset(out, 0, sizeof *out);
     out->steps = ctx->t;
-    out->candidates_last = (ctx->t > 0 && limiter(ctx->cfg.collision)) ? cnt[(ctx->t - 1) & 1] : 0;
+    out->candidates_last = (ctx->t > 0 && limiter(ctx->cfg.collision)) ? cnt[CNT_NVALID] : 0;
     out->limited_total = st[ST_LIMITED];
     out->elbm_solved = st[ST_ELBM_SOLVED];
     out->elbm_skipped = st[ST_ELBM_SKIPPED];
@@ -422,14 +435,26 @@ lbm_status lbm_last_candidates(lbm_ctx* ctx, double* ds, int32_t* site, int32_t*
     LBM_CK(ctx, cudaMemcpyAsync(&n, ctx->p.counters + ((ctx->t - 1) & 1), sizeof n, cudaMemcpyDeviceToHost, S(stream)));
     LBM_CK(ctx, cudaStreamSynchronize(S(stream)));
     if (n > (unsigned)ctx->p.cand_cap) n = (unsigned)ctx->p.cand_cap;
-    *count = (int)n;
-    const size_t m = n < (unsigned)cap ? n : (unsigned)cap;
-    if (m) {
-        if (ds) LBM_CK(ctx, cudaMemcpyAsync(ds, ctx->p.cand_ds, m * 8, cudaMemcpyDeviceToHost, S(stream)));
-        if (site) LBM_CK(ctx, cudaMemcpyAsync(site, ctx->p.cand_site, m * 4, cudaMemcpyDeviceToHost, S(stream)));
-        if (selected) LBM_CK(ctx, cudaMemcpyAsync(selected, ctx->p.cand_sel, m * 4, cudaMemcpyDeviceToHost, S(stream)));
+    // screened sites; the candidates are those with Delta S > delta
+    std::vector<double> hds(n);
+    std::vector<int32_t> hsite(n), hsel(n);
+    if (n) {
+        LBM_CK(ctx, cudaMemcpyAsync(hds.data(), ctx->p.cand_ds, n * 8, cudaMemcpyDeviceToHost, S(stream)));
+        LBM_CK(ctx, cudaMemcpyAsync(hsite.data(), ctx->p.cand_site, n * 4, cudaMemcpyDeviceToHost, S(stream)));
+        LBM_CK(ctx, cudaMemcpyAsync(hsel.data(), ctx->p.cand_sel, n * 4, cudaMemcpyDeviceToHost, S(stream)));
         LBM_CK(ctx, cudaStreamSynchronize(S(stream)));
     }
+    int m = 0;
+    for (unsigned j = 0; j < n; ++j) {
+        if (!(hds[j] > ctx->cfg.delta)) continue;
+        if (m < cap) {
+            if (ds) ds[m] = hds[j];
+            if (site) site[m] = hsite[j];
+            if (selected) selected[m] = hsel[j];
+        }
+        ++m;
+    }
+    *count = m;
     return LBM_OK;
 }
 

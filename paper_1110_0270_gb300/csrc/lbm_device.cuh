@@ -83,34 +83,44 @@ struct StF16 {
 // density (order -, 0, +); the D2Q9 quasi-equilibrium is their product
 // (Section 8).  The textbook polynomial is an option.
 // ---------------------------------------------------------------------------
+// Both 1D equilibria have the form phi_-+ = a -+ u/2, phi_0 = 1 - 2a, with
+// a = (1 + 3u^2)/6 (polynomial) or (2 sqrt(1 + 3u^2) - 1)/6 (entropic) -
+// the printed formulas of Section 6 regrouped into even and odd parts.
+// Written this way the zeroth and first moments are exact up to unbiased
+// rounding: u/2 is exact in binary, and the rounded constants 1/6, 2/3 that
+// the printed forms carry would otherwise bias sum f* (mass) and
+// sum v f* (momentum) upwards by ~6e-8 per step in FP32, a steady drift.
 template <class T>
 __device__ __forceinline__ void eq1d_poly(T u, T& m, T& z, T& p) {
-    const T sixth = T(1) / T(6);
-    T uu3 = T(3) * u * u;
-    m = (T(1) - T(3) * u + uu3) * sixth;
-    p = (T(1) + T(3) * u + uu3) * sixth;
-    z = T(2) / T(3) * (T(1) - T(1.5) * u * u);
+    const T a = (T(1) + T(3) * u * u) * (T(1) / T(6));
+    const T h = T(0.5) * u;
+    m = a - h;
+    p = a + h;
+    z = T(1) - T(2) * a;
 }
 
 template <class T>
 __device__ __forceinline__ void eq1d_entropic(T u, T& m, T& z, T& p) {
-    const T sixth = T(1) / T(6);
-    T s = sqrt(T(1) + T(3) * u * u);
-    m = (T(-3) * u - T(1) + T(2) * s) * sixth;
-    p = (T(3) * u - T(1) + T(2) * s) * sixth;
-    z = T(2) / T(3) * (T(2) - s);
+    const T s = sqrt(T(1) + T(3) * u * u);
+    const T a = (T(2) * s - T(1)) * (T(1) / T(6));
+    const T h = T(0.5) * u;
+    m = a - h;
+    p = a + h;
+    z = T(1) - T(2) * a;
 }
 
 template <int Q, class T>
 __device__ __forceinline__ void equilibrium(int kind, T rho, T ux, T uy, T* feq) {
     using L = Lat<Q>;
     if (Q == 9 && kind == LBM_EQ_POLY_STD) {
-        T uu = ux * ux + uy * uy;
+        T uu = ux * ux + uy * uy, rest = rho;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
+        for (int i = 1; i < Q; ++i) {
             T cu = T(L::cx(i)) * ux + T(L::cy(i)) * uy;
             feq[i] = T(L::w(i)) * rho * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
+            rest -= feq[i];
         }
+        feq[0] = rest;  // = 4/9 rho (1 - 3/2 u^2); keeps sum f* = rho unbiased
         return;
     }
     T ax[3], ay[3];
@@ -219,21 +229,25 @@ __device__ __forceinline__ T delta_s_t(const T* f, const T* feq) {
 }
 
 // Upper bound on Delta S from its quadratic form: with a = max_i |x_i| < 1,
-// g(x) <= x^2 / (2 (1 - a)), so Delta S <= q / (1 - a), q = 1/2 sum f* x^2.
+// g(x) <= x^2 / (2 (1 - a)), so Delta S <= q / (2 (1 - a)), q = sum d^2 / f*,
+// d = f - f*.  Evaluated in FP32 (no FP64 instruction; GB300's FP64 rate is
+// a small fraction of its FP32 rate).  Rounding of f, f* and d to FP32 moves
+// q by at most ~3e-7 sqrt(q rho) + 2e-6 q (|d| summed by Cauchy-Schwarz),
+// covered by the relative 1e-3 and absolute 1e-6 sqrt(q rho) slack.
 // Returns true when the site may exceed delta and needs the FP64 value.
-template <int Q, class T>
-__device__ __forceinline__ bool maybe_above(const T* f, const T* feq, double delta) {
-    T q = T(0), a = T(0);
+template <int Q>
+__device__ __forceinline__ bool maybe_above(const float* f, const float* feq, float delta) {
+    float q = 0.f, a = 0.f, rho = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        T x = (f[i] - feq[i]) / feq[i];
-        q += feq[i] * x * x;
-        a = fmax(a, fabs(x));
+        const float d = f[i] - feq[i];
+        q += __fdividef(d * d, feq[i]);
+        a = fmaxf(a, fabsf(__fdividef(d, feq[i])));
+        rho += f[i];
     }
-    if (!(a < T(0.5))) return true;  // also NaN
-    double bound = 0.5 * (double)q / (1.0 - (double)a);
-    // margin for the rounding of q and f* in T (relative 1e-3 covers FP32)
-    return bound * 1.001 + 1e-12 > delta;
+    if (!(a < 0.5f)) return true;  // also NaN
+    const float lhs = 0.5f * q * 1.001f + 1e-6f * sqrtf(q * fabsf(rho));
+    return lhs >= delta * (1.0f - a);
 }
 
 // ---------------------------------------------------------------------------
@@ -275,7 +289,13 @@ __device__ __forceinline__ bool positivity(const T* feq, T* F) {
 // F = f - M1^T (C1 N^-1) M1 (f - f*).  The conserved rows contribute zero
 // (f and f* share rho and rho u) and are skipped.  rate[k] = C1_k / N_k.
 template <class T>
-__device__ __forceinline__ void mrt_d2q9(const T* f, const T* feq, const MrtRates& r, T* F) {
+__device__ __forceinline__ void mrt_d2q9(const T* f, const T* feq, const MrtRates& rd,
+                                         const MrtRatesF& rf, T* F) {
+    // rates in T (FP32 copies avoid per-site FP64 conversions)
+    struct {
+        T e, eps, q, nu;
+    } r = {sizeof(T) == 8 ? T(rd.e) : T(rf.e), sizeof(T) == 8 ? T(rd.eps) : T(rf.eps),
+           sizeof(T) == 8 ? T(rd.q) : T(rf.q), sizeof(T) == 8 ? T(rd.nu) : T(rf.nu)};
     T d[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) d[i] = f[i] - feq[i];
@@ -288,12 +308,12 @@ __device__ __forceinline__ void mrt_d2q9(const T* f, const T* feq, const MrtRate
     T qy = -d[2] + T(2) * d[3] - d[4] + d[6] - T(2) * d[7] + d[8];
     T pxx = d[1] - d[3] + d[5] - d[7];
     T pxy = -d[2] + d[4] - d[6] + d[8];
-    e *= T(r.e);
-    ep *= T(r.eps);
-    qx *= T(r.q);
-    qy *= T(r.q);
-    pxx *= T(r.nu);
-    pxy *= T(r.nu);
+    e *= r.e;
+    ep *= r.eps;
+    qx *= r.q;
+    qy *= r.q;
+    pxx *= r.nu;
+    pxy *= r.nu;
     // F_i = f_i - sum_k M1[k][i] * m_k
     F[0] = f[0] - (T(-4) * e + T(4) * ep);
     F[1] = f[1] - (-e - T(2) * ep - T(2) * qx + pxx);
@@ -429,53 +449,79 @@ __device__ ElbmOut elbm_alpha(const double* f, const double* feq, const Params& 
 // After an odd step the array is in natural layout again.
 // ---------------------------------------------------------------------------
 template <int Q, class T>
-__device__ __forceinline__ void aa_addresses(const Params& p, int x, int y, bool odd, bool interior,
-                                             int64_t* R, T* lidc) {
+__device__ __forceinline__ int64_t aa_address(const Params& p, int x, int y, int i, bool odd,
+                                              T& lidc) {
     using L = Lat<Q>;
-    const int64_t site = (int64_t)y * p.pitch + x;
+    lidc = T(0);
+    if (!odd) return (int64_t)i * p.plane + (int64_t)y * p.pitch + x;
+    int sx = x - L::cx(i), sy = y - L::cy(i);
+    if (p.periodic_x) sx = sx < 0 ? sx + p.nx : (sx >= p.nx ? sx - p.nx : sx);
+    if (p.periodic_y) sy = sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy);
+    if (sx >= 0 && sx < p.nx && sy >= 0 && sy < p.ny)
+        return (int64_t)L::opp(i) * p.plane + (int64_t)sy * p.pitch + sx;
+    // the population that left x along j = opp(i) crossed the top wall
+    if (y - L::cy(i) >= p.ny)
+        lidc = T(6.0 * L::w(L::opp(i)) * L::cx(L::opp(i))) *
+               (sizeof(T) == 8 ? T(p.lid_u) : T(p.lid_u_f));
+    return (int64_t)i * p.plane + (int64_t)y * p.pitch + x;
+}
+
+// Interior sites (all neighbours in the domain, so no wall terms): the
+// offsets are 32-bit (the library keeps Q * ny * pitch below 2^31) and every
+// address is a kernel-uniform base plus the site offset o = y * pitch + x.
+template <int Q, class ST, bool ODD>
+__device__ __forceinline__ int interior_offset(const Params& p, int o, int i) {
+    using L = Lat<Q>;
+    return ODD ? L::opp(i) * p.plane32 + o - L::cy(i) * p.pitch - L::cx(i) : i * p.plane32 + o;
+}
+
+template <int Q, class ST, bool ODD>
+__device__ __forceinline__ void load_interior(const Params& p, int o, typename ST::T* f) {
+    using T = typename ST::T;
+    using L = Lat<Q>;
+    const typename ST::S* base = (const typename ST::S*)p.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = ST::ld(base + interior_offset<Q, ST, ODD>(p, o, i), T(L::w(i)));
+}
+
+template <int Q, class ST, bool ODD>
+__device__ __forceinline__ void store_interior(const Params& p, int o, const typename ST::T* F) {
+    using T = typename ST::T;
+    using L = Lat<Q>;
+    typename ST::S* base = (typename ST::S*)p.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        ST::st(base + interior_offset<Q, ST, ODD>(p, o, i), F[L::opp(i)], T(L::w(i)));
+}
+
+// Boundary (or any) site: the general addressing with wrap-around and walls,
+// one direction at a time so that no address array stays live.
+// (W_i = W_opp(i), so the deviation formats need no slot bookkeeping.)
+template <int Q, class ST, bool ODD>
+__device__ __forceinline__ void load_general(const Params& p, int x, int y, typename ST::T* f) {
+    using T = typename ST::T;
+    using L = Lat<Q>;
+    const typename ST::S* base = (const typename ST::S*)p.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        lidc[i] = T(0);
-        if (!odd) {
-            R[i] = (int64_t)i * p.plane + site;
-        } else if (interior) {
-            R[i] = (int64_t)L::opp(i) * p.plane + site - (int64_t)L::cy(i) * p.pitch - L::cx(i);
-        } else {
-            int sx = x - L::cx(i), sy = y - L::cy(i);
-            if (p.periodic_x) sx = sx < 0 ? sx + p.nx : (sx >= p.nx ? sx - p.nx : sx);
-            if (p.periodic_y) sy = sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy);
-            bool inside = sx >= 0 && sx < p.nx && sy >= 0 && sy < p.ny;
-            if (inside) {
-                R[i] = (int64_t)L::opp(i) * p.plane + (int64_t)sy * p.pitch + sx;
-            } else {
-                R[i] = (int64_t)i * p.plane + site;
-                // the population that left x along j = opp(i) crossed the top wall
-                if (y - L::cy(i) >= p.ny)
-                    lidc[i] = T(6.0 * L::w(L::opp(i)) * L::cx(L::opp(i))) * T(p.lid_u);
-            }
-        }
+        T lidc;
+        const int64_t r = aa_address<Q, T>(p, x, y, i, ODD, lidc);
+        f[i] = ST::ld(base + r, T(L::w(i))) - lidc;
     }
 }
 
-// Loads the pre-collision populations of a site in arithmetic type T.
-// (W_i = W_opp(i), so the deviation formats need no slot bookkeeping.)
-template <int Q, class ST>
-__device__ __forceinline__ void load_site(const typename ST::S* f, const int64_t* R,
-                                          const typename ST::T* lidc, typename ST::T* out) {
+template <int Q, class ST, bool ODD>
+__device__ __forceinline__ void store_general(const Params& p, int x, int y,
+                                              const typename ST::T* F) {
     using T = typename ST::T;
     using L = Lat<Q>;
+    typename ST::S* base = (typename ST::S*)p.f;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) out[i] = ST::ld(f + R[i], T(L::w(i))) - lidc[i];
-}
-
-// Stores post-collision F at the site's addresses (F_opp(i) to R_i).
-template <int Q, class ST>
-__device__ __forceinline__ void store_site(typename ST::S* f, const int64_t* R,
-                                           const typename ST::T* lidc, const typename ST::T* F) {
-    using T = typename ST::T;
-    using L = Lat<Q>;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) ST::st(f + R[i], F[L::opp(i)] - lidc[i], T(L::w(i)));
+    for (int i = 0; i < Q; ++i) {
+        T lidc;
+        const int64_t r = aa_address<Q, T>(p, x, y, i, ODD, lidc);
+        ST::st(base + r, F[L::opp(i)] - lidc, T(L::w(i)));
+    }
 }
 
 }  // namespace lbm

@@ -26,104 +26,99 @@ __device__ __forceinline__ int lane_id() {
     return (threadIdx.y * blockDim.x + threadIdx.x) & 31;
 }
 
-// The whole step for the site (x, y): addresses, load, collide, store.
-// Returns the FP64 Delta S candidate flag for the limiter collisions.
+// Appends a screened site (Delta S possibly above delta) to the compact list:
+// its pre-collision populations and site index.  Such sites are rare, so one
+// atomic each; a full list sets the overflow flag.  The FP64 Delta S is
+// evaluated afterwards by eval_kernel / median_fixup, off the streaming path.
+template <int Q, class T>
+__device__ __forceinline__ void record_candidate(const Params& p, int x, int y, const T* f) {
+    const unsigned pos = atomicAdd(&p.counters[p.cslot], 1u);
+    if (pos < (unsigned)p.cand_cap) {
+        T* cf = (T*)p.cand_f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) cf[(int64_t)i * p.cand_cap + pos] = f[i];
+        p.cand_site[pos] = y * p.nx + x;
+    } else {
+        atomicExch(&p.counters[CNT_OVERFLOW], 1u);
+    }
+}
+
+// Limiter screen of the pre-collision state.  A division-free FP32 bound on
+// Delta S (Eq. DelS) keeps the sites that may exceed delta; their FP64 value
+// decides later.  The median filter also needs the Delta S field of every
+// site (in the arithmetic type; FP64 in FP64 mode).
+template <int Q, class T, int COLL>
+__device__ __forceinline__ void limiter_screen(const Params& p, int x, int y, const T* f,
+                                               const T* feq) {
+    if (COLL == LBM_MEDIAN) ((T*)p.ds_field)[(int64_t)y * p.nx + x] = delta_s_t<Q, T>(f, feq);
+    float ff[Q], fq[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        ff[i] = (float)f[i];
+        fq[i] = (float)feq[i];
+    }
+    if (maybe_above<Q>(ff, fq, p.delta_f)) record_candidate<Q, T>(p, x, y, f);
+}
+
+// The whole step for the site (x, y): load (streaming in odd steps), moments,
+// equilibrium, limiter screen, collision, store.
 template <int Q, class ST, int COLL, bool ODD>
-__device__ __forceinline__ void site_update(const Params& p, int x, int y, bool& cand, double& ds64,
-                                            typename ST::T* fsave, int& e_code, int& e_iters) {
+__device__ __forceinline__ void site_update(const Params& p, int x, int y, int& e_code,
+                                            int& e_iters) {
     using T = typename ST::T;
-    using S = typename ST::S;
-    S* fs = (S*)p.f;
-    T f[Q], F[Q], feq[Q], lidc[Q];
-    int64_t R[Q];
+    T f[Q], F[Q];
     const bool interior = x > 0 && x < p.nx - 1 && (Q == 3 || (y > 0 && y < p.ny - 1));
-    aa_addresses<Q, T>(p, x, y, ODD, interior, R, lidc);
-    load_site<Q, ST>(fs, R, lidc, f);
+    const int o = y * p.pitch + x;
+    if (interior)
+        load_interior<Q, ST, ODD>(p, o, f);
+    else
+        load_general<Q, ST, ODD>(p, x, y, f);
     T rho, ux, uy;
     moments<Q, T>(f, rho, ux, uy);
     if (!(rho > T(0)) || !(fabs(ux) < T(1e30)) || !(fabs(uy) < T(1e30)))
         atomicExch(&p.counters[CNT_DIVERGED], 1u);
-    const T beta = T(p.beta);
     if (COLL == LBM_ELBM) {
         double fd[Q], fe[Q], r, a, b;
 #pragma unroll
         for (int i = 0; i < Q; ++i) fd[i] = (double)f[i];
         moments<Q, double>(fd, r, a, b);
         equilibrium<Q, double>(LBM_EQ_ENTROPIC, r, a, b, fe);
-        ElbmOut o = elbm_alpha<Q>(fd, fe, p);
-        e_code = o.code;
-        e_iters = o.iters;
-        double ab = o.alpha * p.beta;
+        ElbmOut out = elbm_alpha<Q>(fd, fe, p);
+        e_code = out.code;
+        e_iters = out.iters;
+        const double ab = out.alpha * p.beta;
 #pragma unroll
         for (int i = 0; i < Q; ++i) F[i] = (T)(fd[i] + ab * (fe[i] - fd[i]));
     } else {
+        T feq[Q];
         equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
+        if (COLL == LBM_EHRENFEST || COLL == LBM_MEDIAN) limiter_screen<Q, T, COLL>(p, x, y, f, feq);
         if (COLL == LBM_MRT && Q == 9) {
-            mrt_d2q9<T>(f, feq, p.mrt, F);
+            mrt_d2q9<T>(f, feq, p.mrt, p.mrt_f, F);
         } else {
-            lbgk<Q, T>(f, feq, beta, F);
+            lbgk<Q, T>(f, feq, sizeof(T) == 8 ? T(p.beta) : T(p.beta_f), F);
         }
         if (COLL == LBM_POSITIVITY) {
             if (positivity<Q, T>(feq, F)) atomicAdd(&p.stats[ST_LIMITED], 1ull);
         }
-        if (COLL == LBM_EHRENFEST || COLL == LBM_MEDIAN) {
-            T dsT = T(0);
-            if (sizeof(T) == 8) {
-                dsT = delta_s_t<Q, T>(f, feq);
-                ds64 = (double)dsT;
-                cand = ds64 > p.delta;
-            } else {
-                if (COLL == LBM_MEDIAN) dsT = delta_s_t<Q, T>(f, feq);
-                if (maybe_above<Q, T>(f, feq, p.delta)) {
-                    ds64 = delta_s_fp64<Q, T>(f, p.eq);
-                    cand = ds64 > p.delta;
-                }
-            }
-            if (COLL == LBM_MEDIAN) ((T*)p.ds_field)[(int64_t)y * p.nx + x] = dsT;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) fsave[i] = f[i];
-        }
     }
-    store_site<Q, ST>(fs, R, lidc, F);
+    if (interior)
+        store_interior<Q, ST, ODD>(p, o, F);
+    else
+        store_general<Q, ST, ODD>(p, x, y, F);
 }
 
 template <int Q, class ST, int COLL, bool ODD>
 __global__ void __launch_bounds__(kBlockX* kBlockY) step_kernel(Params p) {
-    using T = typename ST::T;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const bool valid = x < p.nx && y < p.ny;
     constexpr bool kLimiter = (COLL == LBM_EHRENFEST || COLL == LBM_MEDIAN);
-    if (kLimiter && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+    if (kLimiter && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
         p.counters[p.cslot ^ 1] = 0u;  // the next step's list starts empty
-    bool cand = false;
-    double ds64 = 0.0;
-    T fsave[Q];
-    int e_code = -1, e_iters = 0;
-    if (valid) site_update<Q, ST, COLL, ODD>(p, x, y, cand, ds64, fsave, e_code, e_iters);
-    if (kLimiter) {
-        // warp-aggregated append to the candidate list
-        const unsigned m = __ballot_sync(0xffffffffu, cand);
-        if (m) {
-            const int lane = lane_id();
-            const int leader = __ffs(m) - 1;
-            unsigned base = 0;
-            if (lane == leader) base = atomicAdd(&p.counters[p.cslot], (unsigned)__popc(m));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (cand) {
-                unsigned pos = base + __popc(m & ((1u << lane) - 1u));
-                if (pos < (unsigned)p.cand_cap) {
-                    T* cf = (T*)p.cand_f;
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) cf[(int64_t)i * p.cand_cap + pos] = fsave[i];
-                    p.cand_ds[pos] = ds64;
-                    p.cand_site[pos] = y * p.nx + x;
-                } else {
-                    atomicExch(&p.counters[CNT_OVERFLOW], 1u);
-                }
-            }
-        }
+        p.counters[CNT_NVALID] = 0u;   // counted by this step's eval / median kernel
     }
+    int e_code = -1, e_iters = 0;
+    if (x < p.nx && y < p.ny) site_update<Q, ST, COLL, ODD>(p, x, y, e_code, e_iters);
     if (COLL == LBM_ELBM) {
         unsigned solved = __reduce_add_sync(0xffffffffu, e_code == 0 ? 1u : 0u);
         unsigned skipped = __reduce_add_sync(0xffffffffu, e_code == 1 ? 1u : 0u);
@@ -143,13 +138,9 @@ __global__ void __launch_bounds__(kBlockX* kBlockY) step_kernel(Params p) {
 // Writes F for a candidate site recorded by the step kernel (same parity).
 template <int Q, class ST, bool ODD>
 __device__ __forceinline__ void rewrite_site(const Params& p, int site, const typename ST::T* F) {
-    using T = typename ST::T;
-    const int x = site % p.nx, y = site / p.nx;
-    T lidc[Q];
-    int64_t R[Q];
-    aa_addresses<Q, T>(p, x, y, ODD, false, R, lidc);
-    store_site<Q, ST>((typename ST::S*)p.f, R, lidc, F);
+    store_general<Q, ST, ODD>(p, site % p.nx, site / p.nx, F);
 }
+
 
 template <int Q, class ST>
 __device__ __forceinline__ void load_candidate(const Params& p, int j, typename ST::T* f) {
@@ -157,6 +148,26 @@ __device__ __forceinline__ void load_candidate(const Params& p, int j, typename 
     const T* cf = (const T*)p.cand_f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) f[i] = cf[(int64_t)i * p.cand_cap + j];
+}
+
+// FP64 Delta S of every screened site; sites at or below delta get -1 (not
+// candidates).  Counts the candidates of the step.
+template <int Q, class ST>
+__global__ void __launch_bounds__(256) eval_kernel(Params p) {
+    using T = typename ST::T;
+    unsigned M = p.counters[p.cslot];
+    if (M > (unsigned)p.cand_cap) M = (unsigned)p.cand_cap;
+    unsigned n = 0;
+    for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+        T f[Q];
+        load_candidate<Q, ST>(p, (int)j, f);
+        const double d = delta_s_fp64<Q, T>(f, p.eq);
+        const bool c = d > p.delta;
+        p.cand_ds[j] = c ? d : -1.0;
+        n += c;
+    }
+    n = __reduce_add_sync(0xffffffffu, n);
+    if ((threadIdx.x & 31) == 0 && n) atomicAdd(&p.counters[CNT_NVALID], n);
 }
 
 // Ehrenfest regularisation (Section 4): the k candidates with the largest
@@ -173,8 +184,11 @@ __global__ void __launch_bounds__(kFixupThreads) ehrenfest_fixup(Params p) {
     unsigned M = p.counters[p.cslot];
     if (M > (unsigned)p.cand_cap) M = (unsigned)p.cand_cap;
     const unsigned K = p.topk > 0 ? (unsigned)p.topk : 0u;
+    // candidates: screened sites whose FP64 Delta S exceeds delta (eval_kernel
+    // stored -1 for the others); their keys are positive doubles
+    const unsigned nvalid = p.counters[CNT_NVALID];
     if (tid == 0) s_count = 0;
-    const bool all = M <= K;
+    const bool all = nvalid <= K;
     unsigned long long tkey = 0;
     unsigned icut = 0xffffffffu;
     if (!all && K > 0) {
@@ -190,8 +204,9 @@ __global__ void __launch_bounds__(kFixupThreads) ehrenfest_fixup(Params p) {
             __syncthreads();
             const unsigned long long pre = s_prefix, msk = s_mask;
             for (unsigned j = tid; j < M; j += blockDim.x) {
-                unsigned long long key = (unsigned long long)__double_as_longlong(p.cand_ds[j]);
-                if ((key & msk) == pre) atomicAdd(&hist[(key >> shift) & 255ull], 1u);
+                const double ds = p.cand_ds[j];
+                unsigned long long key = (unsigned long long)__double_as_longlong(ds);
+                if (ds > p.delta && (key & msk) == pre) atomicAdd(&hist[(key >> shift) & 255ull], 1u);
             }
             __syncthreads();
             if (tid == 0) {
@@ -208,6 +223,7 @@ __global__ void __launch_bounds__(kFixupThreads) ehrenfest_fixup(Params p) {
             __syncthreads();
         }
         tkey = s_prefix;
+        __syncthreads();  // every thread has read the threshold before it is reused
         // among keys equal to the threshold, take the s_rem smallest sites
         if (tid == 0) {
             s_prefix = 0;
@@ -219,9 +235,11 @@ __global__ void __launch_bounds__(kFixupThreads) ehrenfest_fixup(Params p) {
             __syncthreads();
             const unsigned pre = (unsigned)s_prefix, msk = (unsigned)s_mask;
             for (unsigned j = tid; j < M; j += blockDim.x) {
-                unsigned long long key = (unsigned long long)__double_as_longlong(p.cand_ds[j]);
+                const double ds = p.cand_ds[j];
+                unsigned long long key = (unsigned long long)__double_as_longlong(ds);
                 unsigned site = (unsigned)p.cand_site[j];
-                if (key == tkey && (site & msk) == pre) atomicAdd(&hist[(site >> shift) & 255u], 1u);
+                if (ds > p.delta && key == tkey && (site & msk) == pre)
+                    atomicAdd(&hist[(site >> shift) & 255u], 1u);
             }
             __syncthreads();
             if (tid == 0) {
@@ -243,11 +261,12 @@ __global__ void __launch_bounds__(kFixupThreads) ehrenfest_fixup(Params p) {
     unsigned mine = 0;
     for (unsigned j = tid; j < M; j += blockDim.x) {
         bool sel = false;
-        if (K > 0) {
+        const double ds = p.cand_ds[j];
+        if (K > 0 && ds > p.delta) {
             if (all) {
                 sel = true;
             } else {
-                unsigned long long key = (unsigned long long)__double_as_longlong(p.cand_ds[j]);
+                unsigned long long key = (unsigned long long)__double_as_longlong(ds);
                 unsigned site = (unsigned)p.cand_site[j];
                 sel = key > tkey || (key == tkey && site <= icut);
             }
@@ -280,8 +299,18 @@ __global__ void __launch_bounds__(256) median_fixup(Params p) {
     unsigned M = p.counters[p.cslot];
     if (M > (unsigned)p.cand_cap) M = (unsigned)p.cand_cap;
     const T* field = (const T*)p.ds_field;
-    unsigned count = 0;
+    unsigned count = 0, nvalid = 0;
     for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+        T f[Q];
+        load_candidate<Q, ST>(p, (int)j, f);
+        const double d = delta_s_fp64<Q, T>(f, p.eq);
+        const bool is_cand = d > p.delta;
+        p.cand_ds[j] = is_cand ? d : -1.0;
+        if (!is_cand) {
+            p.cand_sel[j] = 0;
+            continue;
+        }
+        ++nvalid;
         const int site = p.cand_site[j];
         const int x = site % p.nx, y = site / p.nx;
         T w[9];
@@ -307,8 +336,7 @@ __global__ void __launch_bounds__(256) median_fixup(Params p) {
         p.cand_sel[j] = sel ? 1 : 0;
         if (sel) {
             const T phi = isinf(c) ? T(0) : sqrt(med / c);
-            T f[Q], feq[Q], F[Q], rho, ux, uy;
-            load_candidate<Q, ST>(p, (int)j, f);
+            T feq[Q], F[Q], rho, ux, uy;
             moments<Q, T>(f, rho, ux, uy);
             equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
             const T om = T(2) * T(p.beta);
@@ -322,6 +350,7 @@ __global__ void __launch_bounds__(256) median_fixup(Params p) {
         }
     }
     if (count) atomicAdd(&p.stats[ST_LIMITED], (unsigned long long)count);
+    if (nvalid) atomicAdd(&p.counters[CNT_NVALID], nvalid);
 }
 
 // ---------------------------------------------------------------------------
@@ -362,10 +391,10 @@ template <int Q, class ST>
 __device__ __forceinline__ void read_state(const Params& p, int x, int y, bool odd,
                                            typename ST::T* f) {
     using T = typename ST::T;
-    T lidc[Q];
-    int64_t R[Q];
-    aa_addresses<Q, T>(p, x, y, odd, false, R, lidc);
-    load_site<Q, ST>((const typename ST::S*)p.f, R, lidc, f);
+    if (odd)
+        load_general<Q, ST, true>(p, x, y, f);
+    else
+        load_general<Q, ST, false>(p, x, y, f);
 }
 
 template <int Q, class ST, class Out>
@@ -441,6 +470,7 @@ template <class ST>
 struct Launch {
     static cudaError_t step(int Q, int coll, bool odd, const Params& p, cudaStream_t s);
     static cudaError_t fixup(int Q, int coll, bool odd, const Params& p, cudaStream_t s, int nsm);
+    static cudaError_t eval(int Q, const Params& p, cudaStream_t s, int nsm);
     static cudaError_t init(int Q, const Params& p, const double* r, const double* ux,
                             const double* uy, int eqkind, cudaStream_t s);
     static cudaError_t set_state(int Q, const Params& p, const void* src, int dtype, cudaStream_t s);
@@ -482,6 +512,12 @@ cudaError_t launch_step_c(int coll, bool odd, const Params& p, cudaStream_t s) {
 }
 
 template <int Q, class ST>
+cudaError_t launch_eval_q(const Params& p, cudaStream_t s, int nsm) {
+    eval_kernel<Q, ST><<<nsm, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int Q, class ST>
 cudaError_t launch_fixup_q(int coll, bool odd, const Params& p, cudaStream_t s, int nsm) {
     if (coll == LBM_EHRENFEST) {
         if (odd)
@@ -510,6 +546,11 @@ template <class ST>
 cudaError_t Launch<ST>::fixup(int Q, int coll, bool odd, const Params& p, cudaStream_t s, int nsm) {
     return Q == 3 ? launch_fixup_q<3, ST>(coll, odd, p, s, nsm)
                   : launch_fixup_q<9, ST>(coll, odd, p, s, nsm);
+}
+
+template <class ST>
+cudaError_t Launch<ST>::eval(int Q, const Params& p, cudaStream_t s, int nsm) {
+    return Q == 3 ? launch_eval_q<3, ST>(p, s, nsm) : launch_eval_q<9, ST>(p, s, nsm);
 }
 
 template <class ST>

@@ -12,6 +12,9 @@ namespace lbm {
 struct MrtRates {
     double e, eps, q, nu;
 };
+struct MrtRatesF {
+    float e, eps, q, nu;
+};
 
 // Device counters (one 256-byte block of scratch, zeroed at create).
 enum Counter {
@@ -20,6 +23,7 @@ enum Counter {
     CNT_DIVERGED = 2,  // set to 1 on a non-finite / non-positive density
     CNT_OVERFLOW = 3,  // candidate list overflow
     CNT_NSEL = 4,      // number of sites selected in the last Ehrenfest step
+    CNT_NVALID = 5,    // candidates (FP64 Delta S > delta) of the current step
     CNT_WORDS = 8
 };
 enum Stat {
@@ -35,14 +39,17 @@ enum Stat {
 struct Params {
     void* f;          // population storage base (pitched SoA)
     int64_t plane;    // elements per population plane (ny * pitch)
+    int plane32;      // the same as int (Q * plane < 2^31 is enforced)
     int pitch, nx, ny;
     int periodic_x, periodic_y;
     int eq;           // equilibrium kind (LBM_EQ_*)
     double lid_u;     // top wall velocity along +x
     double beta;
+    float beta_f, lid_u_f, delta_f;  // FP32 copies (no FP64 conversions per site)
     int topk;
     double delta;
     MrtRates mrt;
+    MrtRatesF mrt_f;
     double elbm_eps;
     int elbm_max_iter, elbm_norm, elbm_fallback;
     // scratch
@@ -50,7 +57,7 @@ struct Params {
     unsigned long long* stats;       // ST_WORDS words
     int cand_cap;                    // capacity of the candidate list
     void* cand_f;                    // [Q][cand_cap] arithmetic type
-    double* cand_ds;                 // [cand_cap] FP64 Delta S
+    double* cand_ds;                 // [cand_cap] FP64 Delta S (-1: not a candidate)
     int* cand_site;                  // [cand_cap] y * nx + x
     int* cand_sel;                   // [cand_cap] selected flag (Ehrenfest/median)
     void* ds_field;                  // [ny][nx] arithmetic type (median only)

@@ -259,11 +259,11 @@ class Lattice:
         self._check(lib().lbm_profile_enable(self._h, int(enable)), "lbm_profile_enable")
 
     def profile_read(self) -> dict:
-        """{kind: (launches, total_ms)} for 'step' and 'fixup' kernels."""
-        n = (C.c_int * 2)()
-        ms = (C.c_double * 2)()
+        """{kind: (launches, total_ms)} for the 'step', 'fixup' and 'eval' kernels."""
+        n = (C.c_int * 3)()
+        ms = (C.c_double * 3)()
         self._check(lib().lbm_profile_read(self._h, n, ms), "lbm_profile_read")
-        return {"step": (n[0], ms[0]), "fixup": (n[1], ms[1])}
+        return {"step": (n[0], ms[0]), "fixup": (n[1], ms[1]), "eval": (n[2], ms[2])}
 
     def last_candidates(self, cap: int | None = None, stream=None):
         """(delta_s float64, site int32, selected int32) of the last step."""
