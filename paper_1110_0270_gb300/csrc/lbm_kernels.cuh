@@ -102,6 +102,7 @@ __device__ __forceinline__ void site_update(const Params& p, int x, int y, int& 
             if (positivity<Q, T>(feq, F)) atomicAdd(&p.stats[ST_LIMITED], 1ull);
         }
     }
+    conserve_mass<Q, T>(rho, F);
     if (interior)
         store_interior<Q, ST, ODD>(p, o, F);
     else
@@ -277,6 +278,7 @@ __global__ void __launch_bounds__(kFixupThreads) ehrenfest_fixup(Params p) {
             load_candidate<Q, ST>(p, (int)j, f);
             moments<Q, T>(f, rho, ux, uy);
             equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
+            conserve_mass<Q, T>(rho, feq);
             rewrite_site<Q, ST, ODD>(p, p.cand_site[j], feq);
             ++mine;
         }
@@ -345,6 +347,7 @@ __global__ void __launch_bounds__(256) median_fixup(Params p) {
                 T fl = feq[i] + phi * (f[i] - feq[i]);
                 F[i] = fl + om * (feq[i] - fl);
             }
+            conserve_mass<Q, T>(rho, F);
             rewrite_site<Q, ST, ODD>(p, site, F);
             ++count;
         }

@@ -138,8 +138,10 @@ def test_cavity_from_rest_fp64_1000_steps_and_macros():
         Hg = float((g * np.log(g / W[:, None, None])).sum())
         assert abs(H - Hg) < 1e-13 * terms
         assert abs(H - O.total_h(cfg, f)) < 1e-13 * terms + 2 * abs(g.sum() - f.sum())
-        dS_or = O.delta_s_field(cfg, f)
-        assert np.allclose(dS.cpu().numpy(), dS_or, rtol=1e-11, atol=1e-25)
+        # Delta S near equilibrium amplifies state differences by ~1/|x|, so the
+        # field is checked on the GPU's own state
+        dS_or = O.delta_s_field(cfg, g)
+        assert np.allclose(dS.cpu().numpy(), dS_or, rtol=1e-12, atol=1e-25)
 
 
 def test_shock_tube_all_collisions_400_steps():
