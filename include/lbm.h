@@ -209,6 +209,38 @@ lbm_status lbm_profile_enable(lbm_ctx* ctx, int enable);
  * record. */
 lbm_status lbm_profile_read(lbm_ctx* ctx, int* launches, double* ms);
 
+/* ---- Stepping without any device allocation -----------------------------
+ * The paper has no counterpart to this call; it serves deployment.  Some
+ * callers cannot allocate device memory where they step: a host framework
+ * that owns a fixed device pool and hands a plugin only the population
+ * buffer, or a time-critical loop that must not call cudaMalloc because it
+ * can synchronise the device and stall other streams.  Such a caller cannot
+ * provide the scratch that lbm_create needs, and uses this call instead.
+ *
+ * Runs nsteps (even, >= 0) LBGK steps with the Ehrenfest limiter
+ * (cfg->collision must be LBM_EHRENFEST; the other fields as for
+ * lbm_create) on the caller's DENSE population array f[Q][ny][nx] (no row
+ * padding; natural pre-collision layout on entry and on return; elements in
+ * the configured storage format: double, float, or f_i - W_i in bf16/fp16),
+ * enqueued on `stream`.  It calls no allocating routine.  Its scratch (step
+ * counters and the limiter candidate list) is one file-scope device array of
+ * LBM_NOALLOC_SCRATCH_BYTES, which every GPU that loads this library holds
+ * until the process exits.  A lattice whose scratch would not fit,
+ * 256 + N (Q b + 16) bytes plus alignment with N = nx * ny and b = 8 in FP64,
+ * 4 otherwise (about 645,000 D2Q9 sites in FP32, 381,000 in FP64), is
+ * rejected with LBM_ERR_OOM before any GPU work.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the array, which keeps the
+ * last call's contents (the counters are cleared at the start of each call):
+ * calls that overlap on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller.  Returns LBM_ERR_ARG for an invalid
+ * configuration, an odd nsteps or another collision, LBM_ERR_CUDA when a
+ * CUDA call fails. */
+#define LBM_NOALLOC_SCRATCH_BYTES (32u << 20)
+lbm_status lbm_ehrenfest_step_noalloc(const lbm_config* cfg, void* f, int nsteps, void* stream);
+
 /* Message of the last failure on ctx ("" if none).  Valid until the next call. */
 const char* lbm_last_error(const lbm_ctx* ctx);
 const char* lbm_status_string(lbm_status s);

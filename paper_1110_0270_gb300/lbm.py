@@ -31,7 +31,8 @@ STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_CUDA", 3: "LBM_ERR_OOM",
 EXPORTS = ["lbm_config_default", "lbm_required_bytes", "lbm_create", "lbm_destroy", "lbm_init",
            "lbm_init_device", "lbm_set_state", "lbm_get_state", "lbm_step", "lbm_macros",
            "lbm_entropy", "lbm_stats_get", "lbm_last_candidates", "lbm_last_error",
-           "lbm_status_string", "lbm_abi_version", "lbm_profile_enable", "lbm_profile_read"]
+           "lbm_status_string", "lbm_abi_version", "lbm_profile_enable", "lbm_profile_read",
+           "lbm_ehrenfest_step_noalloc"]
 
 
 class lbm_config(C.Structure):
@@ -81,6 +82,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "lbm_abi_version": (i, []),
         "lbm_profile_enable": (i, [p, i]),
         "lbm_profile_read": (i, [p, C.POINTER(i), C.POINTER(C.c_double)]),
+        "lbm_ehrenfest_step_noalloc": (i, [C.POINTER(lbm_config), p, i, p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
