@@ -193,18 +193,49 @@ lbm_status lbm_stats_get(lbm_ctx* ctx, lbm_stats* out, void* stream);
 lbm_status lbm_last_candidates(lbm_ctx* ctx, double* ds, int32_t* site, int32_t* selected,
                                int cap, int* count, void* stream);
 
+/* ---- Batched form: many independent D2Q9 lattices in one context --------
+ * All instances share the lattice (D2Q9) and the precision of cfgs[0]; size,
+ * boundary, collision, beta, lid, limiter and MRT/ELBM parameters are per
+ * instance.  One launch per collision kind covers every instance of that
+ * kind (a CTA per 128 x 2 tile); two steps are captured once, at creation,
+ * into a CUDA graph whose collision groups are independent branches, and
+ * lbm_batch_step replays it.  Memory: one caller device allocation of
+ * lbm_batch_required_bytes (populations, limiter scratch, descriptors and
+ * work lists); nothing is allocated afterwards. */
+typedef struct lbm_batch lbm_batch; /* opaque, owned by the library */
+lbm_status lbm_batch_required_bytes(const lbm_config* cfgs, int n, size_t* bytes);
+/* Creates the batch over dev_mem (256-byte aligned) on the current device;
+ * copies the descriptors and builds the graph (synchronous). */
+lbm_status lbm_batch_create(const lbm_config* cfgs, int n, void* dev_mem, size_t bytes,
+                            lbm_batch** out);
+void lbm_batch_destroy(lbm_batch* b);
+/* Every instance to the equilibrium of a uniform (rho, u) (entropic for ELBM
+ * instances, the configured one otherwise); resets the step counter. */
+lbm_status lbm_batch_init_uniform(lbm_batch* b, double rho, double ux, double uy, void* stream);
+/* Per-instance state transfer, dense DEVICE f[9][ny][nx] as in
+ * lbm_set_state / lbm_get_state.  set_state needs an even step count. */
+lbm_status lbm_batch_set_state(lbm_batch* b, int instance, const void* f, int dtype, void* stream);
+lbm_status lbm_batch_get_state(lbm_batch* b, int instance, void* f, int dtype, void* stream);
+/* Advances every instance nsteps steps.  If status is not NULL it receives,
+ * per instance, LBM_OK or LBM_ERR_DIVERGED (a non-finite or non-positive
+ * density seen since creation or the last init), which synchronises `stream`. */
+lbm_status lbm_batch_step(lbm_batch* b, int nsteps, int* status, void* stream);
+lbm_status lbm_batch_stats(lbm_batch* b, int instance, lbm_stats* out, void* stream);
+const char* lbm_batch_last_error(const lbm_batch* b);
+
 /* Kernel tracing.  While enabled, every kernel lbm_step launches is
  * bracketed by two CUDA events recorded on the caller's stream (timing
  * events; the first LBM_PROFILE_MAX launches after enabling are kept).
  * Enabling clears the record.  Costs two event records per launch. */
 #define LBM_PROFILE_MAX 65536
-enum { LBM_KERNEL_STEP = 0, LBM_KERNEL_FIXUP = 1, LBM_KERNEL_EVAL = 2, LBM_KERNEL_KINDS = 3 };
+enum { LBM_KERNEL_STEP = 0, LBM_KERNEL_FIXUP = 1, LBM_KERNEL_KINDS = 2 };
 lbm_status lbm_profile_enable(lbm_ctx* ctx, int enable);
 
 /* Waits for the recorded events and returns, per kernel kind (index
  * LBM_KERNEL_STEP: the fused stream-collide kernel; LBM_KERNEL_FIXUP: the
- * Ehrenfest selection or median filter fix-up; LBM_KERNEL_EVAL: the FP64
- * Delta S of the screened sites), the number of launches and their summed device
+ * limiter kernel that follows it - FP64 Delta S of the screened sites, then
+ * the Ehrenfest selection or the median filter), the number of launches and
+ * their summed device
  * time in milliseconds (arrays of LBM_KERNEL_KINDS entries), then clears the
  * record. */
 lbm_status lbm_profile_read(lbm_ctx* ctx, int* launches, double* ms);

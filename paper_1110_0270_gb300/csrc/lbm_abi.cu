@@ -359,12 +359,6 @@ lbm_status lbm_step(lbm_ctx* ctx, int nsteps, void* stream) {
                        return decltype(L)::step(ctx->Q, coll, odd, q, S(stream));
                    });
                }));
-        if (coll == LBM_EHRENFEST)
-            LBM_CK(ctx, traced(ctx, LBM_KERNEL_EVAL, S(stream), [&] {
-                       return dispatch(ctx->cfg.precision, [&](auto L) {
-                           return decltype(L)::eval(ctx->Q, q, S(stream), ctx->nsm);
-                       });
-                   }));
         if (limiter(coll))
             LBM_CK(ctx, traced(ctx, LBM_KERNEL_FIXUP, S(stream), [&] {
                        return dispatch(ctx->cfg.precision, [&](auto L) {

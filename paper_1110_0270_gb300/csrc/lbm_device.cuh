@@ -175,20 +175,30 @@ __device__ __forceinline__ double gseries_d(double x) {
     return x * x * p;
 }
 
+// The series length follows |x|: the first omitted term, relative to the
+// leading x^2/2, is below 2^-56 (FP64) or 2^-26 (FP32) in every tier.
 __device__ __forceinline__ double gfun_d(double x) {
     if (x <= -1.0) return 1.0;  // g(-1) = 1; below -1 only for negative populations
-    if (fabs(x) < 0.25) return gseries_d<24>(x);
+    const double ax = fabs(x);
+    if (ax < 0.015625) return gseries_d<8>(x);
+    if (ax < 0.125) return gseries_d<16>(x);
+    if (ax < 0.25) return gseries_d<26>(x);
     return (1.0 + x) * log1p(x) - x;
+}
+
+template <int K>
+__device__ __forceinline__ float gseries_f(float x) {
+    float p = ((K & 1) ? -1.0f : 1.0f) / (float)((K + 1) * (K + 2));
+#pragma unroll
+    for (int k = K - 1; k >= 0; --k) p = fmaf(p, x, ((k & 1) ? -1.0f : 1.0f) / (float)((k + 1) * (k + 2)));
+    return x * x * p;
 }
 
 __device__ __forceinline__ float gfun_f(float x) {
     if (x <= -1.0f) return 1.0f;
-    if (fabsf(x) < 0.25f) {
-        float p = 1.0f / 132.0f;  // k = 10
-#pragma unroll
-        for (int k = 9; k >= 0; --k) p = fmaf(p, x, ((k & 1) ? -1.0f : 1.0f) / (float)((k + 1) * (k + 2)));
-        return x * x * p;
-    }
+    const float ax = fabsf(x);
+    if (ax < 0.03125f) return gseries_f<4>(x);
+    if (ax < 0.25f) return gseries_f<11>(x);
     return (1.0f + x) * log1pf(x) - x;
 }
 
@@ -217,7 +227,12 @@ __device__ double delta_s_fp64(const T* f, int eqkind) {
     return neg ? __longlong_as_double(0x7ff0000000000000ULL) : s;
 }
 
-// Delta S in the arithmetic type T from f and its equilibrium.
+// Delta S in the arithmetic type T from f and its equilibrium (FP32: the
+// relative deviation by the approximate division, good to 2 ulp, which the
+// FP32 field tolerates).
+__device__ __forceinline__ double rel_dev(double d, double q) { return d / q; }
+__device__ __forceinline__ float rel_dev(float d, float q) { return __fdividef(d, q); }
+
 template <int Q, class T>
 __device__ __forceinline__ T delta_s_t(const T* f, const T* feq) {
     T s = T(0);
@@ -225,7 +240,7 @@ __device__ __forceinline__ T delta_s_t(const T* f, const T* feq) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         neg |= (f[i] < T(0)) || !(feq[i] > T(0));
-        s += feq[i] * gfun<T>((f[i] - feq[i]) / feq[i]);
+        s += feq[i] * gfun<T>(rel_dev(f[i] - feq[i], feq[i]));
     }
     return neg ? T(INFINITY) : s;
 }
@@ -237,6 +252,26 @@ __device__ __forceinline__ T delta_s_t(const T* f, const T* feq) {
 // q by at most ~3e-7 sqrt(q rho) + 2e-6 q (|d| summed by Cauchy-Schwarz),
 // covered by the relative 1e-3 and absolute 1e-6 sqrt(q rho) slack.
 // Returns true when the site may exceed delta and needs the FP64 value.
+// Cheaper and looser form for the Ehrenfest screen: with m = min_i f*_i,
+// q <= sum d^2 / m and a <= max |d| / m, so for a < 1/2 Delta S <= sum d^2 / m.
+// One reciprocal per site; the looseness (up to ~30x near equilibrium) only
+// lets more sites through to the exact FP64 test.
+template <int Q>
+__device__ __forceinline__ bool maybe_above_loose(const float* f, const float* feq, float delta) {
+    float s2 = 0.f, dmax = 0.f, m = feq[0], rho = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float d = f[i] - feq[i];
+        s2 = fmaf(d, d, s2);
+        dmax = fmaxf(dmax, fabsf(d));
+        m = fminf(m, feq[i]);
+        rho += f[i];
+    }
+    if (!(dmax < 0.5f * m)) return true;  // also NaN and non-positive f*
+    const float q = s2 * __frcp_rn(m);
+    return q * 1.001f + 1e-6f * sqrtf(q * fabsf(rho)) >= delta;
+}
+
 template <int Q>
 __device__ __forceinline__ bool maybe_above(const float* f, const float* feq, float delta) {
     float q = 0.f, a = 0.f, rho = 0.f;
@@ -348,22 +383,68 @@ __device__ __forceinline__ void mrt_d2q9(const T* f, const T* feq, const MrtRate
 // S(y) = S(f*) - DeltaS(y): with d_i = Delta_i / f*_i and x_i = (alpha-1) d_i,
 //   S_f = sum f*_i [g(-d_i) - g(x_i)],  S_f' = -sum Delta_i ln(1 + x_i),
 //   S_f'' = -sum Delta_i^2 / (f_i + alpha Delta_i).
-template <int Q>
-__device__ __forceinline__ void elbm_eval(const double* f, const double* feq, const double* D,
-                                          const double* gm, double a, double& s0, double& s1,
-                                          double& s2) {
-    double A = 0.0, B = 0.0, C = 0.0;
+// g(x) and ln(1+x) from two Taylor series of the same length (one tier per
+// evaluation, chosen from max |x| so that the lanes of a site stay together):
+// ln(1+x) = x sum_k (-1)^k x^k / (k+1); the first omitted terms are below
+// 2^-54 of the leading ones in every tier.
+template <int KG, int KL>
+__device__ __forceinline__ void gl_series(double x, double& g, double& l) {
+    double pg = ((KG & 1) ? -1.0 : 1.0) / (double)((KG + 1) * (KG + 2));
+#pragma unroll
+    for (int k = KG - 1; k >= 0; --k) pg = fma(pg, x, ((k & 1) ? -1.0 : 1.0) / (double)((k + 1) * (k + 2)));
+    double pl = ((KL & 1) ? -1.0 : 1.0) / (double)(KL + 1);
+#pragma unroll
+    for (int k = KL - 1; k >= 0; --k) pl = fma(pl, x, ((k & 1) ? -1.0 : 1.0) / (double)(k + 1));
+    g = x * x * pg;
+    l = x * pl;
+}
+
+template <int Q, int KG, int KL>
+__device__ __forceinline__ void elbm_sum(const double* feq, const double* D, const double* gm,
+                                         const float* Df, const float* gf, double a, double& s0,
+                                         double& s1, float& s2) {
+    double A = 0.0, B = 0.0;
+    float C = 0.f;
+    const float af = (float)a;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        double x = (a - 1.0) * (D[i] / feq[i]);
-        x = x < -1.0 ? -1.0 : x;
-        A += feq[i] * (gm[i] - gfun_d(x));
-        B -= D[i] * log1p(x);
-        C -= D[i] * D[i] / (f[i] + a * D[i]);
+        const double x = (a - 1.0) * (D[i] / feq[i]);
+        double g, l;
+        if (KG > 0) {
+            gl_series<KG, KL>(x, g, l);
+        } else {
+            const double xc = x < -1.0 ? -1.0 : x;
+            l = log1p(xc);
+            g = xc <= -1.0 ? 1.0 : (1.0 + xc) * l - xc;
+        }
+        A += feq[i] * (gm[i] - g);
+        B -= D[i] * l;
+        // S_f'' only shapes the parabola (S_f and S_f' decide the root and the
+        // stopping test), so FP32 is enough for it
+        C -= Df[i] * Df[i] / fmaxf(gf[i] + af * Df[i], 1e-37f);
     }
     s0 = A;
     s1 = B;
     s2 = C;
+}
+
+// S_f(alpha), S_f'(alpha) (FP64) and S_f''(alpha) (FP32) at one site.
+template <int Q>
+__device__ __forceinline__ void elbm_eval(const double* f, const double* feq, const double* D,
+                                          const double* gm, const float* Df, const float* gf,
+                                          double amax_d, double a, double& s0, double& s1,
+                                          double& s2) {
+    const double ax = fabs(a - 1.0) * amax_d;  // max |x_i| at this alpha
+    float c;
+    if (ax < 0.015625)
+        elbm_sum<Q, 8, 9>(feq, D, gm, Df, gf, a, s0, s1, c);
+    else if (ax < 0.125)
+        elbm_sum<Q, 16, 18>(feq, D, gm, Df, gf, a, s0, s1, c);
+    else if (ax < 0.25)
+        elbm_sum<Q, 26, 27>(feq, D, gm, Df, gf, a, s0, s1, c);
+    else
+        elbm_sum<Q, 0, 0>(feq, D, gm, Df, gf, a, s0, s1, c);
+    s2 = (double)c;
 }
 
 struct ElbmOut {
@@ -385,15 +466,20 @@ __device__ ElbmOut elbm_alpha(const double* f, const double* feq, const Params& 
     ElbmOut o;
     o.iters = 0;
     double D[Q], gm[Q];
-    double dS = 0.0, amax = __longlong_as_double(0x7ff0000000000000ULL);
+    float Df[Q], gf[Q];
+    double dS = 0.0, amax = __longlong_as_double(0x7ff0000000000000ULL), dmax = 0.0;
     bool neg = false;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         D[i] = feq[i] - f[i];
-        gm[i] = gfun_d(-D[i] / feq[i]);
+        const double d = D[i] / feq[i];
+        dmax = fmax(dmax, fabs(d));
+        gm[i] = gfun_d(-d);
         dS += feq[i] * gm[i];
         neg |= f[i] < 0.0;
         if (D[i] < 0.0) amax = fmin(amax, -f[i] / D[i]);
+        Df[i] = (float)D[i];
+        gf[i] = (float)f[i];
     }
     if (!neg && dS < 1e-15) {
         o.alpha = 2.0;
@@ -413,14 +499,20 @@ __device__ ElbmOut elbm_alpha(const double* f, const double* feq, const Params& 
     double lo = 1.0, hi = amax;
     double a = (2.0 < amax) ? 2.0 : 0.5 * (1.0 + amax);
     double s0, s1, s2;
-    elbm_eval<Q>(f, feq, D, gm, a, s0, s1, s2);
+    elbm_eval<Q>(f, feq, D, gm, Df, gf, dmax, a, s0, s1, s2);
     if (s0 > 0.0) {
-        double m0, m1, m2;
-        elbm_eval<Q>(f, feq, D, gm, amax, m0, m1, m2);
-        if (m0 > 0.0) {
-            o.alpha = fb;
-            o.code = 2;
-            return o;
+        // S_f is concave in alpha, so it lies below its tangent at a: if the
+        // tangent reaches zero before alpha_max, so does S_f (a root exists
+        // in (a, alpha_max)); only otherwise is S_f(alpha_max) evaluated.
+        const double at = a - s0 / s1;
+        if (!(s1 < 0.0 && at < amax)) {
+            double m0, m1, m2;
+            elbm_eval<Q>(f, feq, D, gm, Df, gf, dmax, amax, m0, m1, m2);
+            if (m0 > 0.0) {
+                o.alpha = fb;
+                o.code = 2;
+                return o;
+            }
         }
         lo = a;
     } else {
@@ -441,7 +533,7 @@ __device__ ElbmOut elbm_alpha(const double* f, const double* feq, const Params& 
         }
         if (!(next > lo && next < hi)) next = 0.5 * (lo + hi);
         a = next;
-        elbm_eval<Q>(f, feq, D, gm, a, s0, s1, s2);
+        elbm_eval<Q>(f, feq, D, gm, Df, gf, dmax, a, s0, s1, s2);
         if (s0 > 0.0)
             lo = a;
         else

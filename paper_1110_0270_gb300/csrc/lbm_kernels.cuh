@@ -7,9 +7,10 @@
 //                   ELBM, positivity and MRT are complete here, the Ehrenfest
 //                   and median limiters additionally append their candidate
 //                   sites (Delta S > delta) to a compact list.
-//  ehrenfest_fixup  one CTA: k-largest selection over the candidate list by
-//                   MSB radix select on the FP64 Delta S bits, ties by site
-//                   index; selected sites are rewritten with f*.
+//  ehrenfest_eval_select  FP64 Delta S of the screened sites, then (last CTA)
+//                   k-largest selection by MSB radix select on the FP64
+//                   Delta S bits, ties by site index; selected sites are
+//                   rewritten with f*.
 //  median_fixup     grid-stride over candidates: median of the Delta S window,
 //                   homothety of Eq. (entrHom) where it lowers Delta S.
 #pragma once
@@ -20,7 +21,6 @@ namespace lbm {
 
 constexpr int kBlockX = 128;
 constexpr int kBlockY = 2;
-constexpr int kFixupThreads = 1024;
 
 __device__ __forceinline__ int lane_id() {
     return (threadIdx.y * blockDim.x + threadIdx.x) & 31;
@@ -57,7 +57,9 @@ __device__ __forceinline__ void limiter_screen(const Params& p, int x, int y, co
         ff[i] = (float)f[i];
         fq[i] = (float)feq[i];
     }
-    if (maybe_above<Q>(ff, fq, p.delta_f)) record_candidate<Q, T>(p, x, y, f);
+    const bool maybe = COLL == LBM_MEDIAN ? maybe_above<Q>(ff, fq, p.delta_f)
+                                          : maybe_above_loose<Q>(ff, fq, p.delta_f);
+    if (maybe) record_candidate<Q, T>(p, x, y, f);
 }
 
 // The whole step for the site (x, y): load (streaming in odd steps), moments,
@@ -109,6 +111,22 @@ __device__ __forceinline__ void site_update(const Params& p, int x, int y, int& 
         store_general<Q, ST, ODD>(p, x, y, F);
 }
 
+// Warp-aggregated ELBM counters (all 32 lanes of the warp call this).
+__device__ __forceinline__ void elbm_stats(const Params& p, int e_code, int e_iters) {
+    unsigned solved = __reduce_add_sync(0xffffffffu, e_code == 0 ? 1u : 0u);
+    unsigned skipped = __reduce_add_sync(0xffffffffu, e_code == 1 ? 1u : 0u);
+    unsigned fallback = __reduce_add_sync(0xffffffffu, e_code == 2 ? 1u : 0u);
+    unsigned iters = __reduce_add_sync(0xffffffffu, (unsigned)e_iters);
+    unsigned itmax = __reduce_max_sync(0xffffffffu, (unsigned)e_iters);
+    if (lane_id() == 0) {
+        if (solved) atomicAdd(&p.stats[ST_ELBM_SOLVED], (unsigned long long)solved);
+        if (skipped) atomicAdd(&p.stats[ST_ELBM_SKIPPED], (unsigned long long)skipped);
+        if (fallback) atomicAdd(&p.stats[ST_ELBM_FALLBACK], (unsigned long long)fallback);
+        if (iters) atomicAdd(&p.stats[ST_ELBM_ITERS], (unsigned long long)iters);
+        if (itmax) atomicMax(&p.stats[ST_ELBM_ITERS_MAX], (unsigned long long)itmax);
+    }
+}
+
 template <int Q, class ST, int COLL, bool ODD>
 __global__ void __launch_bounds__(kBlockX* kBlockY) step_kernel(Params p) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -120,20 +138,7 @@ __global__ void __launch_bounds__(kBlockX* kBlockY) step_kernel(Params p) {
     }
     int e_code = -1, e_iters = 0;
     if (x < p.nx && y < p.ny) site_update<Q, ST, COLL, ODD>(p, x, y, e_code, e_iters);
-    if (COLL == LBM_ELBM) {
-        unsigned solved = __reduce_add_sync(0xffffffffu, e_code == 0 ? 1u : 0u);
-        unsigned skipped = __reduce_add_sync(0xffffffffu, e_code == 1 ? 1u : 0u);
-        unsigned fallback = __reduce_add_sync(0xffffffffu, e_code == 2 ? 1u : 0u);
-        unsigned iters = __reduce_add_sync(0xffffffffu, (unsigned)e_iters);
-        unsigned itmax = __reduce_max_sync(0xffffffffu, (unsigned)e_iters);
-        if (lane_id() == 0) {
-            if (solved) atomicAdd(&p.stats[ST_ELBM_SOLVED], (unsigned long long)solved);
-            if (skipped) atomicAdd(&p.stats[ST_ELBM_SKIPPED], (unsigned long long)skipped);
-            if (fallback) atomicAdd(&p.stats[ST_ELBM_FALLBACK], (unsigned long long)fallback);
-            if (iters) atomicAdd(&p.stats[ST_ELBM_ITERS], (unsigned long long)iters);
-            if (itmax) atomicMax(&p.stats[ST_ELBM_ITERS_MAX], (unsigned long long)itmax);
-        }
-    }
+    if (COLL == LBM_ELBM) elbm_stats(p, e_code, e_iters);
 }
 
 // Writes F for a candidate site recorded by the step kernel (same parity).
@@ -151,43 +156,22 @@ __device__ __forceinline__ void load_candidate(const Params& p, int j, typename 
     for (int i = 0; i < Q; ++i) f[i] = cf[(int64_t)i * p.cand_cap + j];
 }
 
-// FP64 Delta S of every screened site; sites at or below delta get -1 (not
-// candidates).  Counts the candidates of the step.
-template <int Q, class ST>
-__global__ void __launch_bounds__(256) eval_kernel(Params p) {
-    using T = typename ST::T;
-    unsigned M = p.counters[p.cslot];
-    if (M > (unsigned)p.cand_cap) M = (unsigned)p.cand_cap;
-    unsigned n = 0;
-    for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
-        T f[Q];
-        load_candidate<Q, ST>(p, (int)j, f);
-        const double d = delta_s_fp64<Q, T>(f, p.eq);
-        const bool c = d > p.delta;
-        p.cand_ds[j] = c ? d : -1.0;
-        n += c;
-    }
-    n = __reduce_add_sync(0xffffffffu, n);
-    if ((threadIdx.x & 31) == 0 && n) atomicAdd(&p.counters[CNT_NVALID], n);
-}
-
 // Ehrenfest regularisation (Section 4): the k candidates with the largest
 // Delta S (ties: lower site index) jump to f*.  One CTA; Delta S > delta >= 0
 // so the IEEE bit patterns order like the values (+inf last).
+// Runs in one CTA of any size after every cand_ds entry of the step is final
+// (the entries of other CTAs are read through L2).
 template <int Q, class ST, bool ODD>
-__global__ void __launch_bounds__(kFixupThreads) ehrenfest_fixup(Params p) {
+__device__ void ehrenfest_select_apply(const Params& p, unsigned M, unsigned nvalid) {
     using T = typename ST::T;
     __shared__ unsigned hist[256];
     __shared__ unsigned long long s_prefix, s_mask;
     __shared__ unsigned s_rem;
     __shared__ unsigned s_count;
     const int tid = threadIdx.x;
-    unsigned M = p.counters[p.cslot];
-    if (M > (unsigned)p.cand_cap) M = (unsigned)p.cand_cap;
     const unsigned K = p.topk > 0 ? (unsigned)p.topk : 0u;
-    // candidates: screened sites whose FP64 Delta S exceeds delta (eval_kernel
-    // stored -1 for the others); their keys are positive doubles
-    const unsigned nvalid = p.counters[CNT_NVALID];
+    // candidates: screened sites whose FP64 Delta S exceeds delta (the others
+    // carry -1); their keys are positive doubles
     if (tid == 0) s_count = 0;
     const bool all = nvalid <= K;
     unsigned long long tkey = 0;
@@ -205,7 +189,7 @@ __global__ void __launch_bounds__(kFixupThreads) ehrenfest_fixup(Params p) {
             __syncthreads();
             const unsigned long long pre = s_prefix, msk = s_mask;
             for (unsigned j = tid; j < M; j += blockDim.x) {
-                const double ds = p.cand_ds[j];
+                const double ds = __ldcg(&p.cand_ds[j]);
                 unsigned long long key = (unsigned long long)__double_as_longlong(ds);
                 if (ds > p.delta && (key & msk) == pre) atomicAdd(&hist[(key >> shift) & 255ull], 1u);
             }
@@ -236,7 +220,7 @@ __global__ void __launch_bounds__(kFixupThreads) ehrenfest_fixup(Params p) {
             __syncthreads();
             const unsigned pre = (unsigned)s_prefix, msk = (unsigned)s_mask;
             for (unsigned j = tid; j < M; j += blockDim.x) {
-                const double ds = p.cand_ds[j];
+                const double ds = __ldcg(&p.cand_ds[j]);
                 unsigned long long key = (unsigned long long)__double_as_longlong(ds);
                 unsigned site = (unsigned)p.cand_site[j];
                 if (ds > p.delta && key == tkey && (site & msk) == pre)
@@ -262,7 +246,7 @@ __global__ void __launch_bounds__(kFixupThreads) ehrenfest_fixup(Params p) {
     unsigned mine = 0;
     for (unsigned j = tid; j < M; j += blockDim.x) {
         bool sel = false;
-        const double ds = p.cand_ds[j];
+        const double ds = __ldcg(&p.cand_ds[j]);
         if (K > 0 && ds > p.delta) {
             if (all) {
                 sel = true;
@@ -291,18 +275,50 @@ __global__ void __launch_bounds__(kFixupThreads) ehrenfest_fixup(Params p) {
     }
 }
 
+// Ehrenfest step, second kernel: the FP64 Delta S of every screened site
+// (grid-stride), then the last CTA to finish - found by a ticket counter after
+// a memory fence, no waiting - selects the k largest and rewrites them.
+template <int Q, class ST, bool ODD>
+__global__ void __launch_bounds__(256) ehrenfest_eval_select(Params p) {
+    using T = typename ST::T;
+    __shared__ unsigned s_last;
+    unsigned M = p.counters[p.cslot];
+    if (M > (unsigned)p.cand_cap) M = (unsigned)p.cand_cap;
+    unsigned n = 0;
+    for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+        T f[Q];
+        load_candidate<Q, ST>(p, (int)j, f);
+        const double d = delta_s_fp64<Q, T>(f, p.eq);
+        const bool c = d > p.delta;
+        p.cand_ds[j] = c ? d : -1.0;
+        n += c;
+    }
+    n = __reduce_add_sync(0xffffffffu, n);
+    if ((threadIdx.x & 31) == 0 && n) atomicAdd(&p.counters[CNT_NVALID], n);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&p.counters[CNT_DONE], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const unsigned nvalid = atomicAdd(&p.counters[CNT_NVALID], 0u);
+    ehrenfest_select_apply<Q, ST, ODD>(p, M, nvalid);
+    if (threadIdx.x == 0) p.counters[CNT_DONE] = 0u;
+}
+
 // Median entropy filter (Section 4.4): lower median of Delta S over the site
 // and its neighbours (clipped at walls, wrapped where periodic); where the
 // median is below the site's Delta S the homothety with coefficient
 // sqrt(med / DeltaS) (Eq. entrHom) precedes the LBGK collision.
+// Candidates j0, j0 + stride, ... of the step's list (any launch shape).
 template <int Q, class ST, bool ODD>
-__global__ void __launch_bounds__(256) median_fixup(Params p) {
+__device__ void median_apply(const Params& p, unsigned j0, unsigned stride) {
     using T = typename ST::T;
     unsigned M = p.counters[p.cslot];
     if (M > (unsigned)p.cand_cap) M = (unsigned)p.cand_cap;
     const T* field = (const T*)p.ds_field;
     unsigned count = 0, nvalid = 0;
-    for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+    for (unsigned j = j0; j < M; j += stride) {
         T f[Q];
         load_candidate<Q, ST>(p, (int)j, f);
         const double d = delta_s_fp64<Q, T>(f, p.eq);
@@ -356,6 +372,11 @@ __global__ void __launch_bounds__(256) median_fixup(Params p) {
     if (nvalid) atomicAdd(&p.counters[CNT_NVALID], nvalid);
 }
 
+template <int Q, class ST, bool ODD>
+__global__ void __launch_bounds__(256) median_fixup(Params p) {
+    median_apply<Q, ST, ODD>(p, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
 // ---------------------------------------------------------------------------
 // State transfer, macroscopic fields and entropy.
 // ---------------------------------------------------------------------------
@@ -370,6 +391,22 @@ __global__ void init_kernel(Params p, const double* rho, const double* ux, const
     const int64_t s = (int64_t)y * p.nx + x;
     double feq[Q];
     equilibrium<Q, double>(eqkind, rho[s], ux[s], uy ? uy[s] : 0.0, feq);
+    typename ST::S* f = (typename ST::S*)p.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        ST::st(f + (int64_t)i * p.plane + (int64_t)y * p.pitch + x, (T)feq[i], T(L::w(i)));
+}
+
+// f = f*(rho, u) with the same rho, u at every site.
+template <int Q, class ST>
+__global__ void init_uniform_kernel(Params p, double rho, double ux, double uy, int eqkind) {
+    using T = typename ST::T;
+    using L = Lat<Q>;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    double feq[Q];
+    equilibrium<Q, double>(eqkind, rho, ux, uy, feq);
     typename ST::S* f = (typename ST::S*)p.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i)
@@ -473,9 +510,10 @@ template <class ST>
 struct Launch {
     static cudaError_t step(int Q, int coll, bool odd, const Params& p, cudaStream_t s);
     static cudaError_t fixup(int Q, int coll, bool odd, const Params& p, cudaStream_t s, int nsm);
-    static cudaError_t eval(int Q, const Params& p, cudaStream_t s, int nsm);
     static cudaError_t init(int Q, const Params& p, const double* r, const double* ux,
                             const double* uy, int eqkind, cudaStream_t s);
+    static cudaError_t init_uniform(int Q, const Params& p, double r, double ux, double uy,
+                                    int eqkind, cudaStream_t s);
     static cudaError_t set_state(int Q, const Params& p, const void* src, int dtype, cudaStream_t s);
     static cudaError_t get_state(int Q, const Params& p, void* dst, int dtype, bool odd,
                                  cudaStream_t s);
@@ -515,18 +553,12 @@ cudaError_t launch_step_c(int coll, bool odd, const Params& p, cudaStream_t s) {
 }
 
 template <int Q, class ST>
-cudaError_t launch_eval_q(const Params& p, cudaStream_t s, int nsm) {
-    eval_kernel<Q, ST><<<nsm, 256, 0, s>>>(p);
-    return cudaGetLastError();
-}
-
-template <int Q, class ST>
 cudaError_t launch_fixup_q(int coll, bool odd, const Params& p, cudaStream_t s, int nsm) {
     if (coll == LBM_EHRENFEST) {
         if (odd)
-            ehrenfest_fixup<Q, ST, true><<<1, kFixupThreads, 0, s>>>(p);
+            ehrenfest_eval_select<Q, ST, true><<<nsm, 256, 0, s>>>(p);
         else
-            ehrenfest_fixup<Q, ST, false><<<1, kFixupThreads, 0, s>>>(p);
+            ehrenfest_eval_select<Q, ST, false><<<nsm, 256, 0, s>>>(p);
     } else if (coll == LBM_MEDIAN) {
         // candidate count is only known on the device: a fixed grid of one
         // CTA per SM strides over the list
@@ -552,11 +584,6 @@ cudaError_t Launch<ST>::fixup(int Q, int coll, bool odd, const Params& p, cudaSt
 }
 
 template <class ST>
-cudaError_t Launch<ST>::eval(int Q, const Params& p, cudaStream_t s, int nsm) {
-    return Q == 3 ? launch_eval_q<3, ST>(p, s, nsm) : launch_eval_q<9, ST>(p, s, nsm);
-}
-
-template <class ST>
 cudaError_t Launch<ST>::init(int Q, const Params& p, const double* r, const double* ux,
                              const double* uy, int eqkind, cudaStream_t s) {
     dim3 b = site_block(Q), g = site_grid(p, b);
@@ -564,6 +591,17 @@ cudaError_t Launch<ST>::init(int Q, const Params& p, const double* r, const doub
         init_kernel<3, ST><<<g, b, 0, s>>>(p, r, ux, uy, eqkind);
     else
         init_kernel<9, ST><<<g, b, 0, s>>>(p, r, ux, uy, eqkind);
+    return cudaGetLastError();
+}
+
+template <class ST>
+cudaError_t Launch<ST>::init_uniform(int Q, const Params& p, double r, double ux, double uy,
+                                     int eqkind, cudaStream_t s) {
+    dim3 b = site_block(Q), g = site_grid(p, b);
+    if (Q == 3)
+        init_uniform_kernel<3, ST><<<g, b, 0, s>>>(p, r, ux, uy, eqkind);
+    else
+        init_uniform_kernel<9, ST><<<g, b, 0, s>>>(p, r, ux, uy, eqkind);
     return cudaGetLastError();
 }
 

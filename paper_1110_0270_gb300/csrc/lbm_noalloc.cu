@@ -132,22 +132,18 @@ extern "C" lbm_status lbm_ehrenfest_step_noalloc(const lbm_config* cfg, void* f,
         switch (cfg->precision) {
             case LBM_FP64:
                 e = Launch<StF64>::step(Q, LBM_EHRENFEST, odd, q, st);
-                if (e == cudaSuccess) e = Launch<StF64>::eval(Q, q, st, nsm);
                 if (e == cudaSuccess) e = Launch<StF64>::fixup(Q, LBM_EHRENFEST, odd, q, st, nsm);
                 break;
             case LBM_FP32:
                 e = Launch<StF32>::step(Q, LBM_EHRENFEST, odd, q, st);
-                if (e == cudaSuccess) e = Launch<StF32>::eval(Q, q, st, nsm);
                 if (e == cudaSuccess) e = Launch<StF32>::fixup(Q, LBM_EHRENFEST, odd, q, st, nsm);
                 break;
             case LBM_BF16_DEV:
                 e = Launch<StBF16>::step(Q, LBM_EHRENFEST, odd, q, st);
-                if (e == cudaSuccess) e = Launch<StBF16>::eval(Q, q, st, nsm);
                 if (e == cudaSuccess) e = Launch<StBF16>::fixup(Q, LBM_EHRENFEST, odd, q, st, nsm);
                 break;
             default:
                 e = Launch<StF16>::step(Q, LBM_EHRENFEST, odd, q, st);
-                if (e == cudaSuccess) e = Launch<StF16>::eval(Q, q, st, nsm);
                 if (e == cudaSuccess) e = Launch<StF16>::fixup(Q, LBM_EHRENFEST, odd, q, st, nsm);
                 break;
         }

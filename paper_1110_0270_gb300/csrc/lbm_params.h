@@ -24,6 +24,7 @@ enum Counter {
     CNT_OVERFLOW = 3,  // candidate list overflow
     CNT_NSEL = 4,      // number of sites selected in the last Ehrenfest step
     CNT_NVALID = 5,    // candidates (FP64 Delta S > delta) of the current step
+    CNT_DONE = 6,      // CTAs of ehrenfest_eval_select that have finished
     CNT_WORDS = 8
 };
 enum Stat {

@@ -32,7 +32,9 @@ EXPORTS = ["lbm_config_default", "lbm_required_bytes", "lbm_create", "lbm_destro
            "lbm_init_device", "lbm_set_state", "lbm_get_state", "lbm_step", "lbm_macros",
            "lbm_entropy", "lbm_stats_get", "lbm_last_candidates", "lbm_last_error",
            "lbm_status_string", "lbm_abi_version", "lbm_profile_enable", "lbm_profile_read",
-           "lbm_ehrenfest_step_noalloc"]
+           "lbm_ehrenfest_step_noalloc", "lbm_batch_required_bytes", "lbm_batch_create",
+           "lbm_batch_destroy", "lbm_batch_init_uniform", "lbm_batch_set_state",
+           "lbm_batch_get_state", "lbm_batch_step", "lbm_batch_stats", "lbm_batch_last_error"]
 
 
 class lbm_config(C.Structure):
@@ -83,6 +85,15 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "lbm_profile_enable": (i, [p, i]),
         "lbm_profile_read": (i, [p, C.POINTER(i), C.POINTER(C.c_double)]),
         "lbm_ehrenfest_step_noalloc": (i, [C.POINTER(lbm_config), p, i, p]),
+        "lbm_batch_required_bytes": (i, [C.POINTER(lbm_config), i, C.POINTER(sz)]),
+        "lbm_batch_create": (i, [C.POINTER(lbm_config), i, p, sz, C.POINTER(p)]),
+        "lbm_batch_destroy": (None, [p]),
+        "lbm_batch_init_uniform": (i, [p, C.c_double, C.c_double, C.c_double, p]),
+        "lbm_batch_set_state": (i, [p, i, p, i, p]),
+        "lbm_batch_get_state": (i, [p, i, p, i, p]),
+        "lbm_batch_step": (i, [p, i, C.POINTER(i), p]),
+        "lbm_batch_stats": (i, [p, i, C.POINTER(lbm_stats), p]),
+        "lbm_batch_last_error": (C.c_char_p, [p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -261,11 +272,11 @@ class Lattice:
         self._check(lib().lbm_profile_enable(self._h, int(enable)), "lbm_profile_enable")
 
     def profile_read(self) -> dict:
-        """{kind: (launches, total_ms)} for the 'step', 'fixup' and 'eval' kernels."""
-        n = (C.c_int * 3)()
-        ms = (C.c_double * 3)()
+        """{kind: (launches, total_ms)} for the 'step' and 'fixup' kernels."""
+        n = (C.c_int * 2)()
+        ms = (C.c_double * 2)()
         self._check(lib().lbm_profile_read(self._h, n, ms), "lbm_profile_read")
-        return {"step": (n[0], ms[0]), "fixup": (n[1], ms[1]), "eval": (n[2], ms[2])}
+        return {"step": (n[0], ms[0]), "fixup": (n[1], ms[1])}
 
     def last_candidates(self, cap: int | None = None, stream=None):
         """(delta_s float64, site int32, selected int32) of the last step."""
@@ -279,3 +290,77 @@ class Lattice:
             sel.ctypes.data_as(C.c_void_p), cap, C.byref(n), _stream(stream)), "lbm_last_candidates")
         m = min(n.value, cap)
         return ds[:m], site[:m], sel[:m]
+
+
+def batch_required_bytes(cfgs) -> int:
+    cs = [c if isinstance(c, LBMConfig) else LBMConfig.from_dict(c) for c in cfgs]
+    arr = (lbm_config * len(cs))(*[c.to_c() for c in cs])
+    n = C.c_size_t()
+    rc = lib().lbm_batch_required_bytes(arr, len(cs), C.byref(n))
+    if rc != 0:
+        raise LBMError(f"lbm_batch_required_bytes: {STATUS.get(rc, rc)}")
+    return n.value
+
+
+class Batch:
+    """Many independent D2Q9 lattices advanced together (lbm_batch_*)."""
+
+    def __init__(self, cfgs, device=None):
+        import torch
+        self.cfgs = [c if isinstance(c, LBMConfig) else LBMConfig.from_dict(c) for c in cfgs]
+        self.n = len(self.cfgs)
+        self.device = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        self._arr = (lbm_config * self.n)(*[c.to_c() for c in self.cfgs])
+        self.nbytes = batch_required_bytes(self.cfgs)
+        self.mem = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = lib().lbm_batch_create(self._arr, self.n, _ptr(self.mem), self.nbytes, C.byref(h))
+        if rc != 0:
+            raise LBMError(f"lbm_batch_create: {STATUS.get(rc, rc)}")
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.lbm_batch_destroy(h)
+            self._h = None
+
+    def _check(self, rc, what):
+        if rc != 0:
+            msg = lib().lbm_batch_last_error(self._h)
+            raise LBMError(f"{what}: {STATUS.get(rc, rc)}: {msg.decode() if msg else ''}")
+
+    def shape(self, i):
+        return (9, self.cfgs[i].ny, self.cfgs[i].nx)
+
+    def init_uniform(self, rho=1.0, ux=0.0, uy=0.0, stream=None):
+        self._check(lib().lbm_batch_init_uniform(self._h, rho, ux, uy, _stream(stream)),
+                    "lbm_batch_init_uniform")
+
+    def set_state(self, i, f, stream=None):
+        import torch
+        assert f.is_cuda and f.is_contiguous() and tuple(f.shape) == self.shape(i)
+        dt = DTYPE_F64 if f.dtype == torch.float64 else DTYPE_F32
+        self._check(lib().lbm_batch_set_state(self._h, i, _ptr(f), dt, _stream(stream)),
+                    "lbm_batch_set_state")
+
+    def get_state(self, i, dtype=None, stream=None):
+        import torch
+        dtype = dtype or torch.float64
+        out = torch.empty(self.shape(i), dtype=dtype, device=self.device)
+        dt = DTYPE_F64 if dtype == torch.float64 else DTYPE_F32
+        self._check(lib().lbm_batch_get_state(self._h, i, _ptr(out), dt, _stream(stream)),
+                    "lbm_batch_get_state")
+        return out
+
+    def step(self, n=1, status=False, stream=None):
+        st = (C.c_int * self.n)() if status else None
+        self._check(lib().lbm_batch_step(self._h, int(n), st, _stream(stream)), "lbm_batch_step")
+        return [STATUS[v] for v in st] if status else None
+
+    def stats(self, i, stream=None) -> dict:
+        st = lbm_stats()
+        self._check(lib().lbm_batch_stats(self._h, i, C.byref(st), _stream(stream)), "lbm_batch_stats")
+        return {n: int(getattr(st, n)) for n, _ in lbm_stats._fields_}

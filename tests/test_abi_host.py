@@ -75,3 +75,15 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
     assert lib.lbm_create(C.byref(c), None, 1 << 20, C.byref(h)) == 1
     assert lib.lbm_create(C.byref(c), C.c_void_p(0x1001), 1 << 20, C.byref(h)) == 1
     assert lib.lbm_create(C.byref(c), C.c_void_p(0x100000), 16, C.byref(h)) == 3  # too small
+
+
+def test_batch_validation_is_host_side(lib):
+    ok = [dict(lattice="D2Q9", nx=10, ny=12, beta=0.9, precision="fp32"),
+          dict(lattice="D2Q9", nx=64, ny=8, beta=0.9, precision="fp32", collision="ehrenfest", topk=2)]
+    n = lbm.batch_required_bytes(ok)
+    assert n >= lbm.required_bytes(ok[0])
+    for bad in ([dict(lattice="D2Q9", nx=10, ny=12, beta=0.9, precision="fp32"),
+                 dict(lattice="D2Q9", nx=10, ny=12, beta=0.9, precision="fp64")],
+                [dict(lattice="D1Q3", nx=10, ny=1, beta=0.9)]):
+        with pytest.raises(lbm.LBMError):
+            lbm.batch_required_bytes(bad)
