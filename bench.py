@@ -350,7 +350,9 @@ def gpu_arm(args):
                                f" (Ehrenfest/median: k={TOPK}, delta={DELTA:g}), started from rest",
                    "sites": N, "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "inputs larger than L2 (state 604 MB in FP32), no flush",
-                   "limiter_sites_total": st["limited_total"]},
+                   "limiter_sites_total": st["limited_total"],
+                   "last_step_candidates": st["candidates_last"],
+                   "last_step_screened": st["screened_last"]},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                      "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
                      "kernel": f"step_kernel<D2Q9, {args.precision}, {args.collision}>",

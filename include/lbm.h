@@ -127,6 +127,8 @@ typedef struct {
     uint64_t diverged;         /* 1 once a non-finite or non-positive rho is seen */
     uint64_t overflow;         /* 1 if a candidate list overflowed (never with
                                   the default capacity of one entry per site) */
+    uint64_t screened_last;    /* sites the FP32 screen passed to the FP64
+                                  Delta S test in the last step (limiters) */
 } lbm_stats;
 
 /* Fills *cfg with defaults: D2Q9 16x16 cavity, LBGK, product polynomial

@@ -740,3 +740,171 @@ int orc_step(const orc_config* cfg, double* f, int nsteps, orc_stats* st) {
     free(mask);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Reverse-mode gradient (adjoint) of the kinetic energy after T steps.     */
+/* ------------------------------------------------------------------------ */
+
+double orc_kinetic_energy(const orc_config* cfg, const double* f) {
+    int Q = orc_q(cfg->lattice);
+    long long N = (long long)cfg->nx * cfg->ny;
+    double fs[9], e = 0.0;
+    for (long long s = 0; s < N; ++s) {
+        double r, ux, uy;
+        gather(Q, f, N, s, fs);
+        orc_moments(cfg->lattice, fs, &r, &ux, &uy);
+        e += 0.5 * r * (ux * ux + uy * uy);
+    }
+    return e;
+}
+
+/* Derivatives of the 1D equilibria (per unit density) in u. */
+static void eq1d_deriv(int kind, double u, double phi[3], double dphi[3]) {
+    if (kind == ORC_EQ_ENTROPIC) {
+        double s = sqrt(1.0 + 3.0 * u * u);
+        orc_eq1d_entropic(u, phi);
+        dphi[0] = -0.5 + u / s;
+        dphi[1] = -2.0 * u / s;
+        dphi[2] = 0.5 + u / s;
+    } else {
+        orc_eq1d_poly(u, phi);
+        dphi[0] = u - 0.5;
+        dphi[1] = -2.0 * u;
+        dphi[2] = u + 0.5;
+    }
+}
+
+/* df*_i/d(rho), d/d(ux), d/d(uy) at one site. */
+static void eq_partials(int lattice, int kind, double rho, double ux, double uy, double* dr,
+                        double* dx, double* dy) {
+    int Q = orc_q(lattice);
+    int cx[9], cy[9];
+    double W[9];
+    orc_lattice(lattice, cx, cy, W);
+    if (lattice == ORC_D2Q9 && kind == ORC_EQ_POLY_STD) {
+        double uu = ux * ux + uy * uy;
+        for (int i = 0; i < Q; ++i) {
+            double cu = cx[i] * ux + cy[i] * uy;
+            dr[i] = W[i] * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+            dx[i] = W[i] * rho * (3.0 * cx[i] + 9.0 * cu * cx[i] - 3.0 * ux);
+            dy[i] = W[i] * rho * (3.0 * cy[i] + 9.0 * cu * cy[i] - 3.0 * uy);
+        }
+        return;
+    }
+    double px[3], dpx[3], py[3] = {0.0, 1.0, 0.0}, dpy[3] = {0.0, 0.0, 0.0};
+    eq1d_deriv(kind, ux, px, dpx);
+    if (lattice == ORC_D2Q9) eq1d_deriv(kind, uy, py, dpy);
+    for (int i = 0; i < Q; ++i) {
+        int a = cx[i] + 1, b = cy[i] + 1;
+        dr[i] = px[a] * py[b];
+        dx[i] = rho * dpx[a] * py[b];
+        dy[i] = rho * px[a] * dpy[b];
+    }
+}
+
+int orc_adjoint_ke(const orc_config* cfg, const double* f0, int T, double* J, double* dJ_df0,
+                   double* dJ_dU, double* dJ_dbeta) {
+    if (!config_ok(cfg) || T < 0) return -1;
+    if (cfg->collision != ORC_LBGK && cfg->collision != ORC_EHRENFEST) return -1;
+    int Q = orc_q(cfg->lattice);
+    long long N = (long long)cfg->nx * cfg->ny;
+    size_t S = (size_t)(Q * N);
+    double* tape = (double*)malloc(sizeof(double) * S * (size_t)(T + 1));
+    unsigned char* masks = (unsigned char*)calloc((size_t)N * (size_t)(T > 0 ? T : 1), 1);
+    double* F = (double*)malloc(sizeof(double) * S);
+    double* dS = (double*)malloc(sizeof(double) * (size_t)N);
+    double* lam = (double*)malloc(sizeof(double) * S);
+    double* Lam = (double*)malloc(sizeof(double) * S);
+    if (!tape || !masks || !F || !dS || !lam || !Lam) {
+        free(tape); free(masks); free(F); free(dS); free(lam); free(Lam);
+        return -2;
+    }
+    int cx[9], cy[9];
+    double W[9];
+    orc_lattice(cfg->lattice, cx, cy, W);
+    int px, py;
+    bc_periodicity(cfg, &px, &py);
+    const int kind = eq_kind(cfg);
+    const double om = 2.0 * cfg->beta;
+
+    /* forward, keeping every pre-collision state and the selection masks */
+    memcpy(tape, f0, sizeof(double) * S);
+    for (int t = 0; t < T; ++t) {
+        const double* f = tape + (size_t)t * S;
+        unsigned char* mask = masks + (size_t)t * N;
+        if (cfg->collision == ORC_EHRENFEST) {
+            orc_delta_s_field(cfg, f, dS);
+            orc_select_topk(dS, N, cfg->topk, cfg->delta, mask);
+        }
+        for (long long s = 0; s < N; ++s) {
+            double fs[9], feq[9];
+            gather(Q, f, N, s, fs);
+            site_equilibrium(cfg, fs, feq);
+            for (int i = 0; i < Q; ++i)
+                F[i * N + s] = mask[s] ? feq[i] : fs[i] + om * (feq[i] - fs[i]);
+        }
+        orc_stream(cfg, F, tape + (size_t)(t + 1) * S);
+    }
+    const double* fT = tape + (size_t)T * S;
+    *J = orc_kinetic_energy(cfg, fT);
+
+    /* seed: dJ/df_j = c_j . u - |u|^2 / 2 at every site */
+    for (long long s = 0; s < N; ++s) {
+        double fs[9], r, ux, uy;
+        gather(Q, fT, N, s, fs);
+        orc_moments(cfg->lattice, fs, &r, &ux, &uy);
+        for (int j = 0; j < Q; ++j)
+            lam[j * N + s] = cx[j] * ux + cy[j] * uy - 0.5 * (ux * ux + uy * uy);
+    }
+    double gU = 0.0, gB = 0.0;
+    for (int t = T - 1; t >= 0; --t) {
+        /* transpose of the streaming: F_i(x) went to (i, x + v_i), or bounced
+         * to (opp(i), x) with the moving-wall term -6 W_i v_ix U */
+        for (int i = 0; i < Q; ++i) {
+            int o = orc_opposite(cfg->lattice, i);
+            for (int y = 0; y < cfg->ny; ++y)
+                for (int x = 0; x < cfg->nx; ++x) {
+                    int tx = x + cx[i], ty = y + cy[i];
+                    if (px) tx = (tx + cfg->nx) % cfg->nx;
+                    if (py) ty = (ty + cfg->ny) % cfg->ny;
+                    long long s = (long long)y * cfg->nx + x;
+                    if (tx >= 0 && tx < cfg->nx && ty >= 0 && ty < cfg->ny) {
+                        Lam[i * N + s] = lam[i * N + (long long)ty * cfg->nx + tx];
+                    } else {
+                        Lam[i * N + s] = lam[o * N + s];
+                        if (ty >= cfg->ny) gU += lam[o * N + s] * (-6.0 * W[i] * cx[i]);
+                    }
+                }
+        }
+        /* transpose of the collision at every site */
+        const double* f = tape + (size_t)t * S;
+        const unsigned char* mask = masks + (size_t)t * N;
+        for (long long s = 0; s < N; ++s) {
+            double fs[9], feq[9], dr[9], dx[9], dy[9], r, ux, uy, L[9];
+            gather(Q, f, N, s, fs);
+            gather(Q, Lam, N, s, L);
+            orc_moments(cfg->lattice, fs, &r, &ux, &uy);
+            orc_equilibrium(cfg->lattice, kind, r, ux, uy, feq);
+            eq_partials(cfg->lattice, kind, r, ux, uy, dr, dx, dy);
+            /* a_j = sum_i L_i df*_i/df_j with drho/df_j = 1,
+             * du_x/df_j = (v_jx - u_x)/rho, du_y/df_j = (v_jy - u_y)/rho */
+            double A = 0.0, Bx = 0.0, By = 0.0;
+            for (int i = 0; i < Q; ++i) {
+                A += L[i] * dr[i];
+                Bx += L[i] * dx[i];
+                By += L[i] * dy[i];
+            }
+            for (int j = 0; j < Q; ++j) {
+                double a = A + Bx * (cx[j] - ux) / r + By * (cy[j] - uy) / r;
+                lam[j * N + s] = mask[s] ? a : (1.0 - om) * L[j] + om * a;
+            }
+            if (!mask[s])
+                for (int i = 0; i < Q; ++i) gB += L[i] * 2.0 * (feq[i] - fs[i]);
+        }
+    }
+    memcpy(dJ_df0, lam, sizeof(double) * S);
+    *dJ_dU = gU;
+    *dJ_dbeta = gB;
+    free(tape); free(masks); free(F); free(dS); free(lam); free(Lam);
+    return 0;
+}

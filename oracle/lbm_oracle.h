@@ -127,6 +127,18 @@ int orc_step(const orc_config* cfg, double* f, int nsteps, orc_stats* st);
 /* Pure streaming with the boundary rule (used by the oracle step). */
 void orc_stream(const orc_config* cfg, const double* F, double* fnew);
 
+/* Kinetic energy J = 1/2 sum_x rho |u|^2 of a state. */
+double orc_kinetic_energy(const orc_config* cfg, const double* f);
+
+/* Tape-based reverse-mode gradient of J(f_T) = 1/2 sum_x rho |u|^2 after
+ * T steps from f0, for the LBGK and Ehrenfest collisions (the Ehrenfest
+ * selection of each step is held fixed: the selected branch F = f* is
+ * differentiated).  Outputs J, dJ/df0 (same layout as f0), dJ/d lid_u and
+ * dJ/d beta.  Returns 0, -1 for an unsupported configuration, -2 on
+ * allocation failure. */
+int orc_adjoint_ke(const orc_config* cfg, const double* f0, int T, double* J, double* dJ_df0,
+                   double* dJ_dU, double* dJ_dbeta);
+
 #ifdef __cplusplus
 }
 #endif

@@ -137,6 +137,8 @@ def _L():
                 "orc_total_h": (d, [p, p]),
                 "orc_step": (i, [p, p, i, p]),
                 "orc_stream": (None, [p, p, p]),
+                "orc_kinetic_energy": (d, [p, p]),
+                "orc_adjoint_ke": (i, [p, p, i, p, p, p, p]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -343,7 +345,28 @@ def step(cfg, f, nsteps: int = 1, stats: bool = False):
     return out
 
 
-__all__ = [
+def kinetic_energy(cfg, f) -> float:
+    cfg = _cfg(cfg)
+    c = cfg._c()
+    f = _f64(f)
+    return _L().orc_kinetic_energy(C.byref(c), _ptr(f))
+
+
+def adjoint_ke(cfg, f0, T: int):
+    """(J, dJ/df0, dJ/dU, dJ/dbeta) of J = 1/2 sum rho |u|^2 after T steps."""
+    cfg = _cfg(cfg)
+    c = cfg._c()
+    f0 = _f64(f0)
+    g = np.zeros_like(f0)
+    J, gU, gB = C.c_double(), C.c_double(), C.c_double()
+    rc = _L().orc_adjoint_ke(C.byref(c), _ptr(f0), int(T), C.byref(J), _ptr(g), C.byref(gU),
+                             C.byref(gB))
+    if rc != 0:
+        raise ValueError(f"oracle adjoint failed with code {rc}")
+    return J.value, g, gU.value, gB.value
+
+
+__all__ = ["kinetic_energy", "adjoint_ke", 
     "OracleConfig", "build", "lattice", "opposite", "eq1d", "equilibrium", "moments", "gfun",
     "delta_s", "delta_s_direct", "entropy", "entropy_d1q3_paper", "elbm_alpha", "elbm_sf",
     "mrt_basis", "mrt_matrix", "collide_site", "select_topk", "median_field",

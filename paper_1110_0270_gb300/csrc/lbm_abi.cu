@@ -414,6 +414,7 @@ lbm_status lbm_stats_get(lbm_ctx* ctx, lbm_stats* out, void* stream) {
     out->elbm_iters_max = st[ST_ELBM_ITERS_MAX];
     out->diverged = cnt[CNT_DIVERGED];
     out->overflow = cnt[CNT_OVERFLOW];
+    out->screened_last = (ctx->t > 0 && limiter(ctx->cfg.collision)) ? cnt[(ctx->t - 1) & 1] : 0;
     return LBM_OK;
 }
 

@@ -419,6 +419,7 @@ lbm_status lbm_batch_stats(lbm_batch* b, int instance, lbm_stats* out, void* str
     out->elbm_iters_max = st[ST_ELBM_ITERS_MAX];
     out->diverged = cnt[CNT_DIVERGED];
     out->overflow = cnt[CNT_OVERFLOW];
+    out->screened_last = (b->t > 0 && (coll == LBM_EHRENFEST || coll == LBM_MEDIAN)) ? cnt[(b->t - 1) & 1] : 0;
     return LBM_OK;
 }
 

@@ -159,6 +159,40 @@ __device__ __forceinline__ void load_candidate(const Params& p, int j, typename 
 // Ehrenfest regularisation (Section 4): the k candidates with the largest
 // Delta S (ties: lower site index) jump to f*.  One CTA; Delta S > delta >= 0
 // so the IEEE bit patterns order like the values (+inf last).
+// One radix digit of the selection, by the first warp: the digit d whose bin
+// holds the rem-th key counting from the top (descending) or from the bottom
+// (ascending); rem becomes the rank inside that bin.  Lane l owns eight
+// consecutive bins in scan order; a shuffle prefix sum finds the lane.
+__device__ __forceinline__ int pick_digit(const unsigned* hist, unsigned& rem, bool descending) {
+    const int l = threadIdx.x & 31;
+    unsigned c = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) c += hist[descending ? 255 - 8 * l - k : 8 * l + k];
+    unsigned incl = c;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (l >= off) incl += v;
+    }
+    const unsigned hit = __ballot_sync(0xffffffffu, incl >= rem);
+    const int L = hit ? __ffs(hit) - 1 : 31;
+    int digit = 0;
+    unsigned r = 0;
+    if (l == L) {
+        r = rem - (incl - c);
+        int k = 0;
+        for (; k < 7; ++k) {
+            const unsigned h = hist[descending ? 255 - 8 * l - k : 8 * l + k];
+            if (h >= r) break;
+            r -= h;
+        }
+        digit = descending ? 255 - 8 * l - k : 8 * l + k;
+    }
+    digit = __shfl_sync(0xffffffffu, digit, L);
+    rem = __shfl_sync(0xffffffffu, r, L);
+    return digit;
+}
+
 // Runs in one CTA of any size after every cand_ds entry of the step is final
 // (the entries of other CTAs are read through L2).
 template <int Q, class ST, bool ODD>
@@ -194,16 +228,14 @@ __device__ void ehrenfest_select_apply(const Params& p, unsigned M, unsigned nva
                 if (ds > p.delta && (key & msk) == pre) atomicAdd(&hist[(key >> shift) & 255ull], 1u);
             }
             __syncthreads();
-            if (tid == 0) {
+            if (tid < 32) {
                 unsigned rem = s_rem;
-                int d = 255;
-                for (; d > 0; --d) {
-                    if (hist[d] >= rem) break;
-                    rem -= hist[d];
+                const int d = pick_digit(hist, rem, true);
+                if (tid == 0) {
+                    s_rem = rem;
+                    s_prefix = pre | ((unsigned long long)d << shift);
+                    s_mask = msk | (255ull << shift);
                 }
-                s_rem = rem;
-                s_prefix = pre | ((unsigned long long)d << shift);
-                s_mask = msk | (255ull << shift);
             }
             __syncthreads();
         }
@@ -227,16 +259,14 @@ __device__ void ehrenfest_select_apply(const Params& p, unsigned M, unsigned nva
                     atomicAdd(&hist[(site >> shift) & 255u], 1u);
             }
             __syncthreads();
-            if (tid == 0) {
+            if (tid < 32) {
                 unsigned rem = s_rem;
-                int d = 0;
-                for (; d < 255; ++d) {
-                    if (hist[d] >= rem) break;
-                    rem -= hist[d];
+                const int d = pick_digit(hist, rem, false);
+                if (tid == 0) {
+                    s_rem = rem;
+                    s_prefix = pre | ((unsigned)d << shift);
+                    s_mask = msk | (255u << shift);
                 }
-                s_rem = rem;
-                s_prefix = pre | ((unsigned)d << shift);
-                s_mask = msk | (255u << shift);
             }
             __syncthreads();
         }

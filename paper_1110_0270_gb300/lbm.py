@@ -52,7 +52,8 @@ class lbm_config(C.Structure):
 class lbm_stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in (
         "steps", "candidates_last", "limited_total", "elbm_solved", "elbm_skipped",
-        "elbm_fallbacks", "elbm_iters_total", "elbm_iters_max", "diverged", "overflow")]
+        "elbm_fallbacks", "elbm_iters_total", "elbm_iters_max", "diverged", "overflow",
+        "screened_last")]
 
 
 class LBMError(RuntimeError):

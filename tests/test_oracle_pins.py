@@ -574,3 +574,41 @@ def test_shock_tube_runs_and_conserves_mass():
         out[collision] = np.abs(np.diff(rho)).sum()  # total variation
     assert out["lbgk"] > 0.6  # oscillations: well above the 0.5 jump
     assert out["ehrenfest"] < out["lbgk"]
+
+
+# ----------------------------------------------------------------------------- adjoint
+@pytest.mark.parametrize("case", ["cavity_lbgk", "cavity_ehrenfest", "tube", "periodic"])
+def test_oracle_adjoint_matches_central_differences(case):
+    """The tape adjoint of J = 1/2 sum rho |u|^2 after T steps against central
+    differences of the oracle's own forward run (U, beta and a random
+    direction in f0).  For the Ehrenfest case the step h is small enough that
+    no selection changes, so the selected branch is what is differentiated."""
+    cfgs = {
+        "cavity_lbgk": dict(lattice="D2Q9", nx=12, ny=10, bc="cavity", lid_u=0.1,
+                            collision="lbgk", beta=0.9),
+        "cavity_ehrenfest": dict(lattice="D2Q9", nx=12, ny=10, bc="cavity", lid_u=0.1,
+                                 collision="ehrenfest", beta=0.95, topk=3, delta=1e-4),
+        "tube": dict(lattice="D1Q3", nx=40, ny=1, bc="ends", collision="lbgk", beta=0.97),
+        "periodic": dict(lattice="D2Q9", nx=9, ny=7, bc="periodic", collision="ehrenfest",
+                         beta=0.92, topk=2, delta=1e-4, equilibrium="entropic"),
+    }
+    cfg = cfgs[case]
+    ny, nx = cfg["ny"], cfg["nx"]
+    fl = WL.random_fields(ny, nx, 4, 0.05, 0.05)
+    f0 = O.init_equilibrium(dict(cfg, collision="lbgk"), fl["rho"], fl["ux"],
+                            None if cfg["lattice"] == "D1Q3" else fl["uy"])
+    f0 = f0 * WL.lognormal_factors(f0.shape, 5, 0.02)
+    f0 = f0 * WL.lognormal_factors(f0.shape, 6, 1.0) ** (WL.hot_spots(ny, nx, 7, 4, 0.4)[None])
+    T = 25
+    J, g, gU, gB = O.adjoint_ke(cfg, f0, T)
+    KE = lambda c, f: O.kinetic_energy(c, O.step(c, f, T))
+    assert abs(J - KE(cfg, f0)) < 1e-15 * abs(J) + 1e-300
+    h = 1e-6
+    if cfg["bc"] == "cavity":
+        fd = (KE(dict(cfg, lid_u=cfg["lid_u"] + h), f0) - KE(dict(cfg, lid_u=cfg["lid_u"] - h), f0)) / (2 * h)
+        assert abs(gU - fd) <= 1e-7 * abs(fd) + 1e-12
+    fd = (KE(dict(cfg, beta=cfg["beta"] + h), f0) - KE(dict(cfg, beta=cfg["beta"] - h), f0)) / (2 * h)
+    assert abs(gB - fd) <= 1e-6 * abs(fd) + 1e-11
+    v = np.random.default_rng(8).standard_normal(f0.shape)
+    fd = (KE(cfg, f0 + h * v) - KE(cfg, f0 - h * v)) / (2 * h)
+    assert abs((g * v).sum() - fd) <= 1e-6 * abs(fd) + 1e-11
