@@ -245,6 +245,60 @@ def run_batched(steps, warmup, fp64_mlups=None, separate=True):
     return out
 
 
+def run_adjoint(T=4000, K=100, n=513, fd=True):
+    """The adjoint configuration: D2Q9 cavity n^2, Re 1000, U 0.1, FP32,
+    Ehrenfest k = 32, f0 = equilibrium at rest + N(0, 1e-4) noise; gradient
+    of the kinetic energy after T steps with respect to U, beta and f0,
+    checkpoints every K steps.  Reports backward / forward time and the
+    central differences (h = 1e-3, Richardson with h/2) of FP64 forward runs."""
+    import torch
+    from paper_1110_0270_gb300 import lbm
+    from paper_1110_0270_gb300 import workloads as WL
+    cfg, init = WL.cavity(n, 1000.0, 0.1)
+    cfg.update(collision="ehrenfest", topk=32, delta=1e-3, precision="fp32")
+    beta = 1.0 / (6.0 * cfg["nu"] + 1.0)
+    cfg["beta"] = beta
+    lat = lbm.Lattice(cfg)
+    lat.init(init["rho"], init["ux"], init["uy"])
+    f0 = (lat.get_state(torch.float64) + torch.tensor(
+        WL.normal_noise((9, n, n), 5, 1e-4), device="cuda")).float()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - t0
+
+    work = lat.adjoint_work(T, K)
+    lat.set_state(f0)
+    lat.adjoint_forward(T, K, work)  # warm-up of both passes
+    lat.adjoint_backward(T, K, work)
+    lat.set_state(f0)
+    (J, _), t_f = timed(lambda: lat.adjoint_forward(T, K, work))
+    (g, gU, gB), t_b = timed(lambda: lat.adjoint_backward(T, K, work))
+    out = {"config": f"D2Q9 cavity {n}^2, Re 1000, U 0.1, FP32, Ehrenfest k=32, T={T}, K={K}",
+           "J": J, "dJ_dU": gU, "dJ_dbeta": gB, "forward_s": round(t_f, 4),
+           "backward_s": round(t_b, 4), "backward_over_forward": round(t_b / t_f, 3),
+           "work_bytes": int(work.numel())}
+    if fd:
+        f64 = f0.double()
+
+        def ke(**kw):
+            l2 = lbm.Lattice(dict(cfg, precision="fp64", **kw))
+            l2.set_state(f64)
+            return l2.adjoint_forward(T, T)[0]
+
+        def cd(key, x0, h):
+            d = lambda hh: (ke(**{key: x0 + hh}) - ke(**{key: x0 - hh})) / (2 * hh)
+            return (4 * d(h / 2) - d(h)) / 3
+
+        fdU, fdB = cd("lid_u", 0.1, 1e-3), cd("beta", beta, 1e-3)
+        out.update(fd_dJ_dU=fdU, fd_dJ_dbeta=fdB, rel_err_U=abs(gU - fdU) / abs(fdU),
+                   rel_err_beta=abs(gB - fdB) / abs(fdB))
+    return out
+
+
 def e2e_measure(cfg, init, jobs=3, inner=100):
     """End to end through the public API with host buffers: lbm_init from
     pinned host rho/u (H2D), `inner` steps, lbm_macros and a D2H copy of
@@ -365,6 +419,8 @@ def gpu_arm(args):
         result["clocks"] = sampler.summary(t0, t1) if sampler else None
         if not args.no_variants:
             result["variants"] = run_variants(args.side, args.variant_steps, 3)
+        if args.adjoint_steps > 0:
+            result["adjoint"] = run_adjoint(args.adjoint_steps, 100)
         if args.batch_steps > 0:
             fp64 = result.get("variants", {}).get("lbgk/fp64", {}).get("mlups")
             result["batched"] = run_batched(args.batch_steps, 3, fp64)
@@ -429,6 +485,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16_dev", "bf16_dev"])
     ap.add_argument("--variant-steps", type=int, default=100)
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=4000,
+                    help="T of the adjoint run (0 skips it)")
     ap.add_argument("--batch-steps", type=int, default=20,
                     help="steps of the 512-cavity batched run (0 skips it)")
     ap.add_argument("--no-e2e", action="store_true")

@@ -225,6 +225,38 @@ lbm_status lbm_batch_step(lbm_batch* b, int nsteps, int* status, void* stream);
 lbm_status lbm_batch_stats(lbm_batch* b, int instance, lbm_stats* out, void* stream);
 const char* lbm_batch_last_error(const lbm_batch* b);
 
+/* ---- Adjoint: reverse-mode gradient ---------------------------------------
+ * For the LBGK and Ehrenfest collisions: the gradient of a functional J of
+ * the state f_T after T steps with respect to the initial populations f_0,
+ * the lid velocity (lid_u) and beta.  J defaults to the kinetic energy
+ * 1/2 sum_x rho |u|^2; any J is served by passing its gradient dJ/df_T as
+ * `seed`.  Per step the adjoint is the transpose of the streaming (walls and
+ * moving-lid term included) and of the collision's Jacobian; at the sites
+ * the Ehrenfest step sent to f* the selected branch F = f* is differentiated
+ * (the selection of each step is held fixed).  Checkpoint and recompute:
+ * the forward pass keeps a dense copy of the state every K steps; the
+ * backward pass, segment by segment from the last, recomputes the K states
+ * and selections and runs K adjoint steps.  `work` is caller DEVICE memory
+ * of lbm_adjoint_required_bytes (256-byte aligned): ceil(T/K) checkpoints,
+ * K segment states, K selection masks (Ehrenfest), two adjoint buffers and
+ * the final state, dense in the arithmetic type (double for FP64 storage,
+ * float otherwise).  Nothing is allocated. */
+lbm_status lbm_adjoint_required_bytes(const lbm_config* cfg, int T, int K, size_t* bytes);
+/* Advances ctx T steps from its current state (which must be at an even step
+ * count) keeping the checkpoints; *J_host (if not NULL) receives the kinetic
+ * energy of f_T and then the stream is synchronised. */
+lbm_status lbm_adjoint_forward(lbm_ctx* ctx, int T, int K, void* work, size_t work_bytes,
+                               double* J_host, void* stream);
+/* After lbm_adjoint_forward with the same T, K and work: dJ/df_0 into the
+ * dense DEVICE array dJ_df0 [Q][ny][nx] of out_dtype (may be NULL), dJ/dU and
+ * dJ/dbeta into the host doubles (may be NULL); seed = dJ/df_T (dense DEVICE
+ * array of seed_dtype) or NULL for the kinetic energy.  The context holds
+ * f_T again on return (its step counter and statistics are reset).
+ * Synchronises the stream. */
+lbm_status lbm_adjoint_backward(lbm_ctx* ctx, int T, int K, const void* seed, int seed_dtype,
+                                void* dJ_df0, int out_dtype, double* dJ_dU, double* dJ_dbeta,
+                                void* work, size_t work_bytes, void* stream);
+
 /* Kernel tracing.  While enabled, every kernel lbm_step launches is
  * bracketed by two CUDA events recorded on the caller's stream (timing
  * events; the first LBM_PROFILE_MAX launches after enabling are kept).

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "lbm.h"
+#include "lbm_ctx.h"
 #include "lbm_kernels.cuh"
 
 using namespace lbm;
@@ -21,28 +22,6 @@ extern template struct Launch<StF32>;
 extern template struct Launch<StBF16>;
 extern template struct Launch<StF16>;
 }  // namespace lbm
-
-struct lbm_ctx {
-    lbm_config cfg;
-    int Q = 0;
-    Params p;
-    char* base = nullptr;
-    size_t bytes = 0;
-    int parity = 0;   // 0: natural layout; 1: after an even (in-place) step
-    uint64_t t = 0;   // steps since init / set_state
-    int nsm = 1;
-    int device = 0;
-    double* staging = nullptr;  // 3 * N doubles for lbm_init
-    std::string err;
-    // kernel tracing (lbm_profile_enable)
-    bool profiling = false;
-    std::vector<cudaEvent_t> ev;  // pairs (start, end)
-    std::vector<int> ev_kind;
-    size_t ev_used = 0;
-    ~lbm_ctx() {
-        for (cudaEvent_t e : ev) cudaEventDestroy(e);
-    }
-};
 
 namespace {
 

@@ -34,7 +34,8 @@ EXPORTS = ["lbm_config_default", "lbm_required_bytes", "lbm_create", "lbm_destro
            "lbm_status_string", "lbm_abi_version", "lbm_profile_enable", "lbm_profile_read",
            "lbm_ehrenfest_step_noalloc", "lbm_batch_required_bytes", "lbm_batch_create",
            "lbm_batch_destroy", "lbm_batch_init_uniform", "lbm_batch_set_state",
-           "lbm_batch_get_state", "lbm_batch_step", "lbm_batch_stats", "lbm_batch_last_error"]
+           "lbm_batch_get_state", "lbm_batch_step", "lbm_batch_stats", "lbm_batch_last_error",
+           "lbm_adjoint_required_bytes", "lbm_adjoint_forward", "lbm_adjoint_backward"]
 
 
 class lbm_config(C.Structure):
@@ -95,6 +96,10 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "lbm_batch_step": (i, [p, i, C.POINTER(i), p]),
         "lbm_batch_stats": (i, [p, i, C.POINTER(lbm_stats), p]),
         "lbm_batch_last_error": (C.c_char_p, [p]),
+        "lbm_adjoint_required_bytes": (i, [C.POINTER(lbm_config), i, i, C.POINTER(sz)]),
+        "lbm_adjoint_forward": (i, [p, i, i, p, sz, C.POINTER(C.c_double), p]),
+        "lbm_adjoint_backward": (i, [p, i, i, p, i, p, i, C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double), p, sz, p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -279,6 +284,35 @@ class Lattice:
         self._check(lib().lbm_profile_read(self._h, n, ms), "lbm_profile_read")
         return {"step": (n[0], ms[0]), "fixup": (n[1], ms[1])}
 
+    # -- reverse mode
+    def adjoint_work(self, T: int, K: int):
+        import torch
+        n = C.c_size_t()
+        rc = lib().lbm_adjoint_required_bytes(C.byref(self._c), int(T), int(K), C.byref(n))
+        if rc != 0:
+            raise LBMError(f"lbm_adjoint_required_bytes: {STATUS.get(rc, rc)}")
+        return torch.empty(n.value, dtype=torch.uint8, device=self.device)
+
+    def adjoint_forward(self, T: int, K: int, work=None, stream=None):
+        """T steps with checkpoints every K; returns (J, work)."""
+        work = work if work is not None else self.adjoint_work(T, K)
+        J = C.c_double()
+        self._check(lib().lbm_adjoint_forward(self._h, int(T), int(K), _ptr(work), work.numel(),
+                                              C.byref(J), _stream(stream)), "lbm_adjoint_forward")
+        return J.value, work
+
+    def adjoint_backward(self, T: int, K: int, work, seed=None, stream=None):
+        """(dJ/df0 as a float64 tensor, dJ/dU, dJ/dbeta) after adjoint_forward."""
+        import torch
+        g = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        gU, gB = C.c_double(), C.c_double()
+        sdt = DTYPE_F64 if seed is None or seed.dtype == torch.float64 else DTYPE_F32
+        self._check(lib().lbm_adjoint_backward(
+            self._h, int(T), int(K), _ptr(seed) if seed is not None else None, sdt, _ptr(g),
+            DTYPE_F64, C.byref(gU), C.byref(gB), _ptr(work), work.numel(), _stream(stream)),
+            "lbm_adjoint_backward")
+        return g, gU.value, gB.value
+
     def last_candidates(self, cap: int | None = None, stream=None):
         """(delta_s float64, site int32, selected int32) of the last step."""
         cap = cap if cap is not None else self.cfg.nx * self.cfg.ny
@@ -365,3 +399,41 @@ class Batch:
         st = lbm_stats()
         self._check(lib().lbm_batch_stats(self._h, i, C.byref(st), _stream(stream)), "lbm_batch_stats")
         return {n: int(getattr(st, n)) for n, _ in lbm_stats._fields_}
+
+
+def _kinetic_energy_function():
+    import torch
+
+    class KineticEnergy(torch.autograd.Function):
+        """J = 1/2 sum rho |u|^2 after T steps of the configured LBGK or
+        Ehrenfest step, as a differentiable function of the initial
+        populations f0 [Q, ny, nx], the lid velocity and beta (0-d tensors).
+        Forward runs the CUDA step with checkpoints every K steps; backward
+        runs the hand-written adjoint kernels (lbm_adjoint_backward)."""
+
+        @staticmethod
+        def forward(ctx, f0, lid_u, beta, cfg, T, K):
+            c = LBMConfig.from_dict(dict(cfg, lid_u=float(lid_u), beta=float(beta)))
+            lat = Lattice(c, device=f0.device)
+            dt = torch.float64 if c.precision == "fp64" else torch.float32
+            lat.set_state(f0.detach().to(dt).contiguous())
+            J, work = lat.adjoint_forward(T, K)
+            ctx.lat, ctx.work, ctx.T, ctx.K = lat, work, T, K
+            ctx.dtypes = (f0.dtype, lid_u.dtype, beta.dtype)
+            return torch.tensor(J, dtype=torch.float64, device=f0.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            g, gU, gB = ctx.lat.adjoint_backward(ctx.T, ctx.K, ctx.work)
+            df0, dU, dB = ctx.dtypes
+            dev = g.device
+            f64 = torch.float64
+            return ((gJ * g).to(df0), (gJ * torch.tensor(gU, dtype=f64, device=dev)).to(dU),
+                    (gJ * torch.tensor(gB, dtype=f64, device=dev)).to(dB), None, None, None)
+
+    return KineticEnergy
+
+
+def kinetic_energy(f0, lid_u, beta, cfg, T: int, K: int):
+    """Differentiable kinetic energy after T steps (see KineticEnergy)."""
+    return _kinetic_energy_function().apply(f0, lid_u, beta, cfg, T, K)

@@ -59,6 +59,11 @@ def lognormal_factors(shape: tuple, seed: int, amp: float) -> np.ndarray:
     return np.exp(amp * rng.standard_normal(shape))
 
 
+def normal_noise(shape: tuple, seed: int, sigma: float) -> np.ndarray:
+    """sigma * N(0, 1) samples (additive perturbation of a state)."""
+    return sigma * np.random.default_rng(seed).standard_normal(shape)
+
+
 def hot_spots(ny: int, nx: int, seed: int, count: int, amp: float) -> np.ndarray:
     """Per-site amplitude field that is zero except at `count` random sites,
     where it is amp * U(0.5, 1): used to plant a few strongly
