@@ -245,6 +245,47 @@ def run_batched(steps, warmup, fp64_mlups=None, separate=True):
     return out
 
 
+def run_small_configs(tube_steps=400, cavity_steps=2000):
+    """The two small configurations, timed through lbm_step (which replays
+    its two-step CUDA graph): the D1Q3 shock tube (800 sites, FP64, 400
+    steps, mu s per step) and the 257^2 cavity (Re 5000, U 0.1, FP64 and
+    FP32, MLUPS; its 2.4-4.8 MB state stays in L2)."""
+    import torch
+    from paper_1110_0270_gb300 import lbm
+    from paper_1110_0270_gb300 import workloads as WL
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed_steps(lat, n):
+        lat.step(2)
+        torch.cuda.synchronize()
+        e0.record(s)
+        lat.step(n)
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    out = {"tube_us_per_step": {}, "cavity257_mlups": {}}
+    cfg, init = WL.shock_tube(800, 1e-9)
+    for coll in ["lbgk", "elbm", "ehrenfest", "median", "mrt"]:
+        lat = lbm.Lattice(dict(cfg, collision=coll, precision="fp64", topk=4, delta=1e-3))
+        lat.init(init["rho"], init["ux"])
+        out["tube_us_per_step"][coll] = round(timed_steps(lat, tube_steps) * 1e3 / tube_steps, 3)
+    cfg, init = WL.cavity(257, 5000.0, 0.1)
+    for prec in ["fp64", "fp32"]:
+        for coll in ["lbgk", "elbm", "ehrenfest", "median", "mrt"]:
+            lat = lbm.Lattice(dict(cfg, collision=coll, precision=prec, topk=64, delta=1e-3,
+                                   s_e=1.64, s_eps=1.64, s_q=1.2))
+            lat.init(init["rho"], init["ux"], init["uy"])
+            n = cavity_steps if coll != "elbm" else cavity_steps // 4
+            ms = timed_steps(lat, n)
+            key = f"{coll}/{prec}"
+            out["cavity257_mlups"][key] = round(257 * 257 * n / (ms * 1e-3) / 1e6, 1)
+            if lat.stats()["diverged"]:
+                out.setdefault("cavity257_diverged", []).append(key)
+    return out
+
+
 def run_adjoint(T=4000, K=100, n=513, fd=True):
     """The adjoint configuration: D2Q9 cavity n^2, Re 1000, U 0.1, FP32,
     Ehrenfest k = 32, f0 = equilibrium at rest + N(0, 1e-4) noise; gradient
@@ -419,6 +460,8 @@ def gpu_arm(args):
         result["clocks"] = sampler.summary(t0, t1) if sampler else None
         if not args.no_variants:
             result["variants"] = run_variants(args.side, args.variant_steps, 3)
+        if not args.no_small:
+            result["small_configs"] = run_small_configs()
         if args.adjoint_steps > 0:
             result["adjoint"] = run_adjoint(args.adjoint_steps, 100)
         if args.batch_steps > 0:
@@ -485,6 +528,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16_dev", "bf16_dev"])
     ap.add_argument("--variant-steps", type=int, default=100)
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-small", action="store_true", help="skip the tube and 257^2 runs")
     ap.add_argument("--adjoint-steps", type=int, default=4000,
                     help="T of the adjoint run (0 skips it)")
     ap.add_argument("--batch-steps", type=int, default=20,

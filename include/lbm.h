@@ -143,7 +143,8 @@ lbm_status lbm_required_bytes(const lbm_config* cfg, size_t* bytes);
 /* Creates a context over the caller's device allocation dev_mem (256-byte
  * aligned, at least lbm_required_bytes) on the current CUDA device.  The
  * populations are undefined until lbm_init or lbm_set_state.  Clears the
- * scratch with a synchronous cudaMemset. */
+ * scratch with a synchronous cudaMemset and captures the kernels of two
+ * steps (one A-A period) into a CUDA graph that lbm_step replays. */
 lbm_status lbm_create(const lbm_config* cfg, void* dev_mem, size_t bytes, lbm_ctx** out);
 
 /* Releases the host-side context (not the caller's device memory). */
@@ -169,7 +170,10 @@ lbm_status lbm_set_state(lbm_ctx* ctx, const void* f, int dtype, void* stream);
  * f[Q][ny][nx] of the given dtype (undoing the A-A layout of odd steps). */
 lbm_status lbm_get_state(lbm_ctx* ctx, void* f, int dtype, void* stream);
 
-/* Advances nsteps >= 0 steps.  Allocates nothing. */
+/* Advances nsteps >= 0 steps.  Allocates nothing.  Pairs of steps that start
+ * at an even step count replay the context's graph (one launch instead of
+ * two to four, which matters for small lattices); the rest, and every step
+ * while kernel tracing is on, are launched one by one. */
 lbm_status lbm_step(lbm_ctx* ctx, int nsteps, void* stream);
 
 /* Density rho[ny][nx] and velocity u[2][ny][nx] (u_x plane then u_y plane;

@@ -160,6 +160,50 @@ lbm_status reset_counters(lbm_ctx* ctx, cudaStream_t s) {
 
 }  // namespace
 
+namespace {
+
+// The kernels of one step with counter slot `cslot` and A-A parity `odd`.
+cudaError_t enqueue_one_step(lbm_ctx* ctx, bool odd, int cslot, cudaStream_t s) {
+    const int coll = ctx->cfg.collision;
+    Params q = ctx->p;
+    q.cslot = cslot;
+    cudaError_t e = traced(ctx, LBM_KERNEL_STEP, s, [&] {
+        return dispatch(ctx->cfg.precision, [&](auto L) { return decltype(L)::step(ctx->Q, coll, odd, q, s); });
+    });
+    if (e == cudaSuccess && limiter(coll))
+        e = traced(ctx, LBM_KERNEL_FIXUP, s, [&] {
+            return dispatch(ctx->cfg.precision,
+                            [&](auto L) { return decltype(L)::fixup(ctx->Q, coll, odd, q, s, ctx->nsm); });
+        });
+    return e;
+}
+
+// Captures the two steps of one A-A period (even with counter slot 0, odd
+// with slot 1) into a graph on a private stream; lbm_step replays it.
+cudaError_t build_step_graph(lbm_ctx* ctx) {
+    cudaStream_t cap;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e1 = enqueue_one_step(ctx, false, 0, cap);
+        if (e1 == cudaSuccess) e1 = enqueue_one_step(ctx, true, 1, cap);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(cap, &g);
+        if (e1 != cudaSuccess) e = e1;
+        if (e == cudaSuccess) {
+            ctx->graph = g;
+            e = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+        } else if (g) {
+            cudaGraphDestroy(g);
+        }
+    }
+    cudaStreamDestroy(cap);
+    return e;
+}
+
+}  // namespace
+
 extern "C" {
 
 int lbm_abi_version(void) { return LBM_ABI_VERSION; }
@@ -264,6 +308,7 @@ lbm_status lbm_create(const lbm_config* cfg, void* dev_mem, size_t bytes, lbm_ct
     p.ds_field = ctx->base + L.field_off;
     ctx->staging = (double*)(ctx->base + L.staging_off);
     cudaError_t e = cudaMemset(ctx->base + L.cnt_off, 0, align_up(CNT_WORDS * 4 + ST_WORDS * 8 + 64));
+    if (e == cudaSuccess) e = build_step_graph(ctx);
     if (e != cudaSuccess) {
         delete ctx;
         return LBM_ERR_CUDA;
@@ -328,24 +373,21 @@ lbm_status lbm_get_state(lbm_ctx* ctx, void* f, int dtype, void* stream) {
 lbm_status lbm_step(lbm_ctx* ctx, int nsteps, void* stream) {
     if (!ctx) return LBM_ERR_ARG;
     if (nsteps < 0) return fail(ctx, LBM_ERR_ARG, "nsteps must be >= 0");
-    const int coll = ctx->cfg.collision;
-    for (int k = 0; k < nsteps; ++k) {
-        Params q = ctx->p;
-        q.cslot = (int)(ctx->t & 1);
-        const bool odd = ctx->parity != 0;
-        LBM_CK(ctx, traced(ctx, LBM_KERNEL_STEP, S(stream), [&] {
-                   return dispatch(ctx->cfg.precision, [&](auto L) {
-                       return decltype(L)::step(ctx->Q, coll, odd, q, S(stream));
-                   });
-               }));
-        if (limiter(coll))
-            LBM_CK(ctx, traced(ctx, LBM_KERNEL_FIXUP, S(stream), [&] {
-                       return dispatch(ctx->cfg.precision, [&](auto L) {
-                           return decltype(L)::fixup(ctx->Q, coll, odd, q, S(stream), ctx->nsm);
-                       });
-                   }));
+    // parity == t & 1 always (both reset together), so the graph, whose
+    // steps use counter slots 0 and 1, starts at an even step
+    int k = 0;
+    const bool use_graph = ctx->graph_exec && !ctx->profiling;
+    while (k < nsteps) {
+        if (use_graph && ctx->parity == 0 && nsteps - k >= 2) {
+            LBM_CK(ctx, cudaGraphLaunch(ctx->graph_exec, S(stream)));
+            ctx->t += 2;
+            k += 2;
+            continue;
+        }
+        LBM_CK(ctx, enqueue_one_step(ctx, ctx->parity != 0, (int)(ctx->t & 1), S(stream)));
         ctx->parity ^= 1;
         ctx->t += 1;
+        ++k;
     }
     return LBM_OK;
 }

@@ -56,13 +56,15 @@ __global__ void __launch_bounds__(256)
     unsigned M = sp.counters[cslot];
     if (M > (unsigned)sp.cand_cap) M = (unsigned)sp.cand_cap;
     unsigned n = 0;
-    for (unsigned j = threadIdx.x; j < M; j += blockDim.x) {
-        T f[Q];
-        load_candidate<Q, ST>(sp, (int)j, f);
-        const double d = delta_s_fp64<Q, T>(f, sp.eq);
-        const bool c = d > sp.delta;
-        sp.cand_ds[j] = c ? d : -1.0;
-        n += c;
+    const unsigned groups = blockDim.x >> 4;
+    for (unsigned base = 0; base < M; base += groups) {
+        const unsigned j = base + (threadIdx.x >> 4);
+        const double d = delta_s_group<Q, ST>(sp, j, j < M);
+        if (j < M && (threadIdx.x & 15) == 0) {
+            const bool c = d > sp.delta;
+            sp.cand_ds[j] = c ? d : -1.0;
+            n += c;
+        }
     }
     if (n) atomicAdd(&s_valid, n);
     __syncthreads();

@@ -27,8 +27,13 @@ struct lbm_ctx {
     std::vector<cudaEvent_t> ev;  // pairs (start, end)
     std::vector<int> ev_kind;
     size_t ev_used = 0;
+    // two steps (both A-A parities) captured once at creation and replayed
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
     ~lbm_ctx() {
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        if (graph) cudaGraphDestroy(graph);
     }
 };
 

@@ -77,8 +77,10 @@ __device__ __forceinline__ void site_update(const Params& p, int x, int y, int& 
         load_general<Q, ST, ODD>(p, x, y, f);
     T rho, ux, uy;
     moments<Q, T>(f, rho, ux, uy);
+    // once set the flag is only read: a diverged lattice would otherwise
+    // send every site's atomic to one address
     if (!(rho > T(0)) || !(fabs(ux) < T(1e30)) || !(fabs(uy) < T(1e30)))
-        atomicExch(&p.counters[CNT_DIVERGED], 1u);
+        if (*(volatile unsigned*)&p.counters[CNT_DIVERGED] == 0u) atomicExch(&p.counters[CNT_DIVERGED], 1u);
     if (COLL == LBM_ELBM) {
         double fd[Q], fe[Q], r, a, b;
 #pragma unroll
@@ -154,6 +156,67 @@ __device__ __forceinline__ void load_candidate(const Params& p, int j, typename 
     const T* cf = (const T*)p.cand_f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) f[i] = cf[(int64_t)i * p.cand_cap + j];
+}
+
+// FP64 Delta S of candidate record j, computed by a group of 16 lanes (lane
+// q < Q holds population q): the moments and the sum over populations are
+// shuffle reductions, so the dependent chain of FP64 operations - the
+// latency of this step on GB300's narrow FP64 pipe - is about one
+// population's instead of Q.  All 16 lanes of the group must call it; lanes
+// of a group with j >= M pass valid = false and get 0.
+template <int Q, class ST>
+__device__ __forceinline__ double delta_s_group(const Params& p, unsigned j, bool valid) {
+    using T = typename ST::T;
+    const int q = threadIdx.x & 15;
+    const unsigned gmask = 0xffffu << (threadIdx.x & 16);
+    const bool act = valid && q < Q;
+    const int cx = Q == 3 ? q - 1 : ((q == 1 || q == 2 || q == 8) ? 1 : ((q == 4 || q == 5 || q == 6) ? -1 : 0));
+    const int cy = Q == 3 ? 0 : ((q == 6 || q == 7 || q == 8) ? 1 : ((q == 2 || q == 3 || q == 4) ? -1 : 0));
+    double f = 0.0;
+    if (act) f = (double)((const T*)p.cand_f)[(int64_t)q * p.cand_cap + j];
+    double r = f, jx = cx * f, jy = cy * f;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+        r += __shfl_xor_sync(gmask, r, o);
+        jx += __shfl_xor_sync(gmask, jx, o);
+        jy += __shfl_xor_sync(gmask, jy, o);
+    }
+    double term = 0.0;
+    bool neg = false;
+    if (act) {
+        const double ux = jx / r, uy = jy / r;
+        double ax[3], ay[3];
+        if (p.eq == LBM_EQ_ENTROPIC) {
+            eq1d_entropic<double>(ux, ax[0], ax[1], ax[2]);
+            eq1d_entropic<double>(uy, ay[0], ay[1], ay[2]);
+        } else {
+            eq1d_poly<double>(ux, ax[0], ax[1], ax[2]);
+            eq1d_poly<double>(uy, ay[0], ay[1], ay[2]);
+        }
+        double fe;
+        if (Q == 9 && p.eq == LBM_EQ_POLY_STD) {
+            // same values as equilibrium<9, double>: the rest population is
+            // rho minus the others
+            double fi[9], rest = r;
+            const double uu = ux * ux + uy * uy;
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const double cu = Lat<9>::cx(i) * ux + Lat<9>::cy(i) * uy;
+                fi[i] = Lat<9>::w(i) * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+                rest -= fi[i];
+            }
+            fi[0] = rest;
+            fe = fi[q];
+        } else {
+            fe = Q == 3 ? r * ax[cx + 1] : r * ax[cx + 1] * ay[cy + 1];
+        }
+        neg = f < 0.0 || !(fe > 0.0);
+        term = fe * gfun_d((f - fe) / fe);
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) term += __shfl_xor_sync(gmask, term, o);
+    neg = __any_sync(gmask, neg);
+    return neg ? __longlong_as_double(0x7ff0000000000000ULL) : term;
 }
 
 // Ehrenfest regularisation (Section 4): the k candidates with the largest
@@ -315,13 +378,17 @@ __global__ void __launch_bounds__(256) ehrenfest_eval_select(Params p) {
     unsigned M = p.counters[p.cslot];
     if (M > (unsigned)p.cand_cap) M = (unsigned)p.cand_cap;
     unsigned n = 0;
-    for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
-        T f[Q];
-        load_candidate<Q, ST>(p, (int)j, f);
-        const double d = delta_s_fp64<Q, T>(f, p.eq);
-        const bool c = d > p.delta;
-        p.cand_ds[j] = c ? d : -1.0;
-        n += c;
+    // one record per 16-lane group
+    const unsigned groups = gridDim.x * (blockDim.x >> 4);
+    const unsigned g0 = blockIdx.x * (blockDim.x >> 4) + (threadIdx.x >> 4);
+    for (unsigned base = 0; base < M; base += groups) {
+        const unsigned j = base + g0;
+        const double d = delta_s_group<Q, ST>(p, j, j < M);
+        if (j < M && (threadIdx.x & 15) == 0) {
+            const bool c = d > p.delta;
+            p.cand_ds[j] = c ? d : -1.0;
+            n += c;
+        }
     }
     n = __reduce_add_sync(0xffffffffu, n);
     if ((threadIdx.x & 31) == 0 && n) atomicAdd(&p.counters[CNT_NVALID], n);
