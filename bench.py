@@ -46,6 +46,27 @@ def workload_cfg(collision="ehrenfest", precision="fp32", n=N_SIDE):
     return cfg, init
 
 
+# DRAM bytes per launch of the headline step kernel from the full-size ncu
+# launch list (profiles/step_kernel_d2q9_fp32_ehrenfest_4097.md), valid only
+# for the kernel sources it was taken on.
+TRAFFIC_CAPTURE = {"sources_sha256_16": "eee112cb78e26de8", "collision": "ehrenfest",
+                   "precision": "fp32", "side": 4097, "bytes_per_launch": 1153.0e6}
+TRAFFIC_SOURCES = ["lbm_device.cuh", "lbm_kernels.cuh", "lbm_params.h", "lbm_kernels_f32.cu"]
+
+
+def captured_traffic(collision, precision, side):
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_1110_0270_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    c = TRAFFIC_CAPTURE
+    if (h.hexdigest()[:16] == c["sources_sha256_16"] and collision == c["collision"]
+            and precision == c["precision"] and side == c["side"]):
+        return c["bytes_per_launch"]
+    return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -449,7 +470,8 @@ def gpu_arm(args):
                    "last_step_candidates": st["candidates_last"],
                    "last_step_screened": st["screened_last"]},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
-                     "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                     "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                     "traffic": captured_traffic(args.collision, args.precision, args.side),
                      "kernel": f"step_kernel<D2Q9, {args.precision}, {args.collision}>",
                      "algorithmic_bytes_per_launch": alg,
                      "kernel_ms": round(k_ms, 5), "peak_kind": f"{peak_kind} hbm_gbs",
