@@ -182,7 +182,10 @@ def run_variants(n_side, steps, warmup):
             lat = lbm.Lattice(cfg)
             lat.init(init["rho"], init["ux"], init["uy"])
             k = max(5, steps // 10) if coll == "elbm" else steps
-            ms, prof, _ = time_steps(lat, k, warmup, profile=True)
+            # the step as lbm_step runs it (graph replay), then the same
+            # number of steps again with per-kernel events for the split
+            ms, _, _ = time_steps(lat, k, warmup)
+            _, prof, _ = time_steps(lat, k, 2, profile=True)
             per = ms / k
             mlups = N / (per * 1e-3) / 1e6
             alg = 2 * Q * BYTES_PER_POP[precision] * N
@@ -191,7 +194,9 @@ def run_variants(n_side, steps, warmup):
                 "mlups": round(mlups, 1), "ms_per_step": round(per, 4),
                 "hbm_frac_step": round(alg / (per * 1e-3) / 1e9 / hbm, 4),
                 "hbm_frac_step_kernel": round(alg / (kstep * 1e-3) / 1e9 / hbm, 4),
-                "steps": k}
+                "kernel_ms": round(kstep, 5), "steps": k}
+            if prof["fixup"][0]:
+                out[f"{coll}/{precision}"]["fixup_ms"] = round(prof["fixup"][1] / prof["fixup"][0], 5)
             del lat
             torch.cuda.empty_cache()
     return out

@@ -167,6 +167,7 @@ cudaError_t enqueue_one_step(lbm_ctx* ctx, bool odd, int cslot, cudaStream_t s) 
     const int coll = ctx->cfg.collision;
     Params q = ctx->p;
     q.cslot = cslot;
+    q.pdl = ctx->profiling ? 0 : 1;  // the timing events bracket whole kernels
     cudaError_t e = traced(ctx, LBM_KERNEL_STEP, s, [&] {
         return dispatch(ctx->cfg.precision, [&](auto L) { return decltype(L)::step(ctx->Q, coll, odd, q, s); });
     });

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(256)
     batch_median_kernel(const Params* __restrict__ insts, const int* __restrict__ ids, int cslot) {
     __shared__ Params sp;
     load_params(sp, insts, ids[blockIdx.x], cslot);
-    median_apply<Q, ST, ODD>(sp, threadIdx.x, blockDim.x);
+    median_apply<Q, ST, ODD>(sp, threadIdx.x >> 4, blockDim.x >> 4);
 }
 
 template <class ST>

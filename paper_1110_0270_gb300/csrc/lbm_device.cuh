@@ -51,33 +51,95 @@ template <> struct Lat<9> {
 // formats hold the deviation f_i - W_i (round to nearest even) so that the
 // format's precision is spent on the part that varies.
 // ---------------------------------------------------------------------------
+// ld2 / st2 move the two consecutive elements p[0], p[1] (p 2-element
+// aligned) with one vector access and, for the 16-bit formats, one packed
+// conversion; enc / enc2 / dec / dec2 are the conversions alone (S2: the
+// stored pair type).
 struct StF64 {
     using S = double;
     using T = double;
     static constexpr int code = LBM_FP64;
+    using S2 = double2;
+    __device__ static S enc(T v, T) { return v; }
+    __device__ static S2 enc2(T a, T b, T) { return make_double2(a, b); }
+    __device__ static T dec(S v, T) { return v; }
+    __device__ static void dec2(S2 v, T, T& a, T& b) {
+        a = v.x;
+        b = v.y;
+    }
     __device__ static T ld(const S* p, T) { return *p; }
     __device__ static void st(S* p, T v, T) { *p = v; }
+    __device__ static void ld2(const S* p, T, T& a, T& b) {
+        const double2 v = *(const double2*)p;
+        a = v.x;
+        b = v.y;
+    }
+    __device__ static void st2(S* p, T a, T b, T) { *(double2*)p = make_double2(a, b); }
 };
 struct StF32 {
     using S = float;
     using T = float;
     static constexpr int code = LBM_FP32;
+    using S2 = float2;
+    __device__ static S enc(T v, T) { return v; }
+    __device__ static S2 enc2(T a, T b, T) { return make_float2(a, b); }
+    __device__ static T dec(S v, T) { return v; }
+    __device__ static void dec2(S2 v, T, T& a, T& b) {
+        a = v.x;
+        b = v.y;
+    }
     __device__ static T ld(const S* p, T) { return *p; }
     __device__ static void st(S* p, T v, T) { *p = v; }
+    __device__ static void ld2(const S* p, T, T& a, T& b) {
+        const float2 v = *(const float2*)p;
+        a = v.x;
+        b = v.y;
+    }
+    __device__ static void st2(S* p, T a, T b, T) { *(float2*)p = make_float2(a, b); }
 };
 struct StBF16 {
     using S = __nv_bfloat16;
     using T = float;
     static constexpr int code = LBM_BF16_DEV;
+    using S2 = __nv_bfloat162;
+    __device__ static S enc(T v, T w) { return __float2bfloat16_rn(v - w); }
+    __device__ static S2 enc2(T a, T b, T w) { return __floats2bfloat162_rn(a - w, b - w); }
+    __device__ static T dec(S v, T w) { return w + __bfloat162float(v); }
+    __device__ static void dec2(S2 v, T w, T& a, T& b) {
+        const float2 u = __bfloat1622float2(v);
+        a = w + u.x;
+        b = w + u.y;
+    }
     __device__ static T ld(const S* p, T w) { return w + __bfloat162float(*p); }
     __device__ static void st(S* p, T v, T w) { *p = __float2bfloat16_rn(v - w); }
+    __device__ static void ld2(const S* p, T w, T& a, T& b) {
+        const float2 v = __bfloat1622float2(*(const __nv_bfloat162*)p);
+        a = w + v.x;
+        b = w + v.y;
+    }
+    __device__ static void st2(S* p, T a, T b, T w) { *(__nv_bfloat162*)p = __floats2bfloat162_rn(a - w, b - w); }
 };
 struct StF16 {
     using S = __half;
     using T = float;
     static constexpr int code = LBM_FP16_DEV;
+    using S2 = __half2;
+    __device__ static S enc(T v, T w) { return __float2half_rn(v - w); }
+    __device__ static S2 enc2(T a, T b, T w) { return __floats2half2_rn(a - w, b - w); }
+    __device__ static T dec(S v, T w) { return w + __half2float(v); }
+    __device__ static void dec2(S2 v, T w, T& a, T& b) {
+        const float2 u = __half22float2(v);
+        a = w + u.x;
+        b = w + u.y;
+    }
     __device__ static T ld(const S* p, T w) { return w + __half2float(*p); }
     __device__ static void st(S* p, T v, T w) { *p = __float2half_rn(v - w); }
+    __device__ static void ld2(const S* p, T w, T& a, T& b) {
+        const float2 v = __half22float2(*(const __half2*)p);
+        a = w + v.x;
+        b = w + v.y;
+    }
+    __device__ static void st2(S* p, T a, T b, T w) { *(__half2*)p = __floats2half2_rn(a - w, b - w); }
 };
 
 // ---------------------------------------------------------------------------
@@ -186,12 +248,18 @@ __device__ __forceinline__ double gfun_d(double x) {
     return (1.0 + x) * log1p(x) - x;
 }
 
+// P(x) = sum_{k <= K} (-1)^k x^k / ((k+1)(k+2)), so that g(x) ~ x^2 P(x).
 template <int K>
-__device__ __forceinline__ float gseries_f(float x) {
+__device__ __forceinline__ float gpoly_f(float x) {
     float p = ((K & 1) ? -1.0f : 1.0f) / (float)((K + 1) * (K + 2));
 #pragma unroll
     for (int k = K - 1; k >= 0; --k) p = fmaf(p, x, ((k & 1) ? -1.0f : 1.0f) / (float)((k + 1) * (k + 2)));
-    return x * x * p;
+    return p;
+}
+
+template <int K>
+__device__ __forceinline__ float gseries_f(float x) {
+    return x * x * gpoly_f<K>(x);
 }
 
 __device__ __forceinline__ float gfun_f(float x) {
@@ -245,46 +313,92 @@ __device__ __forceinline__ T delta_s_t(const T* f, const T* feq) {
     return neg ? T(INFINITY) : s;
 }
 
-// Upper bound on Delta S from its quadratic form: with a = max_i |x_i| < 1,
-// g(x) <= x^2 / (2 (1 - a)), so Delta S <= q / (2 (1 - a)), q = sum d^2 / f*,
-// d = f - f*.  Evaluated in FP32 (no FP64 instruction; GB300's FP64 rate is
-// a small fraction of its FP32 rate).  Rounding of f, f* and d to FP32 moves
-// q by at most ~3e-7 sqrt(q rho) + 2e-6 q (|d| summed by Cauchy-Schwarz),
-// covered by the relative 1e-3 and absolute 1e-6 sqrt(q rho) slack.
-// Returns true when the site may exceed delta and needs the FP64 value.
-// Cheaper and looser form for the Ehrenfest screen: with m = min_i f*_i,
-// q <= sum d^2 / m and a <= max |d| / m, so for a < 1/2 Delta S <= sum d^2 / m.
-// One reciprocal per site; the looseness (up to ~30x near equilibrium) only
-// lets more sites through to the exact FP64 test.
+// Limiter screens (FP32, no FP64 instruction: GB300's FP64 rate is a small
+// fraction of its FP32 rate).  Each returns true when the site may exceed
+// delta and needs the exact FP64 Delta S.  With d = f - f*, x = d / f* and
+// q = sum d^2 / f*, rounding f* and d to FP32 moves q by at most about
+// 3e-7 sqrt(q rho) + 2e-6 q (|d| summed by Cauchy-Schwarz); the relative
+// 1e-3 and absolute 1e-6 sqrt(q rho) slack covers it.
+//
+// Ehrenfest: g(x) <= x^2 for |x| < 1/2, and with m = min_i f*_i > 0 and
+// s2 = sum d^2, max |x| <= max |d| / m <= sqrt(s2) / m, so s2 < m^2 / 4 gives
+// Delta S <= sum d^2 / f* <= s2 / m.  One reciprocal per site and no
+// per-population division; the looseness (up to ~30x near equilibrium) only
+// lets more sites through to the exact test.  A negative population fails
+// the first test (|d_i| > f*_i >= m).
 template <int Q>
-__device__ __forceinline__ bool maybe_above_loose(const float* f, const float* feq, float delta) {
-    float s2 = 0.f, dmax = 0.f, m = feq[0], rho = 0.f;
+__device__ __forceinline__ bool maybe_above_loose(const float* f, const float* feq, float rho, float delta) {
+    float s2 = 0.f, m = feq[0];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const float d = f[i] - feq[i];
         s2 = fmaf(d, d, s2);
-        dmax = fmaxf(dmax, fabsf(d));
         m = fminf(m, feq[i]);
-        rho += f[i];
     }
-    if (!(dmax < 0.5f * m)) return true;  // also NaN and non-positive f*
+    if (!(m > 0.f) || !(s2 < 0.25f * m * m)) return true;  // also NaN
     const float q = s2 * __frcp_rn(m);
     return q * 1.001f + 1e-6f * sqrtf(q * fabsf(rho)) >= delta;
 }
 
-template <int Q>
-__device__ __forceinline__ bool maybe_above(const float* f, const float* feq, float delta) {
-    float q = 0.f, a = 0.f, rho = 0.f;
+// Median: the site's Delta S in the arithmetic type is computed anyway (the
+// filter's field), so it is the screen itself.  In the form sum f* g(x) the
+// rounding of the mass of f* cancels to first order (dDelta S / df*_i =
+// -x_i), leaving sum x_i df*_i <= sqrt(q) sqrt(sum df*_i^2 / f*_i), inside the
+// same slack; the series and log1p evaluation of g is accurate to ~1e-5
+// relative.  +inf (a non-positive population) and NaN pass.
+template <int Q, class T>
+__device__ __forceinline__ T delta_s_and_q(const T* f, const T* feq, T& q);
+
+// FP32: one series length per site, chosen by max |x| (the tiers of gfun_f),
+// so the populations share one branch; f* g(x) = d x P(x) with
+// g(x) = x^2 P(x).
+template <>
+__device__ __forceinline__ float delta_s_and_q<9, float>(const float* f, const float* feq, float& q) {
+    float x[9], dx[9], amax = 0.f, fmin_ = f[0], emin = feq[0];
+    q = 0.f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const float d = f[i] - feq[i];
+        x[i] = __fdividef(d, feq[i]);
+        dx[i] = d * x[i];
+        q += dx[i];
+        amax = fmaxf(amax, fabsf(x[i]));
+        fmin_ = fminf(fmin_, f[i]);
+        emin = fminf(emin, feq[i]);
+    }
+    if (!(fmin_ >= 0.f) || !(emin > 0.f)) return INFINITY;
+    float s = 0.f;
+    if (amax < 0.03125f) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) s = fmaf(dx[i], gpoly_f<4>(x[i]), s);
+    } else if (amax < 0.25f) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) s = fmaf(dx[i], gpoly_f<11>(x[i]), s);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) s = fmaf(feq[i], gfun_f(x[i]), s);
+    }
+    return s;
+}
+
+template <int Q, class T>
+__device__ __forceinline__ T delta_s_and_q(const T* f, const T* feq, T& q) {
+    T s = T(0);
+    q = T(0);
+    bool neg = false;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const float d = f[i] - feq[i];
-        q += __fdividef(d * d, feq[i]);
-        a = fmaxf(a, fabsf(__fdividef(d, feq[i])));
-        rho += f[i];
+        neg |= (f[i] < T(0)) || !(feq[i] > T(0));
+        const T d = f[i] - feq[i];
+        const T x = rel_dev(d, feq[i]);
+        s += feq[i] * gfun<T>(x);
+        q += d * x;
     }
-    if (!(a < 0.5f)) return true;  // also NaN
-    const float lhs = 0.5f * q * 1.001f + 1e-6f * sqrtf(q * fabsf(rho));
-    return lhs >= delta * (1.0f - a);
+    return neg ? T(INFINITY) : s;
+}
+
+__device__ __forceinline__ bool median_maybe_above(float ds, float q, float rho, float delta) {
+    return !(ds * 1.001f + 1e-6f * sqrtf(fabsf(q * rho)) < delta);
 }
 
 // ---------------------------------------------------------------------------
@@ -311,7 +425,7 @@ template <int Q, class T>
 __device__ __forceinline__ void lbgk(const T* f, const T* feq, T beta, T* F) {
     T om = T(2) * beta;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) F[i] = f[i] + om * (feq[i] - f[i]);
+    for (int i = 0; i < Q; ++i) F[i] = f[i] - om * (f[i] - feq[i]);  // shares d = f - f* with the screens
 }
 
 // Positivity rule (Section 4, Eq. StrLine): a state with a negative

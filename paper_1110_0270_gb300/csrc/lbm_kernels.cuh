@@ -22,6 +22,17 @@ namespace lbm {
 constexpr int kBlockX = 128;
 constexpr int kBlockY = 2;
 
+// Programmatic dependent launch: a step kernel may be launched while the
+// previous kernel of the stream finishes its last wave.  Every kernel so
+// launched waits, before its first global memory access, until the previous
+// grid has completed and its writes are visible; each CTA then allows the
+// next kernel to launch (it starts once every CTA of this grid has started).
+// Without the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ int lane_id() {
     return (threadIdx.y * blockDim.x + threadIdx.x) & 31;
 }
@@ -43,38 +54,37 @@ __device__ __forceinline__ void record_candidate(const Params& p, int x, int y, 
     }
 }
 
-// Limiter screen of the pre-collision state.  A division-free FP32 bound on
-// Delta S (Eq. DelS) keeps the sites that may exceed delta; their FP64 value
-// decides later.  The median filter also needs the Delta S field of every
-// site (in the arithmetic type; FP64 in FP64 mode).
+// Limiter screen of the pre-collision state: the sites that may exceed
+// delta (FP32 screens of Eq. DelS) are appended to the candidate list; their
+// FP64 value decides later.  The median filter also writes the Delta S field
+// of every site (in the arithmetic type; FP64 in FP64 mode).
 template <int Q, class T, int COLL>
 __device__ __forceinline__ void limiter_screen(const Params& p, int x, int y, const T* f,
-                                               const T* feq) {
-    if (COLL == LBM_MEDIAN) ((T*)p.ds_field)[(int64_t)y * p.nx + x] = delta_s_t<Q, T>(f, feq);
-    float ff[Q], fq[Q];
+                                               const T* feq, T rho) {
+    bool maybe;
+    if (COLL == LBM_MEDIAN) {
+        T q;
+        const T ds = delta_s_and_q<Q, T>(f, feq, q);
+        ((T*)p.ds_field)[(int64_t)y * p.nx + x] = ds;
+        maybe = median_maybe_above((float)ds, (float)q, (float)rho, p.delta_f);
+    } else {
+        float ff[Q], fq[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        ff[i] = (float)f[i];
-        fq[i] = (float)feq[i];
+        for (int i = 0; i < Q; ++i) {
+            ff[i] = (float)f[i];
+            fq[i] = (float)feq[i];
+        }
+        maybe = maybe_above_loose<Q>(ff, fq, (float)rho, p.delta_f);
     }
-    const bool maybe = COLL == LBM_MEDIAN ? maybe_above<Q>(ff, fq, p.delta_f)
-                                          : maybe_above_loose<Q>(ff, fq, p.delta_f);
     if (maybe) record_candidate<Q, T>(p, x, y, f);
 }
 
-// The whole step for the site (x, y): load (streaming in odd steps), moments,
-// equilibrium, limiter screen, collision, store.
-template <int Q, class ST, int COLL, bool ODD>
-__device__ __forceinline__ void site_update(const Params& p, int x, int y, int& e_code,
-                                            int& e_iters) {
+// Collision of one site, pre-collision f to post-collision F: moments,
+// divergence check, equilibrium, limiter screen, collision, exact mass.
+template <int Q, class ST, int COLL>
+__device__ __forceinline__ void collide_site(const Params& p, int x, int y, const typename ST::T* f,
+                                             typename ST::T* F, int& e_code, int& e_iters) {
     using T = typename ST::T;
-    T f[Q], F[Q];
-    const bool interior = x > 0 && x < p.nx - 1 && (Q == 3 || (y > 0 && y < p.ny - 1));
-    const int o = y * p.pitch + x;
-    if (interior)
-        load_interior<Q, ST, ODD>(p, o, f);
-    else
-        load_general<Q, ST, ODD>(p, x, y, f);
     T rho, ux, uy;
     moments<Q, T>(f, rho, ux, uy);
     // once set the flag is only read: a diverged lattice would otherwise
@@ -96,7 +106,7 @@ __device__ __forceinline__ void site_update(const Params& p, int x, int y, int& 
     } else {
         T feq[Q];
         equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
-        if (COLL == LBM_EHRENFEST || COLL == LBM_MEDIAN) limiter_screen<Q, T, COLL>(p, x, y, f, feq);
+        if (COLL == LBM_EHRENFEST || COLL == LBM_MEDIAN) limiter_screen<Q, T, COLL>(p, x, y, f, feq, rho);
         if (COLL == LBM_MRT && Q == 9) {
             mrt_d2q9<T>(f, feq, p.mrt, p.mrt_f, F);
         } else {
@@ -107,6 +117,22 @@ __device__ __forceinline__ void site_update(const Params& p, int x, int y, int& 
         }
     }
     conserve_mass<Q, T>(rho, F);
+}
+
+// The whole step for the site (x, y): load (streaming in odd steps),
+// collision, store.
+template <int Q, class ST, int COLL, bool ODD>
+__device__ __forceinline__ void site_update(const Params& p, int x, int y, int& e_code,
+                                            int& e_iters) {
+    using T = typename ST::T;
+    T f[Q], F[Q];
+    const bool interior = x > 0 && x < p.nx - 1 && (Q == 3 || (y > 0 && y < p.ny - 1));
+    const int o = y * p.pitch + x;
+    if (interior)
+        load_interior<Q, ST, ODD>(p, o, f);
+    else
+        load_general<Q, ST, ODD>(p, x, y, f);
+    collide_site<Q, ST, COLL>(p, x, y, f, F, e_code, e_iters);
     if (interior)
         store_interior<Q, ST, ODD>(p, o, F);
     else
@@ -129,8 +155,16 @@ __device__ __forceinline__ void elbm_stats(const Params& p, int e_code, int e_it
     }
 }
 
+// Six resident 256-thread CTAs per SM (at most 40 registers a thread) for
+// the FP32-arithmetic limiters, MRT and positivity: the streaming step needs
+// the warps to hide HBM latency.  0 leaves the choice to the compiler (LBGK
+// fits in 32-38 registers by itself; ELBM and FP64 storage are not capped).
+template <class ST, int COLL>
+constexpr int kMinBlocks = (COLL != LBM_ELBM && COLL != LBM_LBGK && sizeof(typename ST::T) == 4) ? 6 : 0;
+
 template <int Q, class ST, int COLL, bool ODD>
-__global__ void __launch_bounds__(kBlockX* kBlockY) step_kernel(Params p) {
+__global__ void __launch_bounds__(kBlockX* kBlockY, kMinBlocks<ST, COLL>) step_kernel(Params p) {
+    pdl_enter();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     constexpr bool kLimiter = (COLL == LBM_EHRENFEST || COLL == LBM_MEDIAN);
@@ -141,6 +175,106 @@ __global__ void __launch_bounds__(kBlockX* kBlockY) step_kernel(Params p) {
     int e_code = -1, e_iters = 0;
     if (x < p.nx && y < p.ny) site_update<Q, ST, COLL, ODD>(p, x, y, e_code, e_iters);
     if (COLL == LBM_ELBM) elbm_stats(p, e_code, e_iters);
+}
+
+// Two sites per thread (x0 = 2t, x0 + 1): every population plane moves with
+// one aligned pair access per thread (and one packed conversion in the
+// 16-bit formats).  In odd steps the planes with v_x = +-1 are shifted by one
+// element; the missing neighbour comes from the adjacent lane by a shuffle,
+// and only the two warp-edge elements use scalar accesses.  Each element is
+// still read and written only by the thread of the site that owns it (a
+// pair load may also fetch an unused element owned by the next warp).
+// Warps that touch a wall, the domain edge or a ragged end take the
+// per-site path.
+// Used for the 16-bit formats, whose per-site instruction count (packed
+// conversions, addressing) otherwise limits them below the HBM roofline;
+// with FP32 storage the one-site kernel is as fast or faster, and the median
+// step (two FP32 Delta S evaluations per thread) loses occupancy.
+constexpr int kVecX = 64;
+constexpr int kVecY = 4;
+template <class ST, int COLL>
+constexpr bool kPairedSites = sizeof(typename ST::S) == 2 && COLL != LBM_ELBM && COLL != LBM_MEDIAN;
+
+template <int Q, class ST, int COLL, bool ODD>
+__global__ void __launch_bounds__(kVecX* kVecY) step_kernel_v2(Params p) {
+    pdl_enter();
+    using T = typename ST::T;
+    using S = typename ST::S;
+    using L = Lat<Q>;
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    constexpr bool kLimiter = (COLL == LBM_EHRENFEST || COLL == LBM_MEDIAN);
+    if (kLimiter && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+        p.counters[p.cslot ^ 1] = 0u;
+        p.counters[CNT_NVALID] = 0u;
+    }
+    int e_code = -1, e_iters = 0;
+    const unsigned full = 0xffffffffu;
+    const bool inner = y > 0 && y < p.ny - 1 && x0 > 0 && x0 + 2 < p.nx;
+    if (!__all_sync(full, inner)) {
+        if (y < p.ny) {
+            if (x0 < p.nx) site_update<Q, ST, COLL, ODD>(p, x0, y, e_code, e_iters);
+            if (x0 + 1 < p.nx) site_update<Q, ST, COLL, ODD>(p, x0 + 1, y, e_code, e_iters);
+        }
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const bool first = lane == 0, last = lane == 31;
+    const int o = y * p.pitch + x0;
+    S* base = (S*)p.f;
+    using S2 = typename ST::S2;
+    T fa[Q], fb[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int k = ODD ? L::opp(i) : i;
+        const int off = k * p.plane32 + o - (ODD ? L::cy(i) * p.pitch : 0);
+        const T w = T(L::w(i));
+        T lo, hi;
+        ST::dec2(*(const S2*)(base + off), w, lo, hi);
+        if (!ODD || L::cx(i) == 0) {
+            fa[i] = lo;
+            fb[i] = hi;
+        } else if (L::cx(i) > 0) {  // sources x0 - 1, x0
+            S e = S();
+            if (first) e = base[off - 1];
+            const T prev = __shfl_up_sync(full, hi, 1);
+            fa[i] = first ? ST::dec(e, w) : prev;
+            fb[i] = lo;
+        } else {  // sources x0 + 1, x0 + 2
+            S e = S();
+            if (last) e = base[off + 2];
+            const T next = __shfl_down_sync(full, lo, 1);
+            fa[i] = hi;
+            fb[i] = last ? ST::dec(e, w) : next;
+        }
+    }
+    T Fa[Q], Fb[Q];
+    collide_site<Q, ST, COLL>(p, x0, y, fa, Fa, e_code, e_iters);
+    collide_site<Q, ST, COLL>(p, x0 + 1, y, fb, Fb, e_code, e_iters);
+    // stores: the pair, then (odd steps, shifted planes) the one element at
+    // each warp edge, as one predicated store shared by lanes 0 and 31
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int k = ODD ? L::opp(i) : i;
+        const int off = k * p.plane32 + o - (ODD ? L::cy(i) * p.pitch : 0);
+        const T w = T(L::w(i));
+        const T va = Fa[L::opp(i)], vb = Fb[L::opp(i)];
+        if (!ODD || L::cx(i) == 0) {
+            *(S2*)(base + off) = ST::enc2(va, vb, w);
+        } else if (L::cx(i) > 0) {  // a -> x0 - 1, b -> x0; x0 + 1 belongs to the next lane's a
+            const T nxt = __shfl_down_sync(full, va, 1);
+            const S2 pr = ST::enc2(vb, nxt, w);
+            const S sc = ST::enc(first ? va : vb, w);
+            if (!last) *(S2*)(base + off) = pr;
+            if (first || last) base[off - (first ? 1 : 0)] = sc;
+        } else {  // a -> x0 + 1, b -> x0 + 2; x0 belongs to the previous lane's b
+            const T prv = __shfl_up_sync(full, vb, 1);
+            const S2 pr = ST::enc2(prv, va, w);
+            const S sc = ST::enc(first ? va : vb, w);
+            if (!first) *(S2*)(base + off) = pr;
+            if (first || last) base[off + (first ? 1 : 2)] = sc;
+        }
+    }
 }
 
 // Writes F for a candidate site recorded by the step kernel (same parity).
@@ -373,6 +507,7 @@ __device__ void ehrenfest_select_apply(const Params& p, unsigned M, unsigned nva
 // a memory fence, no waiting - selects the k largest and rewrites them.
 template <int Q, class ST, bool ODD>
 __global__ void __launch_bounds__(256) ehrenfest_eval_select(Params p) {
+    pdl_enter();
     using T = typename ST::T;
     __shared__ unsigned s_last;
     unsigned M = p.counters[p.cslot];
@@ -407,18 +542,22 @@ __global__ void __launch_bounds__(256) ehrenfest_eval_select(Params p) {
 // and its neighbours (clipped at walls, wrapped where periodic); where the
 // median is below the site's Delta S the homothety with coefficient
 // sqrt(med / DeltaS) (Eq. entrHom) precedes the LBGK collision.
-// Candidates j0, j0 + stride, ... of the step's list (any launch shape).
+// Candidates g0, g0 + G, ... of the step's list, one per 16-lane group
+// (g0: this group's index, G: the number of groups; every lane of a group
+// calls this).  The FP64 Delta S is the group's; its first lane does the rest.
 template <int Q, class ST, bool ODD>
-__device__ void median_apply(const Params& p, unsigned j0, unsigned stride) {
+__device__ void median_apply(const Params& p, unsigned g0, unsigned G) {
     using T = typename ST::T;
     unsigned M = p.counters[p.cslot];
     if (M > (unsigned)p.cand_cap) M = (unsigned)p.cand_cap;
     const T* field = (const T*)p.ds_field;
     unsigned count = 0, nvalid = 0;
-    for (unsigned j = j0; j < M; j += stride) {
+    for (unsigned b = 0; b < M; b += G) {
+        const unsigned j = b + g0;
+        const double d = delta_s_group<Q, ST>(p, j, j < M);
+        if (j >= M || (threadIdx.x & 15) != 0) continue;
         T f[Q];
         load_candidate<Q, ST>(p, (int)j, f);
-        const double d = delta_s_fp64<Q, T>(f, p.eq);
         const bool is_cand = d > p.delta;
         p.cand_ds[j] = is_cand ? d : -1.0;
         if (!is_cand) {
@@ -471,7 +610,8 @@ __device__ void median_apply(const Params& p, unsigned j0, unsigned stride) {
 
 template <int Q, class ST, bool ODD>
 __global__ void __launch_bounds__(256) median_fixup(Params p) {
-    median_apply<Q, ST, ODD>(p, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+    pdl_enter();
+    median_apply<Q, ST, ODD>(p, blockIdx.x * (blockDim.x >> 4) + (threadIdx.x >> 4), gridDim.x * (blockDim.x >> 4));
 }
 
 // ---------------------------------------------------------------------------
@@ -620,6 +760,24 @@ struct Launch {
                                cudaStream_t s);
 };
 
+inline cudaError_t launch_p(void (*k)(Params), dim3 g, dim3 b, cudaStream_t s, const Params& p) {
+    if (!p.pdl) {
+        k<<<g, b, 0, s>>>(p);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t c = {};
+    c.gridDim = g;
+    c.blockDim = b;
+    c.dynamicSmemBytes = 0;
+    c.stream = s;
+    cudaLaunchAttribute a[1];
+    a[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    a[0].val.programmaticStreamSerializationAllowed = 1;
+    c.attrs = a;
+    c.numAttrs = 1;
+    return cudaLaunchKernelEx(&c, k, p);
+}
+
 inline dim3 site_grid(const Params& p, dim3 block) {
     return dim3((p.nx + block.x - 1) / block.x, (p.ny + block.y - 1) / block.y);
 }
@@ -628,12 +786,19 @@ inline dim3 site_block(int Q) { return Q == 3 ? dim3(256, 1) : dim3(kBlockX, kBl
 
 template <int Q, class ST, int COLL>
 cudaError_t launch_step_q(bool odd, const Params& p, cudaStream_t s) {
+    // two sites per thread where every row starts on a pair boundary (the
+    // padded layouts; a dense layout of odd width takes the per-site kernel).
+    if constexpr (Q == 9 && kPairedSites<ST, COLL>) {
+        const bool paired = p.pitch % 2 == 0 && p.plane32 % 2 == 0 &&
+                            (uintptr_t)p.f % (2 * sizeof(typename ST::S)) == 0;
+        if (paired) {
+            dim3 b(kVecX, kVecY), g((p.nx + 2 * kVecX - 1) / (2 * kVecX), (p.ny + kVecY - 1) / kVecY);
+            return launch_p(odd ? step_kernel_v2<Q, ST, COLL, true> : step_kernel_v2<Q, ST, COLL, false>, g, b,
+                            s, p);
+        }
+    }
     dim3 b = site_block(Q), g = site_grid(p, b);
-    if (odd)
-        step_kernel<Q, ST, COLL, true><<<g, b, 0, s>>>(p);
-    else
-        step_kernel<Q, ST, COLL, false><<<g, b, 0, s>>>(p);
-    return cudaGetLastError();
+    return launch_p(odd ? step_kernel<Q, ST, COLL, true> : step_kernel<Q, ST, COLL, false>, g, b, s, p);
 }
 
 template <int Q, class ST>
@@ -651,22 +816,14 @@ cudaError_t launch_step_c(int coll, bool odd, const Params& p, cudaStream_t s) {
 
 template <int Q, class ST>
 cudaError_t launch_fixup_q(int coll, bool odd, const Params& p, cudaStream_t s, int nsm) {
-    if (coll == LBM_EHRENFEST) {
-        if (odd)
-            ehrenfest_eval_select<Q, ST, true><<<nsm, 256, 0, s>>>(p);
-        else
-            ehrenfest_eval_select<Q, ST, false><<<nsm, 256, 0, s>>>(p);
-    } else if (coll == LBM_MEDIAN) {
-        // candidate count is only known on the device: a fixed grid of one
-        // CTA per SM strides over the list
-        if (odd)
-            median_fixup<Q, ST, true><<<nsm, 256, 0, s>>>(p);
-        else
-            median_fixup<Q, ST, false><<<nsm, 256, 0, s>>>(p);
-    } else {
-        return cudaSuccess;
-    }
-    return cudaGetLastError();
+    // the candidate count is only known on the device: a fixed grid of one
+    // CTA per SM strides over the list
+    if (coll == LBM_EHRENFEST)
+        return launch_p(odd ? ehrenfest_eval_select<Q, ST, true> : ehrenfest_eval_select<Q, ST, false>, nsm,
+                        256, s, p);
+    if (coll == LBM_MEDIAN)
+        return launch_p(odd ? median_fixup<Q, ST, true> : median_fixup<Q, ST, false>, nsm, 256, s, p);
+    return cudaSuccess;
 }
 
 template <class ST>

@@ -64,6 +64,8 @@ struct Params {
     void* ds_field;                  // [ny][nx] arithmetic type (median only)
     double* scratch_d;               // small FP64 reduction scratch
     int cslot;                       // candidate counter used by this step (t & 1)
+    int pdl;                         // host side: launch the step kernels with
+                                     // programmatic dependent launch
 };
 
 }  // namespace lbm

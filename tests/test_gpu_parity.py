@@ -57,6 +57,10 @@ CASES = {
     "channel": dict(lattice="D2Q9", nx=130, ny=5, bc="channel", lid_u=0.05),
     "tube": dict(lattice="D1Q3", nx=301, ny=1, bc="ends"),
     "ring": dict(lattice="D1Q3", nx=64, ny=1, bc="periodic"),
+    # wide enough for whole warps of two-site threads away from the walls,
+    # with a ragged last block (200 = 128 + 72) and an exact one (256)
+    "wide": dict(lattice="D2Q9", nx=200, ny=12, bc="cavity", lid_u=0.1),
+    "wide_periodic": dict(lattice="D2Q9", nx=256, ny=6, bc="periodic"),
 }
 
 
@@ -90,7 +94,7 @@ def test_limiters_fp64_match_oracle(case, collision):
 
 
 @pytest.mark.parametrize("collision", ["ehrenfest", "median"])
-@pytest.mark.parametrize("case", ["cavity", "tube"])
+@pytest.mark.parametrize("case", ["cavity", "tube", "wide"])
 def test_limiters_fp32_one_step_and_selection_replay(case, collision):
     """FP32 storage: one step from a common state, and the integer selection
     replayed on the CPU from the GPU's own FP64 Delta S keys (bit-exact) and
@@ -161,6 +165,46 @@ def test_shock_tube_all_collisions_400_steps():
         g = lat.get_state(torch.float64).cpu().numpy()
         f = O.step(c, O.init_equilibrium(c, init["rho"], init["ux"]), 400)
         assert rel(g, f) < 1e-12, (collision, rel(g, f))
+
+
+def _spacing16(dev, precision):
+    """Spacing of the 16-bit deviation format at dev (bf16: 8 significant
+    bits, fp16: 11, with fp16's subnormal floor)."""
+    a = np.abs(dev)
+    if precision == "fp16_dev":
+        return np.spacing(a.astype(np.float16)).astype(np.float64)
+    e = np.floor(np.log2(np.maximum(a, 1e-38)))
+    return 2.0 ** (e - 7)
+
+
+@pytest.mark.parametrize("precision", ["fp16_dev", "bf16_dev"])
+@pytest.mark.parametrize("collision", ["lbgk", "mrt", "positivity", "ehrenfest", "median"])
+def test_reduced_precision_one_step_rounding(precision, collision):
+    """16-bit deviation storage, one even and one odd step from a common
+    state: each stored population is the oracle's post-step value of the
+    decoded pre-step state, rounded once to the format (half a spacing of
+    the deviation f_i - W_i, plus FP32 arithmetic).  In the layout after an
+    even step the top row's wall links hold the bounced value before the
+    moving-lid term 6 W_i |v_ix| U (at most U / 6) is added, so there the
+    stored deviation may be larger by that much."""
+    cfg = dict(CASES["wide"], collision=collision, precision=precision, beta=0.97, topk=3,
+               delta=2e-4, s_e=1.64, s_eps=1.54, s_q=1.2)
+    amp = 0.6 if collision == "positivity" else 0.01
+    f0 = perturbed_state(cfg, 17, amp=amp, hot=12 if collision in ("ehrenfest", "median") else 0)
+    lat = lbm.Lattice(cfg)
+    lat.set_state(torch.tensor(f0, dtype=torch.float32, device="cuda"))
+    _, _, w = O.lattice("D2Q9")
+    for parity in (0, 1):
+        pre = lat.get_state(torch.float64).cpu().numpy()
+        lat.step(1)
+        post = lat.get_state(torch.float64).cpu().numpy()
+        want = O.step(cfg, pre, 1)
+        dev = np.abs(want - np.asarray(w)[:, None, None])
+        dev[:, -1, :] += cfg["lid_u"] / 6.0
+        bound = 0.5 * _spacing16(dev, precision) * (1 + 1e-3) + 2e-6
+        err = np.abs(post - want)
+        worst = np.unravel_index(int(np.argmax(err / bound)), err.shape)
+        assert (err <= bound).all(), (parity, float((err / bound).max()), worst, post[worst], want[worst])
 
 
 @pytest.mark.parametrize("precision,tol", [("fp16_dev", 3e-3), ("bf16_dev", 3e-2)])
