@@ -169,8 +169,10 @@ def time_steps(lat, steps, warmup, dist=None, profile=False, sampler=None):
     return ms, prof, (t0, t1)
 
 
-def run_variants(n_side, steps, warmup):
-    """MLUPS and fraction of HBM peak per collision x precision (one GPU)."""
+def run_variants(n_side, steps, warmup, fma_per_s=None):
+    """MLUPS and fraction of HBM peak per collision x precision (one GPU).
+    The FP64-bound ones (ELBM's root solve, FP64 storage) also get their cost
+    in FP64 FMA issue slots per site at the measured FMA rate."""
     import torch
     from paper_1110_0270_gb300 import lbm
     hbm, _ = peaks()
@@ -197,6 +199,8 @@ def run_variants(n_side, steps, warmup):
                 "kernel_ms": round(kstep, 5), "steps": k}
             if prof["fixup"][0]:
                 out[f"{coll}/{precision}"]["fixup_ms"] = round(prof["fixup"][1] / prof["fixup"][0], 5)
+            if fma_per_s and (coll == "elbm" or precision == "fp64"):
+                out[f"{coll}/{precision}"]["fp64_fma_slots_per_site"] = round(fma_per_s / (mlups * 1e6), 1)
             del lat
             torch.cuda.empty_cache()
     return out
@@ -486,7 +490,11 @@ def gpu_arm(args):
     if rank == 0:
         result["clocks"] = sampler.summary(t0, t1) if sampler else None
         if not args.no_variants:
-            result["variants"] = run_variants(args.side, args.variant_steps, 3)
+            r = lbm.fp64_rates()
+            result["fp64_probe"] = {"dfma_tflops": round(r["dfma_flops"] / 1e12, 4),
+                                    "log_gops": round(r["log_per_s"] / 1e9, 2),
+                                    "note": "measured FP64 ceilings of the FP64-bound kernels"}
+            result["variants"] = run_variants(args.side, args.variant_steps, 3, r["dfma_flops"] / 2)
         if not args.no_small:
             result["small_configs"] = run_small_configs()
         if args.adjoint_steps > 0:

@@ -310,7 +310,20 @@ lbm_status lbm_profile_read(lbm_ctx* ctx, int* launches, double* ms);
 #define LBM_NOALLOC_SCRATCH_BYTES (32u << 20)
 lbm_status lbm_ehrenfest_step_noalloc(const lbm_config* cfg, void* f, int nsteps, void* stream);
 
-/* Message of the last failure on ctx ("" if none).  Valid until the next call. */
+/* ---------------------------------------------------------------------------
+ * Measurement support (the paper has no counterpart).  FP64 throughput of the
+ * current GPU: *dfma_flops = FP64 fused multiply-add rate in FLOP/s (2 per
+ * FMA), *log_per_s = FP64 log() evaluations per second, each from one timed
+ * launch after a warm-up launch on `stream` (synchronised).  These are the
+ * ceilings of the step kernels bound by the FP64 pipe (the ELBM root solve,
+ * FP64 storage).  Either output may be NULL, not both (LBM_ERR_ARG).
+ * Allocates and frees 8 bytes of device memory; LBM_ERR_CUDA on failure.
+ * ------------------------------------------------------------------------- */
+lbm_status lbm_fp64_rates(double* dfma_flops, double* log_per_s, void* stream);
+
+/* Message of the last failure on ctx ("" if none).  Valid until the next call.
+ * With ctx NULL: the message of the calling thread's last failed lbm_create
+ * ("" after a successful one). */
 const char* lbm_last_error(const lbm_ctx* ctx);
 const char* lbm_status_string(lbm_status s);
 int lbm_abi_version(void);

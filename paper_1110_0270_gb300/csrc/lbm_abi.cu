@@ -132,6 +132,10 @@ cudaError_t dispatch(int precision, Fn&& fn) {
 
 cudaStream_t S(void* s) { return (cudaStream_t)s; }
 
+// Message of the calling thread's last failed lbm_create (no context exists
+// to hold it).
+thread_local std::string g_create_error;
+
 // Launches fn() bracketed by a pair of timing events when tracing is on.
 template <class Fn>
 cudaError_t traced(lbm_ctx* ctx, int kind, cudaStream_t s, Fn&& fn) {
@@ -222,7 +226,7 @@ const char* lbm_status_string(lbm_status s) {
     return "unknown lbm_status";
 }
 
-const char* lbm_last_error(const lbm_ctx* ctx) { return ctx ? ctx->err.c_str() : "ctx is NULL"; }
+const char* lbm_last_error(const lbm_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
 
 lbm_status lbm_config_default(lbm_config* c) {
     if (!c) return LBM_ERR_ARG;
@@ -267,6 +271,7 @@ lbm_status lbm_create(const lbm_config* cfg, void* dev_mem, size_t bytes, lbm_ct
     ctx->bytes = bytes;
     if (cudaGetDevice(&ctx->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
+        g_create_error = "lbm_create: no current CUDA device";
         delete ctx;
         return LBM_ERR_CUDA;
     }
@@ -309,11 +314,18 @@ lbm_status lbm_create(const lbm_config* cfg, void* dev_mem, size_t bytes, lbm_ct
     p.ds_field = ctx->base + L.field_off;
     ctx->staging = (double*)(ctx->base + L.staging_off);
     cudaError_t e = cudaMemset(ctx->base + L.cnt_off, 0, align_up(CNT_WORDS * 4 + ST_WORDS * 8 + 64));
-    if (e == cudaSuccess) e = build_step_graph(ctx);
+    const char* where = "cudaMemset of the counters";
+    if (e == cudaSuccess) {
+        e = build_step_graph(ctx);
+        where = "capture of the two-step graph";
+    }
     if (e != cudaSuccess) {
+        g_create_error = std::string("lbm_create: ") + where + ": " + cudaGetErrorName(e) + " (" +
+                         cudaGetErrorString(e) + ")";
         delete ctx;
         return LBM_ERR_CUDA;
     }
+    g_create_error.clear();
     *out = ctx;
     return LBM_OK;
 }

@@ -53,20 +53,11 @@ template <> struct Lat<9> {
 // ---------------------------------------------------------------------------
 // ld2 / st2 move the two consecutive elements p[0], p[1] (p 2-element
 // aligned) with one vector access and, for the 16-bit formats, one packed
-// conversion; enc / enc2 / dec / dec2 are the conversions alone (S2: the
-// stored pair type).
+// conversion.
 struct StF64 {
     using S = double;
     using T = double;
     static constexpr int code = LBM_FP64;
-    using S2 = double2;
-    __device__ static S enc(T v, T) { return v; }
-    __device__ static S2 enc2(T a, T b, T) { return make_double2(a, b); }
-    __device__ static T dec(S v, T) { return v; }
-    __device__ static void dec2(S2 v, T, T& a, T& b) {
-        a = v.x;
-        b = v.y;
-    }
     __device__ static T ld(const S* p, T) { return *p; }
     __device__ static void st(S* p, T v, T) { *p = v; }
     __device__ static void ld2(const S* p, T, T& a, T& b) {
@@ -80,14 +71,6 @@ struct StF32 {
     using S = float;
     using T = float;
     static constexpr int code = LBM_FP32;
-    using S2 = float2;
-    __device__ static S enc(T v, T) { return v; }
-    __device__ static S2 enc2(T a, T b, T) { return make_float2(a, b); }
-    __device__ static T dec(S v, T) { return v; }
-    __device__ static void dec2(S2 v, T, T& a, T& b) {
-        a = v.x;
-        b = v.y;
-    }
     __device__ static T ld(const S* p, T) { return *p; }
     __device__ static void st(S* p, T v, T) { *p = v; }
     __device__ static void ld2(const S* p, T, T& a, T& b) {
@@ -101,15 +84,6 @@ struct StBF16 {
     using S = __nv_bfloat16;
     using T = float;
     static constexpr int code = LBM_BF16_DEV;
-    using S2 = __nv_bfloat162;
-    __device__ static S enc(T v, T w) { return __float2bfloat16_rn(v - w); }
-    __device__ static S2 enc2(T a, T b, T w) { return __floats2bfloat162_rn(a - w, b - w); }
-    __device__ static T dec(S v, T w) { return w + __bfloat162float(v); }
-    __device__ static void dec2(S2 v, T w, T& a, T& b) {
-        const float2 u = __bfloat1622float2(v);
-        a = w + u.x;
-        b = w + u.y;
-    }
     __device__ static T ld(const S* p, T w) { return w + __bfloat162float(*p); }
     __device__ static void st(S* p, T v, T w) { *p = __float2bfloat16_rn(v - w); }
     __device__ static void ld2(const S* p, T w, T& a, T& b) {
@@ -123,15 +97,6 @@ struct StF16 {
     using S = __half;
     using T = float;
     static constexpr int code = LBM_FP16_DEV;
-    using S2 = __half2;
-    __device__ static S enc(T v, T w) { return __float2half_rn(v - w); }
-    __device__ static S2 enc2(T a, T b, T w) { return __floats2half2_rn(a - w, b - w); }
-    __device__ static T dec(S v, T w) { return w + __half2float(v); }
-    __device__ static void dec2(S2 v, T w, T& a, T& b) {
-        const float2 u = __half22float2(v);
-        a = w + u.x;
-        b = w + u.y;
-    }
     __device__ static T ld(const S* p, T w) { return w + __half2float(*p); }
     __device__ static void st(S* p, T v, T w) { *p = __float2half_rn(v - w); }
     __device__ static void ld2(const S* p, T w, T& a, T& b) {

@@ -155,12 +155,16 @@ __device__ __forceinline__ void elbm_stats(const Params& p, int e_code, int e_it
     }
 }
 
-// Six resident 256-thread CTAs per SM (at most 40 registers a thread) for
-// the FP32-arithmetic limiters, MRT and positivity: the streaming step needs
-// the warps to hide HBM latency.  0 leaves the choice to the compiler (LBGK
-// fits in 32-38 registers by itself; ELBM and FP64 storage are not capped).
+// Resident 256-thread CTAs per SM the FP32-arithmetic step kernels are
+// compiled for: the streaming step needs the warps to hide HBM latency.
+// Ehrenfest and positivity: eight (32 registers, a few bytes of spills;
+// measured 4% faster than six); median: six (at 32 registers its FP32
+// Delta S spills ~200 bytes).  0 leaves the choice to the compiler (LBGK and
+// MRT fit in 32-38 registers by themselves; ELBM and FP64 storage are not
+// capped).
 template <class ST, int COLL>
-constexpr int kMinBlocks = (COLL != LBM_ELBM && COLL != LBM_LBGK && sizeof(typename ST::T) == 4) ? 6 : 0;
+constexpr int kMinBlocks =
+    sizeof(typename ST::T) != 4 ? 0 : (COLL == LBM_EHRENFEST || COLL == LBM_POSITIVITY) ? 8 : COLL == LBM_MEDIAN ? 6 : 0;
 
 template <int Q, class ST, int COLL, bool ODD>
 __global__ void __launch_bounds__(kBlockX* kBlockY, kMinBlocks<ST, COLL>) step_kernel(Params p) {
@@ -189,14 +193,15 @@ __global__ void __launch_bounds__(kBlockX* kBlockY, kMinBlocks<ST, COLL>) step_k
 // Used for the 16-bit formats, whose per-site instruction count (packed
 // conversions, addressing) otherwise limits them below the HBM roofline;
 // with FP32 storage the one-site kernel is as fast or faster, and the median
-// step (two FP32 Delta S evaluations per thread) loses occupancy.
+// step (two FP32 Delta S evaluations per thread) loses occupancy.  Compiled
+// for six resident CTAs (40 registers): 2-7% faster than five or no cap.
 constexpr int kVecX = 64;
 constexpr int kVecY = 4;
 template <class ST, int COLL>
 constexpr bool kPairedSites = sizeof(typename ST::S) == 2 && COLL != LBM_ELBM && COLL != LBM_MEDIAN;
 
 template <int Q, class ST, int COLL, bool ODD>
-__global__ void __launch_bounds__(kVecX* kVecY) step_kernel_v2(Params p) {
+__global__ void __launch_bounds__(kVecX* kVecY, 6) step_kernel_v2(Params p) {
     pdl_enter();
     using T = typename ST::T;
     using S = typename ST::S;
@@ -219,10 +224,8 @@ __global__ void __launch_bounds__(kVecX* kVecY) step_kernel_v2(Params p) {
         return;
     }
     const int lane = threadIdx.x & 31;
-    const bool first = lane == 0, last = lane == 31;
     const int o = y * p.pitch + x0;
     S* base = (S*)p.f;
-    using S2 = typename ST::S2;
     T fa[Q], fb[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -230,29 +233,25 @@ __global__ void __launch_bounds__(kVecX* kVecY) step_kernel_v2(Params p) {
         const int off = k * p.plane32 + o - (ODD ? L::cy(i) * p.pitch : 0);
         const T w = T(L::w(i));
         T lo, hi;
-        ST::dec2(*(const S2*)(base + off), w, lo, hi);
+        ST::ld2(base + off, w, lo, hi);
         if (!ODD || L::cx(i) == 0) {
             fa[i] = lo;
             fb[i] = hi;
         } else if (L::cx(i) > 0) {  // sources x0 - 1, x0
-            S e = S();
-            if (first) e = base[off - 1];
-            const T prev = __shfl_up_sync(full, hi, 1);
-            fa[i] = first ? ST::dec(e, w) : prev;
+            T prev = __shfl_up_sync(full, hi, 1);
+            if (lane == 0) prev = ST::ld(base + off - 1, w);
+            fa[i] = prev;
             fb[i] = lo;
         } else {  // sources x0 + 1, x0 + 2
-            S e = S();
-            if (last) e = base[off + 2];
-            const T next = __shfl_down_sync(full, lo, 1);
+            T next = __shfl_down_sync(full, lo, 1);
+            if (lane == 31) next = ST::ld(base + off + 2, w);
             fa[i] = hi;
-            fb[i] = last ? ST::dec(e, w) : next;
+            fb[i] = next;
         }
     }
     T Fa[Q], Fb[Q];
     collide_site<Q, ST, COLL>(p, x0, y, fa, Fa, e_code, e_iters);
     collide_site<Q, ST, COLL>(p, x0 + 1, y, fb, Fb, e_code, e_iters);
-    // stores: the pair, then (odd steps, shifted planes) the one element at
-    // each warp edge, as one predicated store shared by lanes 0 and 31
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int k = ODD ? L::opp(i) : i;
@@ -260,19 +259,21 @@ __global__ void __launch_bounds__(kVecX* kVecY) step_kernel_v2(Params p) {
         const T w = T(L::w(i));
         const T va = Fa[L::opp(i)], vb = Fb[L::opp(i)];
         if (!ODD || L::cx(i) == 0) {
-            *(S2*)(base + off) = ST::enc2(va, vb, w);
+            ST::st2(base + off, va, vb, w);
         } else if (L::cx(i) > 0) {  // a -> x0 - 1, b -> x0; x0 + 1 belongs to the next lane's a
             const T nxt = __shfl_down_sync(full, va, 1);
-            const S2 pr = ST::enc2(vb, nxt, w);
-            const S sc = ST::enc(first ? va : vb, w);
-            if (!last) *(S2*)(base + off) = pr;
-            if (first || last) base[off - (first ? 1 : 0)] = sc;
+            if (lane < 31)
+                ST::st2(base + off, vb, nxt, w);
+            else
+                ST::st(base + off, vb, w);
+            if (lane == 0) ST::st(base + off - 1, va, w);
         } else {  // a -> x0 + 1, b -> x0 + 2; x0 belongs to the previous lane's b
             const T prv = __shfl_up_sync(full, vb, 1);
-            const S2 pr = ST::enc2(prv, va, w);
-            const S sc = ST::enc(first ? va : vb, w);
-            if (!first) *(S2*)(base + off) = pr;
-            if (first || last) base[off + (first ? 1 : 2)] = sc;
+            if (lane > 0)
+                ST::st2(base + off, prv, va, w);
+            else
+                ST::st(base + off + 1, va, w);
+            if (lane == 31) ST::st(base + off + 2, vb, w);
         }
     }
 }

@@ -35,7 +35,8 @@ EXPORTS = ["lbm_config_default", "lbm_required_bytes", "lbm_create", "lbm_destro
            "lbm_ehrenfest_step_noalloc", "lbm_batch_required_bytes", "lbm_batch_create",
            "lbm_batch_destroy", "lbm_batch_init_uniform", "lbm_batch_set_state",
            "lbm_batch_get_state", "lbm_batch_step", "lbm_batch_stats", "lbm_batch_last_error",
-           "lbm_adjoint_required_bytes", "lbm_adjoint_forward", "lbm_adjoint_backward"]
+           "lbm_adjoint_required_bytes", "lbm_adjoint_forward", "lbm_adjoint_backward",
+           "lbm_fp64_rates"]
 
 
 class lbm_config(C.Structure):
@@ -87,6 +88,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "lbm_profile_enable": (i, [p, i]),
         "lbm_profile_read": (i, [p, C.POINTER(i), C.POINTER(C.c_double)]),
         "lbm_ehrenfest_step_noalloc": (i, [C.POINTER(lbm_config), p, i, p]),
+        "lbm_fp64_rates": (i, [C.POINTER(C.c_double), C.POINTER(C.c_double), p]),
         "lbm_batch_required_bytes": (i, [C.POINTER(lbm_config), i, C.POINTER(sz)]),
         "lbm_batch_create": (i, [C.POINTER(lbm_config), i, p, sz, C.POINTER(p)]),
         "lbm_batch_destroy": (None, [p]),
@@ -200,7 +202,8 @@ class Lattice:
         with torch.cuda.device(self.device):
             rc = lib().lbm_create(C.byref(self._c), _ptr(self.mem), self.nbytes, C.byref(h))
         if rc != 0:
-            raise LBMError(f"lbm_create: {STATUS.get(rc, rc)}")
+            msg = lib().lbm_last_error(None)
+            raise LBMError(f"lbm_create: {STATUS.get(rc, rc)}: {msg.decode() if msg else ''}")
         self._h = h
 
     def __del__(self):
@@ -325,6 +328,16 @@ class Lattice:
             sel.ctypes.data_as(C.c_void_p), cap, C.byref(n), _stream(stream)), "lbm_last_candidates")
         m = min(n.value, cap)
         return ds[:m], site[:m], sel[:m]
+
+
+def fp64_rates(stream=None) -> dict:
+    """Measured FP64 FMA rate (FLOP/s) and FP64 log() rate (1/s) of the
+    current GPU: the ceilings of the FP64-bound step kernels."""
+    fl, lg = C.c_double(0.0), C.c_double(0.0)
+    rc = lib().lbm_fp64_rates(C.byref(fl), C.byref(lg), _stream(stream))
+    if rc != 0:
+        raise LBMError(f"lbm_fp64_rates: {STATUS.get(rc, rc)}")
+    return {"dfma_flops": fl.value, "log_per_s": lg.value}
 
 
 def batch_required_bytes(cfgs) -> int:

@@ -22,7 +22,7 @@ def lib():
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "lbm.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(lbm_\w+)\s*\(", src)))
 
 
 def test_library_exports_every_declared_symbol(lib):

@@ -225,15 +225,20 @@ def test_reduced_precision_storage_tracks_fp64(precision, tol):
     assert uerr < 20 * tol, uerr
 
 
-@pytest.mark.parametrize("shape", [(1, 1), (1, 7), (7, 1), (2, 2), (33, 3), (129, 3)])
+@pytest.mark.parametrize("shape", [(1, 1), (1, 7), (7, 1), (2, 2), (33, 3), (129, 3), (513, 4),
+                                   (514, 5), (1025, 3)])
 def test_tiny_and_ragged_lattices(shape):
+    """Degenerate and ragged shapes, including widths around the 512-site
+    row segments of the FP32 staged kernel (513: the last column alone past
+    one segment; 514, 1025: a ragged second / third segment)."""
     nx, ny = shape
     for bc in ["cavity", "periodic", "channel"]:
-        cfg = dict(lattice="D2Q9", nx=nx, ny=ny, bc=bc, lid_u=0.1, collision="lbgk",
-                   precision="fp64", beta=0.9)
-        f0 = perturbed_state(cfg, 3)
-        g, _ = gpu_run(cfg, f0, 17)
-        assert rel(g, O.step(cfg, f0, 17)) < 1e-12, (shape, bc)
+        for precision, tol in [("fp64", 1e-12), ("fp32", 1e-5)]:
+            cfg = dict(lattice="D2Q9", nx=nx, ny=ny, bc=bc, lid_u=0.1, collision="lbgk",
+                       precision=precision, beta=0.9)
+            f0 = as_stored(cfg, perturbed_state(cfg, 3))
+            g, _ = gpu_run(cfg, f0, 17)
+            assert rel(g, O.step(cfg, f0, 17)) < tol, (shape, bc, precision)
     for nx1 in (1, 2, 3, 257):
         cfg = dict(lattice="D1Q3", nx=nx1, ny=1, bc="ends", collision="lbgk", precision="fp64", beta=0.9)
         f0 = perturbed_state(cfg, 4)
