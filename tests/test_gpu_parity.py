@@ -228,9 +228,9 @@ def test_reduced_precision_storage_tracks_fp64(precision, tol):
 @pytest.mark.parametrize("shape", [(1, 1), (1, 7), (7, 1), (2, 2), (33, 3), (129, 3), (513, 4),
                                    (514, 5), (1025, 3)])
 def test_tiny_and_ragged_lattices(shape):
-    """Degenerate and ragged shapes, including widths around the 512-site
-    row segments of the FP32 staged kernel (513: the last column alone past
-    one segment; 514, 1025: a ragged second / third segment)."""
+    """Degenerate and ragged shapes in FP64 and FP32 storage, including
+    widths just past whole 128-site blocks (129, 513, 1025: the last column
+    alone in the last block; 514: two columns)."""
     nx, ny = shape
     for bc in ["cavity", "periodic", "channel"]:
         for precision, tol in [("fp64", 1e-12), ("fp32", 1e-5)]:
