@@ -206,6 +206,35 @@ def run_variants(n_side, steps, warmup, fma_per_s=None):
     return out
 
 
+def run_precision_error(n_side, steps):
+    """Storage-precision error at the bandwidth configuration: FP32, FP16 and
+    BF16 deviation storage against FP64 storage (which the parity tests hold
+    to the FP64 oracle within 1e-12), after `steps` steps of the cavity from
+    rest with the Ehrenfest limiter: rel-L2 of rho and u, relative error of
+    the total entropy H."""
+    import torch
+    from paper_1110_0270_gb300 import lbm
+    out = {"steps": steps, "collision": "ehrenfest", "reference": "fp64 storage"}
+    ref = None
+    for precision in ["fp64", "fp32", "fp16_dev", "bf16_dev"]:
+        cfg, init = workload_cfg("ehrenfest", precision, n_side)
+        lat = lbm.Lattice(cfg)
+        lat.init(init["rho"], init["ux"], init["uy"])
+        lat.step(steps)
+        rho, u = lat.macros(torch.float64)
+        H = lat.entropy()
+        if ref is None:
+            ref = (rho, u, H)
+        else:
+            nrm = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+            out[precision] = {"rho_rel_l2": nrm(rho - 1.0, ref[0] - 1.0), "u_rel_l2": nrm(u, ref[1]),
+                              "H_rel": abs(H - ref[2]) / abs(ref[2])}
+        del lat, rho, u
+        torch.cuda.empty_cache()
+    out["note"] = "rho_rel_l2 is taken on rho - 1 (the part that varies)"
+    return out
+
+
 def batched_configs(precision="fp32", seed=0, n=512):
     """The batched configuration: n cavities with seeded sides (64..768) and
     Reynolds numbers (log-uniform 100..20000), lid speed 0.1, collisions
@@ -419,7 +448,46 @@ def cpu_baseline(budget_s=12.0):
             "kind": "oracle",
             "sample": f"D2Q9 cavity {n}x{n} (1/16 of the 4097^2 sites), Re {RE:g}, U {LID_U}, "
                       f"Ehrenfest k={TOPK} delta={DELTA:g}, FP64, {steps} steps, "
-                      f"{os.cpu_count()} host cores present, 1 used"}
+                      f"{os.cpu_count()} host cores present, 1 used",
+            "host": host_cpu(), "per_config": oracle_configs()}
+
+
+def host_cpu():
+    """CPU model line of this host (Linux /proc/cpuinfo), or the machine type."""
+    import platform
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu part", "hardware"):
+                    return f"{platform.machine()} {line.split(':', 1)[1].strip()}, {os.cpu_count()} cores"
+    except OSError:
+        pass
+    return f"{platform.machine()}, {os.cpu_count()} cores"
+
+
+def oracle_configs(budget_s=2.0):
+    """Single-thread oracle MLUPS on the shock tube (800 sites, LBGK), the
+    257^2 cavity (Re 5000, U 0.1, LBGK) and the adjoint configuration's
+    forward step (513^2, Re 1000, U 0.1, Ehrenfest k = 32), each for about
+    budget_s seconds of steps."""
+    import oracle as O
+    from paper_1110_0270_gb300 import workloads as WL
+    out = {}
+    cases = [("tube_800_lbgk", *WL.shock_tube(800)), ("cavity_257_lbgk", *WL.cavity(257, 5000.0, 0.1)),
+             ("adjoint_513_ehrenfest_forward", *WL.cavity(513, 1000.0, 0.1))]
+    for name, cfg, init in cases:
+        cfg = dict(cfg, precision="fp64", collision="ehrenfest" if "ehrenfest" in name else "lbgk",
+                   topk=32, delta=1e-3)
+        f = O.init_equilibrium(cfg, init["rho"], init["ux"], None if cfg["lattice"] == "D1Q3" else init["uy"])
+        t0, steps = time.perf_counter(), 0
+        while time.perf_counter() - t0 < budget_s:
+            f = O.step(cfg, f, 10 if cfg["nx"] * cfg["ny"] < 10000 else 1)
+            steps += 10 if cfg["nx"] * cfg["ny"] < 10000 else 1
+        t = time.perf_counter() - t0
+        out[name] = round(cfg["nx"] * cfg["ny"] * steps / t / 1e6, 3)
+    out["unit"] = "MLUPS, FP64 oracle, 1 thread"
+    return out
 
 
 def gpu_arm(args):
@@ -497,6 +565,8 @@ def gpu_arm(args):
             result["variants"] = run_variants(args.side, args.variant_steps, 3, r["dfma_flops"] / 2)
         if not args.no_small:
             result["small_configs"] = run_small_configs()
+        if args.precision_steps > 0:
+            result["precision_error"] = run_precision_error(args.side, args.precision_steps)
         if args.adjoint_steps > 0:
             result["adjoint"] = run_adjoint(args.adjoint_steps, 100)
         if args.batch_steps > 0:
@@ -564,6 +634,8 @@ def main():
     ap.add_argument("--variant-steps", type=int, default=100)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-small", action="store_true", help="skip the tube and 257^2 runs")
+    ap.add_argument("--precision-steps", type=int, default=200,
+                    help="steps of the storage-precision comparison (0 skips it)")
     ap.add_argument("--adjoint-steps", type=int, default=4000,
                     help="T of the adjoint run (0 skips it)")
     ap.add_argument("--batch-steps", type=int, default=20,

@@ -285,6 +285,13 @@ __device__ __forceinline__ T delta_s_t(const T* f, const T* feq) {
 // 3e-7 sqrt(q rho) + 2e-6 q (|d| summed by Cauchy-Schwarz); the relative
 // 1e-3 and absolute 1e-6 sqrt(q rho) slack covers it.
 //
+// v (1 + 1e-3) + 1e-6 sqrt(|q rho|) >= delta, without the square root: true
+// when v alone reaches delta, else compares the squares (also true for NaN).
+__device__ __forceinline__ bool slack_reaches(float v, float q, float rho, float delta) {
+    const float t = delta - 1.001f * v;
+    return !(t > 0.f) || 1e-12f * fabsf(q * rho) >= t * t;
+}
+
 // Ehrenfest: g(x) <= x^2 for |x| < 1/2, and with m = min_i f*_i > 0 and
 // s2 = sum d^2, max |x| <= max |d| / m <= sqrt(s2) / m, so s2 < m^2 / 4 gives
 // Delta S <= sum d^2 / f* <= s2 / m.  One reciprocal per site and no
@@ -302,7 +309,7 @@ __device__ __forceinline__ bool maybe_above_loose(const float* f, const float* f
     }
     if (!(m > 0.f) || !(s2 < 0.25f * m * m)) return true;  // also NaN
     const float q = s2 * __frcp_rn(m);
-    return q * 1.001f + 1e-6f * sqrtf(q * fabsf(rho)) >= delta;
+    return slack_reaches(q, q, rho, delta);
 }
 
 // Median: the site's Delta S in the arithmetic type is computed anyway (the
@@ -319,7 +326,7 @@ __device__ __forceinline__ T delta_s_and_q(const T* f, const T* feq, T& q);
 // g(x) = x^2 P(x).
 template <>
 __device__ __forceinline__ float delta_s_and_q<9, float>(const float* f, const float* feq, float& q) {
-    float x[9], dx[9], amax = 0.f, fmin_ = f[0], emin = feq[0];
+    float x[9], dx[9], amax = 0.f, emin = feq[0];
     q = 0.f;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -328,10 +335,10 @@ __device__ __forceinline__ float delta_s_and_q<9, float>(const float* f, const f
         dx[i] = d * x[i];
         q += dx[i];
         amax = fmaxf(amax, fabsf(x[i]));
-        fmin_ = fminf(fmin_, f[i]);
         emin = fminf(emin, feq[i]);
     }
-    if (!(fmin_ >= 0.f) || !(emin > 0.f)) return INFINITY;
+    // with f* > 0, a negative population has x < -1: only the last tier sees one
+    if (!(emin > 0.f)) return INFINITY;
     float s = 0.f;
     if (amax < 0.03125f) {
 #pragma unroll
@@ -340,8 +347,13 @@ __device__ __forceinline__ float delta_s_and_q<9, float>(const float* f, const f
 #pragma unroll
         for (int i = 0; i < 9; ++i) s = fmaf(dx[i], gpoly_f<11>(x[i]), s);
     } else {
+        bool neg = false;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) s = fmaf(feq[i], gfun_f(x[i]), s);
+        for (int i = 0; i < 9; ++i) {
+            neg |= f[i] < 0.f;
+            s = fmaf(feq[i], gfun_f(x[i]), s);
+        }
+        if (neg) return INFINITY;
     }
     return s;
 }
@@ -363,7 +375,7 @@ __device__ __forceinline__ T delta_s_and_q(const T* f, const T* feq, T& q) {
 }
 
 __device__ __forceinline__ bool median_maybe_above(float ds, float q, float rho, float delta) {
-    return !(ds * 1.001f + 1e-6f * sqrtf(fabsf(q * rho)) < delta);
+    return slack_reaches(ds, q, rho, delta);
 }
 
 // ---------------------------------------------------------------------------
