@@ -303,6 +303,10 @@ lbm_status lbm_create(const lbm_config* cfg, void* dev_mem, size_t bytes, lbm_ct
     p.elbm_max_iter = cfg->elbm_max_iter;
     p.elbm_norm = cfg->elbm_norm;
     p.elbm_fallback = cfg->elbm_fallback;
+    // the rounding of FP32 (or coarser) storage alone leaves Delta S up to
+    // 2^-49 rho: below that the state is at equilibrium as far as the
+    // storage can tell, and the LBGK step is taken as for Delta S < 1e-15
+    p.elbm_skip_rel = cfg->precision == LBM_FP64 ? 0.0 : 0x1p-48;
     p.counters = (unsigned*)(ctx->base + L.cnt_off);
     p.stats = (unsigned long long*)(ctx->base + L.cnt_off + CNT_WORDS * 4);
     p.scratch_d = (double*)(ctx->base + L.cnt_off + CNT_WORDS * 4 + ST_WORDS * 8);

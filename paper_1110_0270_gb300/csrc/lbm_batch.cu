@@ -292,6 +292,10 @@ lbm_status lbm_batch_create(const lbm_config* cfgs, int n, void* dev_mem, size_t
         p.elbm_max_iter = c->elbm_max_iter;
         p.elbm_norm = c->elbm_norm;
         p.elbm_fallback = c->elbm_fallback;
+        // the rounding of FP32 (or coarser) storage alone leaves Delta S up to
+        // 2^-49 rho: below that the state is at equilibrium as far as the
+        // storage can tell, and the LBGK step is taken as for Delta S < 1e-15
+        p.elbm_skip_rel = c->precision == LBM_FP64 ? 0.0 : 0x1p-48;
         p.counters = (unsigned*)(b->base + I.cnt_off);
         p.stats = (unsigned long long*)(b->base + I.cnt_off + CNT_WORDS * 4);
         p.scratch_d = (double*)(b->base + I.cnt_off + CNT_WORDS * 4 + ST_WORDS * 8);

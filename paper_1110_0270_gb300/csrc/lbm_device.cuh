@@ -340,7 +340,10 @@ __device__ __forceinline__ float delta_s_and_q<9, float>(const float* f, const f
     // with f* > 0, a negative population has x < -1: only the last tier sees one
     if (!(emin > 0.f)) return INFINITY;
     float s = 0.f;
-    if (amax < 0.03125f) {
+    if (amax < 0x1p-12f) {  // fluid at rest or nearly: the omitted x^4/12 is below 2^-26 of x^2/2
+#pragma unroll
+        for (int i = 0; i < 9; ++i) s = fmaf(dx[i], gpoly_f<1>(x[i]), s);
+    } else if (amax < 0.03125f) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) s = fmaf(dx[i], gpoly_f<4>(x[i]), s);
     } else if (amax < 0.25f) {
@@ -548,12 +551,14 @@ struct ElbmOut {
 // greater root of the local second-order Taylor parabola, stop when
 // |S_f / S_f'| ||f* - f|| < eps (Eqs. Stopping, ConvergenceTwo), and take the
 // double Newton step back if the estimate ended above the root.  Sites with
-// Delta S < 1e-15 take the LBGK step.  Where the paper is silent: iterates are
+// Delta S < 1e-15 take the LBGK step (in FP32 or 16-bit storage: below
+// 1e-15 + 2^-48 rho, the floor the storage rounding alone produces).  Where
+// the paper is silent: iterates are
 // kept inside the admissible bracket (1, alpha_max] by bisection; existence
 // of a non-trivial root is decided by the sign of S_f(alpha_max); without a
 // root the configured rule of Section 3.2 applies.
 template <int Q>
-__device__ ElbmOut elbm_alpha(const double* f, const double* feq, const Params& p) {
+__device__ ElbmOut elbm_alpha(const double* f, const double* feq, double rho, const Params& p) {
     ElbmOut o;
     o.iters = 0;
     double D[Q], gm[Q];
@@ -572,7 +577,7 @@ __device__ ElbmOut elbm_alpha(const double* f, const double* feq, const Params& 
         Df[i] = (float)D[i];
         gf[i] = (float)f[i];
     }
-    if (!neg && dS < 1e-15) {
+    if (!neg && dS < 1e-15 + p.elbm_skip_rel * rho) {
         o.alpha = 2.0;
         o.code = 1;
         return o;

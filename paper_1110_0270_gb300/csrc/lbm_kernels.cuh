@@ -42,16 +42,31 @@ __device__ __forceinline__ int lane_id() {
 // atomic each; a full list sets the overflow flag.  The FP64 Delta S is
 // evaluated afterwards by eval_kernel / median_fixup, off the streaming path.
 template <int Q, class T>
-__device__ __forceinline__ void record_candidate(const Params& p, int x, int y, const T* f) {
+struct Pops {
+    T v[Q];
+};
+
+// Out of line: the call is rare, and its address arithmetic and stores stay
+// out of the streaming path's register allocation.
+template <int Q, class T>
+__device__ __noinline__ void record_candidate_cold(const Params& p, int site, Pops<Q, T> f) {
     const unsigned pos = atomicAdd(&p.counters[p.cslot], 1u);
     if (pos < (unsigned)p.cand_cap) {
         T* cf = (T*)p.cand_f;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) cf[(int64_t)i * p.cand_cap + pos] = f[i];
-        p.cand_site[pos] = y * p.nx + x;
+        for (int i = 0; i < Q; ++i) cf[(int64_t)i * p.cand_cap + pos] = f.v[i];
+        p.cand_site[pos] = site;
     } else {
         atomicExch(&p.counters[CNT_OVERFLOW], 1u);
     }
+}
+
+template <int Q, class T>
+__device__ __forceinline__ void record_candidate(const Params& p, int x, int y, const T* f) {
+    Pops<Q, T> v;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) v.v[i] = f[i];
+    record_candidate_cold<Q, T>(p, y * p.nx + x, v);
 }
 
 // Limiter screen of the pre-collision state: the sites that may exceed
@@ -97,7 +112,7 @@ __device__ __forceinline__ void collide_site(const Params& p, int x, int y, cons
         for (int i = 0; i < Q; ++i) fd[i] = (double)f[i];
         moments<Q, double>(fd, r, a, b);
         equilibrium<Q, double>(LBM_EQ_ENTROPIC, r, a, b, fe);
-        ElbmOut out = elbm_alpha<Q>(fd, fe, p);
+        ElbmOut out = elbm_alpha<Q>(fd, fe, r, p);
         e_code = out.code;
         e_iters = out.iters;
         const double ab = out.alpha * p.beta;
@@ -513,6 +528,26 @@ __global__ void __launch_bounds__(256) ehrenfest_eval_select(Params p) {
     __shared__ unsigned s_last;
     unsigned M = p.counters[p.cslot];
     if (M > (unsigned)p.cand_cap) M = (unsigned)p.cand_cap;
+    if (M <= (blockDim.x >> 4)) {
+        // few screened sites (the usual case): the first CTA evaluates them
+        // all, one 16-lane group each, and selects without the ticket and
+        // its memory fences; the other CTAs have nothing to do
+        if (blockIdx.x != 0) return;
+        const unsigned j = threadIdx.x >> 4;
+        if (threadIdx.x == 0) s_last = 0;
+        __syncthreads();
+        const double d = delta_s_group<Q, ST>(p, j, j < M);
+        if (j < M && (threadIdx.x & 15) == 0) {
+            const bool c = d > p.delta;
+            p.cand_ds[j] = c ? d : -1.0;
+            if (c) atomicAdd(&s_last, 1u);
+        }
+        __syncthreads();  // this CTA's cand_ds entries are final
+        const unsigned nvalid = s_last;
+        if (threadIdx.x == 0) p.counters[CNT_NVALID] = nvalid;
+        ehrenfest_select_apply<Q, ST, ODD>(p, M, nvalid);
+        return;
+    }
     unsigned n = 0;
     // one record per 16-lane group
     const unsigned groups = gridDim.x * (blockDim.x >> 4);

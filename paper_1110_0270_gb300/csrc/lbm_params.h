@@ -53,6 +53,7 @@ struct Params {
     MrtRatesF mrt_f;
     double elbm_eps;
     int elbm_max_iter, elbm_norm, elbm_fallback;
+    double elbm_skip_rel;  // near-equilibrium skip: Delta S < 1e-15 + elbm_skip_rel * rho
     // scratch
     unsigned* counters;              // CNT_WORDS words
     unsigned long long* stats;       // ST_WORDS words
