@@ -661,8 +661,73 @@ static int config_ok(const orc_config* cfg) {
     if (cfg->lattice != ORC_D1Q3 && cfg->lattice != ORC_D2Q9) return 0;
     if (cfg->nx < 1 || cfg->ny < 1) return 0;
     if (cfg->lattice == ORC_D1Q3 && cfg->ny != 1) return 0;
-    if (cfg->collision < ORC_LBGK || cfg->collision > ORC_MRT) return 0;
+    if (cfg->collision < ORC_LBGK || cfg->collision > ORC_THRESHOLD) return 0;
     return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Limiter functions of Section 4.2 (smooth regularisation, Eq. smoothReg;  */
+/* ensemble-dependent phi, Eq. phiExamp), Section 4.3 (double monotonic,    */
+/* Eq. DoublMonSpec) and Section 4.4 (threshold, Eqs. EntThresh, entrHom).  */
+/* A state with Delta S = +inf (a negative population) goes to f*: each phi */
+/* tends to 0 as Delta S grows.                                              */
+/* ------------------------------------------------------------------------ */
+
+double orc_phi_smooth(double dS, double alpha, double k) {
+    if (isinf(dS)) return 0.0;
+    return 1.0 / (1.0 + alpha * pow(dS, k));
+}
+
+double orc_phi_double_monotonic(double dS, double dst, double k) {
+    if (isinf(dS)) return 0.0;
+    return pow(1.0 + pow(dS / dst, k), -1.0 / (2.0 * k));
+}
+
+double orc_phi_ensemble(double dS, double alpha, double k, double E) {
+    if (isinf(dS)) return 0.0;
+    if (!(E > 0.0)) return 1.0;
+    double y = dS / (alpha * E);
+    return (1.0 + pow(y, k - 0.5)) / (1.0 + pow(y, k));
+}
+
+static int cmp_desc(const void* a, const void* b) {
+    double x = *(const double*)a, y = *(const double*)b;
+    return x < y ? 1 : (x > y ? -1 : 0);
+}
+
+double orc_threshold_dS0(const double* dS, long long n, double delta0, double beta) {
+    /* finite values, sorted in decreasing order */
+    double* v = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!v) return -1.0;
+    long long m = 0;
+    double total = 0.0;
+    for (long long x = 0; x < n; ++x)
+        if (isfinite(dS[x])) {
+            v[m++] = dS[x];
+            total += dS[x];
+        }
+    qsort(v, (size_t)m, sizeof(double), cmp_desc);
+    double c = 1.0 - (2.0 * beta - 1.0) * (2.0 * beta - 1.0);
+    double R = delta0 * c * total;
+    /* L(t) = sum_x max(v_x - t, 0) is continuous, piecewise linear and
+     * decreasing; on [v_(j+1), v_(j)] (j values above) it is
+     * S_j - j t with S_j the sum of the j largest values.  Walk down the
+     * sorted values until L at the next one reaches R. */
+    double t = 0.0, S = 0.0;
+    int found = 0;
+    for (long long j = 1; j <= m; ++j) {
+        S += v[j - 1];
+        double next = j < m ? v[j] : 0.0;      /* lower end of the piece */
+        double Lnext = S - (double)j * next;   /* L(next) */
+        if (Lnext >= R) {
+            t = (S - R) / (double)j;           /* solve S_j - j t = R */
+            found = 1;
+            break;
+        }
+    }
+    if (!found) t = 0.0;  /* R >= L(0): every value is above the threshold */
+    free(v);
+    return t < 0.0 ? 0.0 : t;
 }
 
 /* One step of Section 2's scheme, collide then stream, applied nsteps times.
@@ -691,14 +756,29 @@ int orc_step(const orc_config* cfg, double* f, int nsteps, orc_stats* st) {
     if (cfg->collision == ORC_MRT) orc_mrt_matrix(cfg, A);
     for (int t = 0; t < nsteps; ++t) {
         double fs[9], feq[9], Fs[9];
-        int nonlocal = cfg->collision == ORC_EHRENFEST || cfg->collision == ORC_MEDIAN;
+        int nonlocal = cfg->collision == ORC_EHRENFEST || cfg->collision == ORC_MEDIAN ||
+                       cfg->collision >= ORC_SMOOTH;
+        double E = 0.0, dSt = 0.0;
         if (nonlocal) {
             orc_delta_s_field(cfg, f, dS);
             if (cfg->collision == ORC_EHRENFEST) {
                 long long nc = orc_select_topk(dS, N, cfg->topk, cfg->delta, mask);
                 if (st) st->candidates += nc;
-            } else {
+            } else if (cfg->collision == ORC_MEDIAN) {
                 orc_median_field(cfg->lattice, cfg->nx, cfg->ny, px, py, dS, med);
+            } else if (cfg->collision == ORC_ENSEMBLE) {
+                /* E(Delta S): mean over the sites with a finite value */
+                long long nf = 0;
+                for (long long x = 0; x < N; ++x)
+                    if (isfinite(dS[x])) {
+                        E += dS[x];
+                        ++nf;
+                    }
+                E = nf > 0 ? E / (double)nf : 0.0;
+            } else if (cfg->collision == ORC_THRESHOLD) {
+                /* Delta S_t = max(Delta S_0, delta) */
+                double d0 = orc_threshold_dS0(dS, N, cfg->lim_delta0, cfg->beta);
+                dSt = d0 > cfg->delta ? d0 : cfg->delta;
             }
         }
         for (long long s = 0; s < N; ++s) {
@@ -714,7 +794,7 @@ int orc_step(const orc_config* cfg, double* f, int nsteps, orc_stats* st) {
                         phi = 0.0; /* Ehrenfest step f -> f* */
                         limited = 1;
                     }
-                } else {
+                } else if (cfg->collision == ORC_MEDIAN) {
                     /* median filter with the homothety of Eq. (entrHom),
                      * accepted only when it lowers Delta S */
                     if (st && dS[s] > cfg->delta) st->candidates++;
@@ -722,6 +802,20 @@ int orc_step(const orc_config* cfg, double* f, int nsteps, orc_stats* st) {
                         phi = isinf(dS[s]) ? 0.0 : sqrt(med[s] / dS[s]);
                         limited = 1;
                     }
+                } else if (cfg->collision == ORC_THRESHOLD) {
+                    /* homothety of Eq. (entrHom) where Delta S >= Delta S_t */
+                    if (dS[s] >= dSt) {
+                        phi = isinf(dS[s]) ? 0.0 : sqrt(dSt / dS[s]);
+                        limited = 1;
+                    }
+                } else {
+                    if (cfg->collision == ORC_SMOOTH)
+                        phi = orc_phi_smooth(dS[s], cfg->lim_alpha, cfg->lim_k);
+                    else if (cfg->collision == ORC_DOUBLE_MONOTONIC)
+                        phi = orc_phi_double_monotonic(dS[s], cfg->lim_dst, cfg->lim_k);
+                    else
+                        phi = orc_phi_ensemble(dS[s], cfg->lim_alpha, cfg->lim_k, E);
+                    limited = phi != 1.0;
                 }
                 /* limiter f -> f* + phi (f - f*) (Eq. LimGenF), then LBGK */
                 for (int i = 0; i < Q; ++i) {

@@ -24,7 +24,13 @@ extern "C" {
 
 enum { ORC_D1Q3 = 1, ORC_D2Q9 = 2 };
 enum { ORC_LBGK = 0, ORC_ELBM = 1, ORC_EHRENFEST = 2, ORC_POSITIVITY = 3,
-       ORC_MEDIAN = 4, ORC_MRT = 5 };
+       ORC_MEDIAN = 4, ORC_MRT = 5,
+       /* limiters of Section 4.2-4.3, each f -> f* + phi(Delta S) (f - f*)
+        * before the LBGK collision */
+       ORC_SMOOTH = 6,            /* phi = 1 / (1 + alpha Delta S^k), Eq. smoothReg */
+       ORC_DOUBLE_MONOTONIC = 7,  /* phi = (1 + (Delta S / Delta S_t)^k)^(-1/(2k)), Eq. DoublMonSpec */
+       ORC_ENSEMBLE = 8,          /* Eq. phiExamp with the lattice mean E(Delta S) */
+       ORC_THRESHOLD = 9 };       /* Eqs. EntThresh, entrHom */
 enum { ORC_EQ_POLY_PRODUCT = 0, ORC_EQ_ENTROPIC = 1, ORC_EQ_POLY_STD = 2 };
 enum { ORC_BC_CAVITY = 0, ORC_BC_ENDS = 1, ORC_BC_PERIODIC = 2,
        ORC_BC_CHANNEL = 3 };
@@ -46,6 +52,10 @@ typedef struct {
     int elbm_max_iter;
     int elbm_norm;     /* ORC_NORM_* */
     int elbm_fallback; /* ORC_FALLBACK_* */
+    double lim_alpha;  /* alpha of Eqs. smoothReg / phiExamp */
+    double lim_k;      /* k of Eqs. smoothReg / phiExamp / DoublMonSpec */
+    double lim_dst;    /* Delta S_t of Eq. DoublMonSpec */
+    double lim_delta0; /* delta_0 of Eqs. LimEntLim / EntThresh */
 } orc_config;
 
 typedef struct {
@@ -108,6 +118,17 @@ void orc_collide_site(const orc_config* cfg, const double* f, double* F,
  * min(k, |C|) sites of C = {x : dS[x] > delta} ordered by (dS desc, x asc). */
 long long orc_select_topk(const double* dS, long long n, int k, double delta,
                           unsigned char* mask);
+/* Limiter functions phi(Delta S) of Section 4.2-4.3 (+inf -> 0). */
+double orc_phi_smooth(double dS, double alpha, double k);
+double orc_phi_double_monotonic(double dS, double dst, double k);
+/* E: the lattice mean of Delta S; E <= 0 (every site at equilibrium) -> 1 */
+double orc_phi_ensemble(double dS, double alpha, double k, double E);
+/* Delta S_0 of Eq. EntThresh for the empirical distribution of the n values
+ * dS (non-finite values are left out): the t >= 0 with
+ * sum_x max(dS_x - t, 0) = delta0 (1 - (2 beta - 1)^2) sum_x dS_x
+ * (0 when the right-hand side reaches the whole sum). */
+double orc_threshold_dS0(const double* dS, long long n, double delta0, double beta);
+
 /* Lower median of the clipped (2r+1)^d window of dS (r = 1). */
 void orc_median_field(int lattice, int nx, int ny, int periodic_x,
                       int periodic_y, const double* dS, double* med);

@@ -20,7 +20,8 @@ _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liblbm_oracle.so")
 
 LATTICES = {"D1Q3": 1, "D2Q9": 2}
-COLLISIONS = {"lbgk": 0, "elbm": 1, "ehrenfest": 2, "positivity": 3, "median": 4, "mrt": 5}
+COLLISIONS = {"lbgk": 0, "elbm": 1, "ehrenfest": 2, "positivity": 3, "median": 4, "mrt": 5,
+              "smooth": 6, "double_monotonic": 7, "ensemble": 8, "threshold": 9}
 EQUILIBRIA = {"poly": 0, "entropic": 1, "poly_std": 2}
 BCS = {"cavity": 0, "ends": 1, "periodic": 2, "channel": 3}
 NORMS = {"entropic": 0, "l1": 1}
@@ -35,6 +36,8 @@ class _Cfg(C.Structure):
         ("delta", C.c_double), ("s_e", C.c_double), ("s_eps", C.c_double),
         ("s_q", C.c_double), ("elbm_eps", C.c_double), ("elbm_max_iter", C.c_int),
         ("elbm_norm", C.c_int), ("elbm_fallback", C.c_int),
+        ("lim_alpha", C.c_double), ("lim_k", C.c_double), ("lim_dst", C.c_double),
+        ("lim_delta0", C.c_double),
     ]
 
 
@@ -64,6 +67,10 @@ class OracleConfig:
     elbm_max_iter: int = 20
     elbm_norm: str = "entropic"
     elbm_fallback: str = "positivity"
+    lim_alpha: float = 1.0
+    lim_k: float = 1.0
+    lim_dst: float = 1e-3
+    lim_delta0: float = 0.01
 
     @classmethod
     def from_dict(cls, d: dict) -> "OracleConfig":
@@ -86,7 +93,9 @@ class OracleConfig:
                     float(self.beta), float(self.lid_u), int(self.topk), float(self.delta),
                     float(self.s_e), float(self.s_eps), float(self.s_q),
                     float(self.elbm_eps), int(self.elbm_max_iter),
-                    NORMS[self.elbm_norm], FALLBACKS[self.elbm_fallback])
+                    NORMS[self.elbm_norm], FALLBACKS[self.elbm_fallback],
+                    float(self.lim_alpha), float(self.lim_k), float(self.lim_dst),
+                    float(self.lim_delta0))
 
 
 _lock = threading.Lock()
@@ -131,6 +140,10 @@ def _L():
                 "orc_collide_site": (None, [p, p, p, p]),
                 "orc_select_topk": (C.c_longlong, [p, C.c_longlong, i, d, p]),
                 "orc_median_field": (None, [i, i, i, i, i, p, p]),
+                "orc_phi_smooth": (d, [d, d, d]),
+                "orc_phi_double_monotonic": (d, [d, d, d]),
+                "orc_phi_ensemble": (d, [d, d, d, d]),
+                "orc_threshold_dS0": (d, [p, C.c_longlong, d, d]),
                 "orc_init_equilibrium": (None, [p, p, p, p, p]),
                 "orc_macros": (None, [p, p, p, p, p]),
                 "orc_delta_s_field": (None, [p, p, p]),
@@ -268,6 +281,27 @@ def select_topk(dS, k: int, delta: float):
     return mask.astype(bool), int(nc)
 
 
+def phi_smooth(dS: float, alpha: float, k: float) -> float:
+    """Eq. smoothReg's example limiter function 1 / (1 + alpha Delta S^k)."""
+    return _L().orc_phi_smooth(float(dS), float(alpha), float(k))
+
+
+def phi_double_monotonic(dS: float, dst: float, k: float) -> float:
+    """Eq. DoublMonSpec: (1 + (Delta S / Delta S_t)^k)^(-1/(2k))."""
+    return _L().orc_phi_double_monotonic(float(dS), float(dst), float(k))
+
+
+def phi_ensemble(dS: float, alpha: float, k: float, E: float) -> float:
+    """Eq. phiExamp with the lattice mean E of Delta S."""
+    return _L().orc_phi_ensemble(float(dS), float(alpha), float(k), float(E))
+
+
+def threshold_dS0(dS, delta0: float, beta: float) -> float:
+    """Delta S_0 of Eq. EntThresh for the empirical distribution of dS."""
+    dS = _f64(dS).ravel()
+    return _L().orc_threshold_dS0(_ptr(dS), dS.size, float(delta0), float(beta))
+
+
 def median_field(name: str, dS, periodic_x=False, periodic_y=False) -> np.ndarray:
     dS = _f64(dS)
     ny, nx = (1, dS.size) if dS.ndim == 1 else dS.shape
@@ -370,5 +404,6 @@ __all__ = ["kinetic_energy", "adjoint_ke",
     "OracleConfig", "build", "lattice", "opposite", "eq1d", "equilibrium", "moments", "gfun",
     "delta_s", "delta_s_direct", "entropy", "entropy_d1q3_paper", "elbm_alpha", "elbm_sf",
     "mrt_basis", "mrt_matrix", "collide_site", "select_topk", "median_field",
+    "phi_smooth", "phi_double_monotonic", "phi_ensemble", "threshold_dS0",
     "init_equilibrium", "macros", "delta_s_field", "total_h", "stream", "step",
 ]

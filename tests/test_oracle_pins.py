@@ -612,3 +612,158 @@ def test_oracle_adjoint_matches_central_differences(case):
     v = np.random.default_rng(8).standard_normal(f0.shape)
     fd = (KE(cfg, f0 + h * v) - KE(cfg, f0 - h * v)) / (2 * h)
     assert abs((g * v).sum() - fd) <= 1e-6 * abs(fd) + 1e-11
+
+
+# ----------------------------------------------------------------------------- Section 4.2-4.4 limiters
+def test_double_monotonic_phi_is_the_general_solution_with_its_eta():
+    """Eq. DoublMonSpec is Eq. DoublMonGen, phi(x) = exp(-1/2 int_0^x eta/chi),
+    with eta(chi) = chi^k / (Delta S_t^k + chi^k): integrated numerically here;
+    and its two limits stated in Section 4.3."""
+    from scipy.integrate import quad
+    for k, dst in [(1.0, 1e-3), (2.0, 5e-4), (0.5, 2e-3), (3.0, 1e-2)]:
+        for x in [1e-6, 3e-4, 1e-3, 7e-3, 0.2]:
+            integral, _ = quad(lambda c: c ** (k - 1) / (dst ** k + c ** k), 0, x, epsabs=0, epsrel=1e-13,
+                               limit=200)
+            assert O.phi_double_monotonic(x, dst, k) == pytest.approx(math.exp(-0.5 * integral), rel=1e-11)
+        # small x: 1 - x^k / (2 k dst^k) + o(x^k); large x: sqrt(dst / x) + o(x^-k)
+        x = 1e-3 * dst
+        assert abs(O.phi_double_monotonic(x, dst, k) - (1 - (x / dst) ** k / (2 * k))) < 2 * (x / dst) ** (2 * k)
+        x = 1e4 * dst
+        assert O.phi_double_monotonic(x, dst, k) == pytest.approx(math.sqrt(dst / x), rel=2 * (dst / x) ** k)
+    assert O.phi_double_monotonic(math.inf, 1e-3, 2.0) == 0.0
+
+
+def _y_phi_monotone(phi, s, ys):
+    v = [y * phi(y * y * s) for y in ys]
+    return all(b >= a * (1 - 1e-12) for a, b in zip(v, v[1:]))
+
+
+def test_smooth_phi_dissipative_and_double_monotonic_only_for_k_at_most_half():
+    """Section 4.3: phi = 1/(1 + alpha Delta S^k) keeps 0 <= phi <= 1 (first
+    condition) and y phi(y^2 s) is non-decreasing (second condition, quadratic
+    approximation) exactly when k <= 1/2."""
+    ys = np.geomspace(1e-3, 1e3, 400)
+    for alpha in [0.5, 10.0, 1e3]:
+        for k in [0.25, 0.5, 1.0, 2.0]:
+            phi = lambda d: O.phi_smooth(d, alpha, k)
+            assert all(0.0 <= phi(d) <= 1.0 for d in np.geomspace(1e-12, 1e6, 50))
+            assert phi(0.0) == 1.0 and phi(math.inf) == 0.0
+            assert _y_phi_monotone(phi, 1e-2, ys) == (k <= 0.5), (alpha, k)
+    # the double monotonic form satisfies both for every k
+    for k in [0.5, 1.0, 3.0]:
+        assert _y_phi_monotone(lambda d: O.phi_double_monotonic(d, 1e-3, k), 1e-2, ys)
+
+
+def test_ensemble_phi_limits():
+    """Eq. phiExamp: phi ~ 1 for Delta S << alpha E and ~ sqrt(alpha E / Delta S)
+    for Delta S >> alpha E (Section 4.2); k = 1 gives (1 + sqrt y)/(1 + y)."""
+    E, alpha = 2e-4, 1.5
+    for k in [1.0, 2.0, 4.0]:
+        for y in [1e-8, 1e-6]:
+            assert O.phi_ensemble(y * alpha * E, alpha, k, E) == pytest.approx(1.0, abs=3 * y ** (k - 0.5))
+        for y in [1e6, 1e8]:
+            d = y * alpha * E
+            assert O.phi_ensemble(d, alpha, k, E) == pytest.approx(math.sqrt(alpha * E / d), rel=3 * y ** -0.5)
+    assert O.phi_ensemble(0.25 * alpha * E, alpha, 1.0, E) == pytest.approx((1 + 0.5) / (1 + 0.25), rel=1e-15)
+    assert O.phi_ensemble(3e-4, alpha, 1.0, 0.0) == 1.0 and O.phi_ensemble(math.inf, alpha, 1.0, E) == 0.0
+
+
+def _L_of_t(v, t):
+    return float(np.maximum(v - t, 0.0).sum())
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_threshold_dS0_solves_entthresh_against_bisection(seed):
+    """Eq. EntThresh on the empirical distribution: sum max(dS - t, 0) equals
+    delta0 (1 - (2 beta - 1)^2) sum dS at the returned t; an independent
+    bisection on the same function agrees; non-finite values are left out."""
+    rng = np.random.default_rng(seed)
+    v = np.exp(rng.normal(-9, 2.5, 2000))
+    v[rng.choice(2000, 30, replace=False)] = 0.0
+    v[:3] = v[3]  # ties
+    beta = 0.93
+    c = 1 - (2 * beta - 1) ** 2
+    for delta0 in [1e-3, 0.05, 0.5]:
+        R = delta0 * c * v.sum()
+        t = O.threshold_dS0(np.concatenate([v, [np.inf, np.nan]]), delta0, beta)
+        assert _L_of_t(v, t) == pytest.approx(R, rel=1e-12)
+        lo, hi = 0.0, float(v.max())
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            lo, hi = (mid, hi) if _L_of_t(v, mid) > R else (lo, mid)
+        assert t == pytest.approx(0.5 * (lo + hi), rel=1e-9)
+    # closed forms: one nonzero value v1 gives t = v1 (1 - delta0 c); a budget
+    # at least the whole sum gives 0
+    assert O.threshold_dS0([2.0, 0.0, 0.0], 0.5, 0.75) == pytest.approx(2.0 * (1 - 0.5 * 0.75))
+    assert O.threshold_dS0([1.0, 3.0], 1.0 / 0.75, 0.75) == 0.0
+
+
+def _limited_state(nx=12, ny=10, seed=31):
+    fl = WL.random_fields(ny, nx, seed, 0.05, 0.05)
+    f = O.init_equilibrium(dict(lattice="D2Q9", nx=nx, ny=ny), fl["rho"], fl["ux"], fl["uy"])
+    f = f * WL.lognormal_factors(f.shape, seed + 1, 0.02)
+    return f * WL.lognormal_factors(f.shape, seed + 2, 1.0) ** (WL.hot_spots(ny, nx, seed + 3, 8, 0.3)[None])
+
+
+def _homothety_then_lbgk_then_stream(cfg, f, phi):
+    """The step of Section 2 with the limiter f -> f* + phi (f - f*) (Eq.
+    LimGenF) before the LBGK collision, built from the oracle's
+    equilibrium, collision-free streaming and per-site phi."""
+    Q, ny, nx = f.shape
+    F = np.empty_like(f)
+    for y in range(ny):
+        for x in range(nx):
+            fe = feq_of("D2Q9", "poly", f[:, y, x])
+            fl = fe + phi[y, x] * (f[:, y, x] - fe)
+            F[:, y, x] = fl + 2 * cfg["beta"] * (fe - fl)
+    return O.stream(cfg, F)
+
+
+@pytest.mark.parametrize("collision", ["smooth", "double_monotonic", "ensemble", "threshold"])
+def test_limiter_steps_compose_phi_homothety_lbgk_and_streaming(collision):
+    """One oracle step of each limiter equals the homothety with the limiter's
+    phi of every site's Delta S (Jacobi), the LBGK collision and the
+    streaming; the limiting cases reduce to LBGK or to the jump to f*."""
+    f = _limited_state()
+    cfg = dict(lattice="D2Q9", nx=12, ny=10, bc="cavity", lid_u=0.05, beta=0.95, collision=collision,
+               lim_alpha=40.0, lim_k=1.0, lim_dst=2e-3, lim_delta0=0.05, delta=1e-4)
+    dS = O.delta_s_field(cfg, f)
+    if collision == "smooth":
+        phi = np.vectorize(lambda d: O.phi_smooth(d, 40.0, 1.0))(dS)
+    elif collision == "double_monotonic":
+        phi = np.vectorize(lambda d: O.phi_double_monotonic(d, 2e-3, 1.0))(dS)
+    elif collision == "ensemble":
+        E = dS[np.isfinite(dS)].mean()
+        phi = np.vectorize(lambda d: O.phi_ensemble(d, 40.0, 1.0, E))(dS)
+    else:
+        dst = max(O.threshold_dS0(dS, 0.05, 0.95), 1e-4)
+        assert dst > 1e-4  # the budget, not delta, sets the threshold here
+        phi = np.where(dS >= dst, np.sqrt(dst / dS), 1.0)
+        assert 0 < np.count_nonzero(phi < 1) < dS.size
+    assert np.abs(O.step(cfg, f, 1) - _homothety_then_lbgk_then_stream(cfg, f, phi)).max() < 1e-14
+    lbgk = O.step(dict(cfg, collision="lbgk"), f, 1)
+    neutral = {"smooth": dict(lim_alpha=0.0), "double_monotonic": dict(lim_dst=1e300),
+               "ensemble": dict(lim_alpha=1e300), "threshold": dict(lim_delta0=0.0, delta=1e300)}
+    assert np.abs(O.step(dict(cfg, **neutral[collision]), f, 1) - lbgk).max() < 1e-14
+
+
+def test_threshold_limiter_removes_the_entropy_budget():
+    """Eq. LimEntLim: when Delta S_0 > delta, the homothety of Eq. entrHom
+    lowers the nonequilibrium entropy of the limited sites by
+    sum (Delta S - Delta S_t) = delta0 (1 - (2 beta - 1)^2) sum Delta S in
+    quadratic approximation; the exact Delta S of the transformed states
+    (computed here) agrees to within the cubic terms."""
+    f = _limited_state(nx=16, ny=16, seed=5)
+    beta, delta0 = 0.9, 0.02
+    cfg = dict(lattice="D2Q9", nx=16, ny=16, beta=beta)
+    dS = O.delta_s_field(cfg, f)
+    dst = O.threshold_dS0(dS, delta0, beta)
+    assert dst > 0
+    removed = 0.0
+    for y, x in zip(*np.nonzero(dS >= dst)):
+        fe = feq_of("D2Q9", "poly", f[:, y, x])
+        fl = fe + math.sqrt(dst / dS[y, x]) * (f[:, y, x] - fe)
+        assert O.delta_s(fl, fe) == pytest.approx(dst, rel=0.05)
+        removed += dS[y, x] - O.delta_s(fl, fe)
+    budget = delta0 * (1 - (2 * beta - 1) ** 2) * dS.sum()
+    assert removed == pytest.approx(budget, rel=0.05)
