@@ -404,6 +404,31 @@ void orc_mrt_matrix(const orc_config* cfg, double* A) {
         }
 }
 
+void orc_mrt2_basis(double* M) {
+    int cx[9], cy[9];
+    double W[9];
+    orc_lattice(ORC_D2Q9, cx, cy, W);
+    for (int i = 0; i < 9; ++i) {
+        double x = cx[i], y = cy[i];
+        double row[9] = {1.0, x, y, x * x + y * y, x * x - y * y, x * y, x * y * y, x * x * y, x * x * y * y};
+        for (int r = 0; r < 9; ++r) M[r * 9 + i] = row[r];
+    }
+}
+
+void orc_mrt2_matrix(const orc_config* cfg, double* A) {
+    double M[81], Minv[81];
+    double snu = 2.0 * cfg->beta;
+    double C[9] = {1.0, 1.0, 1.0, 1.0, snu, snu, 1.0, 1.0, 1.0};
+    orc_mrt2_basis(M);
+    invert(9, M, Minv);
+    for (int r = 0; r < 9; ++r)
+        for (int c = 0; c < 9; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < 9; ++k) s += Minv[r * 9 + k] * C[k] * M[k * 9 + c];
+            A[r * 9 + c] = s;
+        }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Collisions.                                                              */
 /* ------------------------------------------------------------------------ */
@@ -462,7 +487,9 @@ static void collide_local(const orc_config* cfg, const double* A, const double* 
             for (int i = 0; i < Q; ++i) F[i] = f[i] + alpha * cfg->beta * (feq[i] - f[i]);
             break;
         }
-        case ORC_MRT: {
+        case ORC_MRT:
+        case ORC_MRT2: {
+            /* A holds A_1 or A_2 (the caller's choice by collision) */
             for (int r = 0; r < Q; ++r) {
                 double s = 0.0;
                 for (int c = 0; c < Q; ++c) s += A[r * Q + c] * (feq[c] - f[c]);
@@ -483,6 +510,7 @@ static void collide_local(const orc_config* cfg, const double* A, const double* 
 void orc_collide_site(const orc_config* cfg, const double* f, double* F, orc_stats* st) {
     double A[81];
     if (cfg->collision == ORC_MRT) orc_mrt_matrix(cfg, A);
+    if (cfg->collision == ORC_MRT2) orc_mrt2_matrix(cfg, A);
     collide_local(cfg, A, f, F, st);
 }
 
@@ -661,7 +689,8 @@ static int config_ok(const orc_config* cfg) {
     if (cfg->lattice != ORC_D1Q3 && cfg->lattice != ORC_D2Q9) return 0;
     if (cfg->nx < 1 || cfg->ny < 1) return 0;
     if (cfg->lattice == ORC_D1Q3 && cfg->ny != 1) return 0;
-    if (cfg->collision < ORC_LBGK || cfg->collision > ORC_THRESHOLD) return 0;
+    if (cfg->collision < ORC_LBGK || cfg->collision > ORC_MRT_LIMITER) return 0;
+    if ((cfg->collision == ORC_MRT2 || cfg->collision == ORC_MRT_LIMITER) && cfg->lattice != ORC_D2Q9) return 0;
     return 1;
 }
 
@@ -754,14 +783,15 @@ int orc_step(const orc_config* cfg, double* f, int nsteps, orc_stats* st) {
     bc_periodicity(cfg, &px, &py);
     double A[81];
     if (cfg->collision == ORC_MRT) orc_mrt_matrix(cfg, A);
+    if (cfg->collision == ORC_MRT2 || cfg->collision == ORC_MRT_LIMITER) orc_mrt2_matrix(cfg, A);
     for (int t = 0; t < nsteps; ++t) {
         double fs[9], feq[9], Fs[9];
         int nonlocal = cfg->collision == ORC_EHRENFEST || cfg->collision == ORC_MEDIAN ||
-                       cfg->collision >= ORC_SMOOTH;
+                       (cfg->collision >= ORC_SMOOTH && cfg->collision != ORC_MRT2);
         double E = 0.0, dSt = 0.0;
         if (nonlocal) {
             orc_delta_s_field(cfg, f, dS);
-            if (cfg->collision == ORC_EHRENFEST) {
+            if (cfg->collision == ORC_EHRENFEST || cfg->collision == ORC_MRT_LIMITER) {
                 long long nc = orc_select_topk(dS, N, cfg->topk, cfg->delta, mask);
                 if (st) st->candidates += nc;
             } else if (cfg->collision == ORC_MEDIAN) {
@@ -785,6 +815,20 @@ int orc_step(const orc_config* cfg, double* f, int nsteps, orc_stats* st) {
             gather(Q, f, N, s, fs);
             if (!nonlocal) {
                 collide_local(cfg, A, fs, Fs, st);
+            } else if (cfg->collision == ORC_MRT_LIMITER) {
+                /* Section 5: the A_2 collision at the selected sites (the
+                 * Ehrenfest selection of Section 4), LBGK elsewhere */
+                site_equilibrium(cfg, fs, feq);
+                if (mask[s]) {
+                    for (int r = 0; r < Q; ++r) {
+                        double acc = 0.0;
+                        for (int c = 0; c < Q; ++c) acc += A[r * Q + c] * (feq[c] - fs[c]);
+                        Fs[r] = fs[r] + acc;
+                    }
+                    if (st) st->limited_sites++;
+                } else {
+                    lbgk(Q, cfg->beta, fs, feq, Fs);
+                }
             } else {
                 site_equilibrium(cfg, fs, feq);
                 double phi = 1.0;

@@ -30,7 +30,10 @@ enum { ORC_LBGK = 0, ORC_ELBM = 1, ORC_EHRENFEST = 2, ORC_POSITIVITY = 3,
        ORC_SMOOTH = 6,            /* phi = 1 / (1 + alpha Delta S^k), Eq. smoothReg */
        ORC_DOUBLE_MONOTONIC = 7,  /* phi = (1 + (Delta S / Delta S_t)^k)^(-1/(2k)), Eq. DoublMonSpec */
        ORC_ENSEMBLE = 8,          /* Eq. phiExamp with the lattice mean E(Delta S) */
-       ORC_THRESHOLD = 9 };       /* Eqs. EntThresh, entrHom */
+       ORC_THRESHOLD = 9,         /* Eqs. EntThresh, entrHom */
+       /* Section 5's "aggressive" MRT A_2 = M_2^-1 C_2 M_2 */
+       ORC_MRT2 = 10,             /* A_2 collision at every site (D2Q9) */
+       ORC_MRT_LIMITER = 11 };    /* LBGK, A_2 at the Ehrenfest-selected sites */
 enum { ORC_EQ_POLY_PRODUCT = 0, ORC_EQ_ENTROPIC = 1, ORC_EQ_POLY_STD = 2 };
 enum { ORC_BC_CAVITY = 0, ORC_BC_ENDS = 1, ORC_BC_PERIODIC = 2,
        ORC_BC_CHANNEL = 3 };
@@ -108,6 +111,12 @@ void orc_elbm_sf(int Q, const double* f, const double* feq, double alpha,
 /* MRT: A = M^{-1} C M of Section 5 (Q x Q, row major). */
 void orc_mrt_basis(int lattice, double* M);
 void orc_mrt_matrix(const orc_config* cfg, double* A);
+/* M_2 of Section 5: rows 1, v_x, v_y, v_x^2+v_y^2, v_x^2-v_y^2, v_x v_y,
+ * v_x v_y^2, v_x^2 v_y, v_x^2 v_y^2 (the printed row order) evaluated at
+ * the velocities in this oracle's numbering; and A_2 = M_2^-1 C_2 M_2 with
+ * C_2 = diag(1, 1, 1, 1, s_nu, s_nu, 1, 1, 1), s_nu = 2 beta (D2Q9). */
+void orc_mrt2_basis(double* M);
+void orc_mrt2_matrix(const orc_config* cfg, double* A);
 
 /* Collide one site without the nonlocal limiters.  mode: the collision;
  * for EHRENFEST/MEDIAN the caller passes phi (1 = plain LBGK). */

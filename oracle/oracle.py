@@ -21,7 +21,8 @@ _LIB = os.path.join(_HERE, "_build", "liblbm_oracle.so")
 
 LATTICES = {"D1Q3": 1, "D2Q9": 2}
 COLLISIONS = {"lbgk": 0, "elbm": 1, "ehrenfest": 2, "positivity": 3, "median": 4, "mrt": 5,
-              "smooth": 6, "double_monotonic": 7, "ensemble": 8, "threshold": 9}
+              "smooth": 6, "double_monotonic": 7, "ensemble": 8, "threshold": 9, "mrt2": 10,
+              "mrt_limiter": 11}
 EQUILIBRIA = {"poly": 0, "entropic": 1, "poly_std": 2}
 BCS = {"cavity": 0, "ends": 1, "periodic": 2, "channel": 3}
 NORMS = {"entropic": 0, "l1": 1}
@@ -137,6 +138,8 @@ def _L():
                 "orc_elbm_sf": (None, [i, p, p, d, p, p, p]),
                 "orc_mrt_basis": (None, [i, p]),
                 "orc_mrt_matrix": (None, [p, p]),
+                "orc_mrt2_basis": (None, [p]),
+                "orc_mrt2_matrix": (None, [p, p]),
                 "orc_collide_site": (None, [p, p, p, p]),
                 "orc_select_topk": (C.c_longlong, [p, C.c_longlong, i, d, p]),
                 "orc_median_field": (None, [i, i, i, i, i, p, p]),
@@ -261,6 +264,22 @@ def mrt_matrix(cfg) -> np.ndarray:
     c = cfg._c()
     A = np.zeros((cfg.Q, cfg.Q))
     _L().orc_mrt_matrix(C.byref(c), _ptr(A))
+    return A
+
+
+def mrt2_basis() -> np.ndarray:
+    """M_2 of Section 5 in this oracle's velocity numbering."""
+    M = np.zeros((9, 9))
+    _L().orc_mrt2_basis(_ptr(M))
+    return M
+
+
+def mrt2_matrix(cfg) -> np.ndarray:
+    """A_2 = M_2^-1 C_2 M_2 with s_nu = 2 beta."""
+    cfg = _cfg(cfg)
+    c = cfg._c()
+    A = np.zeros((9, 9))
+    _L().orc_mrt2_matrix(C.byref(c), _ptr(A))
     return A
 
 
@@ -404,6 +423,6 @@ __all__ = ["kinetic_energy", "adjoint_ke",
     "OracleConfig", "build", "lattice", "opposite", "eq1d", "equilibrium", "moments", "gfun",
     "delta_s", "delta_s_direct", "entropy", "entropy_d1q3_paper", "elbm_alpha", "elbm_sf",
     "mrt_basis", "mrt_matrix", "collide_site", "select_topk", "median_field",
-    "phi_smooth", "phi_double_monotonic", "phi_ensemble", "threshold_dS0",
+    "phi_smooth", "phi_double_monotonic", "phi_ensemble", "threshold_dS0", "mrt2_basis", "mrt2_matrix",
     "init_equilibrium", "macros", "delta_s_field", "total_h", "stream", "step",
 ]

@@ -767,3 +767,70 @@ def test_threshold_limiter_removes_the_entropy_budget():
         removed += dS[y, x] - O.delta_s(fl, fe)
     budget = delta0 * (1 - (2 * beta - 1) ** 2) * dS.sum()
     assert removed == pytest.approx(budget, rel=0.05)
+
+
+# ----------------------------------------------------------------------------- Section 5, M_2 / A_2
+def test_m2_matches_printed_matrix_after_column_permutation():
+    """The printed M_2 lists its columns in the standard order (rest, E, N, W,
+    S, NE, NW, SW, SE); permuted into the clockwise numbering of Section 5 it
+    equals the oracle's basis built from the monomials."""
+    rows = [list(map(int, l.split())) for l in open(os.path.join(GOLDEN, "m2_matrix.txt"))
+            if l.strip() and not l.startswith("#")]
+    printed = np.array(rows, dtype=float)
+    # clockwise index -> standard column: rest, E, SE, S, SW, W, NW, N, NE
+    to_standard = [0, 1, 8, 4, 7, 3, 6, 2, 5]
+    assert np.array_equal(O.mrt2_basis(), printed[:, to_standard])
+
+
+@pytest.mark.parametrize("beta", [0.6, 0.9, 0.99])
+def test_a2_structure_is_twelve_symmetric_pairs(beta):
+    """A_2 = M_2^-1 C_2 M_2: the rest-free diagonal structure the text
+    describes - off-diagonal entries only as 12 symmetric pairs, each
+    +-(s_nu - 1)/4 (the printed "twelve off diagonal elements" read as pairs)
+    - and A_2 = I for s_nu = 1; it conserves mass and momentum."""
+    A = O.mrt2_matrix(dict(lattice="D2Q9", beta=beta))
+    snu = 2 * beta
+    off = A - np.diag(np.diag(A))
+    nz = np.argwhere(np.abs(off) > 1e-13)
+    assert len(nz) == 24
+    assert np.allclose(off, off.T, atol=1e-14)
+    assert np.allclose(np.abs(off[np.abs(off) > 1e-13]), abs(snu - 1) / 4, atol=1e-14)
+    cx, cy, _ = O.lattice("D2Q9")
+    for row in (np.ones(9), cx, cy):
+        # C_2 = 1 on the conserved moments, which f - f* does not carry: the
+        # collision f - A_2 (f - f*) keeps rho and rho u
+        assert np.allclose(row @ A, row, atol=1e-14)
+    assert np.allclose(O.mrt2_matrix(dict(lattice="D2Q9", beta=0.5)), np.eye(9), atol=1e-14)
+
+
+def test_mrt_limiter_applies_a2_at_the_ehrenfest_selection():
+    """The MRT limiter of Section 5: the sites the Ehrenfest selection picks
+    (k largest Delta S above delta) get F = f - A_2 (f - f*); every other site
+    the LBGK step.  Checked against the LBGK and Ehrenfest steps site by site
+    (periodic, so the streaming is a pure shift)."""
+    ny, nx = 8, 9
+    f = _limited_state(nx=nx, ny=ny, seed=41)
+    common = dict(lattice="D2Q9", nx=nx, ny=ny, beta=0.93, bc="periodic", delta=1e-4, topk=4)
+    dS = O.delta_s_field(common, f)
+    mask, nc = O.select_topk(dS, 4, 1e-4)
+    assert nc > 4
+    g = O.step(dict(common, collision="mrt_limiter"), f, 1)
+    h = O.step(dict(common, collision="lbgk"), f, 1)
+    A = O.mrt2_matrix(common)
+    cx, cy, _ = O.lattice("D2Q9")
+    for y in range(ny):
+        for x in range(nx):
+            fs = f[:, y, x]
+            fe = feq_of("D2Q9", "poly", fs)
+            want = fs - A @ (fs - fe) if mask[y * nx + x] else fs + 2 * 0.93 * (fe - fs)
+            for i in range(9):
+                assert abs(g[i, (y + cy[i]) % ny, (x + cx[i]) % nx] - want[i]) < 1e-15
+    assert np.count_nonzero(np.abs(g - h).sum(0) > 0) <= 9 * 4
+    # the aggressive MRT everywhere: every site with A_2
+    g2 = O.step(dict(common, collision="mrt2"), f, 1)
+    for y in range(ny):
+        for x in range(nx):
+            fs = f[:, y, x]
+            want = fs - A @ (fs - feq_of("D2Q9", "poly", fs))
+            for i in range(9):
+                assert abs(g2[i, (y + cy[i]) % ny, (x + cx[i]) % nx] - want[i]) < 1e-15
