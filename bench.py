@@ -42,8 +42,13 @@ def workload_cfg(collision="ehrenfest", precision="fp32", n=N_SIDE):
     from paper_1110_0270_gb300 import workloads as WL
     cfg, init = WL.cavity(n, RE, LID_U)
     cfg.update(collision=collision, precision=precision, topk=TOPK, delta=DELTA,
-               s_e=1.64, s_eps=1.64, s_q=1.2)
+               s_e=1.64, s_eps=1.64, s_q=1.2, **LIMITER_PARAMS.get(collision, {}))
     return cfg, init
+
+
+# Sections 4.2-4.4 limiters in the variants table
+LIMITER_PARAMS = {"smooth": dict(lim_alpha=40.0, lim_k=1.0), "double_monotonic": dict(lim_dst=2e-3, lim_k=1.5),
+                  "ensemble": dict(lim_alpha=1.0, lim_k=1.0), "threshold": dict(lim_delta0=0.01)}
 
 
 # DRAM bytes per launch of the headline step kernel from the full-size ncu
@@ -179,7 +184,8 @@ def run_variants(n_side, steps, warmup, fma_per_s=None):
     out = {}
     N = n_side * n_side
     for precision in ["fp32", "fp16_dev", "bf16_dev", "fp64"]:
-        for coll in ["lbgk", "ehrenfest", "median", "positivity", "mrt", "elbm"]:
+        for coll in ["lbgk", "ehrenfest", "median", "positivity", "mrt", "elbm", "smooth", "double_monotonic",
+                     "ensemble", "threshold", "mrt2", "mrt_limiter"]:
             cfg, init = workload_cfg(coll, precision, n_side)
             lat = lbm.Lattice(cfg)
             lat.init(init["rho"], init["ux"], init["uy"])

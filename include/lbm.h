@@ -61,7 +61,7 @@
 extern "C" {
 #endif
 
-#define LBM_ABI_VERSION 1
+#define LBM_ABI_VERSION 2
 
 typedef struct lbm_ctx lbm_ctx; /* opaque, owned by the library */
 
@@ -77,7 +77,24 @@ typedef enum {
 
 enum { LBM_D1Q3 = 1, LBM_D2Q9 = 2 };
 enum { LBM_LBGK = 0, LBM_ELBM = 1, LBM_EHRENFEST = 2, LBM_POSITIVITY = 3,
-       LBM_MEDIAN = 4, LBM_MRT = 5 };
+       LBM_MEDIAN = 4, LBM_MRT = 5,
+       /* Limiters of Sections 4.2-4.4: the state moves to
+        * f* + phi(Delta S) (f - f*) before the LBGK collision. */
+       LBM_SMOOTH = 6,           /* phi = 1 / (1 + alpha Delta S^k), Eq. (smoothReg) */
+       LBM_DOUBLE_MONOTONIC = 7, /* phi = (1 + (Delta S / Delta S_t)^k)^(-1/(2k)),
+                                    Eq. (DoublMonSpec) */
+       LBM_ENSEMBLE = 8,         /* Eq. (phiExamp) with E(Delta S) the mean of
+                                    the step's finite Delta S over the lattice */
+       LBM_THRESHOLD = 9,        /* homothety sqrt(Delta S_t / Delta S) where
+                                    Delta S >= Delta S_t = max(Delta S_0, delta),
+                                    Delta S_0 from Eq. (EntThresh) on the step's
+                                    Delta S distribution, Eq. (entrHom) */
+       /* Section 5's "aggressive" MRT A_2 = M_2^-1 C_2 M_2 (D2Q9 only):
+        * every moment but the two shear moments relaxes to equilibrium,
+        * those at s_nu = 2 beta */
+       LBM_MRT2 = 10,            /* F = f - A_2 (f - f*) at every site */
+       LBM_MRT_LIMITER = 11 };   /* LBGK; the Ehrenfest selection (topk, delta)
+                                    gets A_2 instead of f* */
 /* Equilibria: product of the 1D polynomial equilibria of Section 6 (the
  * paper's D2Q9 choice, Section 8), product of the 1D entropic equilibria
  * (always used by ELBM), or the textbook W_i rho (1 + 3cu + 9/2 (cu)^2 - 3/2 u^2). */
@@ -97,7 +114,7 @@ enum { LBM_DTYPE_F64 = 0, LBM_DTYPE_F32 = 1 };
 typedef struct {
     int lattice;     /* LBM_D1Q3 | LBM_D2Q9 */
     int nx, ny;      /* sites; ny = 1 for D1Q3.  nx, ny >= 1 */
-    int collision;   /* LBM_LBGK ... LBM_MRT */
+    int collision;   /* LBM_LBGK ... LBM_MRT_LIMITER */
     int equilibrium; /* LBM_EQ_*; ignored by LBM_ELBM (always entropic) */
     int precision;   /* LBM_FP64 | LBM_FP32 | LBM_BF16_DEV | LBM_FP16_DEV */
     int bc;          /* LBM_BC_* */
@@ -113,12 +130,20 @@ typedef struct {
     int elbm_max_iter;      /* ELBM parabola iterations (>= 1), e.g. 20 */
     int elbm_norm;          /* LBM_NORM_* in the stopping rule */
     int elbm_fallback;      /* rule when no non-trivial root exists */
+    /* Sections 4.2-4.4 limiters (appended in ABI version 2) */
+    double lim_alpha;       /* alpha of Eqs. (smoothReg), (phiExamp); > 0 */
+    double lim_k;           /* k of Eqs. (smoothReg), (phiExamp), (DoublMonSpec); > 0 */
+    double lim_dst;         /* Delta S_t of Eq. (DoublMonSpec); > 0 */
+    double lim_delta0;      /* delta_0 of Eqs. (LimEntLim), (EntThresh); >= 0 */
 } lbm_config;
 
 typedef struct {
     uint64_t steps;            /* steps taken since lbm_init/lbm_set_state */
     uint64_t candidates_last;  /* sites with Delta S > delta in the last step */
-    uint64_t limited_total;    /* limiter corrections applied, cumulative */
+    uint64_t limited_total;    /* limiter corrections applied, cumulative
+                                  (not counted for LBM_SMOOTH,
+                                  LBM_DOUBLE_MONOTONIC, LBM_ENSEMBLE, which act
+                                  on every site) */
     uint64_t elbm_solved;      /* ELBM sites that ran the root finder */
     uint64_t elbm_skipped;     /* ELBM sites with Delta S < 1e-15 */
     uint64_t elbm_fallbacks;   /* ELBM sites without a non-trivial root */
@@ -133,7 +158,8 @@ typedef struct {
 
 /* Fills *cfg with defaults: D2Q9 16x16 cavity, LBGK, product polynomial
  * equilibrium, FP32, beta = 0.9, topk = 0, delta = 1e-3, MRT rates
- * (1.64, 1.54, 1.9), elbm_eps = 1e-15, elbm_max_iter = 20. */
+ * (1.64, 1.54, 1.9), elbm_eps = 1e-15, elbm_max_iter = 20, lim_alpha = 1,
+ * lim_k = 1, lim_dst = 1e-3, lim_delta0 = 0.01. */
 lbm_status lbm_config_default(lbm_config* cfg);
 
 /* Device bytes needed for cfg (populations + scratch).  Fails with
@@ -271,11 +297,11 @@ lbm_status lbm_profile_enable(lbm_ctx* ctx, int enable);
 
 /* Waits for the recorded events and returns, per kernel kind (index
  * LBM_KERNEL_STEP: the fused stream-collide kernel; LBM_KERNEL_FIXUP: the
- * limiter kernel that follows it - FP64 Delta S of the screened sites, then
- * the Ehrenfest selection or the median filter), the number of launches and
- * their summed device
- * time in milliseconds (arrays of LBM_KERNEL_KINDS entries), then clears the
- * record. */
+ * limiter kernels around it - after it, FP64 Delta S of the screened sites
+ * then the Ehrenfest selection, the median filter or the threshold limiter;
+ * before it, the lattice mean of Delta S for LBM_ENSEMBLE), the number of
+ * launches and their summed device time in milliseconds (arrays of
+ * LBM_KERNEL_KINDS entries), then clears the record. */
 lbm_status lbm_profile_read(lbm_ctx* ctx, int* launches, double* ms);
 
 /* ---- Stepping without any device allocation -----------------------------

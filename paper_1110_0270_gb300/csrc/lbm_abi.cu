@@ -34,13 +34,18 @@ size_t storage_bytes(int precision) {
 }
 size_t math_bytes(int precision) { return precision == LBM_FP64 ? 8 : 4; }
 
-bool limiter(int coll) { return coll == LBM_EHRENFEST || coll == LBM_MEDIAN; }
+// collisions with a candidate list and a follow-up kernel
+bool limiter(int coll) {
+    return coll == LBM_EHRENFEST || coll == LBM_MEDIAN || coll == LBM_THRESHOLD || coll == LBM_MRT_LIMITER;
+}
+// collisions that reduce over the lattice each step
+bool reduces(int coll) { return coll == LBM_ENSEMBLE || coll == LBM_THRESHOLD; }
 
 struct Layout {
     int Q, pitch;
     int64_t plane;
     size_t f_off, f_bytes, cnt_off, cand_f_off, cand_ds_off, cand_site_off, cand_sel_off,
-        field_off, staging_off, total;
+        field_off, red_off, staging_off, total;
     int cand_cap;
 };
 
@@ -53,7 +58,9 @@ const char* check_config(const lbm_config* c) {
     if (c->ny > 65535LL * kBlockY) return "ny too large for the launch grid";
     if ((long long)(c->lattice == LBM_D1Q3 ? 3 : 9) * c->ny * ((c->nx + 31) / 32 * 32) >= 0x7fffffffLL)
         return "Q * ny * pitch must be below 2^31 elements";
-    if (c->collision < LBM_LBGK || c->collision > LBM_MRT) return "unknown collision";
+    if (c->collision < LBM_LBGK || c->collision > LBM_MRT_LIMITER) return "unknown collision";
+    if ((c->collision == LBM_MRT2 || c->collision == LBM_MRT_LIMITER) && c->lattice != LBM_D2Q9)
+        return "LBM_MRT2 and LBM_MRT_LIMITER need D2Q9";
     if (c->equilibrium < LBM_EQ_POLY_PRODUCT || c->equilibrium > LBM_EQ_POLY_STD) return "unknown equilibrium";
     if (c->precision < LBM_FP64 || c->precision > LBM_FP16_DEV) return "unknown precision";
     if (c->bc < LBM_BC_CAVITY || c->bc > LBM_BC_CHANNEL) return "unknown boundary condition";
@@ -63,6 +70,15 @@ const char* check_config(const lbm_config* c) {
     if (!std::isfinite(c->lid_u)) return "lid_u must be finite";
     if (c->topk < 0) return "topk must be >= 0";
     if (!(c->delta >= 0.0)) return "delta must be >= 0";
+    if (c->collision == LBM_SMOOTH || c->collision == LBM_ENSEMBLE) {
+        if (!(c->lim_alpha > 0.0 && std::isfinite(c->lim_alpha))) return "lim_alpha must be > 0";
+    }
+    if (c->collision == LBM_SMOOTH || c->collision == LBM_ENSEMBLE || c->collision == LBM_DOUBLE_MONOTONIC) {
+        if (!(c->lim_k > 0.0 && std::isfinite(c->lim_k))) return "lim_k must be > 0";
+    }
+    if (c->collision == LBM_DOUBLE_MONOTONIC && !(c->lim_dst > 0.0)) return "lim_dst must be > 0";
+    if (c->collision == LBM_THRESHOLD && !(c->lim_delta0 >= 0.0 && std::isfinite(c->lim_delta0)))
+        return "lim_delta0 must be >= 0";
     if (c->collision == LBM_ELBM) {
         if (!(c->elbm_eps > 0.0)) return "elbm_eps must be > 0";
         if (c->elbm_max_iter < 1) return "elbm_max_iter must be >= 1";
@@ -97,6 +113,8 @@ Layout layout(const lbm_config* c) {
     off += align_up(cap * 4);
     L.field_off = off;
     off += c->collision == LBM_MEDIAN ? align_up(N * math_bytes(c->precision)) : 0;
+    L.red_off = off;  // kRedSlots sums + kRedSlots counts + E
+    off += reduces(c->collision) ? align_up((2 * kRedSlots + 8) * sizeof(double)) : 0;
     L.staging_off = off;
     off += align_up(3 * N * 8);
     L.total = off;
@@ -172,9 +190,17 @@ cudaError_t enqueue_one_step(lbm_ctx* ctx, bool odd, int cslot, cudaStream_t s) 
     Params q = ctx->p;
     q.cslot = cslot;
     q.pdl = ctx->profiling ? 0 : 1;  // the timing events bracket whole kernels
-    cudaError_t e = traced(ctx, LBM_KERNEL_STEP, s, [&] {
-        return dispatch(ctx->cfg.precision, [&](auto L) { return decltype(L)::step(ctx->Q, coll, odd, q, s); });
-    });
+    cudaError_t e = cudaSuccess;
+    if (coll == LBM_ENSEMBLE)  // E(Delta S) of this step's pre-collision state
+        e = traced(ctx, LBM_KERNEL_FIXUP, s, [&] {
+            return dispatch(ctx->cfg.precision,
+                            [&](auto L) { return decltype(L)::prepass(ctx->Q, coll, odd, q, s); });
+        });
+    if (e == cudaSuccess)
+        e = traced(ctx, LBM_KERNEL_STEP, s, [&] {
+            return dispatch(ctx->cfg.precision,
+                            [&](auto L) { return decltype(L)::step(ctx->Q, coll, odd, q, s); });
+        });
     if (e == cudaSuccess && limiter(coll))
         e = traced(ctx, LBM_KERNEL_FIXUP, s, [&] {
             return dispatch(ctx->cfg.precision,
@@ -246,6 +272,10 @@ lbm_status lbm_config_default(lbm_config* c) {
     c->elbm_max_iter = 20;
     c->elbm_norm = LBM_NORM_ENTROPIC;
     c->elbm_fallback = LBM_FALLBACK_POSITIVITY;
+    c->lim_alpha = 1.0;
+    c->lim_k = 1.0;
+    c->lim_dst = 1e-3;
+    c->lim_delta0 = 0.01;
     return LBM_OK;
 }
 
@@ -307,6 +337,10 @@ lbm_status lbm_create(const lbm_config* cfg, void* dev_mem, size_t bytes, lbm_ct
     // 2^-49 rho: below that the state is at equilibrium as far as the
     // storage can tell, and the LBGK step is taken as for Delta S < 1e-15
     p.elbm_skip_rel = cfg->precision == LBM_FP64 ? 0.0 : 0x1p-48;
+    p.lim_alpha = cfg->lim_alpha;
+    p.lim_k = cfg->lim_k;
+    p.lim_dst = cfg->lim_dst;
+    p.lim_delta0 = cfg->lim_delta0;
     p.counters = (unsigned*)(ctx->base + L.cnt_off);
     p.stats = (unsigned long long*)(ctx->base + L.cnt_off + CNT_WORDS * 4);
     p.scratch_d = (double*)(ctx->base + L.cnt_off + CNT_WORDS * 4 + ST_WORDS * 8);
@@ -316,8 +350,15 @@ lbm_status lbm_create(const lbm_config* cfg, void* dev_mem, size_t bytes, lbm_ct
     p.cand_site = (int*)(ctx->base + L.cand_site_off);
     p.cand_sel = (int*)(ctx->base + L.cand_sel_off);
     p.ds_field = ctx->base + L.field_off;
+    if (reduces(cfg->collision)) {
+        p.red = (double*)(ctx->base + L.red_off);
+        p.lim_E = p.red + 2 * kRedSlots;
+    }
+    p.pipe_ctas = 8 * ctx->nsm;
     ctx->staging = (double*)(ctx->base + L.staging_off);
     cudaError_t e = cudaMemset(ctx->base + L.cnt_off, 0, align_up(CNT_WORDS * 4 + ST_WORDS * 8 + 64));
+    if (e == cudaSuccess && reduces(cfg->collision))
+        e = cudaMemset(ctx->base + L.red_off, 0, (2 * kRedSlots + 8) * sizeof(double));
     const char* where = "cudaMemset of the counters";
     if (e == cudaSuccess) {
         e = build_step_graph(ctx);

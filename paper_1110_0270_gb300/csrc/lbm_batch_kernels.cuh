@@ -38,7 +38,8 @@ __global__ void __launch_bounds__(kBlockX* kBlockY)
     const int x = w.y * kBlockX + threadIdx.x;
     const int y = w.z * kBlockY + threadIdx.y;
     int e_code = -1, e_iters = 0;
-    if (x < sp.nx && y < sp.ny) site_update<Q, ST, COLL, ODD>(sp, x, y, e_code, e_iters);
+    typename ST::T acc = 0;  // no reduction in the batched collisions
+    if (x < sp.nx && y < sp.ny) site_update<Q, ST, COLL, ODD>(sp, x, y, e_code, e_iters, acc);
     if (COLL == LBM_ELBM) elbm_stats(sp, e_code, e_iters);
 }
 

@@ -400,6 +400,35 @@ __device__ __forceinline__ void conserve_mass(T rho, T* F) {
     F[L::rest] = rho - s;
 }
 
+// Section 5's A_2 = M_2^-1 C_2 M_2 on D2Q9: with C_2 = 1 on every monomial
+// moment except v_x^2 - v_y^2 and v_x v_y (rate s_nu = 2 beta), and M_2's
+// rows for those two orthogonal to the others with squared norm 4,
+// A_2 = I + (s_nu - 1)/4 (r4 r4^T + r5 r5^T), r4 = v_x^2 - v_y^2,
+// r5 = v_x v_y per velocity, so F = f - A_2 (f - f*) =
+// f* + (1 - s_nu)/4 (m4 r4 + m5 r5), m = r . (f - f*).
+template <class T>
+__device__ __forceinline__ void mrt2_d2q9(const T* f, const T* feq, T om, T* F) {
+    using L = Lat<9>;
+    T m4 = T(0), m5 = T(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const T d = f[i] - feq[i];
+        const int r4 = L::cx(i) * L::cx(i) - L::cy(i) * L::cy(i), r5 = L::cx(i) * L::cy(i);
+        if (r4 > 0) m4 += d;
+        if (r4 < 0) m4 -= d;
+        if (r5 > 0) m5 += d;
+        if (r5 < 0) m5 -= d;
+    }
+    const T c = (T(1) - om) * T(0.25);
+    m4 *= c;
+    m5 *= c;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int r4 = L::cx(i) * L::cx(i) - L::cy(i) * L::cy(i), r5 = L::cx(i) * L::cy(i);
+        F[i] = feq[i] + T(r4) * m4 + T(r5) * m5;
+    }
+}
+
 // LBGK with over-relaxation, Eq. (CollisionIntegral) with alpha = 2.
 template <int Q, class T>
 __device__ __forceinline__ void lbgk(const T* f, const T* feq, T beta, T* F) {

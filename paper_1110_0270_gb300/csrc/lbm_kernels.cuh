@@ -98,7 +98,8 @@ __device__ __forceinline__ void limiter_screen(const Params& p, int x, int y, co
 // divergence check, equilibrium, limiter screen, collision, exact mass.
 template <int Q, class ST, int COLL>
 __device__ __forceinline__ void collide_site(const Params& p, int x, int y, const typename ST::T* f,
-                                             typename ST::T* F, int& e_code, int& e_iters) {
+                                             typename ST::T* F, int& e_code, int& e_iters,
+                                             typename ST::T& acc) {
     using T = typename ST::T;
     T rho, ux, uy;
     moments<Q, T>(f, rho, ux, uy);
@@ -118,12 +119,42 @@ __device__ __forceinline__ void collide_site(const Params& p, int x, int y, cons
         const double ab = out.alpha * p.beta;
 #pragma unroll
         for (int i = 0; i < Q; ++i) F[i] = (T)(fd[i] + ab * (fe[i] - fd[i]));
+    } else if (COLL >= LBM_SMOOTH && COLL <= LBM_THRESHOLD) {
+        // Sections 4.2-4.4: f -> f* + phi(Delta S) (f - f*), then LBGK, i.e.
+        // F = f* + (1 - 2 beta) phi (f - f*); the threshold limiter's phi is
+        // decided after the step (the sites above Delta S_t are rewritten)
+        T feq[Q], q;
+        equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
+        const T ds = delta_s_and_q<Q, T>(f, feq, q);
+        T phi = T(1);
+        if (COLL == LBM_THRESHOLD) {
+            if (isfinite(ds)) acc += ds;  // the step's sum of Delta S
+            if (median_maybe_above((float)ds, (float)q, (float)rho, p.delta_f)) record_candidate<Q, T>(p, x, y, f);
+        } else if (!(ds < T(INFINITY))) {
+            phi = T(0);  // a negative population: the state goes to f*
+        } else if (COLL == LBM_SMOOTH) {
+            phi = T(1) / (T(1) + T(p.lim_alpha) * pow(ds, T(p.lim_k)));
+        } else if (COLL == LBM_DOUBLE_MONOTONIC) {
+            phi = pow(T(1) + pow(ds / T(p.lim_dst), T(p.lim_k)), T(-0.5) / T(p.lim_k));
+        } else {  // LBM_ENSEMBLE, E from this step's pre-pass
+            const T E = T(*p.lim_E);
+            if (E > T(0)) {
+                const T yv = ds / (T(p.lim_alpha) * E);
+                phi = (T(1) + pow(yv, T(p.lim_k) - T(0.5))) / (T(1) + pow(yv, T(p.lim_k)));
+            }
+        }
+        const T c = (T(1) - (sizeof(T) == 8 ? T(2.0 * p.beta) : T(2) * T(p.beta_f))) * phi;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) F[i] = feq[i] + c * (f[i] - feq[i]);
     } else {
         T feq[Q];
         equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
-        if (COLL == LBM_EHRENFEST || COLL == LBM_MEDIAN) limiter_screen<Q, T, COLL>(p, x, y, f, feq, rho);
+        if (COLL == LBM_EHRENFEST || COLL == LBM_MEDIAN || COLL == LBM_MRT_LIMITER)
+            limiter_screen<Q, T, COLL == LBM_MRT_LIMITER ? LBM_EHRENFEST : COLL>(p, x, y, f, feq, rho);
         if (COLL == LBM_MRT && Q == 9) {
             mrt_d2q9<T>(f, feq, p.mrt, p.mrt_f, F);
+        } else if (COLL == LBM_MRT2 && Q == 9) {
+            mrt2_d2q9<T>(f, feq, sizeof(T) == 8 ? T(2.0 * p.beta) : T(2) * T(p.beta_f), F);
         } else {
             lbgk<Q, T>(f, feq, sizeof(T) == 8 ? T(p.beta) : T(p.beta_f), F);
         }
@@ -138,7 +169,7 @@ __device__ __forceinline__ void collide_site(const Params& p, int x, int y, cons
 // collision, store.
 template <int Q, class ST, int COLL, bool ODD>
 __device__ __forceinline__ void site_update(const Params& p, int x, int y, int& e_code,
-                                            int& e_iters) {
+                                            int& e_iters, typename ST::T& acc) {
     using T = typename ST::T;
     T f[Q], F[Q];
     const bool interior = x > 0 && x < p.nx - 1 && (Q == 3 || (y > 0 && y < p.ny - 1));
@@ -147,7 +178,7 @@ __device__ __forceinline__ void site_update(const Params& p, int x, int y, int& 
         load_interior<Q, ST, ODD>(p, o, f);
     else
         load_general<Q, ST, ODD>(p, x, y, f);
-    collide_site<Q, ST, COLL>(p, x, y, f, F, e_code, e_iters);
+    collide_site<Q, ST, COLL>(p, x, y, f, F, e_code, e_iters, acc);
     if (interior)
         store_interior<Q, ST, ODD>(p, o, F);
     else
@@ -170,30 +201,71 @@ __device__ __forceinline__ void elbm_stats(const Params& p, int e_code, int e_it
     }
 }
 
+// CTA-wide sums of a and b added to partial-sum slot (linear block id mod
+// kRedSlots) of p.red (and, with two, of p.red + kRedSlots).  Every thread
+// of the CTA calls it.  The warp stage adds in T (FP32 in the 16/32-bit
+// modes: 32 values, relative error ~1e-6 at worst, far below the FP32
+// parity bound - GB300's FP64 pipe would otherwise cost more than the
+// step's streaming), the rest in FP64.
+template <class T>
+__device__ __forceinline__ void block_sum_to_slots(const Params& p, T a, T b, bool two) {
+    __shared__ double red_a[32], red_b[32];
+    const unsigned full = 0xffffffffu;
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(full, a, o);
+        if (two) b += __shfl_xor_sync(full, b, o);
+    }
+    const int t = threadIdx.y * blockDim.x + threadIdx.x, w = t >> 5;
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    if ((t & 31) == 0) {
+        red_a[w] = (double)a;
+        red_b[w] = (double)b;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double sa = 0.0, sb = 0.0;
+        for (int k = 0; k < nw; ++k) {
+            sa += red_a[k];
+            sb += red_b[k];
+        }
+        const unsigned slot = (blockIdx.y * gridDim.x + blockIdx.x) & (kRedSlots - 1);
+        if (sa != 0.0) atomicAdd(&p.red[slot], sa);
+        if (two && sb != 0.0) atomicAdd(&p.red[kRedSlots + slot], sb);
+    }
+}
+
 // Resident 256-thread CTAs per SM the FP32-arithmetic step kernels are
 // compiled for: the streaming step needs the warps to hide HBM latency.
 // Ehrenfest and positivity: eight (32 registers, a few bytes of spills;
 // measured 4% faster than six); median: six (at 32 registers its FP32
-// Delta S spills ~200 bytes).  0 leaves the choice to the compiler (LBGK and
+// Delta S spills ~200 bytes) and the Section 4.2-4.4 limiters (four bytes
+// of spills).  0 leaves the choice to the compiler (LBGK and
 // MRT fit in 32-38 registers by themselves; ELBM and FP64 storage are not
 // capped).
 template <class ST, int COLL>
 constexpr int kMinBlocks =
-    sizeof(typename ST::T) != 4 ? 0 : (COLL == LBM_EHRENFEST || COLL == LBM_POSITIVITY) ? 8 : COLL == LBM_MEDIAN ? 6 : 0;
+    sizeof(typename ST::T) != 4
+        ? 0
+        : (COLL == LBM_EHRENFEST || COLL == LBM_POSITIVITY || COLL == LBM_MRT_LIMITER)
+              ? 8
+              : (COLL == LBM_MEDIAN || (COLL >= LBM_SMOOTH && COLL <= LBM_THRESHOLD)) ? 6 : 0;
 
 template <int Q, class ST, int COLL, bool ODD>
 __global__ void __launch_bounds__(kBlockX* kBlockY, kMinBlocks<ST, COLL>) step_kernel(Params p) {
     pdl_enter();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    constexpr bool kLimiter = (COLL == LBM_EHRENFEST || COLL == LBM_MEDIAN);
+    constexpr bool kLimiter =
+        (COLL == LBM_EHRENFEST || COLL == LBM_MEDIAN || COLL == LBM_THRESHOLD || COLL == LBM_MRT_LIMITER);
     if (kLimiter && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
         p.counters[p.cslot ^ 1] = 0u;  // the next step's list starts empty
         p.counters[CNT_NVALID] = 0u;   // counted by this step's eval / median kernel
     }
     int e_code = -1, e_iters = 0;
-    if (x < p.nx && y < p.ny) site_update<Q, ST, COLL, ODD>(p, x, y, e_code, e_iters);
+    typename ST::T acc = 0;
+    if (x < p.nx && y < p.ny) site_update<Q, ST, COLL, ODD>(p, x, y, e_code, e_iters, acc);
     if (COLL == LBM_ELBM) elbm_stats(p, e_code, e_iters);
+    if (COLL == LBM_THRESHOLD) block_sum_to_slots<typename ST::T>(p, acc, 0, false);
 }
 
 // Two sites per thread (x0 = 2t, x0 + 1): every population plane moves with
@@ -213,7 +285,9 @@ __global__ void __launch_bounds__(kBlockX* kBlockY, kMinBlocks<ST, COLL>) step_k
 constexpr int kVecX = 64;
 constexpr int kVecY = 4;
 template <class ST, int COLL>
-constexpr bool kPairedSites = sizeof(typename ST::S) == 2 && COLL != LBM_ELBM && COLL != LBM_MEDIAN;
+constexpr bool kPairedSites = sizeof(typename ST::S) == 2 &&
+                              (COLL == LBM_LBGK || COLL == LBM_EHRENFEST || COLL == LBM_POSITIVITY ||
+                               COLL == LBM_MRT || COLL == LBM_MRT2 || COLL == LBM_MRT_LIMITER);
 
 template <int Q, class ST, int COLL, bool ODD>
 __global__ void __launch_bounds__(kVecX* kVecY, 6) step_kernel_v2(Params p) {
@@ -223,7 +297,8 @@ __global__ void __launch_bounds__(kVecX* kVecY, 6) step_kernel_v2(Params p) {
     using L = Lat<Q>;
     const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    constexpr bool kLimiter = (COLL == LBM_EHRENFEST || COLL == LBM_MEDIAN);
+    constexpr bool kLimiter =
+        (COLL == LBM_EHRENFEST || COLL == LBM_MEDIAN || COLL == LBM_THRESHOLD || COLL == LBM_MRT_LIMITER);
     if (kLimiter && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
         p.counters[p.cslot ^ 1] = 0u;
         p.counters[CNT_NVALID] = 0u;
@@ -233,8 +308,9 @@ __global__ void __launch_bounds__(kVecX* kVecY, 6) step_kernel_v2(Params p) {
     const bool inner = y > 0 && y < p.ny - 1 && x0 > 0 && x0 + 2 < p.nx;
     if (!__all_sync(full, inner)) {
         if (y < p.ny) {
-            if (x0 < p.nx) site_update<Q, ST, COLL, ODD>(p, x0, y, e_code, e_iters);
-            if (x0 + 1 < p.nx) site_update<Q, ST, COLL, ODD>(p, x0 + 1, y, e_code, e_iters);
+            T acc = 0;  // no reduction in the collisions of this kernel
+            if (x0 < p.nx) site_update<Q, ST, COLL, ODD>(p, x0, y, e_code, e_iters, acc);
+            if (x0 + 1 < p.nx) site_update<Q, ST, COLL, ODD>(p, x0 + 1, y, e_code, e_iters, acc);
         }
         return;
     }
@@ -265,8 +341,9 @@ __global__ void __launch_bounds__(kVecX* kVecY, 6) step_kernel_v2(Params p) {
         }
     }
     T Fa[Q], Fb[Q];
-    collide_site<Q, ST, COLL>(p, x0, y, fa, Fa, e_code, e_iters);
-    collide_site<Q, ST, COLL>(p, x0 + 1, y, fb, Fb, e_code, e_iters);
+    T acc = 0;
+    collide_site<Q, ST, COLL>(p, x0, y, fa, Fa, e_code, e_iters, acc);
+    collide_site<Q, ST, COLL>(p, x0 + 1, y, fb, Fb, e_code, e_iters, acc);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int k = ODD ? L::opp(i) : i;
@@ -406,9 +483,152 @@ __device__ __forceinline__ int pick_digit(const unsigned* hist, unsigned& rem, b
     return digit;
 }
 
+// Sum over the CTA, returned to every thread (every thread calls it).
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double part[32];
+    __shared__ double total;
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();  // part / total free from a previous call
+    if ((t & 31) == 0) part[t >> 5] = v;
+    __syncthreads();
+    if (t < 32) {
+        double u = t < nw ? part[t] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+        if (t == 0) total = u;
+    }
+    __syncthreads();
+    return total;
+}
+
+// Threshold limiter (Section 4.4), one CTA after every cand_ds entry of the
+// step is final (FP64 Delta S of the screened sites, -1 where not above
+// delta).  With S the step's sum of Delta S over the lattice (partial sums
+// of the step kernel) and R = delta0 (1 - (2 beta - 1)^2) S, the threshold
+// Delta S_0 of Eq. (EntThresh) solves L(t) = sum max(Delta S - t, 0) = R.
+// Only sites above delta matter when L(delta) > R (otherwise Delta S_t =
+// delta); then the sites whose L(Delta S) < R (the "upper" set, n of them
+// with sum S_u) are found by an MSB radix descent over the FP64 bits of the
+// candidate values with per-bin counts and sums, and Delta S_0 =
+// (S_u - R) / n, the root on the linear piece of L below them.  Sites with
+// Delta S >= Delta S_t = max(Delta S_0, delta) get the homothety
+// sqrt(Delta S_t / Delta S) of Eq. (entrHom) before the LBGK collision.
+template <int Q, class ST, bool ODD>
+__device__ void threshold_select_apply(const Params& p, unsigned M) {
+    using T = typename ST::T;
+    __shared__ unsigned cnt[256];
+    __shared__ double hsum[256];
+    __shared__ unsigned long long s_prefix, s_mask;
+    __shared__ double s_cntA, s_sumA;
+    __shared__ int s_done;
+    __shared__ unsigned s_count;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    // the step's sum of Delta S; the slots are cleared for the next step
+    double S = 0.0;
+    for (int k = tid; k < kRedSlots; k += nt) {
+        S += __ldcg(&p.red[k]);
+        p.red[k] = 0.0;
+    }
+    S = block_sum(S);
+    const double c = 1.0 - (2.0 * p.beta - 1.0) * (2.0 * p.beta - 1.0);
+    const double R = p.lim_delta0 * c * S;
+    double Ld = 0.0;
+    for (unsigned j = tid; j < M; j += nt) {
+        const double v = __ldcg(&p.cand_ds[j]);
+        if (v > p.delta && v < INFINITY) Ld += v - p.delta;
+    }
+    Ld = block_sum(Ld);
+    double dst = p.delta;
+    if (Ld > R) {
+        if (tid == 0) {
+            s_prefix = 0ull;
+            s_mask = 0ull;
+            s_cntA = 0.0;
+            s_sumA = 0.0;
+            s_done = 0;
+        }
+        __syncthreads();
+        for (int shift = 56; shift >= 0; shift -= 8) {
+            if (s_done) break;  // uniform: read after the barrier
+            for (int d = tid; d < 256; d += nt) {
+                cnt[d] = 0u;
+                hsum[d] = 0.0;
+            }
+            __syncthreads();
+            const unsigned long long pre = s_prefix, msk = s_mask;
+            for (unsigned j = tid; j < M; j += nt) {
+                const double v = __ldcg(&p.cand_ds[j]);
+                if (!(v > p.delta && v < INFINITY)) continue;
+                const unsigned long long key = (unsigned long long)__double_as_longlong(v);
+                if ((key & msk) != pre) continue;
+                const int d = (int)((key >> shift) & 255ull);
+                atomicAdd(&cnt[d], 1u);
+                atomicAdd(&hsum[d], v);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                // bins from the top: the first whose lower bound b has
+                // L(b) >= R holds the boundary; the bins above it are upper
+                double cA = s_cntA, sA = s_sumA;
+                int chosen = -1;
+                for (int d = 255; d >= 0; --d) {
+                    const double ci = cA + (double)cnt[d], si = sA + hsum[d];
+                    const double b = __longlong_as_double((long long)(pre | ((unsigned long long)d << shift)));
+                    if (si - b * ci >= R) {
+                        chosen = d;
+                        break;
+                    }
+                    cA = ci;
+                    sA = si;
+                }
+                s_cntA = cA;
+                s_sumA = sA;
+                if (chosen < 0) {
+                    s_done = 1;
+                } else {
+                    s_prefix = pre | ((unsigned long long)chosen << shift);
+                    s_mask = msk | (255ull << shift);
+                }
+            }
+            __syncthreads();
+        }
+        // n = 0: R <= 0 and the boundary is the largest value itself
+        const double t0 = s_cntA > 0.0 ? (s_sumA - R) / s_cntA : __longlong_as_double((long long)s_prefix);
+        dst = t0 > p.delta ? t0 : p.delta;
+    }
+    if (tid == 0) s_count = 0u;
+    __syncthreads();
+    unsigned mine = 0;
+    const T om1 = sizeof(T) == 8 ? T(1.0 - 2.0 * p.beta) : T(1) - T(2) * T(p.beta_f);
+    for (unsigned j = tid; j < M; j += nt) {
+        const double v = __ldcg(&p.cand_ds[j]);
+        const bool sel = v >= dst;  // +inf included, -1 (not above delta) excluded
+        p.cand_sel[j] = sel ? 1 : 0;
+        if (!sel) continue;
+        const T phi = v < INFINITY ? T(sqrt(dst / v)) : T(0);
+        T f[Q], feq[Q], F[Q], rho, ux, uy;
+        load_candidate<Q, ST>(p, (int)j, f);
+        moments<Q, T>(f, rho, ux, uy);
+        equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) F[i] = feq[i] + om1 * phi * (f[i] - feq[i]);
+        conserve_mass<Q, T>(rho, F);
+        rewrite_site<Q, ST, ODD>(p, p.cand_site[j], F);
+        ++mine;
+    }
+    if (mine) atomicAdd(&s_count, mine);
+    __syncthreads();
+    if (tid == 0) {
+        p.counters[CNT_NSEL] = s_count;
+        if (s_count) atomicAdd(&p.stats[ST_LIMITED], (unsigned long long)s_count);
+        *p.lim_E = dst;  // the step's Delta S_t, for inspection
+    }
+}
+
 // Runs in one CTA of any size after every cand_ds entry of the step is final
 // (the entries of other CTAs are read through L2).
-template <int Q, class ST, bool ODD>
+template <int Q, class ST, bool ODD, int COLL = LBM_EHRENFEST>
 __device__ void ehrenfest_select_apply(const Params& p, unsigned M, unsigned nvalid) {
     using T = typename ST::T;
     __shared__ unsigned hist[256];
@@ -505,8 +725,16 @@ __device__ void ehrenfest_select_apply(const Params& p, unsigned M, unsigned nva
             load_candidate<Q, ST>(p, (int)j, f);
             moments<Q, T>(f, rho, ux, uy);
             equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
-            conserve_mass<Q, T>(rho, feq);
-            rewrite_site<Q, ST, ODD>(p, p.cand_site[j], feq);
+            if constexpr (COLL == LBM_MRT_LIMITER && Q == 9) {
+                // Section 5's MRT limiter: the selected site takes A_2, not f*
+                T F[Q];
+                mrt2_d2q9<T>(f, feq, sizeof(T) == 8 ? T(2.0 * p.beta) : T(2) * T(p.beta_f), F);
+                conserve_mass<Q, T>(rho, F);
+                rewrite_site<Q, ST, ODD>(p, p.cand_site[j], F);
+            } else {
+                conserve_mass<Q, T>(rho, feq);
+                rewrite_site<Q, ST, ODD>(p, p.cand_site[j], feq);
+            }
             ++mine;
         }
     }
@@ -521,10 +749,16 @@ __device__ void ehrenfest_select_apply(const Params& p, unsigned M, unsigned nva
 // Ehrenfest step, second kernel: the FP64 Delta S of every screened site
 // (grid-stride), then the last CTA to finish - found by a ticket counter after
 // a memory fence, no waiting - selects the k largest and rewrites them.
-template <int Q, class ST, bool ODD>
-__global__ void __launch_bounds__(256) ehrenfest_eval_select(Params p) {
-    pdl_enter();
-    using T = typename ST::T;
+template <int Q, class ST, bool ODD, int COLL>
+__device__ __forceinline__ void select_apply(const Params& p, unsigned M, unsigned nvalid) {
+    if constexpr (COLL == LBM_THRESHOLD)
+        threshold_select_apply<Q, ST, ODD>(p, M);
+    else
+        ehrenfest_select_apply<Q, ST, ODD, COLL>(p, M, nvalid);
+}
+
+template <int Q, class ST, bool ODD, int COLL>
+__device__ __forceinline__ void eval_then_select(const Params& p) {
     __shared__ unsigned s_last;
     unsigned M = p.counters[p.cslot];
     if (M > (unsigned)p.cand_cap) M = (unsigned)p.cand_cap;
@@ -545,7 +779,7 @@ __global__ void __launch_bounds__(256) ehrenfest_eval_select(Params p) {
         __syncthreads();  // this CTA's cand_ds entries are final
         const unsigned nvalid = s_last;
         if (threadIdx.x == 0) p.counters[CNT_NVALID] = nvalid;
-        ehrenfest_select_apply<Q, ST, ODD>(p, M, nvalid);
+        select_apply<Q, ST, ODD, COLL>(p, M, nvalid);
         return;
     }
     unsigned n = 0;
@@ -570,8 +804,83 @@ __global__ void __launch_bounds__(256) ehrenfest_eval_select(Params p) {
     if (!s_last) return;
     __threadfence();
     const unsigned nvalid = atomicAdd(&p.counters[CNT_NVALID], 0u);
-    ehrenfest_select_apply<Q, ST, ODD>(p, M, nvalid);
+    select_apply<Q, ST, ODD, COLL>(p, M, nvalid);
     if (threadIdx.x == 0) p.counters[CNT_DONE] = 0u;
+}
+
+template <int Q, class ST, bool ODD>
+__global__ void __launch_bounds__(256) ehrenfest_eval_select(Params p) {
+    pdl_enter();
+    eval_then_select<Q, ST, ODD, LBM_EHRENFEST>(p);
+}
+
+// MRT limiter (Section 5), second kernel: the Ehrenfest selection; the
+// selected sites take the A_2 collision.
+template <int Q, class ST, bool ODD>
+__global__ void __launch_bounds__(256) mrt_limiter_eval_select(Params p) {
+    pdl_enter();
+    eval_then_select<Q, ST, ODD, LBM_MRT_LIMITER>(p);
+}
+
+// Threshold limiter, second kernel: FP64 Delta S of the screened sites as
+// above, then (one CTA) Delta S_t and the homothety of the sites above it.
+template <int Q, class ST, bool ODD>
+__global__ void __launch_bounds__(256) threshold_eval_select(Params p) {
+    pdl_enter();
+    eval_then_select<Q, ST, ODD, LBM_THRESHOLD>(p);
+}
+
+// Lattice mean of the finite Delta S of the pre-collision state of the
+// coming step (parity ODD), for the ensemble-dependent limiter: per-CTA sums
+// into slots, then the last CTA to finish (ticket after a fence) adds the
+// slots, clears them and writes E.
+template <int Q, class ST, bool ODD>
+__global__ void __launch_bounds__(256) ensemble_mean(Params p) {
+    pdl_enter();
+    using T = typename ST::T;
+    __shared__ unsigned s_last;
+    // a fixed grid strides over row segments of blockDim.x sites (few CTAs:
+    // few ticket atomics)
+    const int t = threadIdx.x, nt = blockDim.x;
+    const int tpr = (p.nx + nt - 1) / nt;
+    T sum = 0, cnt = 0;
+    for (int tile = blockIdx.x; tile < tpr * p.ny; tile += gridDim.x) {
+        const int y = tile / tpr, x = (tile - y * tpr) * nt + t;
+        if (x >= p.nx) continue;
+        T f[Q], feq[Q], rho, ux, uy, q;
+        const bool interior = x > 0 && x < p.nx - 1 && (Q == 3 || (y > 0 && y < p.ny - 1));
+        if (interior)
+            load_interior<Q, ST, ODD>(p, y * p.pitch + x, f);
+        else
+            load_general<Q, ST, ODD>(p, x, y, f);
+        moments<Q, T>(f, rho, ux, uy);
+        equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
+        const T ds = delta_s_and_q<Q, T>(f, feq, q);
+        if (isfinite(ds)) {
+            sum += ds;
+            cnt += T(1);
+        }
+    }
+    block_sum_to_slots<T>(p, sum, cnt, true);
+    __threadfence();
+    __syncthreads();
+    if (t == 0) s_last = atomicAdd(&p.counters[CNT_DONE], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double S = 0.0, N = 0.0;
+    for (int k = t; k < kRedSlots; k += nt) {
+        S += __ldcg(&p.red[k]);
+        N += __ldcg(&p.red[kRedSlots + k]);
+        p.red[k] = 0.0;
+        p.red[kRedSlots + k] = 0.0;
+    }
+    S = block_sum(S);
+    N = block_sum(N);
+    if (t == 0) {
+        *p.lim_E = N > 0.0 ? S / N : 0.0;
+        p.counters[CNT_DONE] = 0u;
+    }
 }
 
 // Median entropy filter (Section 4.4): lower median of Delta S over the site
@@ -783,6 +1092,7 @@ template <class ST>
 struct Launch {
     static cudaError_t step(int Q, int coll, bool odd, const Params& p, cudaStream_t s);
     static cudaError_t fixup(int Q, int coll, bool odd, const Params& p, cudaStream_t s, int nsm);
+    static cudaError_t prepass(int Q, int coll, bool odd, const Params& p, cudaStream_t s);
     static cudaError_t init(int Q, const Params& p, const double* r, const double* ux,
                             const double* uy, int eqkind, cudaStream_t s);
     static cudaError_t init_uniform(int Q, const Params& p, double r, double ux, double uy,
@@ -846,6 +1156,12 @@ cudaError_t launch_step_c(int coll, bool odd, const Params& p, cudaStream_t s) {
         case LBM_POSITIVITY: return launch_step_q<Q, ST, LBM_POSITIVITY>(odd, p, s);
         case LBM_MEDIAN: return launch_step_q<Q, ST, LBM_MEDIAN>(odd, p, s);
         case LBM_MRT: return launch_step_q<Q, ST, LBM_MRT>(odd, p, s);
+        case LBM_SMOOTH: return launch_step_q<Q, ST, LBM_SMOOTH>(odd, p, s);
+        case LBM_DOUBLE_MONOTONIC: return launch_step_q<Q, ST, LBM_DOUBLE_MONOTONIC>(odd, p, s);
+        case LBM_ENSEMBLE: return launch_step_q<Q, ST, LBM_ENSEMBLE>(odd, p, s);
+        case LBM_THRESHOLD: return launch_step_q<Q, ST, LBM_THRESHOLD>(odd, p, s);
+        case LBM_MRT2: return launch_step_q<Q, ST, LBM_MRT2>(odd, p, s);
+        case LBM_MRT_LIMITER: return launch_step_q<Q, ST, LBM_MRT_LIMITER>(odd, p, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -859,12 +1175,30 @@ cudaError_t launch_fixup_q(int coll, bool odd, const Params& p, cudaStream_t s, 
                         256, s, p);
     if (coll == LBM_MEDIAN)
         return launch_p(odd ? median_fixup<Q, ST, true> : median_fixup<Q, ST, false>, nsm, 256, s, p);
+    if (coll == LBM_THRESHOLD)
+        return launch_p(odd ? threshold_eval_select<Q, ST, true> : threshold_eval_select<Q, ST, false>, nsm,
+                        256, s, p);
+    if (coll == LBM_MRT_LIMITER)
+        return launch_p(odd ? mrt_limiter_eval_select<Q, ST, true> : mrt_limiter_eval_select<Q, ST, false>, nsm,
+                        256, s, p);
     return cudaSuccess;
+}
+
+template <int Q, class ST>
+cudaError_t launch_prepass_q(int coll, bool odd, const Params& p, cudaStream_t s) {
+    if (coll != LBM_ENSEMBLE) return cudaSuccess;
+    return launch_p(odd ? ensemble_mean<Q, ST, true> : ensemble_mean<Q, ST, false>, dim3(p.pipe_ctas), dim3(256),
+                    s, p);
 }
 
 template <class ST>
 cudaError_t Launch<ST>::step(int Q, int coll, bool odd, const Params& p, cudaStream_t s) {
     return Q == 3 ? launch_step_c<3, ST>(coll, odd, p, s) : launch_step_c<9, ST>(coll, odd, p, s);
+}
+
+template <class ST>
+cudaError_t Launch<ST>::prepass(int Q, int coll, bool odd, const Params& p, cudaStream_t s) {
+    return Q == 3 ? launch_prepass_q<3, ST>(coll, odd, p, s) : launch_prepass_q<9, ST>(coll, odd, p, s);
 }
 
 template <class ST>

@@ -27,6 +27,8 @@ enum Counter {
     CNT_DONE = 6,      // CTAs of ehrenfest_eval_select that have finished
     CNT_WORDS = 8
 };
+constexpr int kRedSlots = 1024;  // partial-sum slots (spread the atomics)
+
 enum Stat {
     ST_LIMITED = 0,
     ST_ELBM_SOLVED = 1,
@@ -54,6 +56,11 @@ struct Params {
     double elbm_eps;
     int elbm_max_iter, elbm_norm, elbm_fallback;
     double elbm_skip_rel;  // near-equilibrium skip: Delta S < 1e-15 + elbm_skip_rel * rho
+    // Sections 4.2-4.4 limiters
+    double lim_alpha, lim_k, lim_dst, lim_delta0;
+    double* red;      // kRedSlots partial sums (+ kRedSlots counts), zero between steps
+    double* lim_E;    // the step's E(Delta S) (ensemble limiter)
+    int pipe_ctas;    // host side: CTAs of the grid-stride reduction kernels
     // scratch
     unsigned* counters;              // CNT_WORDS words
     unsigned long long* stats;       // ST_WORDS words

@@ -17,13 +17,16 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "liblbm.so")
 
 LATTICES = {"D1Q3": 1, "D2Q9": 2}
-COLLISIONS = {"lbgk": 0, "elbm": 1, "ehrenfest": 2, "positivity": 3, "median": 4, "mrt": 5}
+COLLISIONS = {"lbgk": 0, "elbm": 1, "ehrenfest": 2, "positivity": 3, "median": 4, "mrt": 5,
+              "smooth": 6, "double_monotonic": 7, "ensemble": 8, "threshold": 9, "mrt2": 10,
+              "mrt_limiter": 11}
 EQUILIBRIA = {"poly": 0, "entropic": 1, "poly_std": 2}
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16_dev": 2, "fp16_dev": 3}
 BCS = {"cavity": 0, "ends": 1, "periodic": 2, "channel": 3}
 NORMS = {"entropic": 0, "l1": 1}
 FALLBACKS = {"positivity": 0, "ehrenfest": 1}
 DTYPE_F64, DTYPE_F32 = 0, 1
+ABI_VERSION = 2  # LBM_ABI_VERSION of include/lbm.h (lbm_config layout)
 STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_CUDA", 3: "LBM_ERR_OOM",
           4: "LBM_ERR_DIVERGED", 5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_STATE"}
 
@@ -48,6 +51,8 @@ class lbm_config(C.Structure):
         ("s_e", C.c_double), ("s_eps", C.c_double), ("s_q", C.c_double),
         ("elbm_eps", C.c_double), ("elbm_max_iter", C.c_int), ("elbm_norm", C.c_int),
         ("elbm_fallback", C.c_int),
+        ("lim_alpha", C.c_double), ("lim_k", C.c_double), ("lim_dst", C.c_double),
+        ("lim_delta0", C.c_double),
     ]
 
 
@@ -107,6 +112,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
+    if lib.lbm_abi_version() != ABI_VERSION:
+        raise LBMError(f"{path}: ABI version {lib.lbm_abi_version()}, this binding needs {ABI_VERSION} "
+                       "(rebuild with paper_1110_0270_gb300.build)")
     return lib
 
 
@@ -143,6 +151,10 @@ class LBMConfig:
     elbm_max_iter: int = 20
     elbm_norm: str = "entropic"
     elbm_fallback: str = "positivity"
+    lim_alpha: float = 1.0
+    lim_k: float = 1.0
+    lim_dst: float = 1e-3
+    lim_delta0: float = 0.01
 
     @classmethod
     def from_dict(cls, d: dict) -> "LBMConfig":
@@ -160,7 +172,8 @@ class LBMConfig:
                           float(self.nu), float(self.lid_u), int(self.topk), float(self.delta),
                           float(self.s_e), float(self.s_eps), float(self.s_q),
                           float(self.elbm_eps), int(self.elbm_max_iter), NORMS[self.elbm_norm],
-                          FALLBACKS[self.elbm_fallback])
+                          FALLBACKS[self.elbm_fallback], float(self.lim_alpha), float(self.lim_k),
+                          float(self.lim_dst), float(self.lim_delta0))
 
 
 def required_bytes(cfg) -> int:
@@ -328,6 +341,26 @@ class Lattice:
             sel.ctypes.data_as(C.c_void_p), cap, C.byref(n), _stream(stream)), "lbm_last_candidates")
         m = min(n.value, cap)
         return ds[:m], site[:m], sel[:m]
+
+
+def mrt_rates(preset: str, beta: float) -> dict:
+    """MRT relaxation rates (s_e, s_eps, s_q) of the presets of Sections 5
+    and 8, with s_nu = 2 beta:
+      'trt'  - two relaxation times: s_e = s_eps = s_nu and
+               s_q = 8 (2 - s_nu) / (8 - s_nu) (reading of the printed
+               "8(2=s_nu)/(8-s_nu)");
+      'mrt'  - s_e = 1.64, s_eps = 1.54, s_q as for TRT;
+      'mrt1' - s_e = 1.64, s_eps = 1.54, s_q = 1.9.
+    Use with collision="mrt"."""
+    snu = 2.0 * beta
+    sq_trt = 8.0 * (2.0 - snu) / (8.0 - snu)
+    if preset == "trt":
+        return {"s_e": snu, "s_eps": snu, "s_q": sq_trt}
+    if preset == "mrt":
+        return {"s_e": 1.64, "s_eps": 1.54, "s_q": sq_trt}
+    if preset == "mrt1":
+        return {"s_e": 1.64, "s_eps": 1.54, "s_q": 1.9}
+    raise ValueError(f"unknown MRT preset {preset!r}")
 
 
 def fp64_rates(stream=None) -> dict:

@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert lib.lbm_abi_version() == 1
+    assert lib.lbm_abi_version() == lbm.ABI_VERSION == 2
     assert lib.lbm_status_string(0) == b"LBM_OK"
     assert lib.lbm_status_string(4) == b"LBM_ERR_DIVERGED"
 
@@ -87,3 +87,37 @@ def test_batch_validation_is_host_side(lib):
                 [dict(lattice="D1Q3", nx=10, ny=1, beta=0.9)]):
         with pytest.raises(lbm.LBMError):
             lbm.batch_required_bytes(bad)
+
+
+def test_limiter_config_defaults_and_validation(lib):
+    """The Section 4.2-4.4 limiter fields: defaults from lbm_config_default
+    match the binding's, and out-of-range values are rejected."""
+    c = lbm.lbm_config()
+    assert lib.lbm_config_default(C.byref(c)) == 0
+    py = lbm.LBMConfig()
+    assert (c.lim_alpha, c.lim_k, c.lim_dst, c.lim_delta0) == (py.lim_alpha, py.lim_k, py.lim_dst, py.lim_delta0)
+    n = C.c_size_t()
+    for coll, field, bad in [(6, "lim_alpha", 0.0), (6, "lim_k", -1.0), (7, "lim_dst", 0.0),
+                             (7, "lim_k", 0.0), (8, "lim_alpha", -2.0), (9, "lim_delta0", -0.1)]:
+        c2 = lbm.lbm_config()
+        lib.lbm_config_default(C.byref(c2))
+        c2.collision = coll
+        assert lib.lbm_required_bytes(C.byref(c2), C.byref(n)) == 0, coll
+        setattr(c2, field, bad)
+        assert lib.lbm_required_bytes(C.byref(c2), C.byref(n)) == 1, (coll, field)
+    c.collision = 12
+    assert lib.lbm_required_bytes(C.byref(c), C.byref(n)) == 1
+    # Section 5's A_2 collisions exist for D2Q9 only
+    for coll in (10, 11):
+        c.collision = coll
+        assert lib.lbm_required_bytes(C.byref(c), C.byref(n)) == 0
+        c.lattice, c.ny = 1, 1
+        assert lib.lbm_required_bytes(C.byref(c), C.byref(n)) == 1
+        c.lattice, c.ny = 2, 16
+    # the threshold limiter carries a candidate list and reduction slots
+    c.collision = 0
+    lib.lbm_required_bytes(C.byref(c), C.byref(n))
+    base = n.value
+    c.collision = 9
+    lib.lbm_required_bytes(C.byref(c), C.byref(n))
+    assert n.value > base
