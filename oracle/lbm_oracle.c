@@ -685,6 +685,48 @@ double orc_total_h(const orc_config* cfg, const double* f) {
     return h;
 }
 
+/* d g / d coordinate at index i of a line of n values with spacing 1. */
+static double diff1(const double* g, long long stride, int i, int n, int periodic) {
+    if (n < 2) return 0.0;
+    if (periodic) {
+        int ip = i + 1 < n ? i + 1 : 0, im = i > 0 ? i - 1 : n - 1;
+        return 0.5 * (g[ip * stride] - g[im * stride]);
+    }
+    if (i == 0) return g[1 * stride] - g[0];
+    if (i == n - 1) return g[(long long)i * stride] - g[(long long)(i - 1) * stride];
+    return 0.5 * (g[(long long)(i + 1) * stride] - g[(long long)(i - 1) * stride]);
+}
+
+double orc_enstrophy(const orc_config* cfg, const double* f) {
+    if (cfg->lattice != ORC_D2Q9) return 0.0;
+    int nx = cfg->nx, ny = cfg->ny, px, py;
+    long long N = (long long)nx * ny;
+    bc_periodicity(cfg, &px, &py);
+    double* rho = (double*)malloc(sizeof(double) * (size_t)N);
+    double* ux = (double*)malloc(sizeof(double) * (size_t)N);
+    double* uy = (double*)malloc(sizeof(double) * (size_t)N);
+    if (!rho || !ux || !uy) {
+        free(rho);
+        free(ux);
+        free(uy);
+        return -1.0;
+    }
+    orc_macros(cfg, f, rho, ux, uy);
+    double e = 0.0;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            /* d u_y / dx along the row, d u_x / dy along the column */
+            double dvdx = diff1(uy + (long long)y * nx + 0, 1, x, nx, px);
+            double dudy = diff1(ux + x, nx, y, ny, py);
+            double w = dvdx - dudy;
+            e += w * w;
+        }
+    free(rho);
+    free(ux);
+    free(uy);
+    return e / (double)N;
+}
+
 static int config_ok(const orc_config* cfg) {
     if (cfg->lattice != ORC_D1Q3 && cfg->lattice != ORC_D2Q9) return 0;
     if (cfg->nx < 1 || cfg->ny < 1) return 0;

@@ -147,6 +147,12 @@ void orc_init_equilibrium(const orc_config* cfg, const double* rho,
 void orc_macros(const orc_config* cfg, const double* f, double* rho,
                 double* ux, double* uy);
 void orc_delta_s_field(const orc_config* cfg, const double* f, double* dS);
+/* Enstrophy of Section 8: the sum over sites of the vorticity squared,
+ * divided by the number of sites, with the vorticity
+ * w = d u_y / dx - d u_x / dy by central differences of the site velocities
+ * (periodic directions wrap; at a wall edge the one-sided difference to the
+ * neighbour inside).  0 for D1Q3. */
+double orc_enstrophy(const orc_config* cfg, const double* f);
 /* H = sum_x sum_i f_i ln(f_i / W_i)  (= -S summed over the lattice). */
 double orc_total_h(const orc_config* cfg, const double* f);
 

@@ -151,6 +151,7 @@ def _L():
                 "orc_macros": (None, [p, p, p, p, p]),
                 "orc_delta_s_field": (None, [p, p, p]),
                 "orc_total_h": (d, [p, p]),
+                "orc_enstrophy": (d, [p, p]),
                 "orc_step": (i, [p, p, i, p]),
                 "orc_stream": (None, [p, p, p]),
                 "orc_kinetic_energy": (d, [p, p]),
@@ -265,6 +266,13 @@ def mrt_matrix(cfg) -> np.ndarray:
     A = np.zeros((cfg.Q, cfg.Q))
     _L().orc_mrt_matrix(C.byref(c), _ptr(A))
     return A
+
+
+def enstrophy(cfg, f) -> float:
+    """Section 8's enstrophy: mean over sites of the vorticity squared."""
+    cfg = _cfg(cfg)
+    c = cfg._c()
+    return _L().orc_enstrophy(C.byref(c), _ptr(_f64(f)))
 
 
 def mrt2_basis() -> np.ndarray:
@@ -423,6 +431,6 @@ __all__ = ["kinetic_energy", "adjoint_ke",
     "OracleConfig", "build", "lattice", "opposite", "eq1d", "equilibrium", "moments", "gfun",
     "delta_s", "delta_s_direct", "entropy", "entropy_d1q3_paper", "elbm_alpha", "elbm_sf",
     "mrt_basis", "mrt_matrix", "collide_site", "select_topk", "median_field",
-    "phi_smooth", "phi_double_monotonic", "phi_ensemble", "threshold_dS0", "mrt2_basis", "mrt2_matrix",
+    "phi_smooth", "phi_double_monotonic", "phi_ensemble", "threshold_dS0", "mrt2_basis", "mrt2_matrix", "enstrophy",
     "init_equilibrium", "macros", "delta_s_field", "total_h", "stream", "step",
 ]

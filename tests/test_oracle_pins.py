@@ -834,3 +834,46 @@ def test_mrt_limiter_applies_a2_at_the_ehrenfest_selection():
             want = fs - A @ (fs - feq_of("D2Q9", "poly", fs))
             for i in range(9):
                 assert abs(g2[i, (y + cy[i]) % ny, (x + cx[i]) % nx] - want[i]) < 1e-15
+
+
+def test_trt_preset_keeps_the_shear_viscosity_and_matches_lbgk_in_the_bulk():
+    """The TRT preset of Section 5 (s_e = s_eps = s_nu, s_q from the magic
+    relation) leaves the shear-wave decay rate of LBGK unchanged: the
+    viscosity is set by s_nu alone.  Checked on a periodic shear wave, where
+    both collisions must give the same decay to within the O(k^4) terms."""
+    from paper_1110_0270_gb300 import lbm as B
+    beta = 0.8
+    rates = B.mrt_rates("trt", beta)
+    snu = 2 * beta
+    assert rates["s_e"] == rates["s_eps"] == snu
+    assert rates["s_q"] == pytest.approx(8 * (2 - snu) / (8 - snu))
+    assert B.mrt_rates("mrt1", beta) == {"s_e": 1.64, "s_eps": 1.54, "s_q": 1.9}
+    cfg, init = WL.shear_wave(32, 0.01, 0.0)
+    cfg = dict(cfg, beta=beta)
+    f0 = O.init_equilibrium(cfg, init["rho"], init["ux"], init["uy"])
+    amp = lambda f: np.abs(O.macros(cfg, f)[2]).max()
+    a_lbgk = amp(O.step(dict(cfg, collision="lbgk"), f0, 200))
+    a_trt = amp(O.step(dict(cfg, collision="mrt", **rates), f0, 200))
+    assert a_trt == pytest.approx(a_lbgk, rel=2e-3)
+
+
+def test_enstrophy_of_closed_form_flows():
+    """Section 8's enstrophy (mean of the vorticity squared): zero for a
+    uniform flow, (2 pi k / L)^2 u0^2 / 2 times the central-difference factor
+    for a periodic shear wave u_y = u0 sin(2 pi x / L), and 1 (vorticity -1
+    ... +1 scaled) for solid-body rotation u = (-y, x) omega away from edges."""
+    L = 32
+    cfg, init = WL.shear_wave(L, 0.01, 0.0)
+    f0 = O.init_equilibrium(cfg, init["rho"], init["ux"], init["uy"])
+    k = 2 * np.pi / L
+    # central difference of sin: sin(k) / 1 instead of k
+    assert O.enstrophy(cfg, f0) == pytest.approx(0.5 * (0.01 * np.sin(k)) ** 2, rel=1e-12)
+    uni = O.init_equilibrium(cfg, np.ones((L, L)), np.full((L, L), 0.02), np.full((L, L), -0.01))
+    assert O.enstrophy(cfg, uni) == pytest.approx(0.0, abs=1e-30)
+    # solid-body rotation in a walled box: vorticity 2 omega everywhere (the
+    # one-sided edge differences are exact for a linear field)
+    n, om = 12, 1e-3
+    yy, xx = np.mgrid[0:n, 0:n].astype(float)
+    box = dict(lattice="D2Q9", nx=n, ny=n, bc="cavity")
+    rot = O.init_equilibrium(box, np.ones((n, n)), -om * yy, om * xx)
+    assert O.enstrophy(box, rot) == pytest.approx((2 * om) ** 2, rel=1e-10)
