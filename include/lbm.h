@@ -213,6 +213,14 @@ lbm_status lbm_macros(lbm_ctx* ctx, void* rho, void* u, int dtype, void* stream)
  * may be NULL), Delta S computed against the configured equilibrium. */
 lbm_status lbm_entropy(lbm_ctx* ctx, double* H_total_host, double* dS_dev, void* stream);
 
+/* Enstrophy of Section 8 into *E_host (synchronises `stream`): the sum over
+ * sites of the vorticity squared divided by the number of sites, with the
+ * vorticity w = d u_y/dx - d u_x/dy of the site velocities by central
+ * differences (wrapped in periodic directions, one-sided to the inside
+ * neighbour at a wall edge).  D2Q9 only (LBM_ERR_ARG for D1Q3).  Uses the
+ * context's scratch; the state is not modified. */
+lbm_status lbm_enstrophy(lbm_ctx* ctx, double* E_host, void* stream);
+
 /* Copies the step counters into *out (synchronises `stream`). */
 lbm_status lbm_stats_get(lbm_ctx* ctx, lbm_stats* out, void* stream);
 

@@ -175,6 +175,41 @@ cudaError_t traced(lbm_ctx* ctx, int kind, cudaStream_t s, Fn&& fn) {
     return err;
 }
 
+// d g / d coordinate at index i of a line of n values (spacing 1, stride
+// between neighbours), as in the enstrophy's definition in include/lbm.h.
+__device__ __forceinline__ double line_diff(const double* g, int64_t stride, int i, int n, int periodic) {
+    if (n < 2) return 0.0;
+    if (periodic) {
+        const int ip = i + 1 < n ? i + 1 : 0, im = i > 0 ? i - 1 : n - 1;
+        return 0.5 * (g[ip * stride] - g[im * stride]);
+    }
+    if (i == 0) return g[stride] - g[0];
+    if (i == n - 1) return g[(int64_t)i * stride] - g[(int64_t)(i - 1) * stride];
+    return 0.5 * (g[(int64_t)(i + 1) * stride] - g[(int64_t)(i - 1) * stride]);
+}
+
+// Sum over sites of w^2 (Section 8's enstrophy times the site count) into
+// *out, from the FP64 site velocities ux, uy [ny][nx].
+__global__ void __launch_bounds__(256) enstrophy_kernel(int nx, int ny, int px, int py, const double* __restrict__ ux,
+                                                        const double* __restrict__ uy, double* out) {
+    __shared__ double part[8];
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double e = 0.0;
+    if (s < (int64_t)nx * ny) {
+        const int y = (int)(s / nx), x = (int)(s - (int64_t)y * nx);
+        const double w = line_diff(uy + (int64_t)y * nx, 1, x, nx, px) - line_diff(ux + x, nx, y, ny, py);
+        e = w * w;
+    }
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += part[k];
+        if (t != 0.0) atomicAdd(out, t);
+    }
+}
+
 lbm_status reset_counters(lbm_ctx* ctx, cudaStream_t s) {
     LBM_CK(ctx, cudaMemsetAsync(ctx->p.counters, 0, CNT_WORDS * 4 + ST_WORDS * 8, s));
     return LBM_OK;
@@ -472,6 +507,27 @@ lbm_status lbm_entropy(lbm_ctx* ctx, double* H_total_host, double* dS_dev, void*
         LBM_CK(ctx, cudaMemcpyAsync(H_total_host, H, sizeof(double), cudaMemcpyDeviceToHost, S(stream)));
         LBM_CK(ctx, cudaStreamSynchronize(S(stream)));
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_enstrophy(lbm_ctx* ctx, double* E_host, void* stream) {
+    if (!ctx || !E_host) return LBM_ERR_ARG;
+    if (ctx->Q != 9) return fail(ctx, LBM_ERR_ARG, "enstrophy needs D2Q9");
+    const int64_t N = (int64_t)ctx->cfg.nx * ctx->cfg.ny;
+    double* rho = ctx->staging;  // 3N doubles: rho, u_x, u_y
+    double* u = ctx->staging + N;
+    double* acc = ctx->p.scratch_d + 2;
+    LBM_CK(ctx, dispatch(ctx->cfg.precision, [&](auto L) {
+               return decltype(L)::macros(ctx->Q, ctx->p, rho, u, LBM_DTYPE_F64, ctx->parity != 0, S(stream));
+           }));
+    LBM_CK(ctx, cudaMemsetAsync(acc, 0, sizeof(double), S(stream)));
+    enstrophy_kernel<<<(unsigned)((N + 255) / 256), 256, 0, S(stream)>>>(ctx->cfg.nx, ctx->cfg.ny, ctx->p.periodic_x,
+                                                                      ctx->p.periodic_y, u, u + N, acc);
+    LBM_CK(ctx, cudaGetLastError());
+    double h = 0.0;
+    LBM_CK(ctx, cudaMemcpyAsync(&h, acc, sizeof(double), cudaMemcpyDeviceToHost, S(stream)));
+    LBM_CK(ctx, cudaStreamSynchronize(S(stream)));
+    *E_host = h / (double)N;
     return LBM_OK;
 }
 

@@ -39,7 +39,7 @@ EXPORTS = ["lbm_config_default", "lbm_required_bytes", "lbm_create", "lbm_destro
            "lbm_batch_destroy", "lbm_batch_init_uniform", "lbm_batch_set_state",
            "lbm_batch_get_state", "lbm_batch_step", "lbm_batch_stats", "lbm_batch_last_error",
            "lbm_adjoint_required_bytes", "lbm_adjoint_forward", "lbm_adjoint_backward",
-           "lbm_fp64_rates"]
+           "lbm_fp64_rates", "lbm_enstrophy"]
 
 
 class lbm_config(C.Structure):
@@ -94,6 +94,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "lbm_profile_read": (i, [p, C.POINTER(i), C.POINTER(C.c_double)]),
         "lbm_ehrenfest_step_noalloc": (i, [C.POINTER(lbm_config), p, i, p]),
         "lbm_fp64_rates": (i, [C.POINTER(C.c_double), C.POINTER(C.c_double), p]),
+        "lbm_enstrophy": (i, [p, C.POINTER(C.c_double), p]),
         "lbm_batch_required_bytes": (i, [C.POINTER(lbm_config), i, C.POINTER(sz)]),
         "lbm_batch_create": (i, [C.POINTER(lbm_config), i, p, sz, C.POINTER(p)]),
         "lbm_batch_destroy": (None, [p]),
@@ -283,6 +284,12 @@ class Lattice:
         self._check(lib().lbm_entropy(self._h, C.byref(H), _ptr(dS) if field else None,
                                       _stream(stream)), "lbm_entropy")
         return (H.value, dS) if field else H.value
+
+    def enstrophy(self, stream=None) -> float:
+        """Section 8's enstrophy: mean over sites of the vorticity squared."""
+        E = C.c_double()
+        self._check(lib().lbm_enstrophy(self._h, C.byref(E), _stream(stream)), "lbm_enstrophy")
+        return E.value
 
     def stats(self, stream=None) -> dict:
         st = lbm_stats()

@@ -153,3 +153,21 @@ def test_a2_collisions_16bit_pair_kernel(collision):
         dev[:, -1, :] += cfg["lid_u"] / 6.0
         bound = 0.5 * np.spacing(dev.astype(np.float16)).astype(np.float64) * (1 + 1e-3) + 2e-6
         assert (np.abs(post - want) <= bound).all()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_enstrophy_matches_oracle(precision, tol):
+    """lbm_enstrophy (Section 8) on a developing cavity and a periodic
+    lattice against the oracle's enstrophy of the oracle's state."""
+    for cfg in [dict(CASES["cavity"], collision="lbgk", beta=0.95),
+                dict(CASES["periodic"], collision="mrt", beta=0.9)]:
+        cfg = dict(cfg, precision=precision)
+        f0 = state(cfg, seed=3)
+        if precision != "fp64":
+            f0 = f0.astype(np.float32).astype(np.float64)
+        lat = lbm.Lattice(cfg)
+        lat.set_state(torch.tensor(f0, dtype=torch.float64 if precision == "fp64" else torch.float32,
+                                   device="cuda"))
+        lat.step(37)  # an odd step count: the A-A layout of odd steps
+        want = O.enstrophy(cfg, O.step(cfg, f0, 37))
+        assert lat.enstrophy() == pytest.approx(want, rel=tol)
