@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -241,6 +242,47 @@ def run_precision_error(n_side, steps):
     out["H_fp64_per_site"] = ref[2] / (n_side * n_side)
     out["note"] = ("rho_dev_rel_l2 is taken on rho - 1, the part that varies; H is near zero for a "
                    "fluid mostly at rest, so its error is given per site, not relative")
+    return out
+
+
+def run_shear_decay(res=(10, 30, 100, 300, 1000, 3000, 10000), Ls=(50, 100), u0=0.05):
+    """Section 7's shear-decay experiment on the GPU (FP64 storage, textbook
+    polynomial equilibrium): L + 1 periodic sites a side, u_y = u0 sin(2 pi x/L),
+    L / u0 steps; lambda = -(L^2 / (nu t)) ln(a(t) / a(0)) from the amplitude a
+    of the sin(2 pi x / L) component of u_y, for LBGK, the aggressive MRT A_2 and
+    the A_1 MRT with the Lallemand-Luo rates (s_e 1.64, s_eps 1.54,
+    s_q = 3 (2 - s_nu)/(3 - s_nu)).  The exact decay has lambda = 4 pi^2."""
+    import numpy as np
+    import torch
+    from paper_1110_0270_gb300 import lbm
+    from paper_1110_0270_gb300 import workloads as WL
+    out = {"lambda_exact": round(4 * math.pi ** 2, 4), "steps": "L / u0", "table": {}}
+    for name, coll in [("lbgk", "lbgk"), ("mrt_a2", "mrt2"), ("mrt_a1_ll", "mrt")]:
+        rows = {}
+        for L in Ls:
+            vals = []
+            for re in res:
+                cfg, init = WL.shear_decay(L, re, u0)
+                beta = 1.0 / (6.0 * cfg["nu"] + 1.0)
+                cfg.update(collision=coll, precision="fp64", equilibrium="poly_std", beta=beta)
+                if coll == "mrt":
+                    cfg.update(lbm.mrt_rates("mrt_ll", beta))
+                lat = lbm.Lattice(cfg)
+                lat.init(init["rho"], init["ux"], init["uy"])
+                n = cfg["nx"]
+                s = np.sin(2 * math.pi * np.arange(n) / L)
+                amp = lambda: float((lat.macros(torch.float64)[1][1].cpu().numpy().mean(0) * s).sum() / (s * s).sum())
+                a0 = amp()
+                T = int(round(L / u0))
+                lat.step(T)
+                ratio = amp() / a0
+                # a non-positive or non-finite amplitude: the run went unstable
+                lam = round(-(L * L) / (cfg["nu"] * T) * math.log(ratio), 3) if ratio > 0 and math.isfinite(ratio) else None
+                vals.append([re, lam])
+                del lat
+            rows[str(L)] = vals
+        out["table"][name] = rows
+    out["columns"] = ["Re", "lambda"]
     return out
 
 
@@ -578,6 +620,8 @@ def gpu_arm(args):
             result["small_configs"] = run_small_configs()
         if args.precision_steps > 0:
             result["precision_error"] = run_precision_error(args.side, args.precision_steps)
+        if not args.no_small:
+            result["shear_decay"] = run_shear_decay()
         if args.adjoint_steps > 0:
             result["adjoint"] = run_adjoint(args.adjoint_steps, 100)
         if args.batch_steps > 0:

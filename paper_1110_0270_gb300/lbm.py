@@ -357,7 +357,9 @@ def mrt_rates(preset: str, beta: float) -> dict:
                s_q = 8 (2 - s_nu) / (8 - s_nu) (reading of the printed
                "8(2=s_nu)/(8-s_nu)");
       'mrt'  - s_e = 1.64, s_eps = 1.54, s_q as for TRT;
-      'mrt1' - s_e = 1.64, s_eps = 1.54, s_q = 1.9.
+      'mrt1' - s_e = 1.64, s_eps = 1.54, s_q = 1.9;
+      'mrt_ll' - the shear-decay MRT of Section 7: s_e = 1.64, s_eps = 1.54,
+               s_q = 3 (2 - s_nu) / (3 - s_nu).
     Use with collision="mrt"."""
     snu = 2.0 * beta
     sq_trt = 8.0 * (2.0 - snu) / (8.0 - snu)
@@ -367,6 +369,8 @@ def mrt_rates(preset: str, beta: float) -> dict:
         return {"s_e": 1.64, "s_eps": 1.54, "s_q": sq_trt}
     if preset == "mrt1":
         return {"s_e": 1.64, "s_eps": 1.54, "s_q": 1.9}
+    if preset == "mrt_ll":
+        return {"s_e": 1.64, "s_eps": 1.54, "s_q": 3.0 * (2.0 - snu) / (3.0 - snu)}
     raise ValueError(f"unknown MRT preset {preset!r}")
 
 

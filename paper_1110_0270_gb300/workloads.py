@@ -35,6 +35,18 @@ def shear_wave(L: int = 64, u0: float = 0.05, nu: float = 0.01) -> tuple[dict, d
     return cfg, dict(rho=rho, ux=np.zeros_like(rho), uy=uy)
 
 
+def shear_decay(L: int, re: float, u0: float = 0.05, points: int | None = None) -> tuple[dict, dict]:
+    """Section 7's shear-decay set-up: a periodic square of `points` (L + 1 by
+    default, the paper's count) sites a side, rho = 1, u_x = 0,
+    u_y = u0 sin(2 pi x / L), viscosity from Re = u0 L / nu."""
+    n = L + 1 if points is None else points
+    x = np.arange(n, dtype=np.float64)
+    uy = np.tile(u0 * np.sin(2.0 * np.pi * x / L), (n, 1))
+    rho = np.ones((n, n))
+    cfg = dict(lattice="D2Q9", nx=n, ny=n, bc="periodic", nu=u0 * L / re, lid_u=0.0)
+    return cfg, dict(rho=rho, ux=np.zeros_like(rho), uy=uy)
+
+
 def cavity(n: int, re: float, lid_u: float) -> tuple[dict, dict]:
     """Lid-driven cavity of Section 8: fluid at rest, lid speed lid_u,
     viscosity from Re = lid_u (n - 1) / nu."""

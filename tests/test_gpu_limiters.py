@@ -171,3 +171,38 @@ def test_enstrophy_matches_oracle(precision, tol):
         lat.step(37)  # an odd step count: the A-A layout of odd steps
         want = O.enstrophy(cfg, O.step(cfg, f0, 37))
         assert lat.enstrophy() == pytest.approx(want, rel=tol)
+
+
+@pytest.mark.parametrize("collision", ["lbgk", "mrt2", "mrt"])
+def test_shear_decay_lambda_matches_oracle(collision):
+    """Section 7's shear decay (L = 50, L + 1 periodic points, u0 = 0.05,
+    textbook polynomial equilibrium, L / u0 steps): the decay constant lambda
+    measured on the GPU equals the oracle's (FP64), and the MRT forms decay
+    like LBGK (the section's observation), within 5% of 4 pi^2 at Re 10 and
+    1000."""
+    import math
+    L, u0 = 50, 0.05
+    lam = {}
+    for re in (10, 1000):
+        cfg, init = WL.shear_decay(L, re, u0)
+        beta = 1.0 / (6.0 * cfg["nu"] + 1.0)
+        cfg.update(collision=collision, equilibrium="poly_std", beta=beta, precision="fp64")
+        if collision == "mrt":
+            cfg.update(lbm.mrt_rates("mrt_ll", beta))
+        n = cfg["nx"]
+        s = np.sin(2 * math.pi * np.arange(n) / L)
+        amp = lambda uy: float((uy.mean(0) * s).sum() / (s * s).sum())
+        T = int(round(L / u0))
+        lat = lbm.Lattice(cfg)
+        lat.init(init["rho"], init["ux"], init["uy"])
+        a0 = amp(lat.macros(torch.float64)[1][1].cpu().numpy())
+        lat.step(T)
+        g = -(L * L) / (cfg["nu"] * T) * math.log(amp(lat.macros(torch.float64)[1][1].cpu().numpy()) / a0)
+        f = O.step(cfg, O.init_equilibrium(cfg, init["rho"], init["ux"], init["uy"]), T)
+        o = -(L * L) / (cfg["nu"] * T) * math.log(amp(O.macros(cfg, f)[2]) / a0)
+        assert g == pytest.approx(o, rel=1e-9)
+        assert g == pytest.approx(4 * math.pi ** 2, rel=0.05)
+        lam[re] = g
+    ref = {10: 37.884, 1000: 39.778}  # LBGK's values of this set-up (oracle)
+    for re in lam:
+        assert lam[re] == pytest.approx(ref[re], rel=0.01)
