@@ -610,31 +610,47 @@ def gpu_arm(args):
     }
     if rank == 0:
         result["clocks"] = sampler.summary(t0, t1) if sampler else None
-        if not args.no_variants:
-            r = lbm.fp64_rates()
-            result["fp64_probe"] = {"dfma_tflops": round(r["dfma_flops"] / 1e12, 4),
-                                    "log_gops": round(r["log_per_s"] / 1e9, 2),
-                                    "note": "measured FP64 ceilings of the FP64-bound kernels"}
-            result["variants"] = run_variants(args.side, args.variant_steps, 3, r["dfma_flops"] / 2)
-        if not args.no_small:
-            result["small_configs"] = run_small_configs()
-        if args.precision_steps > 0:
-            result["precision_error"] = run_precision_error(args.side, args.precision_steps)
-        if not args.no_small:
-            result["shear_decay"] = run_shear_decay()
-        if args.adjoint_steps > 0:
-            result["adjoint"] = run_adjoint(args.adjoint_steps, 100)
-        if args.batch_steps > 0:
-            fp64 = result.get("variants", {}).get("lbgk/fp64", {}).get("mlups")
-            result["batched"] = run_batched(args.batch_steps, 3, fp64)
-        if not args.no_e2e:
-            result["e2e"] = e2e_measure(workload_cfg(args.collision, args.precision, args.side)[0], init)
-        if not args.no_cpu:
-            result["cpu_baseline"] = cpu_baseline(args.cpu_budget)
+        run_sections(args, result, init)
         print(json.dumps(result), flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def guarded(result, key, fn):
+    """One optional section of the JSON line; a failure is recorded there
+    instead of ending the run without the headline line."""
+    try:
+        result[key] = fn()
+    except Exception as e:  # noqa: BLE001
+        result[key] = {"error": f"{type(e).__name__}: {e}"}
+
+
+def run_sections(args, result, init):
+    from paper_1110_0270_gb300 import lbm
+    if not args.no_variants:
+        r = {}
+        guarded(result, "fp64_probe", lambda: r.update(lbm.fp64_rates()) or {
+            "dfma_tflops": round(r["dfma_flops"] / 1e12, 4), "log_gops": round(r["log_per_s"] / 1e9, 2),
+            "note": "measured FP64 ceilings of the FP64-bound kernels"})
+        guarded(result, "variants",
+                lambda: run_variants(args.side, args.variant_steps, 3, r.get("dfma_flops", 0) / 2 or None))
+    if not args.no_small:
+        guarded(result, "small_configs", run_small_configs)
+    if args.precision_steps > 0:
+        guarded(result, "precision_error", lambda: run_precision_error(args.side, args.precision_steps))
+    if not args.no_small:
+        guarded(result, "shear_decay", run_shear_decay)
+    if args.adjoint_steps > 0:
+        guarded(result, "adjoint", lambda: run_adjoint(args.adjoint_steps, 100))
+    if args.batch_steps > 0:
+        fp64 = (result.get("variants") or {}).get("lbgk/fp64", {}).get("mlups")
+        guarded(result, "batched", lambda: run_batched(args.batch_steps, 3, fp64))
+    if not args.no_e2e:
+        guarded(result, "e2e",
+                lambda: e2e_measure(workload_cfg(args.collision, args.precision, args.side)[0], init))
+    if not args.no_cpu:
+        guarded(result, "cpu_baseline", lambda: cpu_baseline(args.cpu_budget))
 
 
 # --------------------------------------------------------------------------- reference arm
