@@ -623,11 +623,59 @@ void orc_stream(const orc_config* cfg, const double* F, double* fnew) {
                     fnew[i * N + (long long)ty * nx + tx] = v;
                 } else {
                     double corr = 0.0;
-                    if (ty >= ny) corr = 6.0 * W[i] * 1.0 * (cx[i] * cfg->lid_u);
+                    if (ty >= ny && cfg->bc != ORC_BC_DIFFUSIVE) corr = 6.0 * W[i] * 1.0 * (cx[i] * cfg->lid_u);
                     fnew[o * N + (long long)y * nx + x] = v - corr;
                 }
             }
     }
+}
+
+void orc_diffusive_rule(const orc_config* cfg, double* f) {
+    if (cfg->bc != ORC_BC_DIFFUSIVE || cfg->lattice != ORC_D2Q9) return;
+    int nx = cfg->nx, ny = cfg->ny;
+    long long N = (long long)nx * ny;
+    int cx[9], cy[9];
+    double W[9];
+    orc_lattice(ORC_D2Q9, cx, cy, W);
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            int nxw = (x == 0 ? -1 : 0) + (x == nx - 1 ? 1 : 0);
+            int nyw = (y == 0 ? -1 : 0) + (y == ny - 1 ? 1 : 0);
+            if (nxw == 0 && nyw == 0) continue; /* a fluid site */
+            long long s = (long long)y * nx + x;
+            if (nxw != 0 && nyw != 0) {
+                /* corner: bounce-back for the populations from outside */
+                double fs[9];
+                for (int i = 0; i < 9; ++i) fs[i] = f[i * N + s];
+                for (int i = 0; i < 9; ++i) {
+                    int sx = x - cx[i], sy = y - cy[i];
+                    if (sx < 0 || sx >= nx || sy < 0 || sy >= ny) {
+                        int o = orc_opposite(ORC_D2Q9, i);
+                        int ox = x - cx[o], oy = y - cy[o];
+                        if (ox >= 0 && ox < nx && oy >= 0 && oy < ny) f[i * N + s] = fs[o];
+                    }
+                }
+                continue;
+            }
+            double uw = (nyw == 1) ? cfg->lid_u : 0.0;
+            double feq[9];
+            orc_equilibrium(ORC_D2Q9, eq_kind(cfg), 1.0, uw, 0.0, feq);
+            double out = 0.0, in = 0.0;
+            for (int i = 0; i < 9; ++i) {
+                int vn = cx[i] * nxw + cy[i] * nyw;
+                if (vn > 0) out += f[i * N + s];
+                if (vn < 0) in += feq[i];
+            }
+            double gamma = out / in;
+            for (int i = 0; i < 9; ++i)
+                if (cx[i] * nxw + cy[i] * nyw < 0) f[i * N + s] = gamma * feq[i];
+        }
+}
+
+static int is_wall_site(const orc_config* cfg, long long s) {
+    if (cfg->bc != ORC_BC_DIFFUSIVE) return 0;
+    int x = (int)(s % cfg->nx), y = (int)(s / cfg->nx);
+    return x == 0 || x == cfg->nx - 1 || y == 0 || y == cfg->ny - 1;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -733,6 +781,7 @@ static int config_ok(const orc_config* cfg) {
     if (cfg->lattice == ORC_D1Q3 && cfg->ny != 1) return 0;
     if (cfg->collision < ORC_LBGK || cfg->collision > ORC_MRT_LIMITER) return 0;
     if ((cfg->collision == ORC_MRT2 || cfg->collision == ORC_MRT_LIMITER) && cfg->lattice != ORC_D2Q9) return 0;
+    if (cfg->bc == ORC_BC_DIFFUSIVE && (cfg->lattice != ORC_D2Q9 || cfg->nx < 3 || cfg->ny < 3)) return 0;
     return 1;
 }
 
@@ -826,16 +875,34 @@ int orc_step(const orc_config* cfg, double* f, int nsteps, orc_stats* st) {
     double A[81];
     if (cfg->collision == ORC_MRT) orc_mrt_matrix(cfg, A);
     if (cfg->collision == ORC_MRT2 || cfg->collision == ORC_MRT_LIMITER) orc_mrt2_matrix(cfg, A);
+    int diffusive = cfg->bc == ORC_BC_DIFFUSIVE;
     for (int t = 0; t < nsteps; ++t) {
         double fs[9], feq[9], Fs[9];
+        if (diffusive) orc_diffusive_rule(cfg, f);
         int nonlocal = cfg->collision == ORC_EHRENFEST || cfg->collision == ORC_MEDIAN ||
                        (cfg->collision >= ORC_SMOOTH && cfg->collision != ORC_MRT2);
         double E = 0.0, dSt = 0.0;
         if (nonlocal) {
             orc_delta_s_field(cfg, f, dS);
+            /* wall sites are not collided: never limiter candidates, and the
+             * median windows are clipped to the fluid sites */
+            if (diffusive)
+                for (long long x = 0; x < N; ++x)
+                    if (is_wall_site(cfg, x)) dS[x] = 0.0;
             if (cfg->collision == ORC_EHRENFEST || cfg->collision == ORC_MRT_LIMITER) {
                 long long nc = orc_select_topk(dS, N, cfg->topk, cfg->delta, mask);
                 if (st) st->candidates += nc;
+            } else if (cfg->collision == ORC_MEDIAN && diffusive) {
+                int ix = cfg->nx - 2, iy = cfg->ny - 2;
+                double* sub = (double*)malloc(sizeof(double) * (size_t)ix * iy * 2);
+                if (!sub) return -2;
+                for (int y = 0; y < iy; ++y)
+                    for (int x = 0; x < ix; ++x) sub[(long long)y * ix + x] = dS[(long long)(y + 1) * cfg->nx + x + 1];
+                orc_median_field(cfg->lattice, ix, iy, 0, 0, sub, sub + (long long)ix * iy);
+                for (int y = 0; y < iy; ++y)
+                    for (int x = 0; x < ix; ++x)
+                        med[(long long)(y + 1) * cfg->nx + x + 1] = sub[(long long)ix * iy + (long long)y * ix + x];
+                free(sub);
             } else if (cfg->collision == ORC_MEDIAN) {
                 orc_median_field(cfg->lattice, cfg->nx, cfg->ny, px, py, dS, med);
             } else if (cfg->collision == ORC_ENSEMBLE) {
@@ -855,6 +922,11 @@ int orc_step(const orc_config* cfg, double* f, int nsteps, orc_stats* st) {
         }
         for (long long s = 0; s < N; ++s) {
             gather(Q, f, N, s, fs);
+            if (diffusive && is_wall_site(cfg, s)) {
+                /* wall sites are not collided (Section 8) */
+                for (int i = 0; i < Q; ++i) F[i * N + s] = fs[i];
+                continue;
+            }
             if (!nonlocal) {
                 collide_local(cfg, A, fs, Fs, st);
             } else if (cfg->collision == ORC_MRT_LIMITER) {

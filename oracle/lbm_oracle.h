@@ -36,7 +36,10 @@ enum { ORC_LBGK = 0, ORC_ELBM = 1, ORC_EHRENFEST = 2, ORC_POSITIVITY = 3,
        ORC_MRT_LIMITER = 11 };    /* LBGK, A_2 at the Ehrenfest-selected sites */
 enum { ORC_EQ_POLY_PRODUCT = 0, ORC_EQ_ENTROPIC = 1, ORC_EQ_POLY_STD = 2 };
 enum { ORC_BC_CAVITY = 0, ORC_BC_ENDS = 1, ORC_BC_PERIODIC = 2,
-       ORC_BC_CHANNEL = 3 };
+       ORC_BC_CHANNEL = 3,
+       /* Section 8's diffusive Maxwell walls (D2Q9): the edge sites are
+        * wall sites, not collided; the top wall moves with lid_u */
+       ORC_BC_DIFFUSIVE = 4 };
 enum { ORC_NORM_ENTROPIC = 0, ORC_NORM_L1 = 1 };
 enum { ORC_FALLBACK_POSITIVITY = 0, ORC_FALLBACK_EHRENFEST = 1 };
 
@@ -159,6 +162,17 @@ double orc_total_h(const orc_config* cfg, const double* f);
 /* Advance nsteps collide-then-stream steps in place.  Returns 0 on success,
  * -1 on an invalid configuration, -2 on allocation failure. */
 int orc_step(const orc_config* cfg, double* f, int nsteps, orc_stats* st);
+
+/* Section 8's diffusive Maxwell rule on the wall sites of f (bc
+ * ORC_BC_DIFFUSIVE), in place: at a site of one wall with outward normal n,
+ * the populations pointing into the fluid (v . n < 0) become
+ * gamma f*_i(u_wall), gamma = sum_{v.n > 0} f_j / sum_{v.n < 0} f*_i(u_wall)
+ * (f* at unit density, u_wall = (lid_u, 0) on the top wall, 0 elsewhere);
+ * at a corner each population whose source lies outside the box takes the
+ * value of its opposite (the rule with a single population is
+ * bounce-back).  Applied to the pre-collision state at the start of each
+ * step. */
+void orc_diffusive_rule(const orc_config* cfg, double* f);
 
 /* Pure streaming with the boundary rule (used by the oracle step). */
 void orc_stream(const orc_config* cfg, const double* F, double* fnew);

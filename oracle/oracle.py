@@ -24,7 +24,7 @@ COLLISIONS = {"lbgk": 0, "elbm": 1, "ehrenfest": 2, "positivity": 3, "median": 4
               "smooth": 6, "double_monotonic": 7, "ensemble": 8, "threshold": 9, "mrt2": 10,
               "mrt_limiter": 11}
 EQUILIBRIA = {"poly": 0, "entropic": 1, "poly_std": 2}
-BCS = {"cavity": 0, "ends": 1, "periodic": 2, "channel": 3}
+BCS = {"cavity": 0, "ends": 1, "periodic": 2, "channel": 3, "diffusive": 4}
 NORMS = {"entropic": 0, "l1": 1}
 FALLBACKS = {"positivity": 0, "ehrenfest": 1}
 
@@ -154,6 +154,7 @@ def _L():
                 "orc_enstrophy": (d, [p, p]),
                 "orc_step": (i, [p, p, i, p]),
                 "orc_stream": (None, [p, p, p]),
+                "orc_diffusive_rule": (None, [p, p]),
                 "orc_kinetic_energy": (d, [p, p]),
                 "orc_adjoint_ke": (i, [p, p, i, p, p, p, p]),
             }
@@ -266,6 +267,15 @@ def mrt_matrix(cfg) -> np.ndarray:
     A = np.zeros((cfg.Q, cfg.Q))
     _L().orc_mrt_matrix(C.byref(c), _ptr(A))
     return A
+
+
+def diffusive_rule(cfg, f) -> np.ndarray:
+    """Section 8's diffusive Maxwell rule applied to the wall sites of f."""
+    cfg = _cfg(cfg)
+    c = cfg._c()
+    out = _f64(f).copy()
+    _L().orc_diffusive_rule(C.byref(c), _ptr(out))
+    return out
 
 
 def enstrophy(cfg, f) -> float:
@@ -431,6 +441,6 @@ __all__ = ["kinetic_energy", "adjoint_ke",
     "OracleConfig", "build", "lattice", "opposite", "eq1d", "equilibrium", "moments", "gfun",
     "delta_s", "delta_s_direct", "entropy", "entropy_d1q3_paper", "elbm_alpha", "elbm_sf",
     "mrt_basis", "mrt_matrix", "collide_site", "select_topk", "median_field",
-    "phi_smooth", "phi_double_monotonic", "phi_ensemble", "threshold_dS0", "mrt2_basis", "mrt2_matrix", "enstrophy",
+    "phi_smooth", "phi_double_monotonic", "phi_ensemble", "threshold_dS0", "mrt2_basis", "mrt2_matrix", "enstrophy", "diffusive_rule",
     "init_equilibrium", "macros", "delta_s_field", "total_h", "stream", "step",
 ]

@@ -877,3 +877,59 @@ def test_enstrophy_of_closed_form_flows():
     box = dict(lattice="D2Q9", nx=n, ny=n, bc="cavity")
     rot = O.init_equilibrium(box, np.ones((n, n)), -om * yy, om * xx)
     assert O.enstrophy(box, rot) == pytest.approx((2 * om) ** 2, rel=1e-10)
+
+
+# ----------------------------------------------------------------------------- Section 8, diffusive walls
+def _box_state(n=9, seed=51):
+    cfg = dict(lattice="D2Q9", nx=n, ny=n + 2, bc="diffusive", lid_u=0.1, beta=0.9, equilibrium="entropic")
+    fl = WL.random_fields(n + 2, n, seed, 0.05, 0.05)
+    f = O.init_equilibrium(cfg, fl["rho"], fl["ux"], fl["uy"])
+    return cfg, f * WL.lognormal_factors(f.shape, seed + 1, 0.05)
+
+
+def test_diffusive_rule_balances_mass_and_is_proportional_to_the_wall_equilibrium():
+    """Section 8: at a site of one wall the populations pointing into the fluid
+    become gamma f*(u_wall) with gamma chosen so that they carry exactly the
+    mass that arrived (sum over v.n > 0); the outgoing set keeps the shape of
+    the wall equilibrium (detailed balance); at a corner the rule with one
+    population is bounce-back."""
+    cfg, f = _box_state()
+    g = O.diffusive_rule(cfg, f)
+    cx, cy, _ = O.lattice("D2Q9")
+    ny, nx = f.shape[1:]
+    for (x, y, n, uw) in [(4, ny - 1, (0, 1), 0.1), (4, 0, (0, -1), 0.0), (0, 5, (-1, 0), 0.0), (nx - 1, 3, (1, 0), 0.0)]:
+        vn = cx * n[0] + cy * n[1]
+        out, inw = vn > 0, vn < 0
+        assert g[inw, y, x].sum() == pytest.approx(f[out, y, x].sum(), rel=1e-14)
+        fe = O.equilibrium("D2Q9", "entropic", 1.0, uw, 0.0)
+        ratio = g[inw, y, x] / fe[inw]
+        assert np.allclose(ratio, ratio[0], rtol=1e-14)
+        assert np.array_equal(g[~inw, y, x], f[~inw, y, x])  # the rest is untouched
+    # bottom-left corner: NE, E, N come from outside and take SW, W, S
+    E, N, NE, W, S, SW = 1, 7, 8, 5, 3, 4
+    for a, b in [(E, W), (N, S), (NE, SW)]:
+        assert g[a, 0, 0] == f[b, 0, 0]
+    # fluid sites are untouched
+    assert np.array_equal(g[:, 1:-1, 1:-1], f[:, 1:-1, 1:-1])
+
+
+@pytest.mark.parametrize("collision", ["lbgk", "median", "ehrenfest"])
+def test_diffusive_box_keeps_rest_and_composes_rule_collision_streaming(collision):
+    """A fluid at rest between resting diffusive walls is a fixed point of the
+    step (gamma = 1 by symmetry); a step is the rule on the wall sites, the
+    collision of the fluid sites only, then the streaming (no moving-wall
+    term: the rule carries the wall velocity)."""
+    cfg = dict(lattice="D2Q9", nx=8, ny=7, bc="diffusive", lid_u=0.0, beta=0.9, collision=collision,
+               equilibrium="entropic", topk=2, delta=1e-6)
+    rest = O.init_equilibrium(cfg, np.ones((7, 8)), np.zeros((7, 8)), np.zeros((7, 8)))
+    assert np.abs(O.step(cfg, rest, 5) - rest).max() < 1e-15
+    cfg2, f = _box_state()
+    cfg2 = dict(cfg2, collision="lbgk")
+    g = O.diffusive_rule(cfg2, f)
+    F = g.copy()
+    ny, nx = f.shape[1:]
+    for y in range(1, ny - 1):
+        for x in range(1, nx - 1):
+            fe = O.equilibrium("D2Q9", "entropic", *O.moments("D2Q9", g[:, y, x]))
+            F[:, y, x] = g[:, y, x] + 2 * 0.9 * (fe - g[:, y, x])
+    assert np.abs(O.step(cfg2, f, 1) - O.stream(cfg2, F)).max() < 1e-15
