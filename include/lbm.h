@@ -103,9 +103,16 @@ enum { LBM_EQ_POLY_PRODUCT = 0, LBM_EQ_ENTROPIC = 1, LBM_EQ_POLY_STD = 2 };
  * store the deviation f_i - W_i rounded to nearest even, with FP32 math. */
 enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_BF16_DEV = 2, LBM_FP16_DEV = 3 };
 /* Boundaries: CAVITY = walls on all four sides, the top one moving with
- * lid_u; ENDS = D1Q3 tube closed at both ends; PERIODIC = both directions
- * wrap; CHANNEL = periodic in x, walls at bottom and top (top moving). */
-enum { LBM_BC_CAVITY = 0, LBM_BC_ENDS = 1, LBM_BC_PERIODIC = 2, LBM_BC_CHANNEL = 3 };
+ * lid_u (half-way bounce-back, every site fluid); ENDS = D1Q3 tube closed at
+ * both ends; PERIODIC = both directions wrap; CHANNEL = periodic in x, walls
+ * at bottom and top (top moving); DIFFUSIVE = Section 8's diffusive Maxwell
+ * walls (D2Q9, nx, ny >= 3): the edge sites are wall sites, not collided;
+ * at the start of each step a wall site's populations pointing into the
+ * fluid become gamma f*_i(u_wall) (f* at unit density, u_wall = (lid_u, 0)
+ * on the top wall, 0 elsewhere; gamma returns the mass that arrived), and a
+ * corner takes bounce-back for the populations from outside; limiters and
+ * median windows see the fluid sites only. */
+enum { LBM_BC_CAVITY = 0, LBM_BC_ENDS = 1, LBM_BC_PERIODIC = 2, LBM_BC_CHANNEL = 3, LBM_BC_DIFFUSIVE = 4 };
 enum { LBM_NORM_ENTROPIC = 0, LBM_NORM_L1 = 1 };
 enum { LBM_FALLBACK_POSITIVITY = 0, LBM_FALLBACK_EHRENFEST = 1 };
 /* Element types of caller buffers exchanged with the library. */
@@ -170,7 +177,9 @@ lbm_status lbm_required_bytes(const lbm_config* cfg, size_t* bytes);
  * aligned, at least lbm_required_bytes) on the current CUDA device.  The
  * populations are undefined until lbm_init or lbm_set_state.  Clears the
  * scratch with a synchronous cudaMemset and captures the kernels of two
- * steps (one A-A period) into a CUDA graph that lbm_step replays. */
+ * steps (one A-A period) into a CUDA graph that lbm_step replays, and of 64
+ * steps into a second one for long runs (lbm_step uses it while at least 64
+ * steps remain). */
 lbm_status lbm_create(const lbm_config* cfg, void* dev_mem, size_t bytes, lbm_ctx** out);
 
 /* Releases the host-side context (not the caller's device memory). */
@@ -220,6 +229,17 @@ lbm_status lbm_entropy(lbm_ctx* ctx, double* H_total_host, double* dS_dev, void*
  * neighbour at a wall edge).  D2Q9 only (LBM_ERR_ARG for D1Q3).  Uses the
  * context's scratch; the state is not modified. */
 lbm_status lbm_enstrophy(lbm_ctx* ctx, double* E_host, void* stream);
+
+/* Control-point probe (the signal of Section 8's Hopf-bifurcation study):
+ * from the next lbm_step on, every step records the velocity (u_x, u_y) of
+ * site (x, y) in the state it produced into the caller's DEVICE ring buffer
+ * buf of 2*cap doubles (sample k at buf[2 (k mod cap)]), with one extra
+ * one-thread launch per step; buf = NULL turns the probe off.  Re-captures
+ * the step graph (synchronous).  lbm_probe_count returns into *count the
+ * number of samples recorded since lbm_probe_set, lbm_init or lbm_set_state
+ * (synchronises `stream`). */
+lbm_status lbm_probe_set(lbm_ctx* ctx, int x, int y, double* buf, int cap);
+lbm_status lbm_probe_count(lbm_ctx* ctx, uint64_t* count, void* stream);
 
 /* Copies the step counters into *out (synchronises `stream`). */
 lbm_status lbm_stats_get(lbm_ctx* ctx, lbm_stats* out, void* stream);

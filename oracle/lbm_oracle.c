@@ -909,7 +909,7 @@ int orc_step(const orc_config* cfg, double* f, int nsteps, orc_stats* st) {
                 /* E(Delta S): mean over the sites with a finite value */
                 long long nf = 0;
                 for (long long x = 0; x < N; ++x)
-                    if (isfinite(dS[x])) {
+                    if (isfinite(dS[x]) && !is_wall_site(cfg, x)) {
                         E += dS[x];
                         ++nf;
                     }

@@ -63,7 +63,9 @@ const char* check_config(const lbm_config* c) {
         return "LBM_MRT2 and LBM_MRT_LIMITER need D2Q9";
     if (c->equilibrium < LBM_EQ_POLY_PRODUCT || c->equilibrium > LBM_EQ_POLY_STD) return "unknown equilibrium";
     if (c->precision < LBM_FP64 || c->precision > LBM_FP16_DEV) return "unknown precision";
-    if (c->bc < LBM_BC_CAVITY || c->bc > LBM_BC_CHANNEL) return "unknown boundary condition";
+    if (c->bc < LBM_BC_CAVITY || c->bc > LBM_BC_DIFFUSIVE) return "unknown boundary condition";
+    if (c->bc == LBM_BC_DIFFUSIVE && (c->lattice != LBM_D2Q9 || c->nx < 3 || c->ny < 3))
+        return "DIFFUSIVE needs D2Q9 with nx, ny >= 3";
     if (c->lattice == LBM_D1Q3 && c->bc == LBM_BC_CHANNEL) return "CHANNEL needs D2Q9";
     double beta = c->beta > 0 ? c->beta : (c->nu > 0 ? 1.0 / (6.0 * c->nu + 1.0) : -1.0);
     if (!(beta > 0.0 && beta <= 1.0)) return "beta must be in (0, 1] (or nu > 0)";
@@ -236,35 +238,55 @@ cudaError_t enqueue_one_step(lbm_ctx* ctx, bool odd, int cslot, cudaStream_t s) 
             return dispatch(ctx->cfg.precision,
                             [&](auto L) { return decltype(L)::step(ctx->Q, coll, odd, q, s); });
         });
+    if (e == cudaSuccess && q.diffusive)  // the wall sites of the same step
+        e = dispatch(ctx->cfg.precision, [&](auto L) { return decltype(L)::walls(odd, q, s); });
     if (e == cudaSuccess && limiter(coll))
         e = traced(ctx, LBM_KERNEL_FIXUP, s, [&] {
             return dispatch(ctx->cfg.precision,
                             [&](auto L) { return decltype(L)::fixup(ctx->Q, coll, odd, q, s, ctx->nsm); });
         });
+    if (e == cudaSuccess && q.probe_buf)  // the control point of the state just produced
+        e = dispatch(ctx->cfg.precision, [&](auto L) { return decltype(L)::probe(ctx->Q, !odd, q, s); });
     return e;
 }
 
 // Captures the two steps of one A-A period (even with counter slot 0, odd
 // with slot 1) into a graph on a private stream; lbm_step replays it.
-cudaError_t build_step_graph(lbm_ctx* ctx) {
+// Captures `periods` A-A periods (even step with counter slot 0, odd with
+// slot 1, repeated) into *graph / *exec on a private stream.
+cudaError_t capture_periods(lbm_ctx* ctx, int periods, cudaGraph_t* graph, cudaGraphExec_t* exec) {
     cudaStream_t cap;
     cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
     e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        cudaError_t e1 = enqueue_one_step(ctx, false, 0, cap);
-        if (e1 == cudaSuccess) e1 = enqueue_one_step(ctx, true, 1, cap);
+        cudaError_t e1 = cudaSuccess;
+        for (int k = 0; k < periods && e1 == cudaSuccess; ++k) {
+            e1 = enqueue_one_step(ctx, false, 0, cap);
+            if (e1 == cudaSuccess) e1 = enqueue_one_step(ctx, true, 1, cap);
+        }
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(cap, &g);
         if (e1 != cudaSuccess) e = e1;
         if (e == cudaSuccess) {
-            ctx->graph = g;
-            e = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+            *graph = g;
+            e = cudaGraphInstantiate(exec, g, 0);
         } else if (g) {
             cudaGraphDestroy(g);
         }
     }
     cudaStreamDestroy(cap);
+    return e;
+}
+
+// The two-step graph lbm_step replays, and for long runs of small lattices
+// (where the host's graph launches, not the GPU, set the pace) one of
+// kLongPeriods periods.
+constexpr int kLongPeriods = 32;
+
+cudaError_t build_step_graph(lbm_ctx* ctx) {
+    cudaError_t e = capture_periods(ctx, 1, &ctx->graph, &ctx->graph_exec);
+    if (e == cudaSuccess) e = capture_periods(ctx, kLongPeriods, &ctx->graph_long, &ctx->graph_long_exec);
     return e;
 }
 
@@ -352,6 +374,8 @@ lbm_status lbm_create(const lbm_config* cfg, void* dev_mem, size_t bytes, lbm_ct
     p.periodic_y = cfg->bc == LBM_BC_PERIODIC;
     p.eq = cfg->equilibrium;
     p.lid_u = (cfg->bc == LBM_BC_CAVITY || cfg->bc == LBM_BC_CHANNEL) ? cfg->lid_u : 0.0;
+    p.diffusive = cfg->bc == LBM_BC_DIFFUSIVE;
+    p.wall_u = p.diffusive ? cfg->lid_u : 0.0;
     p.beta = ctx->cfg.beta;
     p.topk = cfg->topk;
     p.delta = cfg->delta;
@@ -471,6 +495,12 @@ lbm_status lbm_step(lbm_ctx* ctx, int nsteps, void* stream) {
     int k = 0;
     const bool use_graph = ctx->graph_exec && !ctx->profiling;
     while (k < nsteps) {
+        if (use_graph && ctx->parity == 0 && ctx->graph_long_exec && nsteps - k >= 2 * kLongPeriods) {
+            LBM_CK(ctx, cudaGraphLaunch(ctx->graph_long_exec, S(stream)));
+            ctx->t += 2 * kLongPeriods;
+            k += 2 * kLongPeriods;
+            continue;
+        }
         if (use_graph && ctx->parity == 0 && nsteps - k >= 2) {
             LBM_CK(ctx, cudaGraphLaunch(ctx->graph_exec, S(stream)));
             ctx->t += 2;
@@ -507,6 +537,30 @@ lbm_status lbm_entropy(lbm_ctx* ctx, double* H_total_host, double* dS_dev, void*
         LBM_CK(ctx, cudaMemcpyAsync(H_total_host, H, sizeof(double), cudaMemcpyDeviceToHost, S(stream)));
         LBM_CK(ctx, cudaStreamSynchronize(S(stream)));
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_probe_set(lbm_ctx* ctx, int x, int y, double* buf, int cap) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (buf && (x < 0 || x >= ctx->cfg.nx || y < 0 || y >= ctx->cfg.ny || cap < 1))
+        return fail(ctx, LBM_ERR_ARG, "probe site outside the lattice or cap < 1");
+    LBM_CK(ctx, cudaDeviceSynchronize());
+    ctx->p.probe_buf = buf;
+    ctx->p.probe_site = buf ? y * ctx->cfg.nx + x : -1;
+    ctx->p.probe_cap = buf ? cap : 0;
+    LBM_CK(ctx, cudaMemset(ctx->p.counters + CNT_PROBE, 0, sizeof(unsigned)));
+    // the step graphs hold the kernel parameters: capture them again
+    ctx->drop_graphs();
+    LBM_CK(ctx, build_step_graph(ctx));
+    return LBM_OK;
+}
+
+lbm_status lbm_probe_count(lbm_ctx* ctx, uint64_t* count, void* stream) {
+    if (!ctx || !count) return LBM_ERR_ARG;
+    unsigned c = 0;
+    LBM_CK(ctx, cudaMemcpyAsync(&c, ctx->p.counters + CNT_PROBE, sizeof c, cudaMemcpyDeviceToHost, S(stream)));
+    LBM_CK(ctx, cudaStreamSynchronize(S(stream)));
+    *count = c;
     return LBM_OK;
 }
 

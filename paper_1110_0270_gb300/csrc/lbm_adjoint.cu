@@ -24,7 +24,7 @@ struct AdjLayout {
 };
 
 bool adj_supported(const lbm_config* c) {
-    return c->collision == LBM_LBGK || c->collision == LBM_EHRENFEST;
+    return (c->collision == LBM_LBGK || c->collision == LBM_EHRENFEST) && c->bc != LBM_BC_DIFFUSIVE;
 }
 
 AdjLayout adj_layout(const lbm_config* c, int T, int K) {

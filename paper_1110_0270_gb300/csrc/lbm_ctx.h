@@ -27,13 +27,23 @@ struct lbm_ctx {
     std::vector<cudaEvent_t> ev;  // pairs (start, end)
     std::vector<int> ev_kind;
     size_t ev_used = 0;
-    // two steps (both A-A parities) captured once at creation and replayed
+    // two steps (both A-A parities) captured once at creation and replayed,
+    // and the same repeated (long runs of small lattices)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
-    ~lbm_ctx() {
-        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    cudaGraph_t graph_long = nullptr;
+    cudaGraphExec_t graph_long_exec = nullptr;
+    void drop_graphs() {
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
         if (graph) cudaGraphDestroy(graph);
+        if (graph_long_exec) cudaGraphExecDestroy(graph_long_exec);
+        if (graph_long) cudaGraphDestroy(graph_long);
+        graph = graph_long = nullptr;
+        graph_exec = graph_long_exec = nullptr;
+    }
+    ~lbm_ctx() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        drop_graphs();
     }
 };
 

@@ -165,6 +165,47 @@ __device__ __forceinline__ void collide_site(const Params& p, int x, int y, cons
     conserve_mass<Q, T>(rho, F);
 }
 
+// Section 8's diffusive Maxwell rule at wall site (x, y) (bc DIFFUSIVE), on
+// its pre-collision populations: at a site of one wall (outward normal n)
+// the populations with v . n < 0 become gamma f*_i(u_wall), f* at unit
+// density, gamma = sum_{v.n > 0} f_j / sum_{v.n < 0} f*_i; at a corner each
+// population from outside the box takes its opposite's value when that
+// one came from inside (the rule with a single population: bounce-back).
+template <class T>
+__device__ __forceinline__ void diffusive_rule(const Params& p, int x, int y, T* f) {
+    using L = Lat<9>;
+    const int nxw = (x == 0 ? -1 : 0) + (x == p.nx - 1 ? 1 : 0);
+    const int nyw = (y == 0 ? -1 : 0) + (y == p.ny - 1 ? 1 : 0);
+    if (nxw != 0 && nyw != 0) {
+        T g[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i] = f[i];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int sx = x - L::cx(i), sy = y - L::cy(i);
+            const int o = L::opp(i), ox = x - L::cx(o), oy = y - L::cy(o);
+            const bool out_i = sx < 0 || sx >= p.nx || sy < 0 || sy >= p.ny;
+            const bool in_o = ox >= 0 && ox < p.nx && oy >= 0 && oy < p.ny;
+            if (out_i && in_o) f[i] = g[o];
+        }
+        return;
+    }
+    T feq[9];
+    const T uw = nyw == 1 ? T(p.wall_u) : T(0);
+    equilibrium<9, T>(p.eq, T(1), uw, T(0), feq);
+    T out = T(0), in = T(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int vn = L::cx(i) * nxw + L::cy(i) * nyw;
+        if (vn > 0) out += f[i];
+        if (vn < 0) in += feq[i];
+    }
+    const T gamma = out / in;
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        if (L::cx(i) * nxw + L::cy(i) * nyw < 0) f[i] = gamma * feq[i];
+}
+
 // The whole step for the site (x, y): load (streaming in odd steps),
 // collision, store.
 template <int Q, class ST, int COLL, bool ODD>
@@ -174,10 +215,14 @@ __device__ __forceinline__ void site_update(const Params& p, int x, int y, int& 
     T f[Q], F[Q];
     const bool interior = x > 0 && x < p.nx - 1 && (Q == 3 || (y > 0 && y < p.ny - 1));
     const int o = y * p.pitch + x;
-    if (interior)
+    if (interior) {
         load_interior<Q, ST, ODD>(p, o, f);
-    else
+    } else {
+        // diffusive walls: wall sites are updated by diffusive_wall_kernel
+        // (each site owns its addresses, so the two kernels of a step commute)
+        if (Q == 9 && p.diffusive) return;
         load_general<Q, ST, ODD>(p, x, y, f);
+    }
     collide_site<Q, ST, COLL>(p, x, y, f, F, e_code, e_iters, acc);
     if (interior)
         store_interior<Q, ST, ODD>(p, o, F);
@@ -849,6 +894,7 @@ __global__ void __launch_bounds__(256) ensemble_mean(Params p) {
         if (x >= p.nx) continue;
         T f[Q], feq[Q], rho, ux, uy, q;
         const bool interior = x > 0 && x < p.nx - 1 && (Q == 3 || (y > 0 && y < p.ny - 1));
+        if (p.diffusive && !interior) continue;  // wall sites are not in the mean
         if (interior)
             load_interior<Q, ST, ODD>(p, y * p.pitch + x, f);
         else
@@ -915,12 +961,15 @@ __device__ void median_apply(const Params& p, unsigned g0, unsigned G) {
         T w[9];
         int n = 0;
         const int ry = Q == 9 ? 1 : 0;
+        // the window is clipped to the fluid sites (all sites except the
+        // wall sites of diffusive walls)
+        const int lo = p.diffusive ? 1 : 0, hx = p.diffusive ? p.nx - 1 : p.nx, hy = p.diffusive ? p.ny - 1 : p.ny;
         for (int dy = -ry; dy <= ry; ++dy)
             for (int dx = -1; dx <= 1; ++dx) {
                 int xx = x + dx, yy = y + dy;
                 if (p.periodic_x) xx = xx < 0 ? xx + p.nx : (xx >= p.nx ? xx - p.nx : xx);
                 if (p.periodic_y) yy = yy < 0 ? yy + p.ny : (yy >= p.ny ? yy - p.ny : yy);
-                if (xx < 0 || xx >= p.nx || yy < 0 || yy >= p.ny) continue;
+                if (xx < lo || xx >= hx || yy < (Q == 9 ? lo : 0) || yy >= (Q == 9 ? hy : p.ny)) continue;
                 T v = field[(int64_t)yy * p.nx + xx];
                 int k = n++;
                 while (k > 0 && w[k - 1] > v) {  // insertion sort, ascending
@@ -1032,6 +1081,54 @@ __global__ void get_state_kernel(Params p, Out* dst, int odd) {
     for (int i = 0; i < Q; ++i) dst[i * N + s] = (Out)f[i];
 }
 
+// Diffusive Maxwell walls (Section 8): the wall sites of one step - load
+// (streaming), the rule of diffusive_rule, store without collision.  Thread
+// k walks the perimeter: bottom row, top row, then the two side columns.
+template <class ST, bool ODD>
+__global__ void __launch_bounds__(256) diffusive_wall_kernel(Params p) {
+    pdl_enter();
+    using T = typename ST::T;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int side = p.ny - 2;
+    int x, y;
+    if (k < p.nx) {
+        x = k;
+        y = 0;
+    } else if (k < 2 * p.nx) {
+        x = k - p.nx;
+        y = p.ny - 1;
+    } else if (k < 2 * p.nx + side) {
+        x = 0;
+        y = 1 + (k - 2 * p.nx);
+    } else if (k < 2 * p.nx + 2 * side) {
+        x = p.nx - 1;
+        y = 1 + (k - 2 * p.nx - side);
+    } else {
+        return;
+    }
+    T f[9];
+    load_general<9, ST, ODD>(p, x, y, f);
+    diffusive_rule<T>(p, x, y, f);
+    store_general<9, ST, ODD>(p, x, y, f);
+}
+
+// Control-point probe: one thread appends the velocity of site probe_site
+// in the state of parity `odd` (the state a step just produced) to the ring
+// buffer; launched after each step only while a probe is set.
+template <int Q, class ST>
+__global__ void probe_kernel(Params p, int odd) {
+    pdl_enter();
+    using T = typename ST::T;
+    T f[Q], rho, ux, uy;
+    const int x = p.probe_site % p.nx, y = p.probe_site / p.nx;
+    read_state<Q, ST>(p, x, y, odd != 0, f);
+    moments<Q, T>(f, rho, ux, uy);
+    const unsigned k = p.counters[CNT_PROBE];
+    p.probe_buf[2 * (k % (unsigned)p.probe_cap)] = (double)ux;
+    p.probe_buf[2 * (k % (unsigned)p.probe_cap) + 1] = (double)uy;
+    p.counters[CNT_PROBE] = k + 1;
+}
+
 template <int Q, class ST, class Out>
 __global__ void macros_kernel(Params p, Out* rho, Out* u, int odd) {
     using T = typename ST::T;
@@ -1093,6 +1190,8 @@ struct Launch {
     static cudaError_t step(int Q, int coll, bool odd, const Params& p, cudaStream_t s);
     static cudaError_t fixup(int Q, int coll, bool odd, const Params& p, cudaStream_t s, int nsm);
     static cudaError_t prepass(int Q, int coll, bool odd, const Params& p, cudaStream_t s);
+    static cudaError_t probe(int Q, bool odd, const Params& p, cudaStream_t s);
+    static cudaError_t walls(bool odd, const Params& p, cudaStream_t s);
     static cudaError_t init(int Q, const Params& p, const double* r, const double* ux,
                             const double* uy, int eqkind, cudaStream_t s);
     static cudaError_t init_uniform(int Q, const Params& p, double r, double ux, double uy,
@@ -1105,6 +1204,24 @@ struct Launch {
     static cudaError_t entropy(int Q, const Params& p, double* H, double* dS, bool odd, int eqkind,
                                cudaStream_t s);
 };
+
+inline cudaError_t launch_p(void (*k)(Params, int), dim3 g, dim3 b, cudaStream_t s, const Params& p, int a) {
+    if (!p.pdl) {
+        k<<<g, b, 0, s>>>(p, a);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t c = {};
+    c.gridDim = g;
+    c.blockDim = b;
+    c.dynamicSmemBytes = 0;
+    c.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    c.attrs = at;
+    c.numAttrs = 1;
+    return cudaLaunchKernelEx(&c, k, p, a);
+}
 
 inline cudaError_t launch_p(void (*k)(Params), dim3 g, dim3 b, cudaStream_t s, const Params& p) {
     if (!p.pdl) {
@@ -1194,6 +1311,18 @@ cudaError_t launch_prepass_q(int coll, bool odd, const Params& p, cudaStream_t s
 template <class ST>
 cudaError_t Launch<ST>::step(int Q, int coll, bool odd, const Params& p, cudaStream_t s) {
     return Q == 3 ? launch_step_c<3, ST>(coll, odd, p, s) : launch_step_c<9, ST>(coll, odd, p, s);
+}
+
+template <class ST>
+cudaError_t Launch<ST>::walls(bool odd, const Params& p, cudaStream_t s) {
+    const int n = 2 * p.nx + 2 * (p.ny - 2);
+    return launch_p(odd ? diffusive_wall_kernel<ST, true> : diffusive_wall_kernel<ST, false>,
+                    dim3((n + 255) / 256), dim3(256), s, p);
+}
+
+template <class ST>
+cudaError_t Launch<ST>::probe(int Q, bool odd, const Params& p, cudaStream_t s) {
+    return launch_p(Q == 3 ? probe_kernel<3, ST> : probe_kernel<9, ST>, dim3(1), dim3(1), s, p, odd ? 1 : 0);
 }
 
 template <class ST>

@@ -25,6 +25,7 @@ enum Counter {
     CNT_NSEL = 4,      // number of sites selected in the last Ehrenfest step
     CNT_NVALID = 5,    // candidates (FP64 Delta S > delta) of the current step
     CNT_DONE = 6,      // CTAs of ehrenfest_eval_select that have finished
+    CNT_PROBE = 7,     // samples written by the control-point probe
     CNT_WORDS = 8
 };
 constexpr int kRedSlots = 1024;  // partial-sum slots (spread the atomics)
@@ -61,6 +62,10 @@ struct Params {
     double* red;      // kRedSlots partial sums (+ kRedSlots counts), zero between steps
     double* lim_E;    // the step's E(Delta S) (ensemble limiter)
     int pipe_ctas;    // host side: CTAs of the grid-stride reduction kernels
+    double* probe_buf;  // control-point probe: (u_x, u_y) per step, ring of probe_cap
+    int probe_site, probe_cap;
+    int diffusive;    // Section 8's diffusive Maxwell walls on the edge sites
+    double wall_u;    // their top-wall velocity (lid_u; the streaming adds no lid term)
     // scratch
     unsigned* counters;              // CNT_WORDS words
     unsigned long long* stats;       // ST_WORDS words

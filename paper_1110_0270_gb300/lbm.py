@@ -22,7 +22,7 @@ COLLISIONS = {"lbgk": 0, "elbm": 1, "ehrenfest": 2, "positivity": 3, "median": 4
               "mrt_limiter": 11}
 EQUILIBRIA = {"poly": 0, "entropic": 1, "poly_std": 2}
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16_dev": 2, "fp16_dev": 3}
-BCS = {"cavity": 0, "ends": 1, "periodic": 2, "channel": 3}
+BCS = {"cavity": 0, "ends": 1, "periodic": 2, "channel": 3, "diffusive": 4}
 NORMS = {"entropic": 0, "l1": 1}
 FALLBACKS = {"positivity": 0, "ehrenfest": 1}
 DTYPE_F64, DTYPE_F32 = 0, 1
@@ -39,7 +39,7 @@ EXPORTS = ["lbm_config_default", "lbm_required_bytes", "lbm_create", "lbm_destro
            "lbm_batch_destroy", "lbm_batch_init_uniform", "lbm_batch_set_state",
            "lbm_batch_get_state", "lbm_batch_step", "lbm_batch_stats", "lbm_batch_last_error",
            "lbm_adjoint_required_bytes", "lbm_adjoint_forward", "lbm_adjoint_backward",
-           "lbm_fp64_rates", "lbm_enstrophy"]
+           "lbm_fp64_rates", "lbm_enstrophy", "lbm_probe_set", "lbm_probe_count"]
 
 
 class lbm_config(C.Structure):
@@ -95,6 +95,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "lbm_ehrenfest_step_noalloc": (i, [C.POINTER(lbm_config), p, i, p]),
         "lbm_fp64_rates": (i, [C.POINTER(C.c_double), C.POINTER(C.c_double), p]),
         "lbm_enstrophy": (i, [p, C.POINTER(C.c_double), p]),
+        "lbm_probe_set": (i, [p, i, i, p, i]),
+        "lbm_probe_count": (i, [p, C.POINTER(C.c_uint64), p]),
         "lbm_batch_required_bytes": (i, [C.POINTER(lbm_config), i, C.POINTER(sz)]),
         "lbm_batch_create": (i, [C.POINTER(lbm_config), i, p, sz, C.POINTER(p)]),
         "lbm_batch_destroy": (None, [p]),
@@ -284,6 +286,30 @@ class Lattice:
         self._check(lib().lbm_entropy(self._h, C.byref(H), _ptr(dS) if field else None,
                                       _stream(stream)), "lbm_entropy")
         return (H.value, dS) if field else H.value
+
+    def probe(self, x: int, y: int, cap: int):
+        """Record the velocity of site (x, y) at every following step into a
+        device ring buffer of cap samples (None for x turns it off)."""
+        import torch
+        if x is None:
+            self._probe = None
+            self._check(lib().lbm_probe_set(self._h, 0, 0, None, 0), "lbm_probe_set")
+            return
+        self._probe = torch.zeros((cap, 2), dtype=torch.float64, device=self.device)
+        self._check(lib().lbm_probe_set(self._h, int(x), int(y), _ptr(self._probe), int(cap)), "lbm_probe_set")
+
+    def probe_signal(self):
+        """The recorded samples in time order (the last cap of them) as a
+        host array [n, 2] of (u_x, u_y)."""
+        n = C.c_uint64()
+        self._check(lib().lbm_probe_count(self._h, C.byref(n), None), "lbm_probe_count")
+        cap = self._probe.shape[0]
+        buf = self._probe.cpu().numpy()
+        k = int(n.value)
+        if k <= cap:
+            return buf[:k].copy()
+        start = k % cap
+        return np.concatenate([buf[start:], buf[:start]])
 
     def enstrophy(self, stream=None) -> float:
         """Section 8's enstrophy: mean over sites of the vorticity squared."""

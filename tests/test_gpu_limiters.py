@@ -206,3 +206,56 @@ def test_shear_decay_lambda_matches_oracle(collision):
     ref = {10: 37.884, 1000: 39.778}  # LBGK's values of this set-up (oracle)
     for re in lam:
         assert lam[re] == pytest.approx(ref[re], rel=0.01)
+
+
+DIFF_CASES = {"box": dict(lattice="D2Q9", nx=37, ny=29, bc="diffusive", lid_u=0.1),
+              "wide_box": dict(lattice="D2Q9", nx=200, ny=12, bc="diffusive", lid_u=0.1)}
+
+
+@pytest.mark.parametrize("case", list(DIFF_CASES))
+@pytest.mark.parametrize("collision", ["lbgk", "median", "ehrenfest", "mrt", "ensemble", "threshold"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_diffusive_walls_match_oracle(case, collision, precision):
+    """Section 8's diffusive Maxwell walls (entropic equilibria, moving top
+    wall): wall sites not collided, the rule at the start of each step,
+    limiters and median windows on the fluid sites; 101 steps against the
+    oracle."""
+    cfg = dict(DIFF_CASES[case], collision=collision, precision=precision, equilibrium="entropic",
+               beta=0.93, topk=3, delta=2e-4, lim_alpha=1.0, lim_k=1.0, lim_delta0=0.05)
+    f0 = state(cfg)
+    if precision != "fp64":
+        f0 = f0.astype(np.float32).astype(np.float64)
+    n = 101
+    lat = lbm.Lattice(cfg)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    lat.set_state(torch.tensor(f0, dtype=dt, device="cuda"))
+    lat.step(n)
+    g = lat.get_state(torch.float64).cpu().numpy()
+    f, st = O.step(cfg, f0, n, stats=True)
+    assert rel(g, f) < TOL[precision], rel(g, f)
+    if collision in ("median", "ehrenfest", "threshold") and precision == "fp64":
+        assert lat.stats()["limited_total"] == st["limited_sites"]
+
+
+def test_control_point_probe_records_the_velocity_each_step():
+    """lbm_probe_set: the velocity of the control site in the state each step
+    produces, in order, through a ring buffer smaller than the run; equal to
+    the oracle's velocity of each intermediate state."""
+    cfg = dict(DIFF_CASES["box"], collision="median", precision="fp64", equilibrium="entropic", beta=0.93,
+               delta=2e-4)
+    f = state(cfg)
+    lat = lbm.Lattice(cfg)
+    lat.set_state(torch.tensor(f, device="cuda"))
+    xp, yp = 3, 22
+    lat.probe(xp, yp, 16)
+    want = []
+    for _ in range(40):
+        f = O.step(cfg, f, 1)
+        _, ux, uy = O.macros(cfg, f)
+        want.append((ux[yp, xp], uy[yp, xp]))
+    lat.step(40)
+    sig = lat.probe_signal()
+    assert sig.shape == (16, 2)
+    assert np.allclose(sig, np.array(want[-16:]), rtol=1e-12, atol=1e-15)
+    lat.probe(None, None, 0)
+    lat.step(2)

@@ -933,3 +933,18 @@ def test_diffusive_box_keeps_rest_and_composes_rule_collision_streaming(collisio
             fe = O.equilibrium("D2Q9", "entropic", *O.moments("D2Q9", g[:, y, x]))
             F[:, y, x] = g[:, y, x] + 2 * 0.9 * (fe - g[:, y, x])
     assert np.abs(O.step(cfg2, f, 1) - O.stream(cfg2, F)).max() < 1e-15
+
+
+def test_hopf_energy_and_onset_fit():
+    """Eq. (energy): for a sampled sine of amplitude a the energy is
+    a sqrt(L / (2 u0)) (the L2 norm of the zero-mean samples over sqrt of
+    their count); the line fit of E^2 against Re recovers a planted onset."""
+    from paper_1110_0270_gb300.analysis import fit_onset, hopf_energy
+    t = np.arange(40000)
+    a, L, u0 = 3e-3, 99.0, 0.1
+    u = 0.2 + a * np.sin(2 * np.pi * t / 400)
+    assert hopf_energy(u, L, u0) == pytest.approx(a * np.sqrt(L / (2 * u0)), rel=1e-9)
+    re = np.array([6000, 6500, 7000, 7500, 8000, 8500])
+    e2 = np.where(re > 7135, 2e-4 * (re - 7135), 1e-7)
+    fit = fit_onset(re, e2)
+    assert fit["re_c"] == pytest.approx(7135, rel=1e-9)
