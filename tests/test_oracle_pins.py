@@ -948,3 +948,56 @@ def test_hopf_energy_and_onset_fit():
     e2 = np.where(re > 7135, 2e-4 * (re - 7135), 1e-7)
     fit = fit_onset(re, e2)
     assert fit["re_c"] == pytest.approx(7135, rel=1e-9)
+
+
+def test_dominant_frequency_of_planted_sine():
+    """A sine of 25 cycles in the record, buried in white noise 10x smaller:
+    the spectrum peak is at 25 cycles, i.e. f = 25 / n * L / u0 cycles per
+    convective time, and holds most of the power; pure noise holds little
+    at its peak."""
+    from paper_1110_0270_gb300.analysis import dominant_frequency
+    rng = np.random.default_rng(3)
+    n, L, u0 = 40000, 99.0, 0.1
+    t = np.arange(n)
+    u = 0.01 + 1e-3 * np.sin(2 * np.pi * 25 * t / n) + 1e-4 * rng.standard_normal(n)
+    d = dominant_frequency(u, L, u0)
+    assert d["f"] == pytest.approx(25 / n * L / u0, rel=1e-12)
+    assert d["omega"] == pytest.approx(2 * np.pi * d["f"], rel=1e-12)
+    assert d["peak_share"] > 0.9
+    assert dominant_frequency(1e-4 * rng.standard_normal(n), L, u0)["peak_share"] < 0.01
+    assert dominant_frequency(np.ones(100), L, u0)["f"] is None
+
+
+@pytest.mark.parametrize("ny,nx", [(9, 13), (10, 12), (3, 4)])
+def test_stream_function_recovers_cubic(ny, nx):
+    """psi = x^3 - 2 x^2 y + 3 x y^2 - y^3 + x y, u_x = dpsi/dy and
+    u_y = -dpsi/dx are quadratic along each integration line, so the
+    Simpson integration (even and odd end indices alike) returns
+    psi - psi(0, 0) to rounding; the vortex summary finds its extremes."""
+    from paper_1110_0270_gb300.analysis import stream_function, vortex_summary
+    h = 0.25
+    y, x = np.meshgrid(np.arange(ny) * h, np.arange(nx) * h, indexing="ij")
+    psi = x**3 - 2 * x**2 * y + 3 * x * y**2 - y**3 + x * y
+    ux = -2 * x**2 + 6 * x * y - 3 * y**2 + x
+    uy = -(3 * x**2 - 4 * x * y + 3 * y**2 + y)
+    got = stream_function(ux, uy, h)
+    assert np.abs(got - psi).max() < 1e-12 * max(1.0, np.abs(psi).max())
+    s = vortex_summary(got)
+    lo, hi = np.unravel_index(np.argmin(psi), psi.shape), np.unravel_index(np.argmax(psi), psi.shape)
+    ext = {(int(lo[1]), int(lo[0])), (int(hi[1]), int(hi[0]))}
+    assert {(s["primary"]["x"], s["primary"]["y"]), (s["secondary"]["x"], s["secondary"]["y"])} == ext
+
+
+def test_stream_function_of_a_cell_flow_converges():
+    """psi = sin(pi x) sin(pi y) on [0,1]^2: the error falls by about 2^4 per
+    halving of h (fourth-order Simpson), and psi vanishes on the edges."""
+    from paper_1110_0270_gb300.analysis import stream_function
+    errs = []
+    for n in (17, 33, 65):
+        h = 1.0 / (n - 1)
+        y, x = np.meshgrid(np.arange(n) * h, np.arange(n) * h, indexing="ij")
+        ux = np.pi * np.sin(np.pi * x) * np.cos(np.pi * y)
+        uy = -np.pi * np.cos(np.pi * x) * np.sin(np.pi * y)
+        errs.append(np.abs(stream_function(ux, uy, h) - np.sin(np.pi * x) * np.sin(np.pi * y)).max())
+    assert errs[0] / errs[1] > 12 and errs[1] / errs[2] > 12
+    assert errs[2] < 1e-6
