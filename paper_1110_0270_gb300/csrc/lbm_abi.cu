@@ -409,6 +409,13 @@ lbm_status lbm_create(const lbm_config* cfg, void* dev_mem, size_t bytes, lbm_ct
     p.cand_site = (int*)(ctx->base + L.cand_site_off);
     p.cand_sel = (int*)(ctx->base + L.cand_sel_off);
     p.ds_field = ctx->base + L.field_off;
+    // median filter: with FP32 or FP64 storage and 1 - 2 beta away from 0 the
+    // window's Delta S is recovered from the post-collision state and the
+    // step writes no Delta S field (median_recon_fixup)
+    if (cfg->collision == LBM_MEDIAN && (cfg->precision == LBM_FP64 || cfg->precision == LBM_FP32)) {
+        const double b = cfg->precision == LBM_FP64 ? p.beta : (double)p.beta_f;
+        if (std::fabs(1.0 - 2.0 * b) >= 1.0 / 16) p.median_inv = 1.0 / (1.0 - 2.0 * b);
+    }
     if (reduces(cfg->collision)) {
         p.red = (double*)(ctx->base + L.red_off);
         p.lim_E = p.red + 2 * kRedSlots;

@@ -11,8 +11,12 @@
 //                   k-largest selection by MSB radix select on the FP64
 //                   Delta S bits, ties by site index; selected sites are
 //                   rewritten with f*.
-//  median_fixup     grid-stride over candidates: median of the Delta S window,
-//                   homothety of Eq. (entrHom) where it lowers Delta S.
+//  median_fixup     grid-stride over candidates: median of the Delta S window
+//                   (a field the step wrote), homothety of Eq. (entrHom)
+//                   where it lowers Delta S.
+//  median_recon_fixup  the same without a field: the window's Delta S from
+//                   the pre-collision state recovered from the LBGK
+//                   post-collision one (FP32 / FP64 storage).
 #pragma once
 
 #include "lbm_device.cuh"
@@ -430,33 +434,36 @@ __device__ __forceinline__ void load_candidate(const Params& p, int j, typename 
     for (int i = 0; i < Q; ++i) f[i] = cf[(int64_t)i * p.cand_cap + j];
 }
 
-// FP64 Delta S of candidate record j, computed by a group of 16 lanes (lane
-// q < Q holds population q): the moments and the sum over populations are
+// FP64 Delta S of one site, computed by a group of 16 lanes (lane q < Q
+// holds population q in v): the moments and the sum over populations are
 // shuffle reductions, so the dependent chain of FP64 operations - the
 // latency of this step on GB300's narrow FP64 pipe - is about one
-// population's instead of Q.  All 16 lanes of the group must call it; lanes
-// of a group with j >= M pass valid = false and get 0.
-template <int Q, class ST>
-__device__ __forceinline__ double delta_s_group(const Params& p, unsigned j, bool valid) {
-    using T = typename ST::T;
+// population's instead of Q.  With inv = 0, v is the pre-collision f; with
+// inv = 1 / (1 - 2 beta), v is the post-collision state of an LBGK site, and
+// the pre-collision f = f* + (v - f*) inv (LBGK keeps rho and u, so f* is
+// the same).  All 32 lanes of the warp must call it (the series length of
+// g is chosen once per warp, so that the lanes take one branch: the
+// longest any lane needs); inactive lanes (valid = false, or q >= Q)
+// contribute nothing.
+template <int Q>
+__device__ __forceinline__ double delta_s_lanes(const Params& p, double v, bool valid, double inv) {
     const int q = threadIdx.x & 15;
     const unsigned gmask = 0xffffu << (threadIdx.x & 16);
     const bool act = valid && q < Q;
     const int cx = Q == 3 ? q - 1 : ((q == 1 || q == 2 || q == 8) ? 1 : ((q == 4 || q == 5 || q == 6) ? -1 : 0));
     const int cy = Q == 3 ? 0 : ((q == 6 || q == 7 || q == 8) ? 1 : ((q == 2 || q == 3 || q == 4) ? -1 : 0));
-    double f = 0.0;
-    if (act) f = (double)((const T*)p.cand_f)[(int64_t)q * p.cand_cap + j];
-    double r = f, jx = cx * f, jy = cy * f;
+    if (!act) v = 0.0;
+    double r = v, jx = cx * v, jy = cy * v;
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) {
         r += __shfl_xor_sync(gmask, r, o);
         jx += __shfl_xor_sync(gmask, jx, o);
         jy += __shfl_xor_sync(gmask, jy, o);
     }
-    double term = 0.0;
+    double x = 0.0, fe = 0.0;
     bool neg = false;
     if (act) {
-        const double ux = jx / r, uy = jy / r;
+        const double ri = 1.0 / r, ux = jx * ri, uy = jy * ri;
         double ax[3], ay[3];
         if (p.eq == LBM_EQ_ENTROPIC) {
             eq1d_entropic<double>(ux, ax[0], ax[1], ax[2]);
@@ -465,7 +472,6 @@ __device__ __forceinline__ double delta_s_group(const Params& p, unsigned j, boo
             eq1d_poly<double>(ux, ax[0], ax[1], ax[2]);
             eq1d_poly<double>(uy, ay[0], ay[1], ay[2]);
         }
-        double fe;
         if (Q == 9 && p.eq == LBM_EQ_POLY_STD) {
             // same values as equilibrium<9, double>: the rest population is
             // rho minus the others
@@ -482,13 +488,34 @@ __device__ __forceinline__ double delta_s_group(const Params& p, unsigned j, boo
         } else {
             fe = Q == 3 ? r * ax[cx + 1] : r * ax[cx + 1] * ay[cy + 1];
         }
-        neg = f < 0.0 || !(fe > 0.0);
-        term = fe * gfun_d((f - fe) / fe);
+        const double d = inv != 0.0 ? (v - fe) * inv : v - fe;  // f - f*
+        neg = (inv != 0.0 ? fe + d : v) < 0.0 || !(fe > 0.0);
+        x = d / fe;
     }
+    // one tier of gfun_d for the warp: the series (or log) its largest |x| needs
+    const float axf = fminf((float)fabs(x), 2.0f);
+    const float am = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(axf)));
+    double g;
+    if (am < 0.015625f) g = gseries_d<8>(x);
+    else if (am < 0.125f) g = gseries_d<16>(x);
+    else if (am < 0.25f) g = gseries_d<26>(x);
+    else g = x <= -1.0 ? 1.0 : (1.0 + x) * log1p(x) - x;
+    double term = act ? fe * g : 0.0;
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) term += __shfl_xor_sync(gmask, term, o);
     neg = __any_sync(gmask, neg);
     return neg ? __longlong_as_double(0x7ff0000000000000ULL) : term;
+}
+
+// FP64 Delta S of candidate record j (its recorded pre-collision
+// populations); lanes of a group with j >= M pass valid = false and get 0.
+template <int Q, class ST>
+__device__ __forceinline__ double delta_s_group(const Params& p, unsigned j, bool valid) {
+    using T = typename ST::T;
+    const int q = threadIdx.x & 15;
+    double f = 0.0;
+    if (valid && q < Q) f = (double)((const T*)p.cand_f)[(int64_t)q * p.cand_cap + j];
+    return delta_s_lanes<Q>(p, f, valid, 0.0);
 }
 
 // Ehrenfest regularisation (Section 4): the k candidates with the largest
@@ -812,19 +839,70 @@ __device__ __forceinline__ void eval_then_select(const Params& p) {
         // all, one 16-lane group each, and selects without the ticket and
         // its memory fences; the other CTAs have nothing to do
         if (blockIdx.x != 0) return;
+        __shared__ double s_key[16];
+        __shared__ int s_site[16];
+        __shared__ unsigned s_nsel;
         const unsigned j = threadIdx.x >> 4;
-        if (threadIdx.x == 0) s_last = 0;
+        if (threadIdx.x == 0) {
+            s_last = 0;
+            s_nsel = 0;
+        }
         __syncthreads();
         const double d = delta_s_group<Q, ST>(p, j, j < M);
-        if (j < M && (threadIdx.x & 15) == 0) {
-            const bool c = d > p.delta;
+        const bool lead = j < M && (threadIdx.x & 15) == 0;
+        const bool c = lead && d > p.delta;
+        int site = 0;
+        if (lead) {
+            site = p.cand_site[j];
             p.cand_ds[j] = c ? d : -1.0;
+            s_key[j] = c ? d : -1.0;
+            s_site[j] = site;
             if (c) atomicAdd(&s_last, 1u);
         }
         __syncthreads();  // this CTA's cand_ds entries are final
         const unsigned nvalid = s_last;
         if (threadIdx.x == 0) p.counters[CNT_NVALID] = nvalid;
-        select_apply<Q, ST, ODD, COLL>(p, M, nvalid);
+        if constexpr (COLL == LBM_THRESHOLD) {
+            select_apply<Q, ST, ODD, COLL>(p, M, nvalid);
+        } else {
+            // the k largest: a candidate's rank is the number of candidates
+            // before it in (Delta S descending, site ascending) order
+            if (lead) {
+                const unsigned K = p.topk > 0 ? (unsigned)p.topk : 0u;
+                bool sel = false;
+                if (c && K > 0) {
+                    unsigned rank = 0;
+                    for (unsigned i = 0; i < M; ++i) {
+                        const double o = s_key[i];
+                        rank += (o > d || (o == d && s_site[i] < site)) ? 1u : 0u;
+                    }
+                    sel = rank < K;
+                }
+                p.cand_sel[j] = sel ? 1 : 0;
+                if (sel) {
+                    using T = typename ST::T;
+                    T f[Q], feq[Q], rho, ux, uy;
+                    load_candidate<Q, ST>(p, (int)j, f);
+                    moments<Q, T>(f, rho, ux, uy);
+                    equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
+                    if constexpr (COLL == LBM_MRT_LIMITER && Q == 9) {
+                        T F[Q];
+                        mrt2_d2q9<T>(f, feq, sizeof(T) == 8 ? T(2.0 * p.beta) : T(2) * T(p.beta_f), F);
+                        conserve_mass<Q, T>(rho, F);
+                        rewrite_site<Q, ST, ODD>(p, site, F);
+                    } else {
+                        conserve_mass<Q, T>(rho, feq);
+                        rewrite_site<Q, ST, ODD>(p, site, feq);
+                    }
+                    atomicAdd(&s_nsel, 1u);
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                p.counters[CNT_NSEL] = s_nsel;
+                if (s_nsel) atomicAdd(&p.stats[ST_LIMITED], (unsigned long long)s_nsel);
+            }
+        }
         return;
     }
     unsigned n = 0;
@@ -1006,6 +1084,152 @@ template <int Q, class ST, bool ODD>
 __global__ void __launch_bounds__(256) median_fixup(Params p) {
     pdl_enter();
     median_apply<Q, ST, ODD>(p, blockIdx.x * (blockDim.x >> 4) + (threadIdx.x >> 4), gridDim.x * (blockDim.x >> 4));
+}
+
+// Median filter, second kernel, without a Delta S field (FP32 and FP64
+// storage with |1 - 2 beta| >= 1/16): the step ran LBGK and the Ehrenfest
+// screen at every site, so each window value is the FP64 Delta S of the
+// pre-collision state recovered from the post-collision one (delta_s_lanes
+// with inv = 1 / (1 - 2 beta)); the candidate's own value comes from its
+// record.  Per round a CTA takes MedWin::C candidates, one 16-lane group
+// per window site; the first lane of the centre group takes the lower
+// median and, where the filter applies, the new post-collision populations.
+// They are written only after every window of the step has been read: by
+// the CTA itself when it holds all candidates, otherwise by the last CTA to
+// finish (ticket after a fence) from the candidate records they replace.
+template <int Q>
+struct MedWin {
+    static constexpr int W = Q == 9 ? 9 : 3;  // window sites
+    static constexpr int C = 64 / W;          // candidates per round of a 1024-thread CTA
+    static constexpr int centre = W / 2;
+};
+
+template <int Q, class ST, bool ODD>
+__global__ void __launch_bounds__(1024, 1) median_recon_fixup(Params p) {
+    pdl_enter();
+    using T = typename ST::T;
+    using L = Lat<Q>;
+    using MW = MedWin<Q>;
+    __shared__ double win[MW::C][MW::W];
+    __shared__ unsigned s_last;
+    unsigned M = p.counters[p.cslot];
+    if (M > (unsigned)p.cand_cap) M = (unsigned)p.cand_cap;
+    const bool single = M <= (unsigned)MW::C;
+    if (single && blockIdx.x != 0) return;
+    const int q = threadIdx.x & 15;
+    const unsigned g = threadIdx.x >> 4, cl = g / MW::W, k = g % MW::W;
+    const int dx = Q == 9 ? (int)(k % 3) - 1 : (int)k - 1, dy = Q == 9 ? (int)(k / 3) - 1 : 0;
+    // the window is clipped to the fluid sites (all sites except the wall
+    // sites of diffusive walls)
+    const int lo = p.diffusive ? 1 : 0, hx = p.diffusive ? p.nx - 1 : p.nx, hy = p.diffusive ? p.ny - 1 : p.ny;
+    const typename ST::S* base = (const typename ST::S*)p.f;
+    T* cf = (T*)p.cand_f;
+    unsigned nvalid = 0, nsel = 0;
+    bool have = false;
+    int my_site = 0;
+    T Fm[Q];
+    for (unsigned b0 = blockIdx.x * MW::C; b0 < M; b0 += gridDim.x * MW::C) {
+        const unsigned j = b0 + cl;
+        const bool act = cl < (unsigned)MW::C && j < M;
+        int site = 0, xx = 0, yy = 0;
+        bool inw = false;
+        if (act) {
+            site = p.cand_site[j];
+            xx = site % p.nx + dx;
+            yy = site / p.nx + dy;
+            if (p.periodic_x) xx = xx < 0 ? xx + p.nx : (xx >= p.nx ? xx - p.nx : xx);
+            if (p.periodic_y) yy = yy < 0 ? yy + p.ny : (yy >= p.ny ? yy - p.ny : yy);
+            inw = xx >= lo && xx < hx && yy >= (Q == 9 ? lo : 0) && yy < (Q == 9 ? hy : p.ny);
+        }
+        const bool centre = k == (unsigned)MW::centre;
+        double v = 0.0;
+        if (act && inw && q < Q) {
+            if (centre) {
+                v = (double)cf[(int64_t)q * p.cand_cap + j];
+            } else {
+                // population q of the site's post-collision state, where the
+                // step stored it (store_general's addressing, lid term added back)
+                T lidc;
+                const int i = L::opp(q);
+                const int64_t r = aa_address<Q, T>(p, xx, yy, i, ODD, lidc);
+                v = (double)(ST::ld(base + r, T(L::w(i))) + lidc);
+            }
+        }
+        const double ds = delta_s_lanes<Q>(p, v, act && inw, centre ? 0.0 : p.median_inv);
+        if (q == 0 && cl < (unsigned)MW::C) win[cl][k] = act && inw ? ds : __longlong_as_double(0x7ff8000000000000LL);
+        __syncthreads();
+        if (act && centre && q == 0) {
+            const bool cand = ds > p.delta;
+            p.cand_ds[j] = cand ? ds : -1.0;
+            bool sel = false;
+            if (cand) {
+                ++nvalid;
+                double w[MW::W];
+                int n = 0;
+#pragma unroll
+                for (int kk = 0; kk < MW::W; ++kk) {
+                    const double u = win[cl][kk];
+                    if (!(u == u)) continue;  // outside the window
+                    int m = n++;
+                    while (m > 0 && w[m - 1] > u) {  // insertion sort, ascending
+                        w[m] = w[m - 1];
+                        --m;
+                    }
+                    w[m] = u;
+                }
+                const double med = w[(n - 1) / 2];
+                sel = med < ds;
+                if (sel) {
+                    ++nsel;
+                    const T phi = isinf(ds) ? T(0) : T(sqrt(med / ds));
+                    T f[Q], feq[Q], rho, ux, uy;
+                    load_candidate<Q, ST>(p, (int)j, f);
+                    moments<Q, T>(f, rho, ux, uy);
+                    equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
+                    const T om = T(2) * T(p.beta);
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        const T fl = feq[i] + phi * (f[i] - feq[i]);
+                        Fm[i] = fl + om * (feq[i] - fl);
+                    }
+                    conserve_mass<Q, T>(rho, Fm);
+                    if (single) {
+                        have = true;
+                        my_site = site;
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < Q; ++i) cf[(int64_t)i * p.cand_cap + j] = Fm[i];
+                    }
+                }
+            }
+            p.cand_sel[j] = sel ? 1 : 0;
+        }
+        __syncthreads();  // win is reused; every window of this CTA has been read
+    }
+    nvalid = __reduce_add_sync(0xffffffffu, nvalid);
+    nsel = __reduce_add_sync(0xffffffffu, nsel);
+    if ((threadIdx.x & 31) == 0) {
+        if (nvalid) atomicAdd(&p.counters[CNT_NVALID], nvalid);
+        if (nsel) atomicAdd(&p.stats[ST_LIMITED], (unsigned long long)nsel);
+    }
+    if (single) {
+        if (have) rewrite_site<Q, ST, ODD>(p, my_site, Fm);
+        return;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&p.counters[CNT_DONE], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (unsigned j = threadIdx.x; j < M; j += blockDim.x) {
+        if (!__ldcg(&p.cand_sel[j])) continue;
+        T F[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) F[i] = __ldcg(&cf[(int64_t)i * p.cand_cap + j]);
+        rewrite_site<Q, ST, ODD>(p, __ldcg(&p.cand_site[j]), F);
+    }
+    if (threadIdx.x == 0) p.counters[CNT_DONE] = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -1271,7 +1495,11 @@ cudaError_t launch_step_c(int coll, bool odd, const Params& p, cudaStream_t s) {
         case LBM_ELBM: return launch_step_q<Q, ST, LBM_ELBM>(odd, p, s);
         case LBM_EHRENFEST: return launch_step_q<Q, ST, LBM_EHRENFEST>(odd, p, s);
         case LBM_POSITIVITY: return launch_step_q<Q, ST, LBM_POSITIVITY>(odd, p, s);
-        case LBM_MEDIAN: return launch_step_q<Q, ST, LBM_MEDIAN>(odd, p, s);
+        case LBM_MEDIAN:
+            // without a Delta S field the median step is the Ehrenfest one
+            // (LBGK and the screen); median_recon_fixup does the rest
+            if (p.median_inv != 0.0) return launch_step_q<Q, ST, LBM_EHRENFEST>(odd, p, s);
+            return launch_step_q<Q, ST, LBM_MEDIAN>(odd, p, s);
         case LBM_MRT: return launch_step_q<Q, ST, LBM_MRT>(odd, p, s);
         case LBM_SMOOTH: return launch_step_q<Q, ST, LBM_SMOOTH>(odd, p, s);
         case LBM_DOUBLE_MONOTONIC: return launch_step_q<Q, ST, LBM_DOUBLE_MONOTONIC>(odd, p, s);
@@ -1290,6 +1518,9 @@ cudaError_t launch_fixup_q(int coll, bool odd, const Params& p, cudaStream_t s, 
     if (coll == LBM_EHRENFEST)
         return launch_p(odd ? ehrenfest_eval_select<Q, ST, true> : ehrenfest_eval_select<Q, ST, false>, nsm,
                         256, s, p);
+    if (coll == LBM_MEDIAN && p.median_inv != 0.0)
+        return launch_p(odd ? median_recon_fixup<Q, ST, true> : median_recon_fixup<Q, ST, false>, nsm, 1024, s,
+                        p);
     if (coll == LBM_MEDIAN)
         return launch_p(odd ? median_fixup<Q, ST, true> : median_fixup<Q, ST, false>, nsm, 256, s, p);
     if (coll == LBM_THRESHOLD)

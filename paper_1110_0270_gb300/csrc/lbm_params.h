@@ -75,6 +75,9 @@ struct Params {
     int* cand_site;                  // [cand_cap] y * nx + x
     int* cand_sel;                   // [cand_cap] selected flag (Ehrenfest/median)
     void* ds_field;                  // [ny][nx] arithmetic type (median only)
+    double median_inv;               // median filter: 1 / (1 - 2 beta) when the
+                                     // window's Delta S is taken from the
+                                     // post-collision state (no field); 0: field
     double* scratch_d;               // small FP64 reduction scratch
     int cslot;                       // candidate counter used by this step (t & 1)
     int pdl;                         // host side: launch the step kernels with

@@ -117,6 +117,44 @@ def test_limiters_fp32_one_step_and_selection_replay(case, collision):
         assert set(np.flatnonzero(mask).tolist()) == replay
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("collision", ["median", "ehrenfest", "mrt_limiter"])
+def test_few_candidates_match_oracle(collision, precision):
+    """A periodic fluid at rest with two hot sites: a handful of candidates
+    per step (the one-CTA paths of the median and selection kernels; with
+    k = 2 the selection ranks more candidates than it takes), then none."""
+    cfg = dict(CASES["periodic"], collision=collision, precision=precision, beta=0.97, delta=2e-4, topk=2)
+    ny, nx = cfg["ny"], cfg["nx"]
+    f0 = O.init_equilibrium(dict(cfg, collision="lbgk"), np.ones((ny, nx)), np.zeros((ny, nx)),
+                            np.zeros((ny, nx)))
+    f0 = f0 * WL.lognormal_factors(f0.shape, 4, 0.002)
+    rng = np.random.default_rng(1)
+    for y, x in [(5, 7), (11, 20)]:
+        f0[:, y, x] *= np.exp(0.3 * rng.standard_normal(9))
+    f0 = as_stored(cfg, f0)
+    g, lat = gpu_run(cfg, f0, 30)
+    f, st = O.step(cfg, f0, 30, stats=True)
+    assert rel(g, f) < TOL[precision], rel(g, f)
+    assert st["limited_sites"] > 0
+    assert lat.stats()["limited_total"] == st["limited_sites"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("beta", [0.52, 0.7])
+def test_median_window_sources_match_oracle(precision, beta):
+    """The median window's Delta S from the step's field (beta = 0.52, where
+    1 - 2 beta is too small to recover the pre-collision state) and from the
+    post-collision state (beta = 0.7), cavity with hot sites, 60 steps."""
+    cfg = dict(CASES["cavity"], collision="median", precision=precision, beta=beta, delta=2e-4)
+    f0 = as_stored(cfg, perturbed_state(cfg, 9, amp=0.01, hot=12))
+    g, lat = gpu_run(cfg, f0, 60)
+    f, st = O.step(cfg, f0, 60, stats=True)
+    assert rel(g, f) < TOL[precision], rel(g, f)
+    assert st["limited_sites"] > 0
+    if precision == "fp64":
+        assert lat.stats()["limited_total"] == st["limited_sites"]
+
+
 def test_cavity_from_rest_fp64_1000_steps_and_macros():
     cfg, init = WL.cavity(41, 400.0, 0.1)
     cfg.update(collision="lbgk", precision="fp64")
