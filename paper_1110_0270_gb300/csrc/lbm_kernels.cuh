@@ -1088,36 +1088,41 @@ __global__ void __launch_bounds__(256) median_fixup(Params p) {
 
 // Median filter, second kernel, without a Delta S field (FP32 and FP64
 // storage with |1 - 2 beta| >= 1/16): the step ran LBGK and the Ehrenfest
-// screen at every site, so each window value is the FP64 Delta S of the
-// pre-collision state recovered from the post-collision one (delta_s_lanes
-// with inv = 1 / (1 - 2 beta)); the candidate's own value comes from its
-// record.  Per round a CTA takes MedWin::C candidates, one 16-lane group
-// per window site; the first lane of the centre group takes the lower
-// median and, where the filter applies, the new post-collision populations.
-// They are written only after every window of the step has been read: by
-// the CTA itself when it holds all candidates, otherwise by the last CTA to
-// finish (ticket after a fence) from the candidate records they replace.
+// screen at every site, so a window site's pre-collision state is either
+// its record (a screened site) or is recovered from its post-collision one
+// (delta_s_lanes with inv = 1 / (1 - 2 beta)); its Delta S is FP64.  One
+// candidate per CTA and round (one 16-lane group per window site, so the
+// narrow FP64 pipe of several SMs shares the work); the first lane of the
+// centre group takes the lower median and the new populations.  With at
+// most kMedDirect screened sites every window site is looked up in the
+// list, no window reads a post-collision state that a rewrite changes, and
+// each CTA rewrites its candidate at once; with more, the windows are all
+// recovered from the lattice, and the rewrites wait for every window of
+// the step: the new populations go to the records and the last CTA to
+// finish (ticket after a fence) writes them.
 template <int Q>
 struct MedWin {
     static constexpr int W = Q == 9 ? 9 : 3;  // window sites
-    static constexpr int C = 64 / W;          // candidates per round of a 1024-thread CTA
     static constexpr int centre = W / 2;
 };
+constexpr unsigned kMedDirect = 64;
 
 template <int Q, class ST, bool ODD>
-__global__ void __launch_bounds__(1024, 1) median_recon_fixup(Params p) {
+__global__ void __launch_bounds__(256) median_recon_fixup(Params p) {
     pdl_enter();
     using T = typename ST::T;
     using L = Lat<Q>;
     using MW = MedWin<Q>;
-    __shared__ double win[MW::C][MW::W];
+    __shared__ double win[MW::W];
     __shared__ unsigned s_last;
     unsigned M = p.counters[p.cslot];
     if (M > (unsigned)p.cand_cap) M = (unsigned)p.cand_cap;
-    const bool single = M <= (unsigned)MW::C;
-    if (single && blockIdx.x != 0) return;
+    const bool direct = M <= kMedDirect;
     const int q = threadIdx.x & 15;
-    const unsigned g = threadIdx.x >> 4, cl = g / MW::W, k = g % MW::W;
+    const unsigned k = threadIdx.x >> 4;  // window site of this group
+    const unsigned gmask = 0xffffu << (threadIdx.x & 16);
+    // warps without a window site skip the FP64 work (both groups idle)
+    const bool warp_works = (threadIdx.x >> 5) * 2 < (unsigned)MW::W;
     const int dx = Q == 9 ? (int)(k % 3) - 1 : (int)k - 1, dy = Q == 9 ? (int)(k / 3) - 1 : 0;
     // the window is clipped to the fluid sites (all sites except the wall
     // sites of diffusive walls)
@@ -1125,42 +1130,51 @@ __global__ void __launch_bounds__(1024, 1) median_recon_fixup(Params p) {
     const typename ST::S* base = (const typename ST::S*)p.f;
     T* cf = (T*)p.cand_f;
     unsigned nvalid = 0, nsel = 0;
-    bool have = false;
-    int my_site = 0;
-    T Fm[Q];
-    for (unsigned b0 = blockIdx.x * MW::C; b0 < M; b0 += gridDim.x * MW::C) {
-        const unsigned j = b0 + cl;
-        const bool act = cl < (unsigned)MW::C && j < M;
-        int site = 0, xx = 0, yy = 0;
-        bool inw = false;
-        if (act) {
-            site = p.cand_site[j];
-            xx = site % p.nx + dx;
-            yy = site / p.nx + dy;
-            if (p.periodic_x) xx = xx < 0 ? xx + p.nx : (xx >= p.nx ? xx - p.nx : xx);
-            if (p.periodic_y) yy = yy < 0 ? yy + p.ny : (yy >= p.ny ? yy - p.ny : yy);
-            inw = xx >= lo && xx < hx && yy >= (Q == 9 ? lo : 0) && yy < (Q == 9 ? hy : p.ny);
-        }
-        const bool centre = k == (unsigned)MW::centre;
-        double v = 0.0;
-        if (act && inw && q < Q) {
-            if (centre) {
-                v = (double)cf[(int64_t)q * p.cand_cap + j];
-            } else {
-                // population q of the site's post-collision state, where the
-                // step stored it (store_general's addressing, lid term added back)
-                T lidc;
-                const int i = L::opp(q);
-                const int64_t r = aa_address<Q, T>(p, xx, yy, i, ODD, lidc);
-                v = (double)(ST::ld(base + r, T(L::w(i))) + lidc);
+    for (unsigned j = blockIdx.x; j < M; j += gridDim.x) {
+        if (warp_works) {
+            const bool act = k < (unsigned)MW::W;
+            const bool centre = k == (unsigned)MW::centre;
+            int xx = 0, yy = 0;
+            bool inw = false;
+            if (act) {
+                const int site = p.cand_site[j];
+                xx = site % p.nx + dx;
+                yy = site / p.nx + dy;
+                if (p.periodic_x) xx = xx < 0 ? xx + p.nx : (xx >= p.nx ? xx - p.nx : xx);
+                if (p.periodic_y) yy = yy < 0 ? yy + p.ny : (yy >= p.ny ? yy - p.ny : yy);
+                inw = xx >= lo && xx < hx && yy >= (Q == 9 ? lo : 0) && yy < (Q == 9 ? hy : p.ny);
             }
+            // the record of the window site, if it has one (direct mode)
+            int rec = centre ? (int)j : -1;
+            if (direct && act && inw && !centre) {
+                const int want = yy * p.nx + xx;
+                int found = -1;
+                for (unsigned i = q; i < M; i += 16)
+                    if (p.cand_site[i] == want) found = (int)i;
+                const unsigned hit = __ballot_sync(gmask, found >= 0) & gmask;
+                if (hit) rec = __shfl_sync(gmask, found, __ffs(hit) - 1);
+            }
+            double v = 0.0;
+            if (act && inw && q < Q) {
+                if (rec >= 0) {
+                    v = (double)cf[(int64_t)q * p.cand_cap + rec];
+                } else {
+                    // population q of the site's post-collision state, where the
+                    // step stored it (store_general's addressing, lid term added back)
+                    T lidc;
+                    const int i = L::opp(q);
+                    const int64_t r = aa_address<Q, T>(p, xx, yy, i, ODD, lidc);
+                    v = (double)(ST::ld(base + r, T(L::w(i))) + lidc);
+                }
+            }
+            const double ds = delta_s_lanes<Q>(p, v, act && inw, rec >= 0 ? 0.0 : p.median_inv);
+            if (q == 0 && act) win[k] = inw ? ds : __longlong_as_double(0x7ff8000000000000LL);
         }
-        const double ds = delta_s_lanes<Q>(p, v, act && inw, centre ? 0.0 : p.median_inv);
-        if (q == 0 && cl < (unsigned)MW::C) win[cl][k] = act && inw ? ds : __longlong_as_double(0x7ff8000000000000LL);
         __syncthreads();
-        if (act && centre && q == 0) {
-            const bool cand = ds > p.delta;
-            p.cand_ds[j] = cand ? ds : -1.0;
+        if (threadIdx.x == 16 * MW::centre) {
+            const double c = win[MW::centre];
+            const bool cand = c > p.delta;
+            p.cand_ds[j] = cand ? c : -1.0;
             bool sel = false;
             if (cand) {
                 ++nvalid;
@@ -1168,7 +1182,7 @@ __global__ void __launch_bounds__(1024, 1) median_recon_fixup(Params p) {
                 int n = 0;
 #pragma unroll
                 for (int kk = 0; kk < MW::W; ++kk) {
-                    const double u = win[cl][kk];
+                    const double u = win[kk];
                     if (!(u == u)) continue;  // outside the window
                     int m = n++;
                     while (m > 0 && w[m - 1] > u) {  // insertion sort, ascending
@@ -1178,11 +1192,11 @@ __global__ void __launch_bounds__(1024, 1) median_recon_fixup(Params p) {
                     w[m] = u;
                 }
                 const double med = w[(n - 1) / 2];
-                sel = med < ds;
+                sel = med < c;
                 if (sel) {
                     ++nsel;
-                    const T phi = isinf(ds) ? T(0) : T(sqrt(med / ds));
-                    T f[Q], feq[Q], rho, ux, uy;
+                    const T phi = isinf(c) ? T(0) : T(sqrt(med / c));
+                    T f[Q], feq[Q], F[Q], rho, ux, uy;
                     load_candidate<Q, ST>(p, (int)j, f);
                     moments<Q, T>(f, rho, ux, uy);
                     equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
@@ -1190,32 +1204,26 @@ __global__ void __launch_bounds__(1024, 1) median_recon_fixup(Params p) {
 #pragma unroll
                     for (int i = 0; i < Q; ++i) {
                         const T fl = feq[i] + phi * (f[i] - feq[i]);
-                        Fm[i] = fl + om * (feq[i] - fl);
+                        F[i] = fl + om * (feq[i] - fl);
                     }
-                    conserve_mass<Q, T>(rho, Fm);
-                    if (single) {
-                        have = true;
-                        my_site = site;
+                    conserve_mass<Q, T>(rho, F);
+                    if (direct) {
+                        rewrite_site<Q, ST, ODD>(p, p.cand_site[j], F);
                     } else {
 #pragma unroll
-                        for (int i = 0; i < Q; ++i) cf[(int64_t)i * p.cand_cap + j] = Fm[i];
+                        for (int i = 0; i < Q; ++i) cf[(int64_t)i * p.cand_cap + j] = F[i];
                     }
                 }
             }
             p.cand_sel[j] = sel ? 1 : 0;
         }
-        __syncthreads();  // win is reused; every window of this CTA has been read
+        __syncthreads();  // win is reused
     }
-    nvalid = __reduce_add_sync(0xffffffffu, nvalid);
-    nsel = __reduce_add_sync(0xffffffffu, nsel);
-    if ((threadIdx.x & 31) == 0) {
+    if (threadIdx.x == 16 * MW::centre) {
         if (nvalid) atomicAdd(&p.counters[CNT_NVALID], nvalid);
         if (nsel) atomicAdd(&p.stats[ST_LIMITED], (unsigned long long)nsel);
     }
-    if (single) {
-        if (have) rewrite_site<Q, ST, ODD>(p, my_site, Fm);
-        return;
-    }
+    if (direct) return;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) s_last = atomicAdd(&p.counters[CNT_DONE], 1u) == gridDim.x - 1;
@@ -1519,8 +1527,7 @@ cudaError_t launch_fixup_q(int coll, bool odd, const Params& p, cudaStream_t s, 
         return launch_p(odd ? ehrenfest_eval_select<Q, ST, true> : ehrenfest_eval_select<Q, ST, false>, nsm,
                         256, s, p);
     if (coll == LBM_MEDIAN && p.median_inv != 0.0)
-        return launch_p(odd ? median_recon_fixup<Q, ST, true> : median_recon_fixup<Q, ST, false>, nsm, 1024, s,
-                        p);
+        return launch_p(odd ? median_recon_fixup<Q, ST, true> : median_recon_fixup<Q, ST, false>, nsm, 256, s, p);
     if (coll == LBM_MEDIAN)
         return launch_p(odd ? median_fixup<Q, ST, true> : median_fixup<Q, ST, false>, nsm, 256, s, p);
     if (coll == LBM_THRESHOLD)
