@@ -626,7 +626,13 @@ lbm_status lbm_last_candidates(lbm_ctx* ctx, double* ds, int32_t* site, int32_t*
     LBM_CK(ctx, cudaMemcpyAsync(&n, ctx->p.counters + ((ctx->t - 1) & 1), sizeof n, cudaMemcpyDeviceToHost, S(stream)));
     LBM_CK(ctx, cudaStreamSynchronize(S(stream)));
     if (n > (unsigned)ctx->p.cand_cap) n = (unsigned)ctx->p.cand_cap;
-    // screened sites; the candidates are those with Delta S > delta
+    // the FP64 Delta S of every screened site (the step's selection may have
+    // settled them in FP32); the candidates are those with Delta S > delta
+    {
+        const Params& p = ctx->p;
+        const int Q = ctx->Q;
+        LBM_CK(ctx, dispatch(ctx->cfg.precision, [&](auto L) { return decltype(L)::cand_eval(Q, p, n, S(stream)); }));
+    }
     std::vector<double> hds(n);
     std::vector<int32_t> hsite(n), hsel(n);
     if (n) {

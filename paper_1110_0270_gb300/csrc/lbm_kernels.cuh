@@ -50,6 +50,25 @@ struct Pops {
     T v[Q];
 };
 
+// The side of delta a screened site's Delta S is on, where FP32 arithmetic
+// settles it: the site's FP32 Delta S (delta_s_and_q, the median screen's
+// evaluation) lies within 1e-3 relative plus 1e-6 sqrt(q rho) of the exact
+// value (the bound the screens use), so 1 = certainly above delta, 0 =
+// certainly not, 2 = too close (or non-finite): the FP64 value decides.
+// Used by the selection kernel on the recorded populations.
+template <int Q>
+__device__ __forceinline__ int certify_side(const Params& p, const float* f, float& ds) {
+    float rho, ux, uy, feq[Q], q;
+    moments<Q, float>(f, rho, ux, uy);
+    equilibrium<Q, float>(p.eq, rho, ux, uy, feq);
+    ds = delta_s_and_q<Q, float>(f, feq, q);
+    if (!(ds < INFINITY)) return 2;
+    const float s = 1e-6f * sqrtf(fabsf(q * rho));
+    if ((double)(0.999f * ds - s) > p.delta) return 1;
+    if ((double)(1.001f * ds + s) <= p.delta) return 0;
+    return 2;
+}
+
 // Out of line: the call is rare, and its address arithmetic and stores stay
 // out of the streaming path's register allocation.
 template <int Q, class T>
@@ -843,13 +862,58 @@ __device__ __forceinline__ void eval_then_select(const Params& p) {
         __shared__ int s_site[16];
         __shared__ unsigned s_nsel;
         const unsigned j = threadIdx.x >> 4;
+        const bool lead = j < M && (threadIdx.x & 15) == 0;
         if (threadIdx.x == 0) {
             s_last = 0;
             s_nsel = 0;
         }
+        if constexpr (COLL != LBM_THRESHOLD && sizeof(typename ST::T) == 4) {
+            // every screened site certainly on one side of delta in FP32 and
+            // no more candidates than k: all of them are taken, no FP64
+            using T = typename ST::T;
+            T f[Q];
+            float ds32 = 0.f;
+            int side = 0;
+            if (lead) {
+                load_candidate<Q, ST>(p, (int)j, f);
+                side = certify_side<Q>(p, f, ds32);
+            }
+            const int unsure = __syncthreads_or(lead && side == 2);
+            const unsigned ncert = (unsigned)__syncthreads_count(lead && side == 1);
+            const unsigned K = p.topk > 0 ? (unsigned)p.topk : 0u;
+            if (!unsure && ncert <= K) {
+                if (lead) {
+                    const bool sel = side == 1;
+                    p.cand_sel[j] = sel ? 1 : 0;
+                    // the FP32 value of a selected site (lbm_last_candidates
+                    // recomputes FP64 values)
+                    p.cand_ds[j] = sel ? (double)ds32 : -1.0;
+                    if (sel) {
+                        T feq[Q], rho, ux, uy;
+                        moments<Q, T>(f, rho, ux, uy);
+                        equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
+                        const int site = p.cand_site[j];
+                        if constexpr (COLL == LBM_MRT_LIMITER && Q == 9) {
+                            T F[Q];
+                            mrt2_d2q9<T>(f, feq, T(2) * T(p.beta_f), F);
+                            conserve_mass<Q, T>(rho, F);
+                            rewrite_site<Q, ST, ODD>(p, site, F);
+                        } else {
+                            conserve_mass<Q, T>(rho, feq);
+                            rewrite_site<Q, ST, ODD>(p, site, feq);
+                        }
+                    }
+                }
+                if (threadIdx.x == 0) {
+                    p.counters[CNT_NVALID] = ncert;
+                    p.counters[CNT_NSEL] = ncert;
+                    if (ncert) atomicAdd(&p.stats[ST_LIMITED], (unsigned long long)ncert);
+                }
+                return;
+            }
+        }
         __syncthreads();
         const double d = delta_s_group<Q, ST>(p, j, j < M);
-        const bool lead = j < M && (threadIdx.x & 15) == 0;
         const bool c = lead && d > p.delta;
         int site = 0;
         if (lead) {
@@ -1240,6 +1304,19 @@ __global__ void __launch_bounds__(256) median_recon_fixup(Params p) {
     if (threadIdx.x == 0) p.counters[CNT_DONE] = 0u;
 }
 
+// FP64 Delta S of the n records of the last step's list, for
+// lbm_last_candidates (the selection may have settled its sites in FP32).
+template <int Q, class ST>
+__global__ void __launch_bounds__(256) cand_eval_kernel(Params p, unsigned n) {
+    const unsigned groups = gridDim.x * (blockDim.x >> 4);
+    const unsigned g0 = blockIdx.x * (blockDim.x >> 4) + (threadIdx.x >> 4);
+    for (unsigned base = 0; base < n; base += groups) {
+        const unsigned j = base + g0;
+        const double d = delta_s_group<Q, ST>(p, j, j < n);
+        if (j < n && (threadIdx.x & 15) == 0) p.cand_ds[j] = d;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // State transfer, macroscopic fields and entropy.
 // ---------------------------------------------------------------------------
@@ -1435,6 +1512,7 @@ struct Launch {
                               cudaStream_t s);
     static cudaError_t entropy(int Q, const Params& p, double* H, double* dS, bool odd, int eqkind,
                                cudaStream_t s);
+    static cudaError_t cand_eval(int Q, const Params& p, unsigned n, cudaStream_t s);
 };
 
 inline cudaError_t launch_p(void (*k)(Params, int), dim3 g, dim3 b, cudaStream_t s, const Params& p, int a) {
@@ -1556,6 +1634,17 @@ cudaError_t Launch<ST>::walls(bool odd, const Params& p, cudaStream_t s) {
     const int n = 2 * p.nx + 2 * (p.ny - 2);
     return launch_p(odd ? diffusive_wall_kernel<ST, true> : diffusive_wall_kernel<ST, false>,
                     dim3((n + 255) / 256), dim3(256), s, p);
+}
+
+template <class ST>
+cudaError_t Launch<ST>::cand_eval(int Q, const Params& p, unsigned n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const unsigned g = (n + 15) / 16 < 1024u ? (n + 15) / 16 : 1024u;
+    if (Q == 3)
+        cand_eval_kernel<3, ST><<<g, 256, 0, s>>>(p, n);
+    else
+        cand_eval_kernel<9, ST><<<g, 256, 0, s>>>(p, n);
+    return cudaGetLastError();
 }
 
 template <class ST>

@@ -118,12 +118,16 @@ def test_limiters_fp32_one_step_and_selection_replay(case, collision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("collision", ["median", "ehrenfest", "mrt_limiter"])
-def test_few_candidates_match_oracle(collision, precision):
+@pytest.mark.parametrize("collision,topk", [("median", 2), ("ehrenfest", 2), ("ehrenfest", 8),
+                                            ("mrt_limiter", 2), ("mrt_limiter", 16)])
+def test_few_candidates_match_oracle(collision, topk, precision):
     """A periodic fluid at rest with two hot sites: a handful of candidates
     per step (the one-CTA paths of the median and selection kernels; with
-    k = 2 the selection ranks more candidates than it takes), then none."""
-    cfg = dict(CASES["periodic"], collision=collision, precision=precision, beta=0.97, delta=2e-4, topk=2)
+    k = 2 the selection ranks more candidates than it takes, with k >= the
+    count it takes them all, in FP32 without an FP64 evaluation when FP32
+    settles every site's side of delta), then none.  The candidates the
+    ABI reports after one step carry FP64 values either way."""
+    cfg = dict(CASES["periodic"], collision=collision, precision=precision, beta=0.97, delta=2e-4, topk=topk)
     ny, nx = cfg["ny"], cfg["nx"]
     f0 = O.init_equilibrium(dict(cfg, collision="lbgk"), np.ones((ny, nx)), np.zeros((ny, nx)),
                             np.zeros((ny, nx)))
@@ -137,6 +141,14 @@ def test_few_candidates_match_oracle(collision, precision):
     assert rel(g, f) < TOL[precision], rel(g, f)
     assert st["limited_sites"] > 0
     assert lat.stats()["limited_total"] == st["limited_sites"]
+    f1 = O.step(cfg, f0, 1)
+    g1, lat1 = gpu_run(cfg, f0, 1)
+    assert rel(g1, f1) < TOL[precision]
+    ds, site, sel = lat1.last_candidates()
+    dS_or = O.delta_s_field(cfg, f0).ravel()
+    assert sorted(site.tolist()) == np.flatnonzero(dS_or > cfg["delta"]).tolist()
+    assert np.allclose(ds, dS_or[site], rtol=1e-13, atol=0)
+    assert lat1.stats()["candidates_last"] == len(site)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
