@@ -726,10 +726,36 @@ __device__ void ehrenfest_select_apply(const Params& p, unsigned M, unsigned nva
     __shared__ unsigned long long s_prefix, s_mask;
     __shared__ unsigned s_rem;
     __shared__ unsigned s_count;
+    __shared__ int s_ties_all;
     const int tid = threadIdx.x;
     const unsigned K = p.topk > 0 ? (unsigned)p.topk : 0u;
     // candidates: screened sites whose FP64 Delta S exceeds delta (the others
-    // carry -1); their keys are positive doubles
+    // carry -1); their keys are positive doubles.  Up to kCache per thread
+    // are held in registers across the radix passes (else re-read per pass).
+    constexpr int kCache = 4;
+    const bool cached = M <= kCache * blockDim.x;
+    double kds[kCache];
+    unsigned ksite[kCache];
+#pragma unroll
+    for (int i = 0; i < kCache; ++i) {
+        const unsigned j = tid + i * blockDim.x;
+        const bool in = cached && j < M;
+        kds[i] = in ? __ldcg(&p.cand_ds[j]) : -1.0;
+        ksite[i] = in ? (unsigned)__ldcg(&p.cand_site[j]) : 0u;
+    }
+    // visits (ds, site) of every record this thread owns
+    auto each = [&](auto&& fn) {
+        if (cached) {
+#pragma unroll
+            for (int i = 0; i < kCache; ++i) {
+                const unsigned j = tid + i * blockDim.x;
+                if (j < M) fn(j, kds[i], ksite[i]);
+            }
+        } else {
+            for (unsigned j = tid; j < M; j += blockDim.x)
+                fn(j, __ldcg(&p.cand_ds[j]), (unsigned)__ldcg(&p.cand_site[j]));
+        }
+    };
     if (tid == 0) s_count = 0;
     const bool all = nvalid <= K;
     unsigned long long tkey = 0;
@@ -740,17 +766,17 @@ __device__ void ehrenfest_select_apply(const Params& p, unsigned M, unsigned nva
             s_prefix = 0;
             s_mask = 0;
             s_rem = K;
+            s_ties_all = 0;
         }
         __syncthreads();
         for (int shift = 56; shift >= 0; shift -= 8) {
             for (int d = tid; d < 256; d += blockDim.x) hist[d] = 0;
             __syncthreads();
             const unsigned long long pre = s_prefix, msk = s_mask;
-            for (unsigned j = tid; j < M; j += blockDim.x) {
-                const double ds = __ldcg(&p.cand_ds[j]);
-                unsigned long long key = (unsigned long long)__double_as_longlong(ds);
+            each([&](unsigned, double ds, unsigned) {
+                const unsigned long long key = (unsigned long long)__double_as_longlong(ds);
                 if (ds > p.delta && (key & msk) == pre) atomicAdd(&hist[(key >> shift) & 255ull], 1u);
-            }
+            });
             __syncthreads();
             if (tid < 32) {
                 unsigned rem = s_rem;
@@ -759,54 +785,55 @@ __device__ void ehrenfest_select_apply(const Params& p, unsigned M, unsigned nva
                     s_rem = rem;
                     s_prefix = pre | ((unsigned long long)d << shift);
                     s_mask = msk | (255ull << shift);
+                    // the last bin holds the keys equal to the K-th: all taken?
+                    if (shift == 0) s_ties_all = hist[d] == rem;
                 }
             }
             __syncthreads();
         }
         tkey = s_prefix;
+        const bool ties_all = s_ties_all;
         __syncthreads();  // every thread has read the threshold before it is reused
-        // among keys equal to the threshold, take the s_rem smallest sites
-        if (tid == 0) {
-            s_prefix = 0;
-            s_mask = 0;
-        }
-        __syncthreads();
-        for (int shift = 24; shift >= 0; shift -= 8) {
-            for (int d = tid; d < 256; d += blockDim.x) hist[d] = 0;
-            __syncthreads();
-            const unsigned pre = (unsigned)s_prefix, msk = (unsigned)s_mask;
-            for (unsigned j = tid; j < M; j += blockDim.x) {
-                const double ds = __ldcg(&p.cand_ds[j]);
-                unsigned long long key = (unsigned long long)__double_as_longlong(ds);
-                unsigned site = (unsigned)p.cand_site[j];
-                if (ds > p.delta && key == tkey && (site & msk) == pre)
-                    atomicAdd(&hist[(site >> shift) & 255u], 1u);
+        if (!ties_all) {
+            // among keys equal to the threshold, take the s_rem smallest sites
+            if (tid == 0) {
+                s_prefix = 0;
+                s_mask = 0;
             }
             __syncthreads();
-            if (tid < 32) {
-                unsigned rem = s_rem;
-                const int d = pick_digit(hist, rem, false);
-                if (tid == 0) {
-                    s_rem = rem;
-                    s_prefix = pre | ((unsigned)d << shift);
-                    s_mask = msk | (255u << shift);
+            for (int shift = 24; shift >= 0; shift -= 8) {
+                for (int d = tid; d < 256; d += blockDim.x) hist[d] = 0;
+                __syncthreads();
+                const unsigned pre = (unsigned)s_prefix, msk = (unsigned)s_mask;
+                each([&](unsigned, double ds, unsigned site) {
+                    const unsigned long long key = (unsigned long long)__double_as_longlong(ds);
+                    if (ds > p.delta && key == tkey && (site & msk) == pre)
+                        atomicAdd(&hist[(site >> shift) & 255u], 1u);
+                });
+                __syncthreads();
+                if (tid < 32) {
+                    unsigned rem = s_rem;
+                    const int d = pick_digit(hist, rem, false);
+                    if (tid == 0) {
+                        s_rem = rem;
+                        s_prefix = pre | ((unsigned)d << shift);
+                        s_mask = msk | (255u << shift);
+                    }
                 }
+                __syncthreads();
             }
-            __syncthreads();
+            icut = (unsigned)s_prefix;
         }
-        icut = (unsigned)s_prefix;
     }
     __syncthreads();
     unsigned mine = 0;
-    for (unsigned j = tid; j < M; j += blockDim.x) {
+    each([&](unsigned j, double ds, unsigned site) {
         bool sel = false;
-        const double ds = __ldcg(&p.cand_ds[j]);
         if (K > 0 && ds > p.delta) {
             if (all) {
                 sel = true;
             } else {
-                unsigned long long key = (unsigned long long)__double_as_longlong(ds);
-                unsigned site = (unsigned)p.cand_site[j];
+                const unsigned long long key = (unsigned long long)__double_as_longlong(ds);
                 sel = key > tkey || (key == tkey && site <= icut);
             }
         }
@@ -821,14 +848,14 @@ __device__ void ehrenfest_select_apply(const Params& p, unsigned M, unsigned nva
                 T F[Q];
                 mrt2_d2q9<T>(f, feq, sizeof(T) == 8 ? T(2.0 * p.beta) : T(2) * T(p.beta_f), F);
                 conserve_mass<Q, T>(rho, F);
-                rewrite_site<Q, ST, ODD>(p, p.cand_site[j], F);
+                rewrite_site<Q, ST, ODD>(p, (int)site, F);
             } else {
                 conserve_mass<Q, T>(rho, feq);
-                rewrite_site<Q, ST, ODD>(p, p.cand_site[j], feq);
+                rewrite_site<Q, ST, ODD>(p, (int)site, feq);
             }
             ++mine;
         }
-    }
+    });
     if (mine) atomicAdd(&s_count, mine);
     __syncthreads();
     if (tid == 0) {
@@ -1162,8 +1189,26 @@ __global__ void __launch_bounds__(256) median_fixup(Params p) {
 // list, no window reads a post-collision state that a rewrite changes, and
 // each CTA rewrites its candidate at once; with more, the windows are all
 // recovered from the lattice, and the rewrites wait for every window of
-// the step: the new populations go to the records and the last CTA to
-// finish (ticket after a fence) writes them.
+// the step: each selected site's coefficient goes to its record and the
+// last CTA to finish (ticket after a fence) writes the new populations.
+// The post-collision state of median candidate j whose pre-collision state
+// gets the homothety with coefficient phi before the LBGK collision.
+template <int Q, class ST>
+__device__ __forceinline__ void median_homothety(const Params& p, int j, typename ST::T phi, typename ST::T* F) {
+    using T = typename ST::T;
+    T f[Q], feq[Q], rho, ux, uy;
+    load_candidate<Q, ST>(p, j, f);
+    moments<Q, T>(f, rho, ux, uy);
+    equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
+    const T om = T(2) * T(p.beta);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const T fl = feq[i] + phi * (f[i] - feq[i]);
+        F[i] = fl + om * (feq[i] - fl);
+    }
+    conserve_mass<Q, T>(rho, F);
+}
+
 template <int Q>
 struct MedWin {
     static constexpr int W = Q == 9 ? 9 : 3;  // window sites
@@ -1260,22 +1305,12 @@ __global__ void __launch_bounds__(256) median_recon_fixup(Params p) {
                 if (sel) {
                     ++nsel;
                     const T phi = isinf(c) ? T(0) : T(sqrt(med / c));
-                    T f[Q], feq[Q], F[Q], rho, ux, uy;
-                    load_candidate<Q, ST>(p, (int)j, f);
-                    moments<Q, T>(f, rho, ux, uy);
-                    equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
-                    const T om = T(2) * T(p.beta);
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) {
-                        const T fl = feq[i] + phi * (f[i] - feq[i]);
-                        F[i] = fl + om * (feq[i] - fl);
-                    }
-                    conserve_mass<Q, T>(rho, F);
                     if (direct) {
+                        T F[Q];
+                        median_homothety<Q, ST>(p, (int)j, phi, F);
                         rewrite_site<Q, ST, ODD>(p, p.cand_site[j], F);
                     } else {
-#pragma unroll
-                        for (int i = 0; i < Q; ++i) cf[(int64_t)i * p.cand_cap + j] = F[i];
+                        p.cand_ds[j] = (double)phi;  // for the last CTA (lbm_last_candidates recomputes Delta S)
                     }
                 }
             }
@@ -1297,9 +1332,8 @@ __global__ void __launch_bounds__(256) median_recon_fixup(Params p) {
     for (unsigned j = threadIdx.x; j < M; j += blockDim.x) {
         if (!__ldcg(&p.cand_sel[j])) continue;
         T F[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) F[i] = __ldcg(&cf[(int64_t)i * p.cand_cap + j]);
-        rewrite_site<Q, ST, ODD>(p, __ldcg(&p.cand_site[j]), F);
+        median_homothety<Q, ST>(p, (int)j, (T)__ldcg(&p.cand_ds[j]), F);
+        rewrite_site<Q, ST, ODD>(p, p.cand_site[j], F);
     }
     if (threadIdx.x == 0) p.counters[CNT_DONE] = 0u;
 }
