@@ -703,7 +703,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--side", type=int, default=N_SIDE)
     ap.add_argument("--collision", default="ehrenfest",
-                    choices=["lbgk", "elbm", "ehrenfest", "positivity", "median", "mrt"])
+                    choices=["lbgk", "elbm", "ehrenfest", "positivity", "median", "mrt", "smooth",
+                             "double_monotonic", "ensemble", "threshold", "mrt2", "mrt_limiter"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16_dev", "bf16_dev"])
     ap.add_argument("--variant-steps", type=int, default=100)
     ap.add_argument("--no-variants", action="store_true")
