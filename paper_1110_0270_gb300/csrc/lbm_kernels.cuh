@@ -156,14 +156,14 @@ __device__ __forceinline__ void collide_site(const Params& p, int x, int y, cons
         } else if (!(ds < T(INFINITY))) {
             phi = T(0);  // a negative population: the state goes to f*
         } else if (COLL == LBM_SMOOTH) {
-            phi = T(1) / (T(1) + T(p.lim_alpha) * pow(ds, T(p.lim_k)));
+            phi = T(1) / (T(1) + T(p.lim_alpha) * pow_lim(ds, T(p.lim_k)));
         } else if (COLL == LBM_DOUBLE_MONOTONIC) {
-            phi = pow(T(1) + pow(ds / T(p.lim_dst), T(p.lim_k)), T(-0.5) / T(p.lim_k));
+            phi = pow_lim(T(1) + pow_lim(ds / T(p.lim_dst), T(p.lim_k)), T(-0.5) / T(p.lim_k));
         } else {  // LBM_ENSEMBLE, E from this step's pre-pass
             const T E = T(*p.lim_E);
             if (E > T(0)) {
                 const T yv = ds / (T(p.lim_alpha) * E);
-                phi = (T(1) + pow(yv, T(p.lim_k) - T(0.5))) / (T(1) + pow(yv, T(p.lim_k)));
+                phi = (T(1) + pow_lim(yv, T(p.lim_k) - T(0.5))) / (T(1) + pow_lim(yv, T(p.lim_k)));
             }
         }
         const T c = (T(1) - (sizeof(T) == 8 ? T(2.0 * p.beta) : T(2) * T(p.beta_f))) * phi;
@@ -1057,9 +1057,17 @@ __global__ void __launch_bounds__(256) ensemble_mean(Params p) {
     // few ticket atomics)
     const int t = threadIdx.x, nt = blockDim.x;
     const int tpr = (p.nx + nt - 1) / nt;
+    // tile = y * tpr + seg, advanced by gridDim.x without a division per tile
+    const int dy = gridDim.x / tpr, dseg = gridDim.x - dy * tpr;
+    int y = blockIdx.x / tpr, seg = blockIdx.x - y * tpr;
     T sum = 0, cnt = 0;
-    for (int tile = blockIdx.x; tile < tpr * p.ny; tile += gridDim.x) {
-        const int y = tile / tpr, x = (tile - y * tpr) * nt + t;
+    for (; y < p.ny; y += dy, seg += dseg) {
+        if (seg >= tpr) {
+            seg -= tpr;
+            ++y;
+            if (y >= p.ny) break;
+        }
+        const int x = seg * nt + t;
         if (x >= p.nx) continue;
         T f[Q], feq[Q], rho, ux, uy, q;
         const bool interior = x > 0 && x < p.nx - 1 && (Q == 3 || (y > 0 && y < p.ny - 1));
