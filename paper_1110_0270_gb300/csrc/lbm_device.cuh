@@ -538,15 +538,15 @@ __device__ __forceinline__ void gl_series(double x, double& g, double& l) {
 }
 
 template <int Q, int KG, int KL>
-__device__ __forceinline__ void elbm_sum(const double* feq, const double* D, const double* gm,
-                                         const float* Df, const float* gf, double a, double& s0,
-                                         double& s1, float& s2) {
+__device__ __forceinline__ void elbm_sum(const double* feq, const double* D, const double* R,
+                                         const double* gm, const float* Df, const float* gf, double a,
+                                         double& s0, double& s1, float& s2) {
     double A = 0.0, B = 0.0;
     float C = 0.f;
     const float af = (float)a;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const double x = (a - 1.0) * (D[i] / feq[i]);
+        const double x = (a - 1.0) * R[i];  // R = Delta / f*, once per site
         double g, l;
         if (KG > 0) {
             gl_series<KG, KL>(x, g, l);
@@ -568,20 +568,20 @@ __device__ __forceinline__ void elbm_sum(const double* feq, const double* D, con
 
 // S_f(alpha), S_f'(alpha) (FP64) and S_f''(alpha) (FP32) at one site.
 template <int Q>
-__device__ __forceinline__ void elbm_eval(const double* f, const double* feq, const double* D,
+__device__ __forceinline__ void elbm_eval(const double* feq, const double* D, const double* R,
                                           const double* gm, const float* Df, const float* gf,
                                           double amax_d, double a, double& s0, double& s1,
                                           double& s2) {
     const double ax = fabs(a - 1.0) * amax_d;  // max |x_i| at this alpha
     float c;
     if (ax < 0.015625)
-        elbm_sum<Q, 8, 9>(feq, D, gm, Df, gf, a, s0, s1, c);
+        elbm_sum<Q, 8, 9>(feq, D, R, gm, Df, gf, a, s0, s1, c);
     else if (ax < 0.125)
-        elbm_sum<Q, 16, 18>(feq, D, gm, Df, gf, a, s0, s1, c);
+        elbm_sum<Q, 16, 18>(feq, D, R, gm, Df, gf, a, s0, s1, c);
     else if (ax < 0.25)
-        elbm_sum<Q, 26, 27>(feq, D, gm, Df, gf, a, s0, s1, c);
+        elbm_sum<Q, 26, 27>(feq, D, R, gm, Df, gf, a, s0, s1, c);
     else
-        elbm_sum<Q, 0, 0>(feq, D, gm, Df, gf, a, s0, s1, c);
+        elbm_sum<Q, 0, 0>(feq, D, R, gm, Df, gf, a, s0, s1, c);
     s2 = (double)c;
 }
 
@@ -605,7 +605,7 @@ template <int Q>
 __device__ ElbmOut elbm_alpha(const double* f, const double* feq, double rho, const Params& p) {
     ElbmOut o;
     o.iters = 0;
-    double D[Q], gm[Q];
+    double D[Q], R[Q], gm[Q];
     float Df[Q], gf[Q];
     double dS = 0.0, amax = __longlong_as_double(0x7ff0000000000000ULL), dmax = 0.0;
     bool neg = false;
@@ -613,6 +613,7 @@ __device__ ElbmOut elbm_alpha(const double* f, const double* feq, double rho, co
     for (int i = 0; i < Q; ++i) {
         D[i] = feq[i] - f[i];
         const double d = D[i] / feq[i];
+        R[i] = d;
         dmax = fmax(dmax, fabs(d));
         gm[i] = gfun_d(-d);
         dS += feq[i] * gm[i];
@@ -639,7 +640,7 @@ __device__ ElbmOut elbm_alpha(const double* f, const double* feq, double rho, co
     double lo = 1.0, hi = amax;
     double a = (2.0 < amax) ? 2.0 : 0.5 * (1.0 + amax);
     double s0, s1, s2;
-    elbm_eval<Q>(f, feq, D, gm, Df, gf, dmax, a, s0, s1, s2);
+    elbm_eval<Q>(feq, D, R, gm, Df, gf, dmax, a, s0, s1, s2);
     if (s0 > 0.0) {
         // S_f is concave in alpha, so it lies below its tangent at a: if the
         // tangent reaches zero before alpha_max, so does S_f (a root exists
@@ -647,7 +648,7 @@ __device__ ElbmOut elbm_alpha(const double* f, const double* feq, double rho, co
         const double at = a - s0 / s1;
         if (!(s1 < 0.0 && at < amax)) {
             double m0, m1, m2;
-            elbm_eval<Q>(f, feq, D, gm, Df, gf, dmax, amax, m0, m1, m2);
+            elbm_eval<Q>(feq, D, R, gm, Df, gf, dmax, amax, m0, m1, m2);
             if (m0 > 0.0) {
                 o.alpha = fb;
                 o.code = 2;
@@ -673,7 +674,7 @@ __device__ ElbmOut elbm_alpha(const double* f, const double* feq, double rho, co
         }
         if (!(next > lo && next < hi)) next = 0.5 * (lo + hi);
         a = next;
-        elbm_eval<Q>(f, feq, D, gm, Df, gf, dmax, a, s0, s1, s2);
+        elbm_eval<Q>(feq, D, R, gm, Df, gf, dmax, a, s0, s1, s2);
         if (s0 > 0.0)
             lo = a;
         else
