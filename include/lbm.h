@@ -244,12 +244,15 @@ lbm_status lbm_probe_count(lbm_ctx* ctx, uint64_t* count, void* stream);
 /* Copies the step counters into *out (synchronises `stream`). */
 lbm_status lbm_stats_get(lbm_ctx* ctx, lbm_stats* out, void* stream);
 
-/* Limiter candidates of the most recent step (EHRENFEST and MEDIAN only),
- * i.e. the sites whose FP64 Delta S exceeds delta: up to `cap` entries of
- * (Delta S, linear site index y*nx + x, selected flag) into HOST arrays
- * (any may be NULL); *count receives the number of candidates.  Synchronises
- * `stream`.  The candidate order is arbitrary.  Uses a host buffer of one
- * entry per screened site. */
+/* Limiter candidates of the most recent step (the collisions with a
+ * candidate list: EHRENFEST, MEDIAN, THRESHOLD, MRT_LIMITER; LBM_ERR_STATE
+ * otherwise), i.e. the sites whose FP64 Delta S exceeds delta: up to `cap`
+ * entries of (Delta S, linear site index y*nx + x, selected flag) into HOST
+ * arrays (any may be NULL); *count receives the number of candidates.  The
+ * FP64 Delta S of the step's screened sites is evaluated on `stream` by one
+ * small kernel (the step itself may have settled them in FP32), then the
+ * call synchronises `stream`.  The candidate order is arbitrary.  Uses a host
+ * buffer of one entry per screened site. */
 lbm_status lbm_last_candidates(lbm_ctx* ctx, double* ds, int32_t* site, int32_t* selected,
                                int cap, int* count, void* stream);
 

@@ -68,6 +68,26 @@ def test_limiters_match_oracle(case, collision, precision):
         assert gs["limited_total"] == st["limited_sites"] > 0
 
 
+@pytest.mark.parametrize("collision,params", [
+    ("smooth", dict(lim_alpha=40.0, lim_k=1.3, beta=0.95)),
+    ("smooth", dict(lim_alpha=5.0, lim_k=2.0, beta=0.95)),
+    ("double_monotonic", dict(lim_dst=2e-3, lim_k=0.7, beta=0.95)),
+    ("ensemble", dict(lim_alpha=1.0, lim_k=1.3, beta=0.8)),
+    ("ensemble", dict(lim_alpha=1.0, lim_k=0.5, beta=0.8)),
+])
+def test_limiter_exponents_fp32(collision, params):
+    """Exponents k off the exact FP32 forms of the limiter powers (the
+    exp2 / log2 evaluation) and on them (k = 2; the ensemble's k - 1/2 = 0),
+    FP32 storage against the oracle over 201 steps."""
+    cfg = dict(CASES["cavity"], collision=collision, precision="fp32", **params)
+    f0 = state(cfg).astype(np.float32).astype(np.float64)
+    lat = lbm.Lattice(cfg)
+    lat.set_state(torch.tensor(f0, dtype=torch.float32, device="cuda"))
+    lat.step(201)
+    g = lat.get_state(torch.float64).cpu().numpy()
+    assert rel(g, O.step(cfg, f0, 201)) < TOL["fp32"]
+
+
 def test_threshold_budget_and_delta_floor():
     """The threshold limiter in both regimes: Delta S_0 above delta (the
     budget delta0 sets the threshold) and below it (Delta S_t = delta), one
