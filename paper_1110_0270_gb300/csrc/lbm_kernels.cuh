@@ -1612,7 +1612,16 @@ cudaError_t launch_step_q(bool odd, const Params& p, cudaStream_t s) {
                             s, p);
         }
     }
-    dim3 b = site_block(Q), g = site_grid(p, b);
+    dim3 b = site_block(Q);
+    if (Q == 3) {
+        // a D1Q3 line has few sites (the 800-site tube): spread them over the
+        // SMs in CTAs of as few as 32 threads, so that the ELBM root finder's
+        // FP64 chains and the limiter steps run on many SMs at once
+        const int nsm = p.pipe_ctas >= 8 ? p.pipe_ctas / 8 : 1;
+        int t = ((p.nx + nsm - 1) / nsm + 31) / 32 * 32;
+        b = dim3(t < 32 ? 32 : (t > 256 ? 256 : t), 1);
+    }
+    const dim3 g = site_grid(p, b);
     return launch_p(odd ? step_kernel<Q, ST, COLL, true> : step_kernel<Q, ST, COLL, false>, g, b, s, p);
 }
 
