@@ -894,16 +894,21 @@ __device__ __forceinline__ void eval_then_select(const Params& p) {
             s_last = 0;
             s_nsel = 0;
         }
-        if constexpr (COLL != LBM_THRESHOLD && sizeof(typename ST::T) == 4) {
+        if constexpr (COLL != LBM_THRESHOLD) {
             // every screened site certainly on one side of delta in FP32 and
             // no more candidates than k: all of them are taken, no FP64
+            // Delta S (FP64 storage: the records rounded to FP32 move Delta S
+            // by at most 6e-8 sqrt(q rho), inside the same bound)
             using T = typename ST::T;
             T f[Q];
             float ds32 = 0.f;
             int side = 0;
             if (lead) {
                 load_candidate<Q, ST>(p, (int)j, f);
-                side = certify_side<Q>(p, f, ds32);
+                float ff[Q];
+#pragma unroll
+                for (int i = 0; i < Q; ++i) ff[i] = (float)f[i];
+                side = certify_side<Q>(p, ff, ds32);
             }
             const int unsure = __syncthreads_or(lead && side == 2);
             const unsigned ncert = (unsigned)__syncthreads_count(lead && side == 1);
@@ -922,7 +927,7 @@ __device__ __forceinline__ void eval_then_select(const Params& p) {
                         const int site = p.cand_site[j];
                         if constexpr (COLL == LBM_MRT_LIMITER && Q == 9) {
                             T F[Q];
-                            mrt2_d2q9<T>(f, feq, T(2) * T(p.beta_f), F);
+                            mrt2_d2q9<T>(f, feq, sizeof(T) == 8 ? T(2.0 * p.beta) : T(2) * T(p.beta_f), F);
                             conserve_mass<Q, T>(rho, F);
                             rewrite_site<Q, ST, ODD>(p, site, F);
                         } else {
