@@ -14,7 +14,7 @@ def pytest_configure(config):
 
 def pytest_collection_modifyitems(config, items):
     """GPU tests are skipped, not failed, on a machine without a GPU when they
-    are selected implicitly; `-m gpu` on a GPU machine runs them."""
+    are selected implicitly; `-m gpu` on a machine with a GPU runs them."""
     try:
         import torch
         has_gpu = torch.cuda.is_available()

@@ -3,7 +3,7 @@
 Each test runs the same seeded input through ``paper_1110_0270_gb300.lbm``
 (the CUDA path) and through the FP64 oracle, and compares element by
 element: rel-L2 <= 1e-12 for FP64 storage and <= 1e-5 for FP32 storage over
-the stated number of steps (the bounds the task's accuracy target states),
+the stated number of steps (the accuracy targets of the FP64 and FP32 paths),
 bit-exact for the integer limiter-site selection.
 """
 import numpy as np
