@@ -144,6 +144,22 @@ def dist_setup():
     return ws, rank, local
 
 
+def max_over_ranks(ms, dist=None, device="cuda"):
+    """The slowest rank's time (ms): every rank's number is the max."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(ws, sites, steps, ms):
+    """Site updates of all ranks (each advances its own lattice of `sites`)
+    per second of the slowest rank, in millions."""
+    return ws * sites * steps / (ms * 1e-3) / 1e6
+
+
 def time_steps(lat, steps, warmup, dist=None, profile=False, sampler=None):
     """Warm up, then time exactly `steps` lattice steps on the current stream
     with CUDA events, barrier + synchronize on both sides."""
@@ -449,10 +465,12 @@ def run_adjoint(T=4000, K=100, n=513, fd=True):
     return out
 
 
-def e2e_measure(cfg, init, jobs=3, inner=100):
+def e2e_measure(cfg, init, jobs=3, inner=100, dist=None, ws=1):
     """End to end through the public API with host buffers: lbm_init from
     pinned host rho/u (H2D), `inner` steps, lbm_macros and a D2H copy of
-    rho and u into pinned host memory, per job."""
+    rho and u into pinned host memory, per job.  With several ranks every
+    rank runs its own jobs at the same time; a job takes the slowest rank's
+    time and the value counts the sites of all ranks."""
     import torch
     from paper_1110_0270_gb300 import lbm
     lat = lbm.Lattice(cfg)
@@ -463,6 +481,8 @@ def e2e_measure(cfg, init, jobs=3, inner=100):
     times = []
     for j in range(jobs + 1):
         torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
         t0 = time.perf_counter()
         lat.init(host["rho"].numpy(), host["ux"].numpy(), host["uy"].numpy())
         lat.step(inner)
@@ -470,11 +490,12 @@ def e2e_measure(cfg, init, jobs=3, inner=100):
         out_rho.copy_(rho, non_blocking=True)
         out_u.copy_(u, non_blocking=True)
         torch.cuda.synchronize()
+        dt = max_over_ranks((time.perf_counter() - t0) * 1e3, dist) * 1e-3
         if j > 0:  # the first job warms the pinned buffers
-            times.append(time.perf_counter() - t0)
+            times.append(dt)
     t = statistics.median(times)
     N = nx * ny
-    return {"value": round(N * inner / t / 1e6, 1), "unit": "MLUPS",
+    return {"value": round(whole_job_mlups(ws, N, inner, t * 1e3), 1), "unit": "MLUPS",
             "h2d_bytes_per_step": int(3 * 8 * N), "d2h_bytes_per_step": int(3 * 4 * N),
             "steps_per_job": inner, "jobs": jobs,
             "note": "one e2e step = lbm_init from pinned host rho,u + 100 lattice steps + "
@@ -576,13 +597,10 @@ def gpu_arm(args):
         time.sleep(0.25)
         sampler.stop()
     _, prof, _ = time_steps(lat, args.steps, 0, dist, profile=True)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     st = lat.stats()
     per = ms / args.steps
-    value = ws * N * args.steps / (ms * 1e-3) / 1e6
+    value = whole_job_mlups(ws, N, args.steps, ms)
     hbm, peak_kind = peaks()
     alg = 2 * Q * BYTES_PER_POP[args.precision] * N  # bytes per launch of the fused step kernel
     k_ms = prof["step"][1] / max(1, prof["step"][0])
@@ -611,6 +629,8 @@ def gpu_arm(args):
                      "fixup_ms": round(prof["fixup"][1] / max(1, prof["fixup"][0]), 5)},
         "gpu_launches": launches,
     }
+    if not args.no_e2e:  # every rank at once
+        guarded(result, "e2e", lambda: e2e_measure(cfg, init, dist=dist, ws=ws))
     if rank == 0:
         result["clocks"] = sampler.summary(t0, t1) if sampler else None
         run_sections(args, result, init)
@@ -649,9 +669,6 @@ def run_sections(args, result, init):
     if args.batch_steps > 0:
         fp64 = (result.get("variants") or {}).get("lbgk/fp64", {}).get("mlups")
         guarded(result, "batched", lambda: run_batched(args.batch_steps, 3, fp64))
-    if not args.no_e2e:
-        guarded(result, "e2e",
-                lambda: e2e_measure(workload_cfg(args.collision, args.precision, args.side)[0], init))
     if not args.no_cpu:
         guarded(result, "cpu_baseline", lambda: cpu_baseline(args.cpu_budget))
 
