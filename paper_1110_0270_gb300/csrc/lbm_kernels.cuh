@@ -1676,8 +1676,13 @@ cudaError_t launch_fixup_q(int coll, bool odd, const Params& p, cudaStream_t s, 
 template <int Q, class ST>
 cudaError_t launch_prepass_q(int coll, bool odd, const Params& p, cudaStream_t s) {
     if (coll != LBM_ENSEMBLE) return cudaSuccess;
-    return launch_p(odd ? ensemble_mean<Q, ST, true> : ensemble_mean<Q, ST, false>, dim3(p.pipe_ctas), dim3(256),
-                    s, p);
+    void (*k)(Params) = odd ? ensemble_mean<Q, ST, true> : ensemble_mean<Q, ST, false>;
+    // one full wave (the CTAs that fit on the SMs at once) strides over the
+    // lattice: a partial second wave would leave SMs idle for its length
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    const int nsm = p.pipe_ctas >= 8 ? p.pipe_ctas / 8 : 1;
+    return launch_p(k, dim3(per_sm * nsm), dim3(256), s, p);
 }
 
 template <class ST>
