@@ -349,3 +349,67 @@ def test_full_size_4097_sampled_sites_and_mass():
                 assert abs(got - F[i]) < 2e-6 * abs(F[i]) + 1e-7, (collision, x, y, i, got, F[i])
         del lat, pre, post
         torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("collision", ["ehrenfest", "median"])
+def test_full_size_4097_limiters(collision):
+    """The benchmark's lattice (4097^2, FP32, lbm_step's launch) with 300
+    strongly perturbed sites, one step: the candidate set equals the
+    oracle's (FP64 Delta S of the whole field), the selection is the
+    oracle's (the k = 64 largest; the median rule), the populations that
+    selected sites stream out equal the oracle's limited collision, sampled
+    other sites equal its LBGK collision, and the mass is kept."""
+    n, k, delta = 4097, 64, 1e-3
+    cfg = dict(lattice="D2Q9", nx=n, ny=n, bc="cavity", lid_u=0.05, collision=collision, precision="fp32",
+               nu=0.05 * (n - 1) / 10000.0, topk=k, delta=delta)
+    beta = 1.0 / (6 * cfg["nu"] + 1)
+    fields = WL.random_fields(n, n, 7, 0.05, 0.05)
+    f0 = O.init_equilibrium(dict(cfg, collision="lbgk"), fields["rho"], fields["ux"], fields["uy"])
+    rng = np.random.default_rng(11)
+    hx, hy = rng.integers(2, n - 2, 300), rng.integers(2, n - 2, 300)
+    f0[:, hy, hx] *= np.exp(0.3 * rng.standard_normal((9, 300)))
+    pre = f0.astype(np.float32)
+    del f0
+    lat = lbm.Lattice(cfg)
+    lat.set_state(torch.from_numpy(pre).cuda())
+    lat.step(1)
+    post = lat.get_state(torch.float32).cpu().numpy()
+    pre64 = pre.astype(np.float64)
+    assert abs(float(post.astype(np.float64).sum()) - float(pre64.sum())) < 1e-6 * float(pre64.sum())
+    dS = O.delta_s_field(cfg, pre64)
+    cand = np.flatnonzero(dS.ravel() > delta)
+    ds, site, sel = lat.last_candidates()
+    assert sorted(site.tolist()) == cand.tolist()
+    assert np.allclose(ds, dS.ravel()[site], rtol=1e-12, atol=0)
+    if collision == "ehrenfest":
+        mask, _ = O.select_topk(dS, k, delta)
+        want = np.flatnonzero(mask)
+    else:
+        med = O.median_field("D2Q9", dS).ravel()
+        want = cand[med[cand] < dS.ravel()[cand]]
+    got = np.sort(site[sel == 1])
+    assert got.tolist() == want.tolist()
+    assert 0 < len(want) and (collision == "median" or len(want) == k)
+    cx, cy, _ = O.lattice("D2Q9")
+    lb = dict(cfg, collision="lbgk", nx=1, ny=1, beta=beta)
+    med_all = None if collision == "ehrenfest" else O.median_field("D2Q9", dS)
+
+    def expected(y, x):
+        f = pre64[:, y, x]
+        if y * n + x not in chosen:
+            return O.collide_site(lb, f)
+        r, ux, uy = O.moments("D2Q9", f)
+        fe = O.equilibrium("D2Q9", "poly", r, ux, uy)
+        if collision == "ehrenfest":
+            return fe
+        phi = np.sqrt(med_all[y, x] / dS[y, x])
+        return fe + (1 - 2 * beta) * phi * (f - fe)
+
+    chosen = set(want.tolist())
+    checks = [(s // n, s % n) for s in want if 1 <= s // n < n - 1 and 1 <= s % n < n - 1]
+    checks += list(zip(rng.integers(1, n - 1, 300), rng.integers(1, n - 1, 300)))
+    for y, x in checks:
+        F = expected(y, x)
+        for i in range(9):  # F_i(x) streams to x + v_i
+            got_i = float(post[i, y + cy[i], x + cx[i]])
+            assert abs(got_i - F[i]) < 2e-6 * abs(F[i]) + 1e-7, (collision, x, y, i, got_i, F[i])
