@@ -271,13 +271,13 @@ __device__ __forceinline__ void elbm_stats(const Params& p, int e_code, int e_it
 
 // CTA-wide sums of a and b added to partial-sum slot (linear block id mod
 // kRedSlots) of p.red (and, with two, of p.red + kRedSlots).  Every thread
-// of the CTA calls it.  The warp stage adds in T (FP32 in the 16/32-bit
-// modes: 32 values, relative error ~1e-6 at worst, far below the FP32
-// parity bound - GB300's FP64 pipe would otherwise cost more than the
-// step's streaming), the rest in FP64.
+// of the CTA calls it.  The CTA's sum is formed in T (FP32 in the 16/32-bit
+// modes: 256 values, relative error ~5e-7 at worst, far below the FP32
+// parity bound) by two shuffle stages, and one FP64 atomic per CTA adds it:
+// GB300's narrow FP64 pipe would otherwise hold every CTA at its end.
 template <class T>
 __device__ __forceinline__ void block_sum_to_slots(const Params& p, T a, T b, bool two) {
-    __shared__ double red_a[32], red_b[32];
+    __shared__ T red_a[32], red_b[32];
     const unsigned full = 0xffffffffu;
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_xor_sync(full, a, o);
@@ -286,19 +286,22 @@ __device__ __forceinline__ void block_sum_to_slots(const Params& p, T a, T b, bo
     const int t = threadIdx.y * blockDim.x + threadIdx.x, w = t >> 5;
     const int nw = (blockDim.x * blockDim.y + 31) >> 5;
     if ((t & 31) == 0) {
-        red_a[w] = (double)a;
-        red_b[w] = (double)b;
+        red_a[w] = a;
+        red_b[w] = b;
     }
     __syncthreads();
-    if (t == 0) {
-        double sa = 0.0, sb = 0.0;
-        for (int k = 0; k < nw; ++k) {
-            sa += red_a[k];
-            sb += red_b[k];
+    if (t < 32) {
+        a = t < nw ? red_a[t] : T(0);
+        b = (two && t < nw) ? red_b[t] : T(0);
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(full, a, o);
+            if (two) b += __shfl_xor_sync(full, b, o);
         }
-        const unsigned slot = (blockIdx.y * gridDim.x + blockIdx.x) & (kRedSlots - 1);
-        if (sa != 0.0) atomicAdd(&p.red[slot], sa);
-        if (two && sb != 0.0) atomicAdd(&p.red[kRedSlots + slot], sb);
+        if (t == 0) {
+            const unsigned slot = (blockIdx.y * gridDim.x + blockIdx.x) & (kRedSlots - 1);
+            if (a != T(0)) atomicAdd(&p.red[slot], (double)a);
+            if (two && b != T(0)) atomicAdd(&p.red[kRedSlots + slot], (double)b);
+        }
     }
 }
 
