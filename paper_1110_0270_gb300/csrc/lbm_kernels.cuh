@@ -878,11 +878,111 @@ __device__ __forceinline__ void select_apply(const Params& p, unsigned M, unsign
         ehrenfest_select_apply<Q, ST, ODD, COLL>(p, M, nvalid);
 }
 
+// Up to two screened records per thread of one CTA (the many-screened-site
+// steps of small lattices): each record's side of delta is first settled in
+// FP32 (certify_side); when every side is settled and at most k are above,
+// all of those are taken without FP64 work; otherwise only the records FP32
+// did not place below delta get their FP64 Delta S (16-lane groups over a
+// compact list), and the k-largest selection follows in the same CTA.
+template <int Q, class ST, bool ODD, int COLL>
+__device__ void settle_then_select(const Params& p, unsigned M) {
+    using T = typename ST::T;
+    __shared__ unsigned s_list[512];
+    __shared__ unsigned s_n, s_valid;
+    const unsigned tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) {
+        s_n = 0;
+        s_valid = 0;
+    }
+    int side[2];
+    float ds32[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const unsigned j = tid + r * nt;
+        side[r] = 0;
+        ds32[r] = 0.f;
+        if (j < M) {
+            T f[Q];
+            float ff[Q];
+            load_candidate<Q, ST>(p, (int)j, f);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) ff[i] = (float)f[i];
+            side[r] = certify_side<Q>(p, ff, ds32[r]);
+        }
+    }
+    const int unsure = __syncthreads_or(side[0] == 2 || side[1] == 2);
+    const unsigned nabove = (unsigned)__syncthreads_count(side[0] == 1) + (unsigned)__syncthreads_count(side[1] == 1);
+    const unsigned K = p.topk > 0 ? (unsigned)p.topk : 0u;
+    if (!unsure && nabove <= K) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const unsigned j = tid + r * nt;
+            if (j >= M) continue;
+            const bool sel = side[r] == 1;
+            p.cand_sel[j] = sel ? 1 : 0;
+            p.cand_ds[j] = sel ? (double)ds32[r] : -1.0;  // lbm_last_candidates recomputes FP64 values
+            if (!sel) continue;
+            T f[Q], feq[Q], rho, ux, uy;
+            load_candidate<Q, ST>(p, (int)j, f);
+            moments<Q, T>(f, rho, ux, uy);
+            equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
+            const int site = p.cand_site[j];
+            if constexpr (COLL == LBM_MRT_LIMITER && Q == 9) {
+                T F[Q];
+                mrt2_d2q9<T>(f, feq, sizeof(T) == 8 ? T(2.0 * p.beta) : T(2) * T(p.beta_f), F);
+                conserve_mass<Q, T>(rho, F);
+                rewrite_site<Q, ST, ODD>(p, site, F);
+            } else {
+                conserve_mass<Q, T>(rho, feq);
+                rewrite_site<Q, ST, ODD>(p, site, feq);
+            }
+        }
+        if (tid == 0) {
+            p.counters[CNT_NVALID] = nabove;
+            p.counters[CNT_NSEL] = nabove;
+            if (nabove) atomicAdd(&p.stats[ST_LIMITED], (unsigned long long)nabove);
+        }
+        return;
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const unsigned j = tid + r * nt;
+        if (j >= M) continue;
+        if (side[r] == 0)
+            p.cand_ds[j] = -1.0;
+        else
+            s_list[atomicAdd(&s_n, 1u)] = j;
+    }
+    __syncthreads();
+    const unsigned nl = s_n, groups = nt >> 4;
+    for (unsigned base = 0; base < nl; base += groups) {
+        const unsigned g = base + (tid >> 4);
+        const bool v = g < nl;
+        const unsigned j = v ? s_list[g] : 0u;
+        const double d = delta_s_group<Q, ST>(p, j, v);
+        if (v && (tid & 15) == 0) {
+            const bool c = d > p.delta;
+            p.cand_ds[j] = c ? d : -1.0;
+            if (c) atomicAdd(&s_valid, 1u);
+        }
+    }
+    __syncthreads();  // this CTA's cand_ds entries are final
+    const unsigned nvalid = s_valid;
+    if (tid == 0) p.counters[CNT_NVALID] = nvalid;
+    ehrenfest_select_apply<Q, ST, ODD, COLL>(p, M, nvalid);
+}
+
 template <int Q, class ST, bool ODD, int COLL>
 __device__ __forceinline__ void eval_then_select(const Params& p) {
     __shared__ unsigned s_last;
     unsigned M = p.counters[p.cslot];
     if (M > (unsigned)p.cand_cap) M = (unsigned)p.cand_cap;
+    if constexpr (COLL != LBM_THRESHOLD) {
+        if (M > (blockDim.x >> 4) && M <= 2 * blockDim.x) {
+            if (blockIdx.x == 0) settle_then_select<Q, ST, ODD, COLL>(p, M);
+            return;
+        }
+    }
     if (M <= (blockDim.x >> 4)) {
         // few screened sites (the usual case): the first CTA evaluates them
         // all, one 16-lane group each, and selects without the ticket and

@@ -152,6 +152,36 @@ def test_few_candidates_match_oracle(collision, topk, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("collision,topk", [("ehrenfest", 4), ("ehrenfest", 600), ("mrt_limiter", 4)])
+def test_tens_to_hundreds_of_candidates_match_oracle(collision, topk, precision):
+    """A periodic fluid at rest with 40 hot sites: 36 candidates in the first
+    step, then hundreds (the selection kernel's one-CTA path for up to 512
+    screened sites, then its multi-CTA path), 12 steps; k = 4 ranks many
+    candidates, k = 600 takes them all."""
+    cfg = dict(CASES["periodic"], collision=collision, precision=precision, beta=0.97, delta=2e-4, topk=topk)
+    ny, nx = cfg["ny"], cfg["nx"]
+    f0 = O.init_equilibrium(dict(cfg, collision="lbgk"), np.ones((ny, nx)), np.zeros((ny, nx)),
+                            np.zeros((ny, nx)))
+    f0 = f0 * WL.lognormal_factors(f0.shape, 4, 0.002)
+    rng = np.random.default_rng(2)
+    for y, x in zip(rng.integers(0, ny, 40), rng.integers(0, nx, 40)):
+        f0[:, y, x] *= np.exp(0.3 * rng.standard_normal(9))
+    f0 = as_stored(cfg, f0)
+    g, lat = gpu_run(cfg, f0, 12)
+    f, st = O.step(cfg, f0, 12, stats=True)
+    assert rel(g, f) < TOL[precision], rel(g, f)
+    assert lat.stats()["limited_total"] == st["limited_sites"] > 0
+    # the second step's candidates against the oracle's Delta S of the GPU's
+    # own state after one step (the step's input)
+    g1, lat1 = gpu_run(cfg, f0, 1)
+    lat1.step(1)
+    ds, site, sel = lat1.last_candidates()
+    dS_or = O.delta_s_field(cfg, g1).ravel()
+    assert sorted(site.tolist()) == np.flatnonzero(dS_or > cfg["delta"]).tolist()
+    assert np.allclose(ds, dS_or[site], rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("beta", [0.52, 0.7])
 def test_median_window_sources_match_oracle(precision, beta):
     """The median window's Delta S from the step's field (beta = 0.52, where
