@@ -880,19 +880,59 @@ __device__ __forceinline__ void select_apply(const Params& p, unsigned M, unsign
 
 // Up to two screened records per thread of one CTA (the many-screened-site
 // steps of small lattices): each record's side of delta is first settled in
-// FP32 (certify_side); when every side is settled and at most k are above,
-// all of those are taken without FP64 work; otherwise only the records FP32
-// did not place below delta get their FP64 Delta S (16-lane groups over a
-// compact list), and the k-largest selection follows in the same CTA.
+// FP32 (certify_side); only the records FP32 leaves open get their FP64
+// Delta S (16-lane groups over a compact list).  When no more than k are
+// then above delta, all of those are taken; otherwise the order matters, the
+// records FP32 placed above get their FP64 values too, and the k-largest
+// selection follows in the same CTA.
+template <int Q, class ST, int COLL, bool ODD>
+__device__ __forceinline__ void rewrite_selected(const Params& p, unsigned j) {
+    using T = typename ST::T;
+    T f[Q], feq[Q], rho, ux, uy;
+    load_candidate<Q, ST>(p, (int)j, f);
+    moments<Q, T>(f, rho, ux, uy);
+    equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
+    const int site = p.cand_site[j];
+    if constexpr (COLL == LBM_MRT_LIMITER && Q == 9) {
+        T F[Q];
+        mrt2_d2q9<T>(f, feq, sizeof(T) == 8 ? T(2.0 * p.beta) : T(2) * T(p.beta_f), F);
+        conserve_mass<Q, T>(rho, F);
+        rewrite_site<Q, ST, ODD>(p, site, F);
+    } else {
+        conserve_mass<Q, T>(rho, feq);
+        rewrite_site<Q, ST, ODD>(p, site, feq);
+    }
+}
+
+// FP64 Delta S of the records of s_list[0, n) by 16-lane groups of the CTA
+// (every thread calls it); returns the number above delta (to thread 0 via
+// the shared counter).
+template <int Q, class ST>
+__device__ __forceinline__ void fp64_of_list(const Params& p, const unsigned* list, unsigned n,
+                                             unsigned* above) {
+    const unsigned tid = threadIdx.x, groups = blockDim.x >> 4;
+    for (unsigned base = 0; base < n; base += groups) {
+        const unsigned g = base + (tid >> 4);
+        const bool v = g < n;
+        const unsigned j = v ? list[g] : 0u;
+        const double d = delta_s_group<Q, ST>(p, j, v);
+        if (v && (tid & 15) == 0) {
+            const bool c = d > p.delta;
+            p.cand_ds[j] = c ? d : -1.0;
+            if (c) atomicAdd(above, 1u);
+        }
+    }
+}
+
 template <int Q, class ST, bool ODD, int COLL>
 __device__ void settle_then_select(const Params& p, unsigned M) {
     using T = typename ST::T;
     __shared__ unsigned s_list[512];
-    __shared__ unsigned s_n, s_valid;
+    __shared__ unsigned s_n, s_above;
     const unsigned tid = threadIdx.x, nt = blockDim.x;
     if (tid == 0) {
         s_n = 0;
-        s_valid = 0;
+        s_above = 0;
     }
     int side[2];
     float ds32[2];
@@ -910,65 +950,67 @@ __device__ void settle_then_select(const Params& p, unsigned M) {
             side[r] = certify_side<Q>(p, ff, ds32[r]);
         }
     }
-    const int unsure = __syncthreads_or(side[0] == 2 || side[1] == 2);
-    const unsigned nabove = (unsigned)__syncthreads_count(side[0] == 1) + (unsigned)__syncthreads_count(side[1] == 1);
+    __syncthreads();
+    // FP64 for the records FP32 leaves open
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+        if (tid + r * nt < M && side[r] == 2) s_list[atomicAdd(&s_n, 1u)] = tid + r * nt;
+    const unsigned ncert = (unsigned)__syncthreads_count(side[0] == 1) + (unsigned)__syncthreads_count(side[1] == 1);
+    fp64_of_list<Q, ST>(p, s_list, s_n, &s_above);
+    __syncthreads();
+    const unsigned nvalid = ncert + s_above;
     const unsigned K = p.topk > 0 ? (unsigned)p.topk : 0u;
-    if (!unsure && nabove <= K) {
+    if (tid == 0) p.counters[CNT_NVALID] = nvalid;
+    if (nvalid <= K) {
+        // every candidate is taken: no order needed
+        unsigned mine = 0;
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             const unsigned j = tid + r * nt;
             if (j >= M) continue;
-            const bool sel = side[r] == 1;
-            p.cand_sel[j] = sel ? 1 : 0;
-            p.cand_ds[j] = sel ? (double)ds32[r] : -1.0;  // lbm_last_candidates recomputes FP64 values
-            if (!sel) continue;
-            T f[Q], feq[Q], rho, ux, uy;
-            load_candidate<Q, ST>(p, (int)j, f);
-            moments<Q, T>(f, rho, ux, uy);
-            equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
-            const int site = p.cand_site[j];
-            if constexpr (COLL == LBM_MRT_LIMITER && Q == 9) {
-                T F[Q];
-                mrt2_d2q9<T>(f, feq, sizeof(T) == 8 ? T(2.0 * p.beta) : T(2) * T(p.beta_f), F);
-                conserve_mass<Q, T>(rho, F);
-                rewrite_site<Q, ST, ODD>(p, site, F);
+            bool sel;
+            if (side[r] == 2) {
+                sel = K > 0 && __ldcg(&p.cand_ds[j]) > p.delta;
             } else {
-                conserve_mass<Q, T>(rho, feq);
-                rewrite_site<Q, ST, ODD>(p, site, feq);
+                sel = K > 0 && side[r] == 1;
+                // FP32 value of a record settled above (lbm_last_candidates
+                // recomputes FP64 values), -1 below
+                p.cand_ds[j] = side[r] == 1 ? (double)ds32[r] : -1.0;
+            }
+            p.cand_sel[j] = sel ? 1 : 0;
+            if (sel) {
+                rewrite_selected<Q, ST, COLL, ODD>(p, j);
+                ++mine;
             }
         }
+        __shared__ unsigned s_sel;
+        if (tid == 0) s_sel = 0;
+        __syncthreads();
+        if (mine) atomicAdd(&s_sel, mine);
+        __syncthreads();
         if (tid == 0) {
-            p.counters[CNT_NVALID] = nabove;
-            p.counters[CNT_NSEL] = nabove;
-            if (nabove) atomicAdd(&p.stats[ST_LIMITED], (unsigned long long)nabove);
+            p.counters[CNT_NSEL] = s_sel;
+            if (s_sel) atomicAdd(&p.stats[ST_LIMITED], (unsigned long long)s_sel);
         }
         return;
     }
+    // more candidates than k: the order decides, in FP64 for every candidate
+    __syncthreads();
+    if (tid == 0) {
+        s_n = 0;
+        s_above = 0;
+    }
+    __syncthreads();
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const unsigned j = tid + r * nt;
         if (j >= M) continue;
-        if (side[r] == 0)
-            p.cand_ds[j] = -1.0;
-        else
-            s_list[atomicAdd(&s_n, 1u)] = j;
+        if (side[r] == 1) s_list[atomicAdd(&s_n, 1u)] = j;
+        if (side[r] == 0) p.cand_ds[j] = -1.0;
     }
     __syncthreads();
-    const unsigned nl = s_n, groups = nt >> 4;
-    for (unsigned base = 0; base < nl; base += groups) {
-        const unsigned g = base + (tid >> 4);
-        const bool v = g < nl;
-        const unsigned j = v ? s_list[g] : 0u;
-        const double d = delta_s_group<Q, ST>(p, j, v);
-        if (v && (tid & 15) == 0) {
-            const bool c = d > p.delta;
-            p.cand_ds[j] = c ? d : -1.0;
-            if (c) atomicAdd(&s_valid, 1u);
-        }
-    }
+    fp64_of_list<Q, ST>(p, s_list, s_n, &s_above);
     __syncthreads();  // this CTA's cand_ds entries are final
-    const unsigned nvalid = s_valid;
-    if (tid == 0) p.counters[CNT_NVALID] = nvalid;
     ehrenfest_select_apply<Q, ST, ODD, COLL>(p, M, nvalid);
 }
 
