@@ -924,6 +924,8 @@ __device__ __forceinline__ void fp64_of_list(const Params& p, const unsigned* li
     }
 }
 
+constexpr unsigned kSettleMin = 64;
+
 template <int Q, class ST, bool ODD, int COLL>
 __device__ void settle_then_select(const Params& p, unsigned M) {
     using T = typename ST::T;
@@ -1020,7 +1022,9 @@ __device__ __forceinline__ void eval_then_select(const Params& p) {
     unsigned M = p.counters[p.cslot];
     if (M > (unsigned)p.cand_cap) M = (unsigned)p.cand_cap;
     if constexpr (COLL != LBM_THRESHOLD) {
-        if (M > (blockDim.x >> 4) && M <= 2 * blockDim.x) {
+        // tens of screened sites: the grid-wide FP64 pass below (measured
+        // faster there); hundreds: settled in FP32 by one CTA
+        if (M > kSettleMin && M <= 2 * blockDim.x) {
             if (blockIdx.x == 0) settle_then_select<Q, ST, ODD, COLL>(p, M);
             return;
         }
