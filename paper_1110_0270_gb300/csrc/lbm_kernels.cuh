@@ -878,13 +878,8 @@ __device__ __forceinline__ void select_apply(const Params& p, unsigned M, unsign
         ehrenfest_select_apply<Q, ST, ODD, COLL>(p, M, nvalid);
 }
 
-// Up to two screened records per thread of one CTA (the many-screened-site
-// steps of small lattices): each record's side of delta is first settled in
-// FP32 (certify_side); only the records FP32 leaves open get their FP64
-// Delta S (16-lane groups over a compact list).  When no more than k are
-// then above delta, all of those are taken; otherwise the order matters, the
-// records FP32 placed above get their FP64 values too, and the k-largest
-// selection follows in the same CTA.
+// The post-collision state of selected record j written back (f*, or A_2
+// for the MRT limiter).
 template <int Q, class ST, int COLL, bool ODD>
 __device__ __forceinline__ void rewrite_selected(const Params& p, unsigned j) {
     using T = typename ST::T;
@@ -904,38 +899,17 @@ __device__ __forceinline__ void rewrite_selected(const Params& p, unsigned j) {
     }
 }
 
-// FP64 Delta S of the records of s_list[0, n) by 16-lane groups of the CTA
-// (every thread calls it); returns the number above delta (to thread 0 via
-// the shared counter).
-template <int Q, class ST>
-__device__ __forceinline__ void fp64_of_list(const Params& p, const unsigned* list, unsigned n,
-                                             unsigned* above) {
-    const unsigned tid = threadIdx.x, groups = blockDim.x >> 4;
-    for (unsigned base = 0; base < n; base += groups) {
-        const unsigned g = base + (tid >> 4);
-        const bool v = g < n;
-        const unsigned j = v ? list[g] : 0u;
-        const double d = delta_s_group<Q, ST>(p, j, v);
-        if (v && (tid & 15) == 0) {
-            const bool c = d > p.delta;
-            p.cand_ds[j] = c ? d : -1.0;
-            if (c) atomicAdd(above, 1u);
-        }
-    }
-}
-
-constexpr unsigned kSettleMin = 64;
-
+// Up to two screened records per thread: every CTA settles every record's
+// side of delta in FP32 (certify_side; the same result in each CTA).  When
+// every side is settled and at most k records are above delta, the first
+// CTA takes all of those without FP64 work and the call returns true in
+// every CTA; otherwise it returns false everywhere and the grid-wide FP64
+// evaluation decides.
 template <int Q, class ST, bool ODD, int COLL>
-__device__ void settle_then_select(const Params& p, unsigned M) {
+__device__ bool settle_all_taken(const Params& p, unsigned M) {
     using T = typename ST::T;
-    __shared__ unsigned s_list[512];
-    __shared__ unsigned s_n, s_above;
+    __shared__ unsigned s_sel;
     const unsigned tid = threadIdx.x, nt = blockDim.x;
-    if (tid == 0) {
-        s_n = 0;
-        s_above = 0;
-    }
     int side[2];
     float ds32[2];
 #pragma unroll
@@ -952,68 +926,27 @@ __device__ void settle_then_select(const Params& p, unsigned M) {
             side[r] = certify_side<Q>(p, ff, ds32[r]);
         }
     }
-    __syncthreads();
-    // FP64 for the records FP32 leaves open
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-        if (tid + r * nt < M && side[r] == 2) s_list[atomicAdd(&s_n, 1u)] = tid + r * nt;
-    const unsigned ncert = (unsigned)__syncthreads_count(side[0] == 1) + (unsigned)__syncthreads_count(side[1] == 1);
-    fp64_of_list<Q, ST>(p, s_list, s_n, &s_above);
-    __syncthreads();
-    const unsigned nvalid = ncert + s_above;
+    if (tid == 0) s_sel = 0;
+    const int unsure = __syncthreads_or(side[0] == 2 || side[1] == 2);
+    const unsigned nabove = (unsigned)__syncthreads_count(side[0] == 1) + (unsigned)__syncthreads_count(side[1] == 1);
     const unsigned K = p.topk > 0 ? (unsigned)p.topk : 0u;
-    if (tid == 0) p.counters[CNT_NVALID] = nvalid;
-    if (nvalid <= K) {
-        // every candidate is taken: no order needed
-        unsigned mine = 0;
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const unsigned j = tid + r * nt;
-            if (j >= M) continue;
-            bool sel;
-            if (side[r] == 2) {
-                sel = K > 0 && __ldcg(&p.cand_ds[j]) > p.delta;
-            } else {
-                sel = K > 0 && side[r] == 1;
-                // FP32 value of a record settled above (lbm_last_candidates
-                // recomputes FP64 values), -1 below
-                p.cand_ds[j] = side[r] == 1 ? (double)ds32[r] : -1.0;
-            }
-            p.cand_sel[j] = sel ? 1 : 0;
-            if (sel) {
-                rewrite_selected<Q, ST, COLL, ODD>(p, j);
-                ++mine;
-            }
-        }
-        __shared__ unsigned s_sel;
-        if (tid == 0) s_sel = 0;
-        __syncthreads();
-        if (mine) atomicAdd(&s_sel, mine);
-        __syncthreads();
-        if (tid == 0) {
-            p.counters[CNT_NSEL] = s_sel;
-            if (s_sel) atomicAdd(&p.stats[ST_LIMITED], (unsigned long long)s_sel);
-        }
-        return;
-    }
-    // more candidates than k: the order decides, in FP64 for every candidate
-    __syncthreads();
-    if (tid == 0) {
-        s_n = 0;
-        s_above = 0;
-    }
-    __syncthreads();
+    if (unsure || nabove > K) return false;
+    if (blockIdx.x != 0) return true;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const unsigned j = tid + r * nt;
         if (j >= M) continue;
-        if (side[r] == 1) s_list[atomicAdd(&s_n, 1u)] = j;
-        if (side[r] == 0) p.cand_ds[j] = -1.0;
+        const bool sel = side[r] == 1;
+        p.cand_sel[j] = sel ? 1 : 0;
+        p.cand_ds[j] = sel ? (double)ds32[r] : -1.0;  // lbm_last_candidates recomputes FP64 values
+        if (sel) rewrite_selected<Q, ST, COLL, ODD>(p, j);
     }
-    __syncthreads();
-    fp64_of_list<Q, ST>(p, s_list, s_n, &s_above);
-    __syncthreads();  // this CTA's cand_ds entries are final
-    ehrenfest_select_apply<Q, ST, ODD, COLL>(p, M, nvalid);
+    if (tid == 0) {
+        p.counters[CNT_NVALID] = nabove;
+        p.counters[CNT_NSEL] = nabove;
+        if (nabove) atomicAdd(&p.stats[ST_LIMITED], (unsigned long long)nabove);
+    }
+    return true;
 }
 
 template <int Q, class ST, bool ODD, int COLL>
@@ -1022,12 +955,7 @@ __device__ __forceinline__ void eval_then_select(const Params& p) {
     unsigned M = p.counters[p.cslot];
     if (M > (unsigned)p.cand_cap) M = (unsigned)p.cand_cap;
     if constexpr (COLL != LBM_THRESHOLD) {
-        // tens of screened sites: the grid-wide FP64 pass below (measured
-        // faster there); hundreds: settled in FP32 by one CTA
-        if (M > kSettleMin && M <= 2 * blockDim.x) {
-            if (blockIdx.x == 0) settle_then_select<Q, ST, ODD, COLL>(p, M);
-            return;
-        }
+        if (M > (blockDim.x >> 4) && M <= 2 * blockDim.x && settle_all_taken<Q, ST, ODD, COLL>(p, M)) return;
     }
     if (M <= (blockDim.x >> 4)) {
         // few screened sites (the usual case): the first CTA evaluates them

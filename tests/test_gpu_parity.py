@@ -155,10 +155,11 @@ def test_few_candidates_match_oracle(collision, topk, precision):
 @pytest.mark.parametrize("collision,topk", [("ehrenfest", 4), ("ehrenfest", 600), ("mrt_limiter", 4)])
 def test_tens_to_hundreds_of_candidates_match_oracle(collision, topk, precision):
     """A periodic fluid at rest with 40 hot sites: 36 candidates in the first
-    step, then hundreds (the selection kernel's multi-CTA path for tens of
-    screened sites, its one-CTA path for 65 to 512, the multi-CTA path
-    again beyond), 12 steps; k = 4 ranks many candidates, k = 600 takes them
-    all."""
+    step, then hundreds (for up to 512 screened sites every CTA of the
+    selection kernel settles the sides of delta in FP32, and the first takes
+    all candidates without FP64 when at most k are above; else, and beyond
+    512, the grid-wide FP64 pass), 12 steps; k = 4 ranks many candidates,
+    k = 600 takes them all."""
     cfg = dict(CASES["periodic"], collision=collision, precision=precision, beta=0.97, delta=2e-4, topk=topk)
     ny, nx = cfg["ny"], cfg["nx"]
     f0 = O.init_equilibrium(dict(cfg, collision="lbgk"), np.ones((ny, nx)), np.zeros((ny, nx)),
