@@ -899,6 +899,8 @@ __device__ __forceinline__ void rewrite_selected(const Params& p, unsigned j) {
     }
 }
 
+constexpr int64_t kSettleSites = 1 << 21;
+
 // Up to two screened records per thread: every CTA settles every record's
 // side of delta in FP32 (certify_side; the same result in each CTA).  When
 // every side is settled and at most k records are above delta, the first
@@ -955,7 +957,12 @@ __device__ __forceinline__ void eval_then_select(const Params& p) {
     unsigned M = p.counters[p.cslot];
     if (M > (unsigned)p.cand_cap) M = (unsigned)p.cand_cap;
     if constexpr (COLL != LBM_THRESHOLD) {
-        if (M > (blockDim.x >> 4) && M <= 2 * blockDim.x && settle_all_taken<Q, ST, ODD, COLL>(p, M)) return;
+        // small lattices only: there the selection's latency is most of the
+        // step, while on large ones the grid-wide pass hides under the next
+        // step's launch and a failed attempt would only add to it (measured)
+        if ((int64_t)p.nx * p.ny <= kSettleSites && M > (blockDim.x >> 4) && M <= 2 * blockDim.x &&
+            settle_all_taken<Q, ST, ODD, COLL>(p, M))
+            return;
     }
     if (M <= (blockDim.x >> 4)) {
         // few screened sites (the usual case): the first CTA evaluates them
