@@ -906,9 +906,10 @@ constexpr int64_t kSettleSites = 1 << 21;
 // every side is settled and at most k records are above delta, the first
 // CTA takes all of those without FP64 work and the call returns true in
 // every CTA; otherwise it returns false everywhere and the grid-wide FP64
-// evaluation decides.
+// evaluation decides.  Out of line: inlined, its code in front of the other
+// paths slowed the selection kernel of large lattices (measured).
 template <int Q, class ST, bool ODD, int COLL>
-__device__ bool settle_all_taken(const Params& p, unsigned M) {
+__device__ __noinline__ bool settle_all_taken(const Params& p, unsigned M) {
     using T = typename ST::T;
     __shared__ unsigned s_sel;
     const unsigned tid = threadIdx.x, nt = blockDim.x;
