@@ -400,6 +400,12 @@ lbm_status lbm_create(const lbm_config* cfg, void* dev_mem, size_t bytes, lbm_ct
     p.lim_k = cfg->lim_k;
     p.lim_dst = cfg->lim_dst;
     p.lim_delta0 = cfg->lim_delta0;
+    // the limiter constants in FP32, so the 16/32-bit step kernels convert
+    // no FP64 parameter per site (GB300's FP64 pipe is narrow)
+    p.lim_f[0] = (float)cfg->lim_alpha;
+    p.lim_f[1] = (float)cfg->lim_k;
+    p.lim_f[2] = cfg->lim_dst > 0.0 ? (float)(1.0 / cfg->lim_dst) : 0.f;
+    p.lim_f[3] = cfg->lim_k > 0.0 ? (float)(-0.5 / cfg->lim_k) : 0.f;
     p.counters = (unsigned*)(ctx->base + L.cnt_off);
     p.stats = (unsigned long long*)(ctx->base + L.cnt_off + CNT_WORDS * 4);
     p.scratch_d = (double*)(ctx->base + L.cnt_off + CNT_WORDS * 4 + ST_WORDS * 8);
@@ -419,6 +425,7 @@ lbm_status lbm_create(const lbm_config* cfg, void* dev_mem, size_t bytes, lbm_ct
     if (reduces(cfg->collision)) {
         p.red = (double*)(ctx->base + L.red_off);
         p.lim_E = p.red + 2 * kRedSlots;
+        p.lim_E_f = (float*)(p.lim_E + 1);
     }
     p.pipe_ctas = 8 * ctx->nsm;
     ctx->staging = (double*)(ctx->base + L.staging_off);

@@ -264,7 +264,7 @@ __device__ double delta_s_fp64(const T* f, int eqkind) {
 // relative deviation by the approximate division, good to 2 ulp, which the
 // FP32 field tolerates).
 // x^k for x >= 0 in the limiter functions of Sections 4.2-4.3.  FP64: pow.
-// FP32: the exponents 0, 1/2, 1, 3/2 and 2 exactly (sqrt and products),
+// FP32: the exponents 0, +-1/2, 1, 3/2 and 2 by sqrt, rsqrt and products,
 // others as exp2(k log2 x) (a few units in the last place, well inside the
 // FP32 parity bound) instead of powf's special-case handling; k is the same
 // for every thread, so the branches do not diverge.
@@ -275,6 +275,7 @@ __device__ __forceinline__ float pow_lim(float x, float k) {
     if (k == 2.f) return x * x;
     if (k == 1.5f) return x * sqrtf(x);
     if (k == 0.f) return 1.f;
+    if (k == -0.5f) return rsqrtf(x);
     return exp2f(k * log2f(x));
 }
 

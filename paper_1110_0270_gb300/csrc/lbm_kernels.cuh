@@ -155,15 +155,20 @@ __device__ __forceinline__ void collide_site(const Params& p, int x, int y, cons
             if (median_maybe_above((float)ds, (float)q, (float)rho, p.delta_f)) record_candidate<Q, T>(p, x, y, f);
         } else if (!(ds < T(INFINITY))) {
             phi = T(0);  // a negative population: the state goes to f*
-        } else if (COLL == LBM_SMOOTH) {
-            phi = T(1) / (T(1) + T(p.lim_alpha) * pow_lim(ds, T(p.lim_k)));
-        } else if (COLL == LBM_DOUBLE_MONOTONIC) {
-            phi = pow_lim(T(1) + pow_lim(ds / T(p.lim_dst), T(p.lim_k)), T(-0.5) / T(p.lim_k));
-        } else {  // LBM_ENSEMBLE, E from this step's pre-pass
-            const T E = T(*p.lim_E);
-            if (E > T(0)) {
-                const T yv = ds / (T(p.lim_alpha) * E);
-                phi = (T(1) + pow_lim(yv, T(p.lim_k) - T(0.5))) / (T(1) + pow_lim(yv, T(p.lim_k)));
+        } else {
+            constexpr bool d = sizeof(T) == 8;  // FP64 parameters, else their FP32 copies
+            const T alpha = d ? T(p.lim_alpha) : T(p.lim_f[0]), k = d ? T(p.lim_k) : T(p.lim_f[1]);
+            if (COLL == LBM_SMOOTH) {
+                phi = T(1) / (T(1) + alpha * pow_lim(ds, k));
+            } else if (COLL == LBM_DOUBLE_MONOTONIC) {
+                const T z = d ? ds / T(p.lim_dst) : ds * T(p.lim_f[2]);
+                phi = pow_lim(T(1) + pow_lim(z, k), d ? T(-0.5) / k : T(p.lim_f[3]));
+            } else {  // LBM_ENSEMBLE, E from this step's pre-pass
+                const T E = d ? T(*p.lim_E) : T(*p.lim_E_f);
+                if (E > T(0)) {
+                    const T yv = ds / (alpha * E);
+                    phi = (T(1) + pow_lim(yv, k - T(0.5))) / (T(1) + pow_lim(yv, k));
+                }
             }
         }
         const T c = (T(1) - (sizeof(T) == 8 ? T(2.0 * p.beta) : T(2) * T(p.beta_f))) * phi;
@@ -1192,6 +1197,7 @@ __global__ void __launch_bounds__(256) ensemble_mean(Params p) {
     N = block_sum(N);
     if (t == 0) {
         *p.lim_E = N > 0.0 ? S / N : 0.0;
+        *p.lim_E_f = (float)*p.lim_E;
         p.counters[CNT_DONE] = 0u;
     }
 }

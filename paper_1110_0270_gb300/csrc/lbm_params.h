@@ -61,6 +61,8 @@ struct Params {
     double lim_alpha, lim_k, lim_dst, lim_delta0;
     double* red;      // kRedSlots partial sums (+ kRedSlots counts), zero between steps
     double* lim_E;    // the step's E(Delta S) (ensemble limiter)
+    float* lim_E_f;   // the same in FP32 (read by the 16/32-bit step kernels)
+    float lim_f[4];   // FP32 copies: alpha, k, 1 / Delta S_t, -1 / (2 k)
     int pipe_ctas;    // host side: CTAs of the grid-stride reduction kernels
     double* probe_buf;  // control-point probe: (u_x, u_y) per step, ring of probe_cap
     int probe_site, probe_cap;

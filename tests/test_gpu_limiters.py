@@ -72,13 +72,15 @@ def test_limiters_match_oracle(case, collision, precision):
     ("smooth", dict(lim_alpha=40.0, lim_k=1.3, beta=0.95)),
     ("smooth", dict(lim_alpha=5.0, lim_k=2.0, beta=0.95)),
     ("double_monotonic", dict(lim_dst=2e-3, lim_k=0.7, beta=0.95)),
+    ("double_monotonic", dict(lim_dst=2e-3, lim_k=1.0, beta=0.95)),
     ("ensemble", dict(lim_alpha=1.0, lim_k=1.3, beta=0.8)),
     ("ensemble", dict(lim_alpha=1.0, lim_k=0.5, beta=0.8)),
 ])
 def test_limiter_exponents_fp32(collision, params):
     """Exponents k off the exact FP32 forms of the limiter powers (the
-    exp2 / log2 evaluation) and on them (k = 2; the ensemble's k - 1/2 = 0),
-    FP32 storage against the oracle over 201 steps."""
+    exp2 / log2 evaluation) and on them (k = 2; the ensemble's k - 1/2 = 0;
+    the double-monotonic outer power -1/(2k) = -1/2), FP32 storage against
+    the oracle over 201 steps."""
     cfg = dict(CASES["cavity"], collision=collision, precision="fp32", **params)
     f0 = state(cfg).astype(np.float32).astype(np.float64)
     lat = lbm.Lattice(cfg)
