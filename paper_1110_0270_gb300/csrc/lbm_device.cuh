@@ -328,8 +328,11 @@ __device__ __forceinline__ bool maybe_above_loose(const float* f, const float* f
     return slack_reaches(q, q, rho, delta);
 }
 
-// Median: the site's Delta S in the arithmetic type is computed anyway (the
-// filter's field), so it is the screen itself.  In the form sum f* g(x) the
+// Median with a Delta S field (16-bit storage, or 1 - 2 beta near 0): the
+// site's Delta S in the arithmetic type is computed anyway (the filter's
+// field), so it is the screen itself; it also serves the threshold limiter,
+// the selection kernel's FP32 settling and the limiters of Sections 4.2-4.3
+// (their phi).  In the form sum f* g(x) the
 // rounding of the mass of f* cancels to first order (dDelta S / df*_i =
 // -x_i), leaving sum x_i df*_i <= sqrt(q) sqrt(sum df*_i^2 / f*_i), inside the
 // same slack; the series and log1p evaluation of g is accurate to ~1e-5

@@ -7,10 +7,11 @@
 //                   ELBM, positivity and MRT are complete here, the Ehrenfest
 //                   and median limiters additionally append their candidate
 //                   sites (Delta S > delta) to a compact list.
-//  ehrenfest_eval_select  FP64 Delta S of the screened sites, then (last CTA)
-//                   k-largest selection by MSB radix select on the FP64
-//                   Delta S bits, ties by site index; selected sites are
-//                   rewritten with f*.
+//  ehrenfest_eval_select  the side of delta of each screened site, settled
+//                   in FP32 where the error bound allows, else by its FP64
+//                   Delta S; then the k-largest selection (ranks, or an MSB
+//                   radix select on the FP64 Delta S bits in the last CTA),
+//                   ties by site index; selected sites are rewritten with f*.
 //  median_fixup     grid-stride over candidates: median of the Delta S window
 //                   (a field the step wrote), homothety of Eq. (entrHom)
 //                   where it lowers Delta S.
@@ -94,8 +95,9 @@ __device__ __forceinline__ void record_candidate(const Params& p, int x, int y, 
 
 // Limiter screen of the pre-collision state: the sites that may exceed
 // delta (FP32 screens of Eq. DelS) are appended to the candidate list; their
-// FP64 value decides later.  The median filter also writes the Delta S field
-// of every site (in the arithmetic type; FP64 in FP64 mode).
+// FP64 value decides later.  The median filter with a Delta S field also
+// writes every site's Delta S there (in the arithmetic type; FP64 in FP64
+// mode); without the field the median step screens like the Ehrenfest one.
 template <int Q, class T, int COLL>
 __device__ __forceinline__ void limiter_screen(const Params& p, int x, int y, const T* f,
                                                const T* feq, T rho) {
@@ -916,7 +918,6 @@ constexpr int64_t kSettleSites = 1 << 21;
 template <int Q, class ST, bool ODD, int COLL>
 __device__ __noinline__ bool settle_all_taken(const Params& p, unsigned M) {
     using T = typename ST::T;
-    __shared__ unsigned s_sel;
     const unsigned tid = threadIdx.x, nt = blockDim.x;
     int side[2];
     float ds32[2];
@@ -934,7 +935,6 @@ __device__ __noinline__ bool settle_all_taken(const Params& p, unsigned M) {
             side[r] = certify_side<Q>(p, ff, ds32[r]);
         }
     }
-    if (tid == 0) s_sel = 0;
     const int unsure = __syncthreads_or(side[0] == 2 || side[1] == 2);
     const unsigned nabove = (unsigned)__syncthreads_count(side[0] == 1) + (unsigned)__syncthreads_count(side[1] == 1);
     const unsigned K = p.topk > 0 ? (unsigned)p.topk : 0u;
