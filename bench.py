@@ -55,7 +55,7 @@ LIMITER_PARAMS = {"smooth": dict(lim_alpha=40.0, lim_k=1.0), "double_monotonic":
 # DRAM bytes per launch of the headline step kernel from the full-size ncu
 # launch list (profiles/step_kernel_d2q9_fp32_ehrenfest_4097.md), valid only
 # for the kernel sources it was taken on.
-TRAFFIC_CAPTURE = {"sources_sha256_16": "683c1938b56d80b8", "collision": "ehrenfest",
+TRAFFIC_CAPTURE = {"sources_sha256_16": "0ffa72a8912f6606", "collision": "ehrenfest",
                    "precision": "fp32", "side": 4097, "bytes_per_launch": 1160.9e6}
 TRAFFIC_SOURCES = ["lbm_device.cuh", "lbm_kernels.cuh", "lbm_params.h", "lbm_kernels_f32.cu"]
 
