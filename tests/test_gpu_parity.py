@@ -445,3 +445,45 @@ def test_full_size_4097_limiters(collision):
         for i in range(9):  # F_i(x) streams to x + v_i
             got_i = float(post[i, y + cy[i], x + cx[i]])
             assert abs(got_i - F[i]) < 2e-6 * abs(F[i]) + 1e-7, (collision, x, y, i, got_i, F[i])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_init_from_device_arrays_equals_host_init(precision):
+    """lbm_init_device (device rho, u) produces the same state as lbm_init
+    from host arrays, which is the oracle's equilibrium; D1Q3 takes no u_y."""
+    for cfg in [dict(CASES["cavity"], collision="lbgk", precision=precision, beta=0.9),
+                dict(CASES["tube"], collision="lbgk", precision=precision, beta=0.9)]:
+        ny, nx = cfg["ny"], cfg["nx"]
+        fl = WL.random_fields(ny, nx, 21, 0.05, 0.05)
+        uy = None if cfg["lattice"] == "D1Q3" else fl["uy"]
+        a = lbm.Lattice(cfg)
+        a.init(fl["rho"], fl["ux"], uy)
+        b = lbm.Lattice(cfg)
+        dev = [torch.tensor(v, dtype=torch.float64, device="cuda") if v is not None else None
+               for v in (fl["rho"], fl["ux"], uy)]
+        b.init_device(*dev)
+        ga, gb = a.get_state(torch.float64), b.get_state(torch.float64)
+        assert torch.equal(ga, gb)
+        want = as_stored(cfg, O.init_equilibrium(cfg, fl["rho"], fl["ux"], uy))
+        assert rel(ga.cpu().numpy(), want) < TOL[precision]
+
+
+def test_profile_counts_every_kernel_launch():
+    """lbm_profile_enable: each step is timed kernel by kernel (one step and
+    one selection launch per Ehrenfest step, positive times); with the
+    profile off again lbm_step replays its graphs and the state continues
+    identically to an unprofiled run."""
+    cfg = dict(CASES["cavity"], collision="ehrenfest", precision="fp64", beta=0.97, topk=3, delta=2e-4)
+    f0 = perturbed_state(cfg, 5, amp=0.01, hot=12)
+    lat = lbm.Lattice(cfg)
+    lat.set_state(torch.tensor(f0, device="cuda"))
+    lat.profile(True)
+    lat.step(7)
+    prof = lat.profile_read()
+    lat.profile(False)
+    lat.step(6)
+    assert prof["step"][0] == 7 and prof["fixup"][0] == 7
+    assert prof["step"][1] > 0 and prof["fixup"][1] > 0
+    g, _ = gpu_run(cfg, f0, 13)
+    assert np.array_equal(lat.get_state(torch.float64).cpu().numpy(), g)
+    assert rel(g, O.step(cfg, f0, 13)) < TOL["fp64"]
