@@ -1060,21 +1060,81 @@ static void eq_partials(int lattice, int kind, double rho, double ux, double uy,
     }
 }
 
+/* Delta S at one site and its gradient dDelta S / df_j (Eq. DelS):
+ * Delta S = sum_i f_i ln(f_i / f*_i(f)), so
+ * dDelta S / df_j = ln(f_j / f*_j) + 1 - sum_i (f_i / f*_i) df*_i / df_j
+ * with df*_i / df_j = df*_i/drho + df*_i/du_x (v_jx - u_x)/rho + df*_i/du_y (v_jy - u_y)/rho. */
+static double delta_s_grad(const orc_config* cfg, const double* f, double* grad) {
+    int Q = orc_q(cfg->lattice);
+    int cx[9], cy[9];
+    double W[9], feq[9], dr[9], dx[9], dy[9], r, ux, uy;
+    orc_lattice(cfg->lattice, cx, cy, W);
+    orc_moments(cfg->lattice, f, &r, &ux, &uy);
+    orc_equilibrium(cfg->lattice, eq_kind(cfg), r, ux, uy, feq);
+    eq_partials(cfg->lattice, eq_kind(cfg), r, ux, uy, dr, dx, dy);
+    for (int j = 0; j < Q; ++j) {
+        double s = 0.0;
+        for (int i = 0; i < Q; ++i)
+            s += f[i] / feq[i] * (dr[i] + dx[i] * (cx[j] - ux) / r + dy[i] * (cy[j] - uy) / r);
+        grad[j] = log(f[j] / feq[j]) + 1.0 - s;
+    }
+    return orc_delta_s(Q, f, feq);
+}
+
+/* The window site whose Delta S is the lower median of the clipped window
+ * of site s (the value orc_median_field takes), with ties in Delta S
+ * ordered by the site index. */
+static long long median_site(const orc_config* cfg, int px, int py, const double* dS, long long s) {
+    int ry = cfg->lattice == ORC_D2Q9 ? 1 : 0;
+    int x = (int)(s % cfg->nx), y = (int)(s / cfg->nx);
+    long long w[9];
+    int n = 0;
+    for (int dy = -ry; dy <= ry; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+            int xx = x + dx, yy = y + dy;
+            if (px) xx = (xx + cfg->nx) % cfg->nx;
+            if (py) yy = (yy + cfg->ny) % cfg->ny;
+            if (xx < 0 || xx >= cfg->nx || yy < 0 || yy >= cfg->ny) continue;
+            long long v = (long long)yy * cfg->nx + xx;
+            int k = n++;
+            while (k > 0 && (dS[w[k - 1]] > dS[v] || (dS[w[k - 1]] == dS[v] && w[k - 1] > v))) {
+                w[k] = w[k - 1];
+                --k;
+            }
+            w[k] = v;
+        }
+    return w[(n - 1) / 2];
+}
+
+/* Branch codes of one site in one step of the tape (the selection that the
+ * adjoint holds fixed); every branch has the form F = f* + psi (f - f*):
+ *   AUX_LBGK          psi = 1 - 2 beta (Eq. CollisionIntegral)
+ *   AUX_FSTAR         psi = 0 (the Ehrenfest step of Section 4)
+ *   AUX_POS0 - k      the positivity rule of Eq. (StrLine) binding at
+ *                     population k: psi = f*_k / (f*_k - f_k)
+ *   m >= 0            the median filter of Section 4.4 with the window's
+ *                     lower median at site m: psi = (1 - 2 beta) sqrt(Delta S(m) / Delta S) */
+enum { AUX_LBGK = -1, AUX_FSTAR = -2, AUX_POS0 = -3 };
+
 int orc_adjoint_ke(const orc_config* cfg, const double* f0, int T, double* J, double* dJ_df0,
                    double* dJ_dU, double* dJ_dbeta) {
     if (!config_ok(cfg) || T < 0) return -1;
-    if (cfg->collision != ORC_LBGK && cfg->collision != ORC_EHRENFEST) return -1;
+    if (cfg->collision != ORC_LBGK && cfg->collision != ORC_EHRENFEST && cfg->collision != ORC_MEDIAN &&
+        cfg->collision != ORC_POSITIVITY)
+        return -1;
+    if (cfg->bc == ORC_BC_DIFFUSIVE) return -1;
     int Q = orc_q(cfg->lattice);
     long long N = (long long)cfg->nx * cfg->ny;
     size_t S = (size_t)(Q * N);
     double* tape = (double*)malloc(sizeof(double) * S * (size_t)(T + 1));
-    unsigned char* masks = (unsigned char*)calloc((size_t)N * (size_t)(T > 0 ? T : 1), 1);
+    long long* aux = (long long*)malloc(sizeof(long long) * (size_t)N * (size_t)(T > 0 ? T : 1));
+    unsigned char* mask = (unsigned char*)malloc((size_t)N);
     double* F = (double*)malloc(sizeof(double) * S);
     double* dS = (double*)malloc(sizeof(double) * (size_t)N);
     double* lam = (double*)malloc(sizeof(double) * S);
     double* Lam = (double*)malloc(sizeof(double) * S);
-    if (!tape || !masks || !F || !dS || !lam || !Lam) {
-        free(tape); free(masks); free(F); free(dS); free(lam); free(Lam);
+    if (!tape || !aux || !mask || !F || !dS || !lam || !Lam) {
+        free(tape); free(aux); free(mask); free(F); free(dS); free(lam); free(Lam);
         return -2;
     }
     int cx[9], cy[9];
@@ -1083,23 +1143,60 @@ int orc_adjoint_ke(const orc_config* cfg, const double* f0, int T, double* J, do
     int px, py;
     bc_periodicity(cfg, &px, &py);
     const int kind = eq_kind(cfg);
-    const double om = 2.0 * cfg->beta;
+    const double c = 1.0 - 2.0 * cfg->beta;
 
-    /* forward, keeping every pre-collision state and the selection masks */
+    /* forward, keeping every pre-collision state and each site's branch */
     memcpy(tape, f0, sizeof(double) * S);
     for (int t = 0; t < T; ++t) {
         const double* f = tape + (size_t)t * S;
-        unsigned char* mask = masks + (size_t)t * N;
+        long long* a = aux + (size_t)t * N;
+        for (long long s = 0; s < N; ++s) a[s] = AUX_LBGK;
+        if (cfg->collision == ORC_EHRENFEST || cfg->collision == ORC_MEDIAN) orc_delta_s_field(cfg, f, dS);
         if (cfg->collision == ORC_EHRENFEST) {
-            orc_delta_s_field(cfg, f, dS);
             orc_select_topk(dS, N, cfg->topk, cfg->delta, mask);
+            for (long long s = 0; s < N; ++s)
+                if (mask[s]) a[s] = AUX_FSTAR;
         }
+        /* the same arithmetic as orc_step, branch by branch */
         for (long long s = 0; s < N; ++s) {
-            double fs[9], feq[9];
+            double fs[9], feq[9], Fs[9];
             gather(Q, f, N, s, fs);
             site_equilibrium(cfg, fs, feq);
-            for (int i = 0; i < Q; ++i)
-                F[i * N + s] = mask[s] ? feq[i] : fs[i] + om * (feq[i] - fs[i]);
+            if (cfg->collision == ORC_LBGK || cfg->collision == ORC_POSITIVITY) {
+                lbgk(Q, cfg->beta, fs, feq, Fs);
+                if (cfg->collision == ORC_POSITIVITY) {
+                    /* the rule's binding population: the first i with the
+                     * smallest f*_i / (f*_i - F_i) over F_i < 0 */
+                    double lam_min = 1.0;
+                    int k = -1;
+                    for (int i = 0; i < Q; ++i)
+                        if (Fs[i] < 0.0) {
+                            double l = feq[i] / (feq[i] - Fs[i]);
+                            if (l < lam_min) {
+                                lam_min = l;
+                                k = i;
+                            }
+                        }
+                    if (k >= 0) {
+                        a[s] = AUX_POS0 - k;
+                        positivity(Q, feq, Fs);
+                    }
+                }
+            } else {
+                double phi = a[s] == AUX_FSTAR ? 0.0 : 1.0;
+                if (cfg->collision == ORC_MEDIAN && dS[s] > cfg->delta) {
+                    long long m = median_site(cfg, px, py, dS, s);
+                    if (dS[m] < dS[s]) {
+                        a[s] = m;
+                        phi = isinf(dS[s]) ? 0.0 : sqrt(dS[m] / dS[s]);
+                    }
+                }
+                for (int i = 0; i < Q; ++i) {
+                    double fl = feq[i] + phi * (fs[i] - feq[i]);
+                    Fs[i] = fl + 2.0 * cfg->beta * (feq[i] - fl);
+                }
+            }
+            for (int i = 0; i < Q; ++i) F[i * N + s] = Fs[i];
         }
         orc_stream(cfg, F, tape + (size_t)(t + 1) * S);
     }
@@ -1134,11 +1231,14 @@ int orc_adjoint_ke(const orc_config* cfg, const double* f0, int T, double* J, do
                     }
                 }
         }
-        /* transpose of the collision at every site */
+        /* transpose of the collision F = f* + psi (f - f*) at every site:
+         * dF_i/df_j = (1 - psi) df*_i/df_j + psi delta_ij + (f_i - f*_i) dpsi/df_j,
+         * dF_i/dbeta = (f_i - f*_i) dpsi/dbeta; the median's psi also depends
+         * on the state at its window site m (added there) */
         const double* f = tape + (size_t)t * S;
-        const unsigned char* mask = masks + (size_t)t * N;
+        const long long* a = aux + (size_t)t * N;
         for (long long s = 0; s < N; ++s) {
-            double fs[9], feq[9], dr[9], dx[9], dy[9], r, ux, uy, L[9];
+            double fs[9], feq[9], dr[9], dx[9], dy[9], r, ux, uy, L[9], dfk[9];
             gather(Q, f, N, s, fs);
             gather(Q, Lam, N, s, L);
             orc_moments(cfg->lattice, fs, &r, &ux, &uy);
@@ -1146,23 +1246,69 @@ int orc_adjoint_ke(const orc_config* cfg, const double* f0, int T, double* J, do
             eq_partials(cfg->lattice, kind, r, ux, uy, dr, dx, dy);
             /* a_j = sum_i L_i df*_i/df_j with drho/df_j = 1,
              * du_x/df_j = (v_jx - u_x)/rho, du_y/df_j = (v_jy - u_y)/rho */
-            double A = 0.0, Bx = 0.0, By = 0.0;
+            double A = 0.0, Bx = 0.0, By = 0.0, g = 0.0;
             for (int i = 0; i < Q; ++i) {
                 A += L[i] * dr[i];
                 Bx += L[i] * dx[i];
                 By += L[i] * dy[i];
+                g += L[i] * (fs[i] - feq[i]);
+            }
+            double psi = c, dpsi_db = -2.0, dpsi[9] = {0.0};
+            if (a[s] == AUX_FSTAR) {
+                psi = 0.0;
+                dpsi_db = 0.0;
+            } else if (a[s] <= AUX_POS0) {
+                /* psi = f*_k / (f*_k - f_k): independent of beta */
+                int k = (int)(AUX_POS0 - a[s]);
+                double D = feq[k] - fs[k];
+                psi = feq[k] / D;
+                dpsi_db = 0.0;
+                for (int j = 0; j < Q; ++j) {
+                    dfk[j] = dr[k] + dx[k] * (cx[j] - ux) / r + dy[k] * (cy[j] - uy) / r;
+                    dpsi[j] = (-fs[k] * dfk[j] + (j == k ? feq[k] : 0.0)) / (D * D);
+                }
+            } else if (a[s] >= 0) {
+                /* psi = c sqrt(M / C), C = Delta S here, M = Delta S at m */
+                double gradC[9], gradM[9], fm[9];
+                double C = delta_s_grad(cfg, fs, gradC);
+                gather(Q, f, N, a[s], fm);
+                double M = delta_s_grad(cfg, fm, gradM);
+                double phi = isinf(C) ? 0.0 : sqrt(M / C);
+                psi = c * phi;
+                dpsi_db = -2.0 * phi;
+                if (!isinf(C) && M > 0.0) {
+                    for (int j = 0; j < Q; ++j) dpsi[j] = -c * phi / (2.0 * C) * gradC[j];
+                }
             }
             for (int j = 0; j < Q; ++j) {
-                double a = A + Bx * (cx[j] - ux) / r + By * (cy[j] - uy) / r;
-                lam[j * N + s] = mask[s] ? a : (1.0 - om) * L[j] + om * a;
+                double aj = A + Bx * (cx[j] - ux) / r + By * (cy[j] - uy) / r;
+                lam[j * N + s] = (1.0 - psi) * aj + psi * L[j] + g * dpsi[j];
             }
-            if (!mask[s])
-                for (int i = 0; i < Q; ++i) gB += L[i] * 2.0 * (feq[i] - fs[i]);
+            gB += g * dpsi_db;
+        }
+        /* median: psi of a selected site s depends on f at its median site m
+         * through M = Delta S(m): dpsi/df(m)_j = c phi / (2 M) dM/df(m)_j */
+        if (cfg->collision == ORC_MEDIAN) {
+            for (long long s = 0; s < N; ++s) {
+                if (a[s] < 0) continue;
+                double fs[9], feq[9], L[9], fm[9], gradM[9];
+                gather(Q, f, N, s, fs);
+                gather(Q, Lam, N, s, L);
+                site_equilibrium(cfg, fs, feq);
+                double g = 0.0;
+                for (int i = 0; i < Q; ++i) g += L[i] * (fs[i] - feq[i]);
+                double C = orc_delta_s(Q, fs, feq);
+                gather(Q, f, N, a[s], fm);
+                double M = delta_s_grad(cfg, fm, gradM);
+                if (isinf(C) || !(M > 0.0)) continue;
+                double phi = sqrt(M / C);
+                for (int j = 0; j < Q; ++j) lam[j * N + a[s]] += g * c * phi / (2.0 * M) * gradM[j];
+            }
         }
     }
     memcpy(dJ_df0, lam, sizeof(double) * S);
     *dJ_dU = gU;
     *dJ_dbeta = gB;
-    free(tape); free(masks); free(F); free(dS); free(lam); free(Lam);
+    free(tape); free(aux); free(mask); free(F); free(dS); free(lam); free(Lam);
     return 0;
 }

@@ -181,11 +181,16 @@ void orc_stream(const orc_config* cfg, const double* F, double* fnew);
 double orc_kinetic_energy(const orc_config* cfg, const double* f);
 
 /* Tape-based reverse-mode gradient of J(f_T) = 1/2 sum_x rho |u|^2 after
- * T steps from f0, for the LBGK and Ehrenfest collisions (the Ehrenfest
- * selection of each step is held fixed: the selected branch F = f* is
- * differentiated).  Outputs J, dJ/df0 (same layout as f0), dJ/d lid_u and
- * dJ/d beta.  Returns 0, -1 for an unsupported configuration, -2 on
- * allocation failure. */
+ * T steps from f0, for the LBGK, Ehrenfest, median-filter and positivity
+ * collisions (no diffusive walls).  The selection of each step is held
+ * fixed and the selected branch differentiated: F = f* at the Ehrenfest
+ * sites; F = f* + (1 - 2 beta) sqrt(M / C) (f - f*) at the median's sites,
+ * with C = Delta S of the site and M = Delta S of the window site holding
+ * the lower median (ties by site index) both differentiated; F = f* +
+ * f*_k / (f*_k - f_k) (f - f*) where the positivity rule binds at population
+ * k.  Outputs J, dJ/df0 (same layout as f0), dJ/d lid_u and dJ/d beta.
+ * Returns 0, -1 for an unsupported configuration, -2 on allocation
+ * failure. */
 int orc_adjoint_ke(const orc_config* cfg, const double* f0, int T, double* J, double* dJ_df0,
                    double* dJ_dU, double* dJ_dbeta);
 

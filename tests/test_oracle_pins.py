@@ -622,12 +622,15 @@ def test_kinetic_energy_closed_forms():
     assert O.kinetic_energy(c, rest) < 1e-30  # rounding of the momentum sums only
 
 
-@pytest.mark.parametrize("case", ["cavity_lbgk", "cavity_ehrenfest", "tube", "periodic"])
+@pytest.mark.parametrize("case", ["cavity_lbgk", "cavity_ehrenfest", "tube", "periodic", "cavity_median",
+                                  "periodic_median", "tube_median", "cavity_positivity", "tube_positivity"])
 def test_oracle_adjoint_matches_central_differences(case):
     """The tape adjoint of J = 1/2 sum rho |u|^2 after T steps against central
     differences of the oracle's own forward run (U, beta and a random
-    direction in f0).  For the Ehrenfest case the step h is small enough that
-    no selection changes, so the selected branch is what is differentiated."""
+    direction in f0).  For the Ehrenfest, median and positivity cases the step
+    h is small enough that no selection changes (nor the median's window site
+    or the positivity rule's binding population), so the selected branch is
+    what is differentiated."""
     cfgs = {
         "cavity_lbgk": dict(lattice="D2Q9", nx=12, ny=10, bc="cavity", lid_u=0.1,
                             collision="lbgk", beta=0.9),
@@ -636,6 +639,17 @@ def test_oracle_adjoint_matches_central_differences(case):
         "tube": dict(lattice="D1Q3", nx=40, ny=1, bc="ends", collision="lbgk", beta=0.97),
         "periodic": dict(lattice="D2Q9", nx=9, ny=7, bc="periodic", collision="ehrenfest",
                          beta=0.92, topk=2, delta=1e-4, equilibrium="entropic"),
+        # the median filter of Section 4.4 (the window's median site held fixed)
+        "cavity_median": dict(lattice="D2Q9", nx=12, ny=10, bc="cavity", lid_u=0.1,
+                              collision="median", beta=0.9, delta=1e-4),
+        "periodic_median": dict(lattice="D2Q9", nx=9, ny=7, bc="periodic", collision="median",
+                                beta=0.95, delta=5e-5, equilibrium="entropic"),
+        "tube_median": dict(lattice="D1Q3", nx=40, ny=1, bc="ends", collision="median", beta=0.97,
+                            delta=1e-4),
+        # the positivity rule of Eq. (StrLine) (its binding population held fixed)
+        "cavity_positivity": dict(lattice="D2Q9", nx=12, ny=10, bc="cavity", lid_u=0.1,
+                                  collision="positivity", beta=0.99),
+        "tube_positivity": dict(lattice="D1Q3", nx=40, ny=1, bc="ends", collision="positivity", beta=0.99),
     }
     cfg = cfgs[case]
     ny, nx = cfg["ny"], cfg["nx"]
@@ -643,12 +657,19 @@ def test_oracle_adjoint_matches_central_differences(case):
     f0 = O.init_equilibrium(dict(cfg, collision="lbgk"), fl["rho"], fl["ux"],
                             None if cfg["lattice"] == "D1Q3" else fl["uy"])
     f0 = f0 * WL.lognormal_factors(f0.shape, 5, 0.02)
-    f0 = f0 * WL.lognormal_factors(f0.shape, 6, 1.0) ** (WL.hot_spots(ny, nx, 7, 4, 0.4)[None])
+    hot = 1.2 if cfg["collision"] == "positivity" else 0.4  # strong enough to make F_i < 0
+    f0 = f0 * WL.lognormal_factors(f0.shape, 6, 1.0) ** (WL.hot_spots(ny, nx, 7, 4, hot)[None])
     T = 25
+    if cfg["collision"] in ("median", "positivity"):
+        _, st = O.step(cfg, f0, T, stats=True)
+        assert st["limited_sites"] > 0  # the branch is exercised
     J, g, gU, gB = O.adjoint_ke(cfg, f0, T)
     KE = lambda c, f: O.kinetic_energy(c, O.step(c, f, T))
     assert abs(J - KE(cfg, f0)) < 1e-15 * abs(J) + 1e-300
-    h = 1e-6
+    # the median's window sites are close in Delta S at a few sites here: a
+    # step of 1e-6 along a random direction in f0 moves one of them across
+    # another (FD then measures that jump), 1e-7 stays on the branch
+    h = 1e-7 if cfg["collision"] == "median" else 1e-6
     if cfg["bc"] == "cavity":
         fd = (KE(dict(cfg, lid_u=cfg["lid_u"] + h), f0) - KE(dict(cfg, lid_u=cfg["lid_u"] - h), f0)) / (2 * h)
         assert abs(gU - fd) <= 1e-7 * abs(fd) + 1e-12
