@@ -169,6 +169,21 @@ typedef struct {
  * lim_k = 1, lim_dst = 1e-3, lim_delta0 = 0.01. */
 lbm_status lbm_config_default(lbm_config* cfg);
 
+/* MRT relaxation rates of the presets of Sections 5, 7 and 8, written into
+ * cfg->s_e, s_eps, s_q with s_nu = 2 beta (beta = cfg->beta, or 1/(6 nu + 1)
+ * when cfg->beta <= 0); the other fields are left as they are.  Use with
+ * collision = LBM_MRT.
+ *   LBM_MRT_PRESET_TRT   two relaxation times (Section 5): s_e = s_eps = s_nu,
+ *                        s_q = 8 (2 - s_nu) / (8 - s_nu) (the printed
+ *                        "8(2=s_nu)/(8-s_nu)" read with a minus sign)
+ *   LBM_MRT_PRESET_MRT   s_e = 1.64, s_eps = 1.54, s_q as for TRT (Section 8)
+ *   LBM_MRT_PRESET_MRT1  s_e = 1.64, s_eps = 1.54, s_q = 1.9 (Section 8)
+ *   LBM_MRT_PRESET_LL    s_e = 1.64, s_eps = 1.54, s_q = 3 (2 - s_nu) / (3 - s_nu),
+ *                        the A_1 rates of Section 7's shear-decay comparison
+ * LBM_ERR_ARG for a NULL cfg, an unknown preset or beta outside (0, 1]. */
+enum { LBM_MRT_PRESET_TRT = 0, LBM_MRT_PRESET_MRT = 1, LBM_MRT_PRESET_MRT1 = 2, LBM_MRT_PRESET_LL = 3 };
+lbm_status lbm_mrt_preset(lbm_config* cfg, int preset);
+
 /* Device bytes needed for cfg (populations + scratch).  Fails with
  * LBM_ERR_ARG for an invalid configuration. */
 lbm_status lbm_required_bytes(const lbm_config* cfg, size_t* bytes);
@@ -287,21 +302,27 @@ lbm_status lbm_batch_stats(lbm_batch* b, int instance, lbm_stats* out, void* str
 const char* lbm_batch_last_error(const lbm_batch* b);
 
 /* ---- Adjoint: reverse-mode gradient ---------------------------------------
- * For the LBGK and Ehrenfest collisions: the gradient of a functional J of
- * the state f_T after T steps with respect to the initial populations f_0,
- * the lid velocity (lid_u) and beta.  J defaults to the kinetic energy
- * 1/2 sum_x rho |u|^2; any J is served by passing its gradient dJ/df_T as
- * `seed`.  Per step the adjoint is the transpose of the streaming (walls and
- * moving-lid term included) and of the collision's Jacobian; at the sites
- * the Ehrenfest step sent to f* the selected branch F = f* is differentiated
- * (the selection of each step is held fixed).  Checkpoint and recompute:
- * the forward pass keeps a dense copy of the state every K steps; the
- * backward pass, segment by segment from the last, recomputes the K states
- * and selections and runs K adjoint steps.  `work` is caller DEVICE memory
+ * For the LBGK, Ehrenfest, median-filter and positivity collisions (no
+ * diffusive walls): the gradient of a functional J of the state f_T after T
+ * steps with respect to the initial populations f_0, the lid velocity
+ * (lid_u) and beta.  J defaults to the kinetic energy 1/2 sum_x rho |u|^2;
+ * any J is served by passing its gradient dJ/df_T as `seed`.  Per step the
+ * adjoint is the transpose of the streaming (walls and moving-lid term
+ * included) and of the collision's Jacobian.  Through the limiters the
+ * selected branch is differentiated with the selection of each step held
+ * fixed: F = f* at the sites the Ehrenfest step selected (Section 4);
+ * F = f* + (1 - 2 beta) sqrt(M / C) (f - f*) at the median filter's sites
+ * (Section 4.4, Eq. entrHom), through both C = Delta S of the site and
+ * M = Delta S of the window site holding the lower median (ties by site
+ * index); F = f* + f*_k / (f*_k - f_k) (f - f*) where the positivity rule
+ * (Eq. StrLine) binds at population k.  Checkpoint and recompute: the
+ * forward pass keeps a dense copy of the state every K steps; the backward
+ * pass, segment by segment from the last, recomputes the K states and each
+ * site's branch and runs K adjoint steps.  `work` is caller DEVICE memory
  * of lbm_adjoint_required_bytes (256-byte aligned): ceil(T/K) checkpoints,
- * K segment states, K selection masks (Ehrenfest), two adjoint buffers and
- * the final state, dense in the arithmetic type (double for FP64 storage,
- * float otherwise).  Nothing is allocated. */
+ * K segment states, K branch records of one int per site (limiters), two
+ * adjoint buffers and the final state, dense in the arithmetic type (double
+ * for FP64 storage, float otherwise).  Nothing is allocated. */
 lbm_status lbm_adjoint_required_bytes(const lbm_config* cfg, int T, int K, size_t* bytes);
 /* Advances ctx T steps from its current state (which must be at an even step
  * count) keeping the checkpoints; *J_host (if not NULL) receives the kinetic
@@ -362,8 +383,12 @@ lbm_status lbm_profile_read(lbm_ctx* ctx, int* launches, double* ms);
  * last call's contents (the counters are cleared at the start of each call):
  * calls that overlap on the GPU (other streams, other host threads) race and
  * must be serialised by the caller.  Returns LBM_ERR_ARG for an invalid
- * configuration, an odd nsteps or another collision, LBM_ERR_CUDA when a
- * CUDA call fails. */
+ * configuration (the checks of lbm_create), an odd nsteps, another collision
+ * or diffusive walls, LBM_ERR_CUDA when a CUDA call fails.  The call does
+ * not wait for its kernels, so it cannot report what they find: a diverged
+ * state (non-finite or non-positive density) is not reported, and neither
+ * are the limiter statistics; a caller that needs them uses lbm_create and
+ * lbm_stats_get. */
 #define LBM_NOALLOC_SCRATCH_BYTES (32u << 20)
 lbm_status lbm_ehrenfest_step_noalloc(const lbm_config* cfg, void* f, int nsteps, void* stream);
 

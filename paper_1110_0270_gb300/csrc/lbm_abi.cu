@@ -13,6 +13,7 @@
 #include "lbm.h"
 #include "lbm_ctx.h"
 #include "lbm_kernels.cuh"
+#include "lbm_setup.h"
 
 using namespace lbm;
 
@@ -21,34 +22,6 @@ extern template struct Launch<StF64>;
 extern template struct Launch<StF32>;
 extern template struct Launch<StBF16>;
 extern template struct Launch<StF16>;
-}  // namespace lbm
-
-namespace {
-
-constexpr size_t kAlign = 256;
-
-size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
-
-size_t storage_bytes(int precision) {
-    return precision == LBM_FP64 ? 8 : (precision == LBM_FP32 ? 4 : 2);
-}
-size_t math_bytes(int precision) { return precision == LBM_FP64 ? 8 : 4; }
-
-// collisions with a candidate list and a follow-up kernel
-bool limiter(int coll) {
-    return coll == LBM_EHRENFEST || coll == LBM_MEDIAN || coll == LBM_THRESHOLD || coll == LBM_MRT_LIMITER;
-}
-// collisions that reduce over the lattice each step
-bool reduces(int coll) { return coll == LBM_ENSEMBLE || coll == LBM_THRESHOLD; }
-
-struct Layout {
-    int Q, pitch;
-    int64_t plane;
-    size_t f_off, f_bytes, cnt_off, cand_f_off, cand_ds_off, cand_site_off, cand_sel_off,
-        field_off, red_off, staging_off, total;
-    int cand_cap;
-};
-
 const char* check_config(const lbm_config* c) {
     if (!c) return "config is NULL";
     if (c->lattice != LBM_D1Q3 && c->lattice != LBM_D2Q9) return "lattice must be LBM_D1Q3 or LBM_D2Q9";
@@ -90,6 +63,91 @@ const char* check_config(const lbm_config* c) {
     }
     return nullptr;
 }
+
+
+double config_beta(const lbm_config* c) { return c->beta > 0 ? c->beta : 1.0 / (6.0 * c->nu + 1.0); }
+
+void fill_params(const lbm_config* cfg, int nsm, Params& p) {
+    p.nx = cfg->nx;
+    p.ny = cfg->ny;
+    p.periodic_x = cfg->bc == LBM_BC_PERIODIC || cfg->bc == LBM_BC_CHANNEL;
+    p.periodic_y = cfg->bc == LBM_BC_PERIODIC;
+    p.eq = cfg->equilibrium;
+    p.lid_u = (cfg->bc == LBM_BC_CAVITY || cfg->bc == LBM_BC_CHANNEL) ? cfg->lid_u : 0.0;
+    p.diffusive = cfg->bc == LBM_BC_DIFFUSIVE;
+    p.wall_u = p.diffusive ? cfg->lid_u : 0.0;
+    p.beta = config_beta(cfg);
+    p.topk = cfg->topk;
+    p.delta = cfg->delta;
+    p.beta_f = (float)p.beta;
+    p.lid_u_f = (float)p.lid_u;
+    p.delta_f = (float)cfg->delta;
+    const double snu = 2.0 * p.beta;
+    p.mrt.e = cfg->s_e / 36.0;
+    p.mrt.eps = cfg->s_eps / 36.0;
+    p.mrt.q = cfg->s_q / 12.0;
+    p.mrt.nu = snu / 4.0;
+    p.mrt_f = {(float)p.mrt.e, (float)p.mrt.eps, (float)p.mrt.q, (float)p.mrt.nu};
+    p.elbm_eps = cfg->elbm_eps;
+    p.elbm_max_iter = cfg->elbm_max_iter;
+    p.elbm_norm = cfg->elbm_norm;
+    p.elbm_fallback = cfg->elbm_fallback;
+    // the rounding of FP32 (or coarser) storage alone leaves Delta S up to
+    // 2^-49 rho: below that the state is at equilibrium as far as the
+    // storage can tell, and the LBGK step is taken as for Delta S < 1e-15
+    p.elbm_skip_rel = cfg->precision == LBM_FP64 ? 0.0 : 0x1p-48;
+    p.lim_alpha = cfg->lim_alpha;
+    p.lim_k = cfg->lim_k;
+    p.lim_dst = cfg->lim_dst;
+    p.lim_delta0 = cfg->lim_delta0;
+    // the limiter constants in FP32, so the 16/32-bit step kernels convert
+    // no FP64 parameter per site (GB300's FP64 pipe is narrow)
+    p.lim_f[0] = (float)cfg->lim_alpha;
+    p.lim_f[1] = (float)cfg->lim_k;
+    p.lim_f[2] = cfg->lim_dst > 0.0 ? (float)(1.0 / cfg->lim_dst) : 0.f;
+    p.lim_f[3] = cfg->lim_k > 0.0 ? (float)(-0.5 / cfg->lim_k) : 0.f;
+    // median filter: with 1 - 2 beta away from 0 the window's Delta S is
+    // recovered from the post-collision state, f - f* = (F - f*) / (1 - 2 beta),
+    // and the step writes no Delta S field (median_recon_fixup).  The
+    // recovery multiplies the stored rounding of F by 1 / |1 - 2 beta|: up to
+    // 16 for FP32 / FP64 storage, up to 4 for the 16-bit formats, whose own
+    // rounding is coarser; closer to beta = 1/2 the step writes the field.
+    p.median_inv = 0.0;
+    if (cfg->collision == LBM_MEDIAN) {
+        const bool wide = cfg->precision == LBM_FP64 || cfg->precision == LBM_FP32;
+        const double b = cfg->precision == LBM_FP64 ? p.beta : (double)p.beta_f;
+        if (std::fabs(1.0 - 2.0 * b) >= (wide ? 1.0 / 16 : 0.25)) p.median_inv = 1.0 / (1.0 - 2.0 * b);
+    }
+    p.pipe_ctas = 8 * nsm;
+}
+
+}  // namespace lbm
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+size_t storage_bytes(int precision) {
+    return precision == LBM_FP64 ? 8 : (precision == LBM_FP32 ? 4 : 2);
+}
+size_t math_bytes(int precision) { return precision == LBM_FP64 ? 8 : 4; }
+
+// collisions with a candidate list and a follow-up kernel
+bool limiter(int coll) {
+    return coll == LBM_EHRENFEST || coll == LBM_MEDIAN || coll == LBM_THRESHOLD || coll == LBM_MRT_LIMITER;
+}
+// collisions that reduce over the lattice each step
+bool reduces(int coll) { return coll == LBM_ENSEMBLE || coll == LBM_THRESHOLD; }
+
+struct Layout {
+    int Q, pitch;
+    int64_t plane;
+    size_t f_off, f_bytes, cnt_off, cand_f_off, cand_ds_off, cand_site_off, cand_sel_off,
+        field_off, red_off, staging_off, total;
+    int cand_cap;
+};
 
 Layout layout(const lbm_config* c) {
     Layout L;
@@ -336,6 +394,38 @@ lbm_status lbm_config_default(lbm_config* c) {
     return LBM_OK;
 }
 
+lbm_status lbm_mrt_preset(lbm_config* cfg, int preset) {
+    if (!cfg) return LBM_ERR_ARG;
+    const double beta = cfg->beta > 0 ? cfg->beta : (cfg->nu > 0 ? 1.0 / (6.0 * cfg->nu + 1.0) : -1.0);
+    if (!(beta > 0.0 && beta <= 1.0)) return LBM_ERR_ARG;
+    const double snu = 2.0 * beta;
+    // the "magic" relation of Section 5's TRT, s_q = 8 (2 - s_nu) / (8 - s_nu)
+    const double sq_trt = 8.0 * (2.0 - snu) / (8.0 - snu);
+    switch (preset) {
+        case LBM_MRT_PRESET_TRT:
+            cfg->s_e = snu;
+            cfg->s_eps = snu;
+            cfg->s_q = sq_trt;
+            return LBM_OK;
+        case LBM_MRT_PRESET_MRT:
+            cfg->s_e = 1.64;
+            cfg->s_eps = 1.54;
+            cfg->s_q = sq_trt;
+            return LBM_OK;
+        case LBM_MRT_PRESET_MRT1:
+            cfg->s_e = 1.64;
+            cfg->s_eps = 1.54;
+            cfg->s_q = 1.9;
+            return LBM_OK;
+        case LBM_MRT_PRESET_LL:
+            cfg->s_e = 1.64;
+            cfg->s_eps = 1.54;
+            cfg->s_q = 3.0 * (2.0 - snu) / (3.0 - snu);
+            return LBM_OK;
+    }
+    return LBM_ERR_ARG;
+}
+
 lbm_status lbm_required_bytes(const lbm_config* cfg, size_t* bytes) {
     if (!bytes || check_config(cfg)) return LBM_ERR_ARG;
     *bytes = layout(cfg).total;
@@ -352,7 +442,7 @@ lbm_status lbm_create(const lbm_config* cfg, void* dev_mem, size_t bytes, lbm_ct
     lbm_ctx* ctx = new (std::nothrow) lbm_ctx();
     if (!ctx) return LBM_ERR_OOM;
     ctx->cfg = *cfg;
-    if (!(ctx->cfg.beta > 0)) ctx->cfg.beta = 1.0 / (6.0 * cfg->nu + 1.0);
+    ctx->cfg.beta = config_beta(cfg);
     ctx->Q = L.Q;
     ctx->base = (char*)dev_mem;
     ctx->bytes = bytes;
@@ -364,48 +454,11 @@ lbm_status lbm_create(const lbm_config* cfg, void* dev_mem, size_t bytes, lbm_ct
     }
     Params& p = ctx->p;
     std::memset(&p, 0, sizeof p);
+    fill_params(&ctx->cfg, ctx->nsm, p);
     p.f = ctx->base + L.f_off;
     p.plane = L.plane;
     p.plane32 = (int)L.plane;
     p.pitch = L.pitch;
-    p.nx = cfg->nx;
-    p.ny = cfg->ny;
-    p.periodic_x = cfg->bc == LBM_BC_PERIODIC || cfg->bc == LBM_BC_CHANNEL;
-    p.periodic_y = cfg->bc == LBM_BC_PERIODIC;
-    p.eq = cfg->equilibrium;
-    p.lid_u = (cfg->bc == LBM_BC_CAVITY || cfg->bc == LBM_BC_CHANNEL) ? cfg->lid_u : 0.0;
-    p.diffusive = cfg->bc == LBM_BC_DIFFUSIVE;
-    p.wall_u = p.diffusive ? cfg->lid_u : 0.0;
-    p.beta = ctx->cfg.beta;
-    p.topk = cfg->topk;
-    p.delta = cfg->delta;
-    p.beta_f = (float)p.beta;
-    p.lid_u_f = (float)p.lid_u;
-    p.delta_f = (float)cfg->delta;
-    const double snu = 2.0 * p.beta;
-    p.mrt.e = cfg->s_e / 36.0;
-    p.mrt.eps = cfg->s_eps / 36.0;
-    p.mrt.q = cfg->s_q / 12.0;
-    p.mrt.nu = snu / 4.0;
-    p.mrt_f = {(float)p.mrt.e, (float)p.mrt.eps, (float)p.mrt.q, (float)p.mrt.nu};
-    p.elbm_eps = cfg->elbm_eps;
-    p.elbm_max_iter = cfg->elbm_max_iter;
-    p.elbm_norm = cfg->elbm_norm;
-    p.elbm_fallback = cfg->elbm_fallback;
-    // the rounding of FP32 (or coarser) storage alone leaves Delta S up to
-    // 2^-49 rho: below that the state is at equilibrium as far as the
-    // storage can tell, and the LBGK step is taken as for Delta S < 1e-15
-    p.elbm_skip_rel = cfg->precision == LBM_FP64 ? 0.0 : 0x1p-48;
-    p.lim_alpha = cfg->lim_alpha;
-    p.lim_k = cfg->lim_k;
-    p.lim_dst = cfg->lim_dst;
-    p.lim_delta0 = cfg->lim_delta0;
-    // the limiter constants in FP32, so the 16/32-bit step kernels convert
-    // no FP64 parameter per site (GB300's FP64 pipe is narrow)
-    p.lim_f[0] = (float)cfg->lim_alpha;
-    p.lim_f[1] = (float)cfg->lim_k;
-    p.lim_f[2] = cfg->lim_dst > 0.0 ? (float)(1.0 / cfg->lim_dst) : 0.f;
-    p.lim_f[3] = cfg->lim_k > 0.0 ? (float)(-0.5 / cfg->lim_k) : 0.f;
     p.counters = (unsigned*)(ctx->base + L.cnt_off);
     p.stats = (unsigned long long*)(ctx->base + L.cnt_off + CNT_WORDS * 4);
     p.scratch_d = (double*)(ctx->base + L.cnt_off + CNT_WORDS * 4 + ST_WORDS * 8);
@@ -415,19 +468,11 @@ lbm_status lbm_create(const lbm_config* cfg, void* dev_mem, size_t bytes, lbm_ct
     p.cand_site = (int*)(ctx->base + L.cand_site_off);
     p.cand_sel = (int*)(ctx->base + L.cand_sel_off);
     p.ds_field = ctx->base + L.field_off;
-    // median filter: with FP32 or FP64 storage and 1 - 2 beta away from 0 the
-    // window's Delta S is recovered from the post-collision state and the
-    // step writes no Delta S field (median_recon_fixup)
-    if (cfg->collision == LBM_MEDIAN && (cfg->precision == LBM_FP64 || cfg->precision == LBM_FP32)) {
-        const double b = cfg->precision == LBM_FP64 ? p.beta : (double)p.beta_f;
-        if (std::fabs(1.0 - 2.0 * b) >= 1.0 / 16) p.median_inv = 1.0 / (1.0 - 2.0 * b);
-    }
     if (reduces(cfg->collision)) {
         p.red = (double*)(ctx->base + L.red_off);
         p.lim_E = p.red + 2 * kRedSlots;
         p.lim_E_f = (float*)(p.lim_E + 1);
     }
-    p.pipe_ctas = 8 * ctx->nsm;
     ctx->staging = (double*)(ctx->base + L.staging_off);
     cudaError_t e = cudaMemset(ctx->base + L.cnt_off, 0, align_up(CNT_WORDS * 4 + ST_WORDS * 8 + 64));
     if (e == cudaSuccess && reduces(cfg->collision))

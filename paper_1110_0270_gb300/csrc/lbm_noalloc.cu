@@ -9,6 +9,7 @@
 
 #include "lbm.h"
 #include "lbm_kernels.cuh"
+#include "lbm_setup.h"
 
 using namespace lbm;
 
@@ -64,20 +65,12 @@ cudaError_t scratch_address(void** out) {
 extern "C" lbm_status lbm_ehrenfest_step_noalloc(const lbm_config* cfg, void* f, int nsteps,
                                                  void* stream) {
     if (!cfg || !f || nsteps < 0 || (nsteps & 1)) return LBM_ERR_ARG;
-    if (cfg->collision != LBM_EHRENFEST) return LBM_ERR_ARG;
-    if (cfg->lattice != LBM_D1Q3 && cfg->lattice != LBM_D2Q9) return LBM_ERR_ARG;
-    if (cfg->nx < 1 || cfg->ny < 1 || (cfg->lattice == LBM_D1Q3 && cfg->ny != 1)) return LBM_ERR_ARG;
-    if (cfg->precision < LBM_FP64 || cfg->precision > LBM_FP16_DEV) return LBM_ERR_ARG;
-    if (cfg->bc < LBM_BC_CAVITY || cfg->bc > LBM_BC_CHANNEL) return LBM_ERR_ARG;
-    if (cfg->lattice == LBM_D1Q3 && cfg->bc == LBM_BC_CHANNEL) return LBM_ERR_ARG;
-    if (cfg->ny > 65535LL * kBlockY) return LBM_ERR_ARG;
-    if (cfg->equilibrium < LBM_EQ_POLY_PRODUCT || cfg->equilibrium > LBM_EQ_POLY_STD) return LBM_ERR_ARG;
-    if (cfg->topk < 0 || !(cfg->delta >= 0.0)) return LBM_ERR_ARG;
-    const double beta = cfg->beta > 0 ? cfg->beta : (cfg->nu > 0 ? 1.0 / (6.0 * cfg->nu + 1.0) : -1.0);
-    if (!(beta > 0.0 && beta <= 1.0)) return LBM_ERR_ARG;
+    // the checks of lbm_create, then what this entry point does not cover:
+    // other collisions and the diffusive walls (their wall kernel)
+    if (check_config(cfg)) return LBM_ERR_ARG;
+    if (cfg->collision != LBM_EHRENFEST || cfg->bc == LBM_BC_DIFFUSIVE) return LBM_ERR_ARG;
     const int Q = cfg->lattice == LBM_D1Q3 ? 3 : 9;
     const size_t N = (size_t)cfg->nx * cfg->ny;
-    if ((long long)Q * (long long)N >= 0x7fffffffLL) return LBM_ERR_OOM;
     if (scratch_need(Q, N, cfg->precision) > (size_t)LBM_NOALLOC_SCRATCH_BYTES) return LBM_ERR_OOM;
 
     void* scratch = nullptr;
@@ -87,25 +80,15 @@ extern "C" lbm_status lbm_ehrenfest_step_noalloc(const lbm_config* cfg, void* f,
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return LBM_ERR_CUDA;
 
-    // dense caller layout: pitch = nx, one plane of ny * nx per direction
+    // the parameters lbm_create derives from cfg; the layout is the caller's
+    // dense one: pitch = nx, one plane of ny * nx per direction
     Params p;
     std::memset(&p, 0, sizeof p);
+    fill_params(cfg, nsm, p);
     p.f = f;
     p.plane = (int64_t)N;
     p.plane32 = (int)N;
     p.pitch = cfg->nx;
-    p.nx = cfg->nx;
-    p.ny = cfg->ny;
-    p.periodic_x = cfg->bc == LBM_BC_PERIODIC || cfg->bc == LBM_BC_CHANNEL;
-    p.periodic_y = cfg->bc == LBM_BC_PERIODIC;
-    p.eq = cfg->equilibrium;
-    p.lid_u = (cfg->bc == LBM_BC_CAVITY || cfg->bc == LBM_BC_CHANNEL) ? cfg->lid_u : 0.0;
-    p.beta = beta;
-    p.beta_f = (float)beta;
-    p.lid_u_f = (float)p.lid_u;
-    p.delta = cfg->delta;
-    p.delta_f = (float)cfg->delta;
-    p.topk = cfg->topk;
     char* s = (char*)scratch;
     p.counters = (unsigned*)s;
     p.stats = (unsigned long long*)(s + CNT_WORDS * 4);

@@ -39,7 +39,8 @@ EXPORTS = ["lbm_config_default", "lbm_required_bytes", "lbm_create", "lbm_destro
            "lbm_batch_destroy", "lbm_batch_init_uniform", "lbm_batch_set_state",
            "lbm_batch_get_state", "lbm_batch_step", "lbm_batch_stats", "lbm_batch_last_error",
            "lbm_adjoint_required_bytes", "lbm_adjoint_forward", "lbm_adjoint_backward",
-           "lbm_fp64_rates", "lbm_enstrophy", "lbm_probe_set", "lbm_probe_count"]
+           "lbm_fp64_rates", "lbm_enstrophy", "lbm_probe_set", "lbm_probe_count",
+           "lbm_mrt_preset"]
 
 
 class lbm_config(C.Structure):
@@ -76,6 +77,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     sig = {
         "lbm_config_default": (i, [C.POINTER(lbm_config)]),
         "lbm_required_bytes": (i, [C.POINTER(lbm_config), C.POINTER(sz)]),
+        "lbm_mrt_preset": (i, [C.POINTER(lbm_config), i]),
         "lbm_create": (i, [C.POINTER(lbm_config), p, sz, C.POINTER(p)]),
         "lbm_destroy": (None, [p]),
         "lbm_init": (i, [p, p, p, p, p]),
@@ -376,28 +378,21 @@ class Lattice:
         return ds[:m], site[:m], sel[:m]
 
 
+MRT_PRESETS = {"trt": 0, "mrt": 1, "mrt1": 2, "mrt_ll": 3}
+
+
 def mrt_rates(preset: str, beta: float) -> dict:
-    """MRT relaxation rates (s_e, s_eps, s_q) of the presets of Sections 5
-    and 8, with s_nu = 2 beta:
-      'trt'  - two relaxation times: s_e = s_eps = s_nu and
-               s_q = 8 (2 - s_nu) / (8 - s_nu) (reading of the printed
-               "8(2=s_nu)/(8-s_nu)");
-      'mrt'  - s_e = 1.64, s_eps = 1.54, s_q as for TRT;
-      'mrt1' - s_e = 1.64, s_eps = 1.54, s_q = 1.9;
-      'mrt_ll' - the shear-decay MRT of Section 7: s_e = 1.64, s_eps = 1.54,
-               s_q = 3 (2 - s_nu) / (3 - s_nu).
-    Use with collision="mrt"."""
-    snu = 2.0 * beta
-    sq_trt = 8.0 * (2.0 - snu) / (8.0 - snu)
-    if preset == "trt":
-        return {"s_e": snu, "s_eps": snu, "s_q": sq_trt}
-    if preset == "mrt":
-        return {"s_e": 1.64, "s_eps": 1.54, "s_q": sq_trt}
-    if preset == "mrt1":
-        return {"s_e": 1.64, "s_eps": 1.54, "s_q": 1.9}
-    if preset == "mrt_ll":
-        return {"s_e": 1.64, "s_eps": 1.54, "s_q": 3.0 * (2.0 - snu) / (3.0 - snu)}
-    raise ValueError(f"unknown MRT preset {preset!r}")
+    """MRT relaxation rates (s_e, s_eps, s_q) of a preset, from the library's
+    lbm_mrt_preset (Sections 5, 7 and 8; s_nu = 2 beta): 'trt', 'mrt',
+    'mrt1' or 'mrt_ll' (LBM_MRT_PRESET_TRT / _MRT / _MRT1 / _LL).  Use with
+    collision="mrt"."""
+    if preset not in MRT_PRESETS:
+        raise ValueError(f"unknown MRT preset {preset!r}")
+    c = LBMConfig(beta=float(beta)).to_c()
+    rc = lib().lbm_mrt_preset(C.byref(c), MRT_PRESETS[preset])
+    if rc != 0:
+        raise LBMError(f"lbm_mrt_preset: {STATUS.get(rc, rc)} for {preset!r}, beta={beta}")
+    return {"s_e": c.s_e, "s_eps": c.s_eps, "s_q": c.s_q}
 
 
 def fp64_rates(stream=None) -> dict:

@@ -121,3 +121,32 @@ def test_limiter_config_defaults_and_validation(lib):
     c.collision = 9
     lib.lbm_required_bytes(C.byref(c), C.byref(n))
     assert n.value > base
+
+
+def test_mrt_presets_follow_sections_5_7_8(lib):
+    """lbm_mrt_preset writes the MRT rates of each preset (s_nu = 2 beta):
+    TRT (Section 5) s_e = s_eps = s_nu and the magic s_q = 8 (2 - s_nu)/(8 - s_nu);
+    MRT and MRT1 (Section 8); the Lallemand-Luo A_1 rates of Section 7; beta
+    may come from nu; unknown presets and beta outside (0, 1] are refused."""
+    for beta in (0.55, 0.8, 0.97):
+        snu = 2 * beta
+        magic = 8 * (2 - snu) / (8 - snu)
+        want = {"trt": (snu, snu, magic), "mrt": (1.64, 1.54, magic), "mrt1": (1.64, 1.54, 1.9),
+                "mrt_ll": (1.64, 1.54, 3 * (2 - snu) / (3 - snu))}
+        for name, (se, seps, sq) in want.items():
+            r = lbm.mrt_rates(name, beta)
+            assert r["s_e"] == pytest.approx(se, rel=1e-15)
+            assert r["s_eps"] == pytest.approx(seps, rel=1e-15)
+            assert r["s_q"] == pytest.approx(sq, rel=1e-15)
+    # the TRT magic relation: (1/s_nu - 1/2)(1/s_q - 1/2) = 3/16
+    r = lbm.mrt_rates("trt", 0.9)
+    assert (1 / 1.8 - 0.5) * (1 / r["s_q"] - 0.5) == pytest.approx(3 / 16, rel=1e-14)
+    c = lbm.LBMConfig(beta=0.0, nu=0.01).to_c()
+    assert lib.lbm_mrt_preset(C.byref(c), 0) == 0
+    assert c.s_e == pytest.approx(2 / (6 * 0.01 + 1), rel=1e-15)
+    assert lib.lbm_mrt_preset(C.byref(c), 7) == 1
+    bad = lbm.LBMConfig(beta=1.5).to_c()
+    assert lib.lbm_mrt_preset(C.byref(bad), 0) == 1
+    assert lib.lbm_mrt_preset(None, 0) == 1
+    with pytest.raises(ValueError):
+        lbm.mrt_rates("nope", 0.9)
