@@ -411,17 +411,20 @@ def run_small_configs(tube_steps=400, cavity_steps=2000):
     return out
 
 
-def run_adjoint(T=4000, K=100, n=513, fd=True):
-    """The adjoint configuration: D2Q9 cavity n^2, Re 1000, U 0.1, FP32,
-    Ehrenfest k = 32, f0 = equilibrium at rest + N(0, 1e-4) noise; gradient
-    of the kinetic energy after T steps with respect to U, beta and f0,
-    checkpoints every K steps.  Reports backward / forward time and the
-    central differences (h = 1e-3, Richardson with h/2) of FP64 forward runs."""
+def run_adjoint(T=4000, K=100, n=513, fd=True, collision="ehrenfest"):
+    """The adjoint configuration: D2Q9 cavity n^2, Re 1000, U 0.1, FP32, with
+    the Ehrenfest limiter (k = 32) or the median filter (delta = 1e-3),
+    f0 = equilibrium at rest + N(0, 1e-4) noise; gradient of the kinetic
+    energy after T steps with respect to U, beta and f0, checkpoints every K
+    steps.  Reports backward / forward time and the central differences
+    (h = 1e-3, Richardson with h/2) of FP64 forward runs, with a flag when a
+    perturbed run limited a different number of sites than the base run
+    (the difference then crosses a selection boundary)."""
     import torch
     from paper_1110_0270_gb300 import lbm
     from paper_1110_0270_gb300 import workloads as WL
     cfg, init = WL.cavity(n, 1000.0, 0.1)
-    cfg.update(collision="ehrenfest", topk=32, delta=1e-3, precision="fp32")
+    cfg.update(collision=collision, topk=32, delta=1e-3, precision="fp32")
     beta = 1.0 / (6.0 * cfg["nu"] + 1.0)
     cfg["beta"] = beta
     lat = lbm.Lattice(cfg)
@@ -442,26 +445,36 @@ def run_adjoint(T=4000, K=100, n=513, fd=True):
     lat.adjoint_backward(T, K, work)
     lat.set_state(f0)
     (J, _), t_f = timed(lambda: lat.adjoint_forward(T, K, work))
+    limited = lat.stats()["limited_total"]
     (g, gU, gB), t_b = timed(lambda: lat.adjoint_backward(T, K, work))
-    out = {"config": f"D2Q9 cavity {n}^2, Re 1000, U 0.1, FP32, Ehrenfest k=32, T={T}, K={K}",
+    lim = "Ehrenfest k=32" if collision == "ehrenfest" else "median filter delta=1e-3"
+    out = {"config": f"D2Q9 cavity {n}^2, Re 1000, U 0.1, FP32, {lim}, T={T}, K={K}",
            "J": J, "dJ_dU": gU, "dJ_dbeta": gB, "forward_s": round(t_f, 4),
            "backward_s": round(t_b, 4), "backward_over_forward": round(t_b / t_f, 3),
-           "work_bytes": int(work.numel())}
+           "work_bytes": int(work.numel()), "limited_sites": limited}
     if fd:
         f64 = f0.double()
+        crossed = []
 
         def ke(**kw):
             l2 = lbm.Lattice(dict(cfg, precision="fp64", **kw))
             l2.set_state(f64)
-            return l2.adjoint_forward(T, T)[0]
+            J2 = l2.adjoint_forward(T, T)[0]
+            crossed.append(l2.stats()["limited_total"])
+            return J2
 
         def cd(key, x0, h):
             d = lambda hh: (ke(**{key: x0 + hh}) - ke(**{key: x0 - hh})) / (2 * hh)
             return (4 * d(h / 2) - d(h)) / 3
 
+        base = lbm.Lattice(dict(cfg, precision="fp64"))
+        base.set_state(f64)
+        base.adjoint_forward(T, T)
+        lim0 = base.stats()["limited_total"]
         fdU, fdB = cd("lid_u", 0.1, 1e-3), cd("beta", beta, 1e-3)
         out.update(fd_dJ_dU=fdU, fd_dJ_dbeta=fdB, rel_err_U=abs(gU - fdU) / abs(fdU),
-                   rel_err_beta=abs(gB - fdB) / abs(fdB))
+                   rel_err_beta=abs(gB - fdB) / abs(fdB),
+                   fd_branch_crossing=any(c != lim0 for c in crossed))
     return out
 
 
@@ -666,6 +679,7 @@ def run_sections(args, result, init):
         guarded(result, "shear_decay", run_shear_decay)
     if args.adjoint_steps > 0:
         guarded(result, "adjoint", lambda: run_adjoint(args.adjoint_steps, 100))
+        guarded(result, "adjoint_median", lambda: run_adjoint(args.adjoint_steps, 100, collision="median"))
     if args.batch_steps > 0:
         fp64 = (result.get("variants") or {}).get("lbgk/fp64", {}).get("mlups")
         guarded(result, "batched", lambda: run_batched(args.batch_steps, 3, fp64))

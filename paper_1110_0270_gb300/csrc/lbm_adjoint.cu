@@ -1,8 +1,10 @@
 // Reverse-mode gradient of a functional of the state after T steps
 // (declared in include/lbm.h): checkpoints every K steps in the forward pass,
 // and in the backward pass, segment by segment from the last, recomputation
-// of the K states and of the Ehrenfest selections followed by K adjoint steps
-// (lbm_adjoint_kernels.cuh).  All buffers live in the caller's work memory.
+// of the K states and of each step's branch per site (Ehrenfest selection,
+// median window site, positivity binding population) followed by K adjoint
+// steps (lbm_adjoint_kernels.cuh).  All buffers live in the caller's work
+// memory.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,13 +21,18 @@ namespace {
 size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 
 struct AdjLayout {
-    size_t acc, fT, lam0, lam1, masks, seg, ckpt, total, dense;
+    size_t acc, fT, lam0, lam1, aux, wbuf, seg, ckpt, total, dense;
     int nseg;
 };
 
 bool adj_supported(const lbm_config* c) {
-    return (c->collision == LBM_LBGK || c->collision == LBM_EHRENFEST) && c->bc != LBM_BC_DIFFUSIVE;
+    return (c->collision == LBM_LBGK || c->collision == LBM_EHRENFEST || c->collision == LBM_MEDIAN ||
+            c->collision == LBM_POSITIVITY) &&
+           c->bc != LBM_BC_DIFFUSIVE;
 }
+
+// collisions whose branch per site and step is recorded
+bool has_branches(int coll) { return coll == LBM_EHRENFEST || coll == LBM_MEDIAN || coll == LBM_POSITIVITY; }
 
 AdjLayout adj_layout(const lbm_config* c, int T, int K) {
     AdjLayout L;
@@ -43,8 +50,10 @@ AdjLayout adj_layout(const lbm_config* c, int T, int K) {
     off += L.dense;
     L.lam1 = off;
     off += L.dense;
-    L.masks = off;
-    off += c->collision == LBM_EHRENFEST ? up256((size_t)K * N) : 0;
+    L.aux = off;
+    off += has_branches(c->collision) ? up256((size_t)K * N * sizeof(int)) : 0;
+    L.wbuf = off;
+    off += c->collision == LBM_MEDIAN ? up256(N * sizeof(double)) : 0;
     L.seg = off;
     off += (size_t)K * L.dense;
     L.ckpt = off;
@@ -91,7 +100,9 @@ lbm_status check(lbm_ctx* ctx, int T, int K, void* work, size_t bytes) {
     if (T < 0 || K < 1 || !work || ((uintptr_t)work % 256) != 0)
         return afail(ctx, LBM_ERR_ARG, "adjoint: T >= 0, K >= 1 and 256-byte aligned work needed");
     if (!adj_supported(&ctx->cfg))
-        return afail(ctx, LBM_ERR_ARG, "adjoint: collision must be LBM_LBGK or LBM_EHRENFEST");
+        return afail(ctx, LBM_ERR_ARG,
+                     "adjoint: collision must be LBM_LBGK, LBM_EHRENFEST, LBM_MEDIAN or LBM_POSITIVITY "
+                     "(and no diffusive walls)");
     if (bytes < adj_layout(&ctx->cfg, T, K).total) return afail(ctx, LBM_ERR_OOM, "adjoint: work too small");
     return LBM_OK;
 }
@@ -106,8 +117,10 @@ lbm_status backward_t(lbm_ctx* ctx, int T_, int K, const void* seed, int seed_dt
     double* acc = (double*)(w + L.acc);
     T* fT = (T*)(w + L.fT);
     T* lam[2] = {(T*)(w + L.lam0), (T*)(w + L.lam1)};
-    unsigned char* masks = (unsigned char*)(w + L.masks);
-    const bool ehr = ctx->cfg.collision == LBM_EHRENFEST;
+    int* aux = (int*)(w + L.aux);
+    double* wbuf = (double*)(w + L.wbuf);
+    const int coll = ctx->cfg.collision;
+    const bool branches = has_branches(coll);
     ACK(ctx, cudaMemsetAsync(acc, 0, 256, s));
     if (!seed) {
         ACK(ctx, AdjLaunch<T>::seed(Q, g, fT, lam[0], acc + 2, s));
@@ -119,17 +132,21 @@ lbm_status backward_t(lbm_ctx* ctx, int T_, int K, const void* seed, int seed_dt
     int cur = 0;
     for (int sg = L.nseg - 1; sg >= 0; --sg) {
         const int len = std::min(K, T_ - sg * K);
-        // recompute the segment: its pre-collision states and selections
+        // recompute the segment: its pre-collision states and branches
         AST(lbm_set_state(ctx, w + L.ckpt + (size_t)sg * L.dense, dtype_of(ctx), s));
-        if (ehr) ACK(ctx, cudaMemsetAsync(masks, 0, (size_t)len * N, s));
+        if (branches) ACK(ctx, cudaMemsetAsync(aux, 0xff, (size_t)len * N * sizeof(int), s));  // AUX_LBGK
         for (int k = 0; k < len; ++k) {
-            AST(lbm_get_state(ctx, w + L.seg + (size_t)k * L.dense, dtype_of(ctx), s));
+            const T* fk = (const T*)(w + L.seg + (size_t)k * L.dense);
+            AST(lbm_get_state(ctx, (void*)fk, dtype_of(ctx), s));
             AST(lbm_step(ctx, 1, s));
-            if (ehr) ACK(ctx, AdjLaunch<T>::mask(Q, ctx->p, (int)((ctx->t - 1) & 1), masks + (size_t)k * N, ctx->nsm, s));
+            if (branches)
+                ACK(ctx, AdjLaunch<T>::record(Q, ctx->p, coll, (int)((ctx->t - 1) & 1), fk, aux + (size_t)k * N,
+                                              ctx->nsm, s));
         }
         for (int k = len - 1; k >= 0; --k) {
             ACK(ctx, AdjLaunch<T>::step(Q, g, (const T*)(w + L.seg + (size_t)k * L.dense),
-                                        ehr ? masks + (size_t)k * N : nullptr, lam[cur], lam[cur ^ 1], acc, s));
+                                        branches ? aux + (size_t)k * N : nullptr, lam[cur], lam[cur ^ 1], acc,
+                                        wbuf, coll == LBM_MEDIAN, s));
             cur ^= 1;
         }
     }

@@ -1,17 +1,28 @@
-// Reverse-mode (adjoint) kernels of the step for the LBGK and Ehrenfest
-// collisions, on dense natural-layout states f[i][y][x].
+// Reverse-mode (adjoint) kernels of the step for the LBGK, Ehrenfest,
+// median-filter and positivity collisions, on dense natural-layout states
+// f[i][y][x].
 //
 // One step is f_{t+1} = P(C(f_t)): C the collision at every site, P the
 // streaming with half-way bounce-back and the moving-lid term
-// -6 W_i v_ix U on links through the top wall.  Given lambda_{t+1} =
-// dJ/df_{t+1}:
+// -6 W_i v_ix U on links through the top wall.  Every branch of these
+// collisions has the form F = f* + psi (f - f*):
+//   LBGK (Eq. CollisionIntegral)         psi = 1 - 2 beta
+//   Ehrenfest step (Section 4)           psi = 0
+//   median filter (Section 4.4, entrHom) psi = (1 - 2 beta) sqrt(M / C), C the
+//                                        site's Delta S, M that of the window
+//                                        site m holding the lower median
+//   positivity rule (Section 4, StrLine) psi = f*_k / (f*_k - f_k), k the
+//                                        population that binds the rule
+// and the selection of each step (which branch, m, k) is held fixed.  Given
+// lambda_{t+1} = dJ/df_{t+1}:
 //   Lambda = P^T lambda_{t+1}:  Lambda_i(x) = lambda_{t+1, i}(x + v_i), or
 //     lambda_{t+1, opp(i)}(x) for a wall link (which also adds
 //     lambda_{t+1, opp(i)}(x) (-6 W_i v_ix) to dJ/dU on the lid);
-//   lambda_t = (dC/df)^T Lambda, with dC/df = (1 - 2 beta) I + 2 beta df*/df for
-//     LBGK sites and df*/df for the sites the Ehrenfest step sent to f*
-//     (the selection of that step is held fixed);
-//   dJ/dbeta += Lambda . 2 (f* - f) at LBGK sites.
+//   lambda_t,j = (1 - psi) a_j + psi Lambda_j + g dpsi/df_j,
+//     a_j = sum_i Lambda_i df*_i/df_j,  g = sum_i Lambda_i (f_i - f*_i);
+//   dJ/dbeta += g dpsi/dbeta (-2 for LBGK, -2 sqrt(M / C) for the median,
+//     0 for the Ehrenfest step and the positivity rule);
+//   the median's psi also depends on f at m: lambda_t(m) += g dpsi/df(m).
 // df*/df_j = df*/drho + df*/du_x (v_jx - u_x)/rho + df*/du_y (v_jy - u_y)/rho.
 #pragma once
 
@@ -125,21 +136,122 @@ __global__ void __launch_bounds__(256) adj_seed_ke(AdjGeo g, const T* __restrict
     block_add2(e, 0.0, J, nullptr);
 }
 
-// Sites the Ehrenfest step of this parity sent to f* (from its candidate list).
+// Branch of a site in one step (the int recorded per site and step).
+enum { AUX_LBGK = -1, AUX_FSTAR = -2, AUX_POS0 = -3 };  // AUX_POS0 - k; m >= 0: median
+
+// Delta S of one site in FP64 (the cancellation-free form of Eq. DelS) and
+// its gradient dDelta S/df_j = ln(f_j/f*_j) + 1 - sum_i (f_i/f*_i) df*_i/df_j.
+// +inf (gradient 0) with a non-positive population.
 template <int Q>
-__global__ void adj_mask(Params p, int cslot, unsigned char* mask) {
+__device__ double delta_s_grad(int eqkind, const double* f, double* grad) {
+    using L = Lat<Q>;
+    double rho, ux, uy, feq[Q], dr[Q], dx[Q], dy[Q];
+    moments<Q, double>(f, rho, ux, uy);
+    eq_partials<Q, double>(eqkind, rho, ux, uy, feq, dr, dx, dy);
+    double ds = 0.0;
+    bool neg = false;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        neg |= !(f[i] > 0.0) || !(feq[i] > 0.0);
+        ds += feq[i] * gfun_d((f[i] - feq[i]) / feq[i]);
+    }
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            s += f[i] / feq[i] * (dr[i] + dx[i] * (L::cx(j) - ux) / rho + dy[i] * (L::cy(j) - uy) / rho);
+        grad[j] = neg ? 0.0 : log(f[j] / feq[j]) + 1.0 - s;
+    }
+    return neg ? __longlong_as_double(0x7ff0000000000000ULL) : ds;
+}
+
+template <int Q, class T>
+__device__ __forceinline__ void dense_site_d(const T* a, int64_t N, int64_t s, double* out) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) out[i] = (double)a[(int64_t)i * N + s];
+}
+
+// Records the branch of every site of one recomputed step (aux cleared to
+// AUX_LBGK beforehand), from the step's candidate list (Ehrenfest, median:
+// the selection the step made) or, for the positivity rule, by the step's own
+// test on the dense pre-collision state f (the same device functions in the
+// same precision, so the same decision).  The median's window site m: the
+// lower median of the clipped window's FP64 Delta S, ties by site index.
+template <int Q, class T>
+__global__ void __launch_bounds__(256) adj_record(Params p, int coll, int cslot, const T* __restrict__ f,
+                                                 int* __restrict__ aux) {
+    const int64_t N = (int64_t)p.nx * p.ny;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
+    if (coll == LBM_POSITIVITY) {
+        for (int64_t s = tid; s < N; s += nt) {
+            T fs[Q], feq[Q], F[Q], rho, ux, uy;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) fs[i] = f[(int64_t)i * N + s];
+            moments<Q, T>(fs, rho, ux, uy);
+            equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
+            lbgk<Q, T>(fs, feq, sizeof(T) == 8 ? T(p.beta) : T(p.beta_f), F);
+            T lam = T(1);
+            int k = -1;
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                if (F[i] < T(0)) {
+                    const T l = feq[i] / (feq[i] - F[i]);
+                    if (l < lam) {  // the first of equal values, as positivity()
+                        lam = l;
+                        k = i;
+                    }
+                }
+            if (k >= 0) aux[s] = AUX_POS0 - k;
+        }
+        return;
+    }
     unsigned M = p.counters[cslot];
     if (M > (unsigned)p.cand_cap) M = (unsigned)p.cand_cap;
-    for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x)
-        if (p.cand_sel[j] && p.cand_ds[j] > p.delta) mask[p.cand_site[j]] = 1;
+    for (int64_t j = tid; j < (int64_t)M; j += nt) {
+        if (!p.cand_sel[j]) continue;
+        const int site = p.cand_site[j];
+        if (coll == LBM_EHRENFEST) {
+            if (p.cand_ds[j] > p.delta) aux[site] = AUX_FSTAR;
+            continue;
+        }
+        // median: the window site of the lower median
+        const int x = site % p.nx, y = site / p.nx;
+        const int ry = Q == 9 ? 1 : 0;
+        int w[9];
+        double v[9];
+        int n = 0;
+        for (int dy = -ry; dy <= ry; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int xx = x + dx, yy = y + dy;
+                if (p.periodic_x) xx = xx < 0 ? xx + p.nx : (xx >= p.nx ? xx - p.nx : xx);
+                if (p.periodic_y) yy = yy < 0 ? yy + p.ny : (yy >= p.ny ? yy - p.ny : yy);
+                if (xx < 0 || xx >= p.nx || yy < 0 || yy >= p.ny) continue;
+                const int q = yy * p.nx + xx;
+                double fq[Q], g[Q];
+                dense_site_d<Q, T>(f, N, q, fq);
+                const double d = delta_s_grad<Q>(p.eq, fq, g);
+                int k = n++;
+                while (k > 0 && (v[k - 1] > d || (v[k - 1] == d && w[k - 1] > q))) {  // ascending
+                    v[k] = v[k - 1];
+                    w[k] = w[k - 1];
+                    --k;
+                }
+                v[k] = d;
+                w[k] = q;
+            }
+        aux[site] = w[(n - 1) / 2];
+    }
 }
 
 // lambda_t from lambda_{t+1} (see the header), with dJ/dU in acc[0] and
-// dJ/dbeta in acc[1].
+// dJ/dbeta in acc[1]; aux (NULL: every site LBGK) holds each site's branch.
+// For a median site the coefficient w = g (1 - 2 beta) sqrt(M / C) / (2 M) of
+// its cross term goes to wbuf[s] (adj_median_cross adds it at m).
 template <int Q, class T>
 __global__ void __launch_bounds__(256)
-    adj_step(AdjGeo g, const T* __restrict__ f, const unsigned char* __restrict__ mask,
-             const T* __restrict__ lam_in, T* __restrict__ lam_out, double* acc) {
+    adj_step(AdjGeo g, const T* __restrict__ f, const int* __restrict__ aux, const T* __restrict__ lam_in,
+             T* __restrict__ lam_out, double* acc, double* __restrict__ wbuf) {
     using L = Lat<Q>;
     const int64_t N = (int64_t)g.nx * g.ny;
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -163,29 +275,91 @@ __global__ void __launch_bounds__(256)
         dense_site<Q, T>(f, N, s, fs);
         moments<Q, T>(fs, rho, ux, uy);
         eq_partials<Q, T>(g.eq, rho, ux, uy, feq, dr, dx, dy);
-        T A = T(0), Bx = T(0), By = T(0);
+        T A = T(0), Bx = T(0), By = T(0), gs = T(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             A += Lam[i] * dr[i];
             Bx += Lam[i] * dx[i];
             By += Lam[i] * dy[i];
+            gs += Lam[i] * (fs[i] - feq[i]);
         }
         const T inv = T(1) / rho;
-        const bool sel = mask && mask[s];
-        const T om = T(2) * T(g.beta);
+        const int br = aux ? aux[s] : AUX_LBGK;
+        const T c = T(1) - T(2) * T(g.beta);
+        T psi = c, dpsi_db = T(-2), dpsi[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) dpsi[j] = T(0);
+        if (br == AUX_FSTAR) {
+            psi = T(0);
+            dpsi_db = T(0);
+        } else if (br <= AUX_POS0) {
+            // psi = f*_k / (f*_k - f_k), independent of beta
+            const int k = AUX_POS0 - br;
+            T fk = T(0), ek = T(0), drk = T(0), dxk = T(0), dyk = T(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                if (i == k) {
+                    fk = fs[i];
+                    ek = feq[i];
+                    drk = dr[i];
+                    dxk = dx[i];
+                    dyk = dy[i];
+                }
+            const T D = ek - fk;
+            psi = ek / D;
+            dpsi_db = T(0);
+#pragma unroll
+            for (int j = 0; j < Q; ++j) {
+                const T dfk = drk + dxk * (T(L::cx(j)) - ux) * inv + dyk * (T(L::cy(j)) - uy) * inv;
+                dpsi[j] = (-fk * dfk + (j == k ? ek : T(0))) / (D * D);
+            }
+        } else if (br >= 0) {
+            // psi = c sqrt(M / C): C and its gradient here, M at site br (FP64)
+            double fd[Q], gC[Q], fm[Q], gM[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) fd[i] = (double)fs[i];
+            const double C = delta_s_grad<Q>(g.eq, fd, gC);
+            dense_site_d<Q, T>(f, N, br, fm);
+            const double Mv = delta_s_grad<Q>(g.eq, fm, gM);
+            const double phi = isinf(C) ? 0.0 : sqrt(Mv / C);
+            psi = T(c * T(phi));
+            dpsi_db = T(-2.0 * phi);
+            double w = 0.0;
+            if (!isinf(C) && Mv > 0.0) {
+#pragma unroll
+                for (int j = 0; j < Q; ++j) dpsi[j] = T(-(double)c * phi / (2.0 * C) * gC[j]);
+                w = (double)gs * (double)c * phi / (2.0 * Mv);
+            }
+            wbuf[s] = w;
+        }
 #pragma unroll
         for (int j = 0; j < Q; ++j) {
             const T a = A + Bx * (T(L::cx(j)) - ux) * inv + By * (T(L::cy(j)) - uy) * inv;
-            lam_out[(int64_t)j * N + s] = sel ? a : (T(1) - om) * Lam[j] + om * a;
+            lam_out[(int64_t)j * N + s] = (T(1) - psi) * a + psi * Lam[j] + gs * dpsi[j];
         }
-        if (!sel) {
-            T b = T(0);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) b += Lam[i] * (feq[i] - fs[i]);
-            dB = 2.0 * (double)b;
-        }
+        dB = (double)gs * (double)dpsi_db;
     }
     block_add2(dU, dB, acc, acc + 1);
+}
+
+// The median's cross term: a selected site s with window site m = aux[s]
+// adds wbuf[s] dM/df(m) to lambda_t(m) (after adj_step has written it).
+template <int Q, class T>
+__global__ void __launch_bounds__(256) adj_median_cross(AdjGeo g, const T* __restrict__ f,
+                                                       const int* __restrict__ aux,
+                                                       const double* __restrict__ wbuf, T* lam_out) {
+    const int64_t N = (int64_t)g.nx * g.ny;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+        const int m = aux[s];
+        if (m < 0) continue;
+        const double w = wbuf[s];
+        if (w == 0.0) continue;
+        double fm[Q], gM[Q];
+        dense_site_d<Q, T>(f, N, m, fm);
+        delta_s_grad<Q>(g.eq, fm, gM);
+#pragma unroll
+        for (int j = 0; j < Q; ++j) atomicAdd(&lam_out[(int64_t)j * N + m], T(w * gM[j]));
+    }
 }
 
 template <class T, class U>
@@ -206,21 +380,31 @@ struct AdjLaunch {
             adj_seed_ke<9, T><<<blocks, 256, 0, s>>>(g, f, lam, J);
         return cudaGetLastError();
     }
-    static cudaError_t step(int Q, const AdjGeo& g, const T* f, const unsigned char* mask,
-                            const T* lin, T* lout, double* acc, cudaStream_t s) {
+    static cudaError_t step(int Q, const AdjGeo& g, const T* f, const int* aux, const T* lin, T* lout,
+                            double* acc, double* wbuf, bool median, cudaStream_t s) {
         const int64_t N = (int64_t)g.nx * g.ny;
         const unsigned blocks = (unsigned)((N + 255) / 256);
         if (Q == 3)
-            adj_step<3, T><<<blocks, 256, 0, s>>>(g, f, mask, lin, lout, acc);
+            adj_step<3, T><<<blocks, 256, 0, s>>>(g, f, aux, lin, lout, acc, wbuf);
         else
-            adj_step<9, T><<<blocks, 256, 0, s>>>(g, f, mask, lin, lout, acc);
+            adj_step<9, T><<<blocks, 256, 0, s>>>(g, f, aux, lin, lout, acc, wbuf);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess || !median) return e;
+        if (Q == 3)
+            adj_median_cross<3, T><<<blocks, 256, 0, s>>>(g, f, aux, wbuf, lout);
+        else
+            adj_median_cross<9, T><<<blocks, 256, 0, s>>>(g, f, aux, wbuf, lout);
         return cudaGetLastError();
     }
-    static cudaError_t mask(int Q, const Params& p, int cslot, unsigned char* m, int nsm, cudaStream_t s) {
+    static cudaError_t record(int Q, const Params& p, int coll, int cslot, const T* f, int* aux, int nsm,
+                              cudaStream_t s) {
+        const int64_t N = (int64_t)p.nx * p.ny;
+        const unsigned blocks =
+            coll == LBM_POSITIVITY ? (unsigned)std::min<int64_t>((N + 255) / 256, 8 * nsm) : (unsigned)nsm;
         if (Q == 3)
-            adj_mask<3><<<nsm, 256, 0, s>>>(p, cslot, m);
+            adj_record<3, T><<<blocks, 256, 0, s>>>(p, coll, cslot, f, aux);
         else
-            adj_mask<9><<<nsm, 256, 0, s>>>(p, cslot, m);
+            adj_record<9, T><<<blocks, 256, 0, s>>>(p, coll, cslot, f, aux);
         return cudaGetLastError();
     }
     template <class U>

@@ -1,6 +1,9 @@
 """Hand-written adjoint (lbm_adjoint_*): FP64 against the oracle's FP64 tape
 adjoint, FP32 against central differences of FP64 forward runs, and the
-torch.autograd.Function built on it."""
+torch.autograd.Function built on it.  Collisions: LBGK, the Ehrenfest step
+(Section 4), the median filter (Section 4.4, Eq. entrHom) and the positivity
+rule (Section 4, Eq. StrLine); through the limiters the selected branch is
+differentiated with the selection of each step held fixed."""
 import numpy as np
 import pytest
 
@@ -13,13 +16,16 @@ from paper_1110_0270_gb300 import workloads as WL  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 
-def start_state(cfg, seed, amp=0.02, hot=4):
+def start_state(cfg, seed, amp=0.02, hot=4, hot_amp=None):
     ny, nx = cfg["ny"], cfg["nx"]
     fl = WL.random_fields(ny, nx, seed, 0.05, 0.05)
     f0 = O.init_equilibrium(dict(cfg, collision="lbgk"), fl["rho"], fl["ux"],
                             None if cfg["lattice"] == "D1Q3" else fl["uy"])
     f0 = f0 * WL.lognormal_factors(f0.shape, seed + 1, amp)
-    return f0 * WL.lognormal_factors(f0.shape, seed + 2, 1.0) ** (WL.hot_spots(ny, nx, seed + 3, hot, 0.4)[None])
+    # hot sites strong enough that the positivity rule fires
+    if hot_amp is None:
+        hot_amp = 1.2 if cfg.get("collision") == "positivity" else 0.4
+    return f0 * WL.lognormal_factors(f0.shape, seed + 2, 1.0) ** (WL.hot_spots(ny, nx, seed + 3, hot, hot_amp)[None])
 
 
 def gpu_adjoint(cfg, f0, T, K):
@@ -38,6 +44,14 @@ CASES = {
     "tube": dict(lattice="D1Q3", nx=64, ny=1, bc="ends", collision="lbgk", beta=0.97),
     "periodic_entropic": dict(lattice="D2Q9", nx=24, ny=20, bc="periodic", collision="ehrenfest",
                               beta=0.92, topk=2, delta=1e-4, equilibrium="entropic"),
+    "cavity_median": dict(lattice="D2Q9", nx=33, ny=29, bc="cavity", lid_u=0.1, collision="median",
+                          beta=0.9, delta=1e-4),
+    "periodic_median": dict(lattice="D2Q9", nx=24, ny=20, bc="periodic", collision="median", beta=0.95,
+                            delta=5e-5, equilibrium="entropic"),
+    "tube_median": dict(lattice="D1Q3", nx=64, ny=1, bc="ends", collision="median", beta=0.97, delta=1e-4),
+    "cavity_positivity": dict(lattice="D2Q9", nx=33, ny=29, bc="cavity", lid_u=0.1, collision="positivity",
+                              beta=0.99),
+    "tube_positivity": dict(lattice="D1Q3", nx=64, ny=1, bc="ends", collision="positivity", beta=0.99),
 }
 
 
@@ -46,6 +60,9 @@ def test_adjoint_fp64_matches_oracle_tape(case):
     cfg = dict(CASES[case], precision="fp64")
     f0 = start_state(cfg, 12)
     T, K = 60, 16  # four segments, the last one partial
+    if cfg["collision"] in ("median", "positivity"):
+        _, st = O.step(cfg, f0, T, stats=True)
+        assert st["limited_sites"] > 0  # the limiter branch is exercised
     J, g, gU, gB, lat = gpu_adjoint(cfg, f0, T, K)
     Jo, go, gUo, gBo = O.adjoint_ke(cfg, f0, T)
     assert abs(J - Jo) <= 1e-12 * abs(Jo)
@@ -65,25 +82,48 @@ def _ke_fp64(cfg, f0, T):
     return J
 
 
-def test_adjoint_fp32_against_central_differences_and_oracle():
-    """A 65^2 copy of the adjoint configuration (Re 1000, U 0.1, Ehrenfest
-    k = 32): the FP32 adjoint against central differences of FP64 forward
-    runs (U, beta, a random direction in f0) and against the oracle's FP64
-    tape adjoint, within 1e-4 relative.  In the first steps this copy has up
-    to 118 candidates for 32 slots, so a step of 1e-3 moves sites across the
-    selection boundary (the finite difference then measures a jump, not the
-    derivative of either branch); h = 1e-6 stays on the branch."""
+def _fp32_copy(collision):
+    """A 65^2 copy of the adjoint configuration (Re 1000, U 0.1) with the
+    given limiter: Ehrenfest k = 32 or the median filter at delta = 1e-3 from
+    the resting state with N(0, 1e-4) noise; the positivity rule from a
+    random state with strong hot sites (beta 0.99)."""
     n = 65
     cfg, init = WL.cavity(n, 1000.0, 0.1)
-    cfg.update(collision="ehrenfest", topk=32, delta=1e-3, precision="fp32")
+    cfg.update(collision=collision, topk=32, delta=1e-3, precision="fp32")
     beta = 1.0 / (6.0 * cfg["nu"] + 1.0)
-    cfg["beta"] = beta
-    f0 = O.init_equilibrium(cfg, init["rho"], init["ux"], init["uy"])
-    f0 = f0 + WL.normal_noise(f0.shape, 4, 1e-4)
-    f0 = f0.astype(np.float32).astype(np.float64)
-    T, K = 300, 50
+    if collision == "positivity":
+        beta = 0.99
+        cfg["beta"] = beta
+        f0 = start_state(cfg, 31, hot=40)
+    else:
+        cfg["beta"] = beta
+        f0 = O.init_equilibrium(cfg, init["rho"], init["ux"], init["uy"])
+        f0 = f0 + WL.normal_noise(f0.shape, 4, 1e-4)
+    return cfg, beta, f0.astype(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("collision", ["ehrenfest", "median", "positivity"])
+def test_adjoint_fp32_against_central_differences_and_oracle(collision):
+    """FP32 adjoint on a 65^2 cavity against central differences of FP64
+    forward runs (U, beta, a random direction in f0) and against the oracle's
+    FP64 tape adjoint, within 1e-4 relative.  In the first steps the
+    Ehrenfest copy has up to 118 candidates for 32 slots, so a step of 1e-3
+    moves sites across the selection boundary (the finite difference then
+    measures a jump, not the derivative of either branch); h = 1e-6 stays on
+    the branch, as it does for the median's window sites and the positivity
+    rule's binding populations."""
+    cfg, beta, f0 = _fp32_copy(collision)
+    # the positivity rule fires at a few sites in every step; where it binds
+    # near its boundary the FP32 and FP64 trajectories separate after 100 to
+    # 300 steps (GPU FP32 against the oracle: 4e-7 at T = 100, 5e-4 at
+    # T = 300; GPU FP64 1e-12 at both), so its FP32 check runs 100 steps
+    T, K = (100, 25) if collision == "positivity" else (300, 50)
+    _, st = O.step(cfg, f0, T, stats=True)
+    assert st["limited_sites"] > 0
     J, g, gU, gB, _ = gpu_adjoint(cfg, f0, T, K)
-    h = 1e-6
+    # the median's window sites can lie within 1e-5 of each other in Delta S:
+    # the smaller step keeps their order (FP64 forward noise stays ~1e-7)
+    h = 1e-7 if collision == "median" else 1e-6
     cd = lambda key, x0: (_ke_fp64(dict(cfg, **{key: x0 + h}), f0, T) -
                           _ke_fp64(dict(cfg, **{key: x0 - h}), f0, T)) / (2 * h)
     fdU, fdB = cd("lid_u", 0.1), cd("beta", beta)
