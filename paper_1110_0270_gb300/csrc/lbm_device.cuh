@@ -92,6 +92,16 @@ struct StBF16 {
         b = w + v.y;
     }
     __device__ static void st2(S* p, T a, T b, T w) { *(__nv_bfloat162*)p = __floats2bfloat162_rn(a - w, b - w); }
+    // a pair as one 32-bit word (element at the lower address in the low half)
+    __device__ static float2 unpack(uint32_t u) {
+        __nv_bfloat162 h;
+        *reinterpret_cast<uint32_t*>(&h) = u;
+        return __bfloat1622float2(h);
+    }
+    __device__ static uint32_t pack(float a, float b) {  // round to nearest even, as st2
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    }
 };
 struct StF16 {
     using S = __half;
@@ -105,6 +115,15 @@ struct StF16 {
         b = w + v.y;
     }
     __device__ static void st2(S* p, T a, T b, T w) { *(__half2*)p = __floats2half2_rn(a - w, b - w); }
+    __device__ static float2 unpack(uint32_t u) {
+        __half2 h;
+        *reinterpret_cast<uint32_t*>(&h) = u;
+        return __half22float2(h);
+    }
+    __device__ static uint32_t pack(float a, float b) {
+        const __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    }
 };
 
 // ---------------------------------------------------------------------------
@@ -328,7 +347,7 @@ __device__ __forceinline__ bool maybe_above_loose(const float* f, const float* f
     return slack_reaches(q, q, rho, delta);
 }
 
-// Median with a Delta S field (16-bit storage, or 1 - 2 beta near 0): the
+// Median with a Delta S field (1 - 2 beta near 0): the
 // site's Delta S in the arithmetic type is computed anyway (the filter's
 // field), so it is the screen itself; it also serves the threshold limiter,
 // the selection kernel's FP32 settling and the limiters of Sections 4.2-4.3

@@ -347,19 +347,20 @@ __global__ void __launch_bounds__(kBlockX* kBlockY, kMinBlocks<ST, COLL>) step_k
 }
 
 // Two sites per thread (x0 = 2t, x0 + 1): every population plane moves with
-// one aligned pair access per thread (and one packed conversion in the
-// 16-bit formats).  In odd steps the planes with v_x = +-1 are shifted by one
-// element; the missing neighbour comes from the adjacent lane by a shuffle,
-// and only the two warp-edge elements use scalar accesses.  Each element is
-// still read and written only by the thread of the site that owns it (a
-// pair load may also fetch an unused element owned by the next warp).
-// Warps that touch a wall, the domain edge or a ragged end take the
-// per-site path.
+// one aligned 32-bit access per thread holding the pair (and one packed
+// conversion).  In odd steps the planes with v_x = +-1 are one element off:
+// a thread's shifted pair is half its own word and half a neighbour lane's,
+// so the packed word itself crosses lanes by one shuffle and one byte
+// permute assembles the pair; at the two warp edges a single lane makes one
+// extra 32-bit load (still an aligned pair of the same row) or one 16-bit
+// store, each a single conditional access.  Each element is still written
+// only by the thread of the site that owns it (loads may also fetch an
+// unused element of a neighbour).  Warps that touch a wall, the domain edge
+// or a ragged end take the per-site path.
 // Used for the 16-bit formats, whose per-site instruction count (packed
 // conversions, addressing) otherwise limits them below the HBM roofline;
-// with FP32 storage the one-site kernel is as fast or faster, and the median
-// step (two FP32 Delta S evaluations per thread) loses occupancy.  Compiled
-// for six resident CTAs (40 registers): 2-7% faster than five or no cap.
+// with FP32 storage the one-site kernel is as fast or faster.  Compiled for
+// six resident CTAs (40 registers): 2-7% faster than five or no cap.
 constexpr int kVecX = 64;
 constexpr int kVecY = 4;
 template <class ST, int COLL>
@@ -367,11 +368,20 @@ constexpr bool kPairedSites = sizeof(typename ST::S) == 2 &&
                               (COLL == LBM_LBGK || COLL == LBM_EHRENFEST || COLL == LBM_POSITIVITY ||
                                COLL == LBM_MRT || COLL == LBM_MRT2 || COLL == LBM_MRT_LIMITER);
 
+__device__ __forceinline__ uint32_t ld_word(const void* base, int off) {
+    return *reinterpret_cast<const uint32_t*>(reinterpret_cast<const uint16_t*>(base) + off);
+}
+__device__ __forceinline__ void st_word(void* base, int off, uint32_t v) {
+    *reinterpret_cast<uint32_t*>(reinterpret_cast<uint16_t*>(base) + off) = v;
+}
+__device__ __forceinline__ void st_half(void* base, int off, uint32_t v16) {
+    reinterpret_cast<uint16_t*>(base)[off] = (uint16_t)v16;
+}
+
 template <int Q, class ST, int COLL, bool ODD>
 __global__ void __launch_bounds__(kVecX* kVecY, 6) step_kernel_v2(Params p) {
     pdl_enter();
     using T = typename ST::T;
-    using S = typename ST::S;
     using L = Lat<Q>;
     const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -393,30 +403,28 @@ __global__ void __launch_bounds__(kVecX* kVecY, 6) step_kernel_v2(Params p) {
         return;
     }
     const int lane = threadIdx.x & 31;
-    const int o = y * p.pitch + x0;
-    S* base = (S*)p.f;
+    const int o = y * p.pitch + x0;  // even: every word access is 4-byte aligned
+    void* base = p.f;
     T fa[Q], fb[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int k = ODD ? L::opp(i) : i;
         const int off = k * p.plane32 + o - (ODD ? L::cy(i) * p.pitch : 0);
         const T w = T(L::w(i));
-        T lo, hi;
-        ST::ld2(base + off, w, lo, hi);
-        if (!ODD || L::cx(i) == 0) {
-            fa[i] = lo;
-            fb[i] = hi;
-        } else if (L::cx(i) > 0) {  // sources x0 - 1, x0
-            T prev = __shfl_up_sync(full, hi, 1);
-            if (lane == 0) prev = ST::ld(base + off - 1, w);
-            fa[i] = prev;
-            fb[i] = lo;
-        } else {  // sources x0 + 1, x0 + 2
-            T next = __shfl_down_sync(full, lo, 1);
-            if (lane == 31) next = ST::ld(base + off + 2, w);
-            fa[i] = hi;
-            fb[i] = next;
+        const uint32_t W = ld_word(base, off);  // elements x0, x0 + 1 of the plane row
+        uint32_t pair = W;
+        if (ODD && L::cx(i) > 0) {  // sources x0 - 1, x0: the lane below's high half, our low half
+            uint32_t Wp = __shfl_up_sync(full, W, 1);
+            if (lane == 0) Wp = ld_word(base, off - 2);  // x0 >= 2 here
+            pair = __byte_perm(Wp, W, 0x5432);
+        } else if (ODD && L::cx(i) < 0) {  // sources x0 + 1, x0 + 2: our high half, the lane above's low
+            uint32_t Wn = __shfl_down_sync(full, W, 1);
+            if (lane == 31) Wn = ld_word(base, off + 2);  // x0 + 2 < nx here
+            pair = __byte_perm(W, Wn, 0x5432);
         }
+        const float2 v = ST::unpack(pair);
+        fa[i] = w + v.x;
+        fb[i] = w + v.y;
     }
     T Fa[Q], Fb[Q];
     T acc = 0;
@@ -427,23 +435,23 @@ __global__ void __launch_bounds__(kVecX* kVecY, 6) step_kernel_v2(Params p) {
         const int k = ODD ? L::opp(i) : i;
         const int off = k * p.plane32 + o - (ODD ? L::cy(i) * p.pitch : 0);
         const T w = T(L::w(i));
-        const T va = Fa[L::opp(i)], vb = Fb[L::opp(i)];
+        const uint32_t P = ST::pack(Fa[L::opp(i)] - w, Fb[L::opp(i)] - w);  // (a, b)
         if (!ODD || L::cx(i) == 0) {
-            ST::st2(base + off, va, vb, w);
-        } else if (L::cx(i) > 0) {  // a -> x0 - 1, b -> x0; x0 + 1 belongs to the next lane's a
-            const T nxt = __shfl_down_sync(full, va, 1);
-            if (lane < 31)
-                ST::st2(base + off, vb, nxt, w);
-            else
-                ST::st(base + off, vb, w);
-            if (lane == 0) ST::st(base + off - 1, va, w);
-        } else {  // a -> x0 + 1, b -> x0 + 2; x0 belongs to the previous lane's b
-            const T prv = __shfl_up_sync(full, vb, 1);
-            if (lane > 0)
-                ST::st2(base + off, prv, va, w);
-            else
-                ST::st(base + off + 1, va, w);
-            if (lane == 31) ST::st(base + off + 2, vb, w);
+            st_word(base, off, P);
+        } else if (L::cx(i) > 0) {
+            // a -> x0 - 1, b -> x0: the word at x0 is (b, the lane above's a);
+            // lane 31's x0 + 1 is the next warp's, lane 0 also writes x0 - 1
+            const uint32_t Pn = __shfl_down_sync(full, P, 1);
+            if (lane < 31) st_word(base, off, __byte_perm(P, Pn, 0x5432));
+            if (lane == 31) st_half(base, off, P >> 16);
+            if (lane == 0) st_half(base, off - 1, P & 0xffffu);
+        } else {
+            // a -> x0 + 1, b -> x0 + 2: the word at x0 is (the lane below's b,
+            // a); lane 0's x0 is the previous warp's, lane 31 also writes x0 + 2
+            const uint32_t Pp = __shfl_up_sync(full, P, 1);
+            if (lane > 0) st_word(base, off, __byte_perm(Pp, P, 0x5432));
+            if (lane == 0) st_half(base, off + 1, P & 0xffffu);
+            if (lane == 31) st_half(base, off + 2, P >> 16);
         }
     }
 }
@@ -1281,8 +1289,8 @@ __global__ void __launch_bounds__(256) median_fixup(Params p) {
     median_apply<Q, ST, ODD>(p, blockIdx.x * (blockDim.x >> 4) + (threadIdx.x >> 4), gridDim.x * (blockDim.x >> 4));
 }
 
-// Median filter, second kernel, without a Delta S field (FP32 and FP64
-// storage with |1 - 2 beta| >= 1/16): the step ran LBGK and the Ehrenfest
+// Median filter, second kernel, without a Delta S field (|1 - 2 beta| >= 1/16
+// for FP32 and FP64 storage, >= 1/4 for 16-bit): the step ran LBGK and the Ehrenfest
 // screen at every site, so a window site's pre-collision state is either
 // its record (a screened site) or is recovered from its post-collision one
 // (delta_s_lanes with inv = 1 / (1 - 2 beta)); its Delta S is FP64.  One
