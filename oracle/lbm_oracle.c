@@ -779,7 +779,7 @@ static int config_ok(const orc_config* cfg) {
     if (cfg->lattice != ORC_D1Q3 && cfg->lattice != ORC_D2Q9) return 0;
     if (cfg->nx < 1 || cfg->ny < 1) return 0;
     if (cfg->lattice == ORC_D1Q3 && cfg->ny != 1) return 0;
-    if (cfg->collision < ORC_LBGK || cfg->collision > ORC_MRT_LIMITER) return 0;
+    if (cfg->collision < ORC_LBGK || cfg->collision > ORC_ENSEMBLE_LAGGED) return 0;
     if ((cfg->collision == ORC_MRT2 || cfg->collision == ORC_MRT_LIMITER) && cfg->lattice != ORC_D2Q9) return 0;
     if (cfg->bc == ORC_BC_DIFFUSIVE && (cfg->lattice != ORC_D2Q9 || cfg->nx < 3 || cfg->ny < 3)) return 0;
     return 1;
@@ -876,6 +876,7 @@ int orc_step(const orc_config* cfg, double* f, int nsteps, orc_stats* st) {
     if (cfg->collision == ORC_MRT) orc_mrt_matrix(cfg, A);
     if (cfg->collision == ORC_MRT2 || cfg->collision == ORC_MRT_LIMITER) orc_mrt2_matrix(cfg, A);
     int diffusive = cfg->bc == ORC_BC_DIFFUSIVE;
+    double E_prev = 0.0; /* the lagged ensemble limiter's E of the previous step */
     for (int t = 0; t < nsteps; ++t) {
         double fs[9], feq[9], Fs[9];
         if (diffusive) orc_diffusive_rule(cfg, f);
@@ -911,7 +912,7 @@ int orc_step(const orc_config* cfg, double* f, int nsteps, orc_stats* st) {
                 free(sub);
             } else if (cfg->collision == ORC_MEDIAN) {
                 orc_median_field(cfg->lattice, cfg->nx, cfg->ny, px, py, dS, med);
-            } else if (cfg->collision == ORC_ENSEMBLE) {
+            } else if (cfg->collision == ORC_ENSEMBLE || cfg->collision == ORC_ENSEMBLE_LAGGED) {
                 /* E(Delta S): mean over the sites with a finite value */
                 long long nf = 0;
                 for (long long x = 0; x < N; ++x)
@@ -920,6 +921,13 @@ int orc_step(const orc_config* cfg, double* f, int nsteps, orc_stats* st) {
                         ++nf;
                     }
                 E = nf > 0 ? E / (double)nf : 0.0;
+                if (cfg->collision == ORC_ENSEMBLE_LAGGED) {
+                    /* reading: E of the previous step's pre-collision state,
+                     * this step's own in the first step */
+                    double E_now = E;
+                    if (t > 0) E = E_prev;
+                    E_prev = E_now;
+                }
             } else if (cfg->collision == ORC_THRESHOLD) {
                 /* Delta S_t = max(Delta S_0, delta) */
                 double d0 = orc_threshold_dS0(dS, N, cfg->lim_delta0, cfg->beta);

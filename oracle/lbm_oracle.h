@@ -33,7 +33,10 @@ enum { ORC_LBGK = 0, ORC_ELBM = 1, ORC_EHRENFEST = 2, ORC_POSITIVITY = 3,
        ORC_THRESHOLD = 9,         /* Eqs. EntThresh, entrHom */
        /* Section 5's "aggressive" MRT A_2 = M_2^-1 C_2 M_2 */
        ORC_MRT2 = 10,             /* A_2 collision at every site (D2Q9) */
-       ORC_MRT_LIMITER = 11 };    /* LBGK, A_2 at the Ehrenfest-selected sites */
+       ORC_MRT_LIMITER = 11,      /* LBGK, A_2 at the Ehrenfest-selected sites */
+       /* Eq. phiExamp with E the mean of the PREVIOUS step's Delta S (the
+        * first step of a call uses its own) */
+       ORC_ENSEMBLE_LAGGED = 12 };
 enum { ORC_EQ_POLY_PRODUCT = 0, ORC_EQ_ENTROPIC = 1, ORC_EQ_POLY_STD = 2 };
 enum { ORC_BC_CAVITY = 0, ORC_BC_ENDS = 1, ORC_BC_PERIODIC = 2,
        ORC_BC_CHANNEL = 3,

@@ -22,7 +22,7 @@ _LIB = os.path.join(_HERE, "_build", "liblbm_oracle.so")
 LATTICES = {"D1Q3": 1, "D2Q9": 2}
 COLLISIONS = {"lbgk": 0, "elbm": 1, "ehrenfest": 2, "positivity": 3, "median": 4, "mrt": 5,
               "smooth": 6, "double_monotonic": 7, "ensemble": 8, "threshold": 9, "mrt2": 10,
-              "mrt_limiter": 11}
+              "mrt_limiter": 11, "ensemble_lagged": 12}
 EQUILIBRIA = {"poly": 0, "entropic": 1, "poly_std": 2}
 BCS = {"cavity": 0, "ends": 1, "periodic": 2, "channel": 3, "diffusive": 4}
 NORMS = {"entropic": 0, "l1": 1}

@@ -813,6 +813,35 @@ def test_limiter_steps_compose_phi_homothety_lbgk_and_streaming(collision):
     assert np.abs(O.step(dict(cfg, **neutral[collision]), f, 1) - lbgk).max() < 1e-14
 
 
+def test_lagged_ensemble_limiter_uses_the_previous_steps_mean():
+    """Reading of Eq. phiExamp for the lagged variant: step t uses E(Delta S)
+    of step t - 1's pre-collision state (the first step its own).  Three
+    oracle steps equal the composition f1 = H(f0, E(f0)), f2 = H(f1, E(f0)),
+    f3 = H(f2, E(f1)) of the homothety with phi, the LBGK collision and the
+    streaming; the first step equals the unlagged limiter's, later ones do
+    not."""
+    f0 = _limited_state()
+    cfg = dict(lattice="D2Q9", nx=12, ny=10, bc="cavity", lid_u=0.05, beta=0.95, collision="ensemble_lagged",
+               lim_alpha=40.0, lim_k=1.0)
+
+    def mean_ds(f):
+        d = O.delta_s_field(cfg, f)
+        return d[np.isfinite(d)].mean()
+
+    def H(f, E):
+        phi = np.vectorize(lambda d: O.phi_ensemble(d, 40.0, 1.0, E))(O.delta_s_field(cfg, f))
+        return _homothety_then_lbgk_then_stream(cfg, f, phi)
+
+    f1 = H(f0, mean_ds(f0))
+    f2 = H(f1, mean_ds(f0))
+    f3 = H(f2, mean_ds(f1))
+    assert np.abs(O.step(cfg, f0, 1) - f1).max() < 1e-14
+    assert np.abs(O.step(cfg, f0, 3) - f3).max() < 1e-14
+    plain = O.step(dict(cfg, collision="ensemble"), f0, 1)
+    assert np.abs(O.step(cfg, f0, 1) - plain).max() < 1e-15
+    assert np.abs(O.step(cfg, f0, 3) - O.step(dict(cfg, collision="ensemble"), f0, 3)).max() > 1e-9
+
+
 def test_threshold_limiter_removes_the_entropy_budget():
     """Eq. LimEntLim: when Delta S_0 > delta, the homothety of Eq. entrHom
     lowers the nonequilibrium entropy of the limited sites by
