@@ -31,6 +31,16 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build liblbm.so")
 
 
+def extra_flags(src: str) -> list[str]:
+    """Per-unit flags: the persistent batched kernels read, within one
+    launch, populations and candidate records that CTAs on other SMs wrote
+    in an earlier step of the same launch, so their global loads default to
+    the L2-coherent cache-global mode (no stale L1 lines)."""
+    if os.path.basename(src).startswith("lbm_batch_kernels_"):
+        return ["-Xptxas", "-dlcm=cg"]
+    return []
+
+
 def sources() -> list[str]:
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
@@ -56,7 +66,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src: str) -> str:
         obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *extra_flags(src), "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
