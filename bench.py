@@ -49,7 +49,8 @@ def workload_cfg(collision="ehrenfest", precision="fp32", n=N_SIDE):
 
 # Sections 4.2-4.4 limiters in the variants table
 LIMITER_PARAMS = {"smooth": dict(lim_alpha=40.0, lim_k=1.0), "double_monotonic": dict(lim_dst=2e-3, lim_k=1.5),
-                  "ensemble": dict(lim_alpha=1.0, lim_k=1.0), "threshold": dict(lim_delta0=0.01)}
+                  "ensemble": dict(lim_alpha=1.0, lim_k=1.0), "ensemble_lagged": dict(lim_alpha=1.0, lim_k=1.0),
+                  "threshold": dict(lim_delta0=0.01)}
 
 
 # DRAM bytes per launch of the headline step kernel from the full-size ncu
@@ -201,7 +202,7 @@ def run_variants(n_side, steps, warmup, fma_per_s=None):
     N = n_side * n_side
     for precision in ["fp32", "fp16_dev", "bf16_dev", "fp64"]:
         for coll in ["lbgk", "ehrenfest", "median", "positivity", "mrt", "elbm", "smooth", "double_monotonic",
-                     "ensemble", "threshold", "mrt2", "mrt_limiter"]:
+                     "ensemble", "ensemble_lagged", "threshold", "mrt2", "mrt_limiter"]:
             cfg, init = workload_cfg(coll, precision, n_side)
             lat = lbm.Lattice(cfg)
             lat.init(init["rho"], init["ux"], init["uy"])
@@ -228,35 +229,95 @@ def run_variants(n_side, steps, warmup, fma_per_s=None):
     return out
 
 
-def run_precision_error(n_side, steps):
-    """Storage-precision error at the bandwidth configuration: FP32, FP16 and
-    BF16 deviation storage against FP64 storage (which the parity tests hold
-    to the FP64 oracle within 1e-12), after `steps` steps of the cavity from
-    rest with the Ehrenfest limiter: rel-L2 of rho and u, relative error of
-    the total entropy H."""
+def run_loaded_selection(n_side, hots=(300, 3000, 30000), reps=5):
+    """The headline lattice (4097^2, FP32) one step after lbm_set_state of
+    the cavity at rest with `hot` random sites perturbed (each population
+    times exp(0.3 N(0, 1))): the Ehrenfest (k = 64) and median steps with
+    hundreds to tens of thousands of screened sites, so that the grid-wide
+    FP64 Delta S pass, the radix selection and the median windows are
+    timed, not only the settled-in-FP32 few-candidate path of a flow
+    started from rest.  Per case the median of `reps` single steps (step
+    kernel and follow-up, CUDA events per kernel)."""
     import torch
     from paper_1110_0270_gb300 import lbm
-    out = {"steps": steps, "collision": "ehrenfest", "reference": "fp64 storage"}
-    ref = None
-    for precision in ["fp64", "fp32", "fp16_dev", "bf16_dev"]:
-        cfg, init = workload_cfg("ehrenfest", precision, n_side)
+    w = np.array([4 / 9, 1 / 9, 1 / 36, 1 / 9, 1 / 36, 1 / 9, 1 / 36, 1 / 9, 1 / 36], np.float32)
+    base = np.broadcast_to(w[:, None, None], (9, n_side, n_side))
+    rng = np.random.default_rng(17)
+    out = {}
+    for coll in ["ehrenfest", "median"]:
+        cfg, _ = workload_cfg(coll, "fp32", n_side)
         lat = lbm.Lattice(cfg)
-        lat.init(init["rho"], init["ux"], init["uy"])
-        lat.step(steps)
-        rho, u = lat.macros(torch.float64)
-        H = lat.entropy()
-        if ref is None:
-            ref = (rho, u, H)
-        else:
-            nrm = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
-            out[precision] = {"rho_rel_l2": nrm(rho, ref[0]), "rho_dev_rel_l2": nrm(rho - 1.0, ref[0] - 1.0),
-                              "u_rel_l2": nrm(u, ref[1]),
-                              "H_abs_diff_per_site": abs(H - ref[2]) / (n_side * n_side)}
-        del lat, rho, u
+        rows = []
+        for hot in hots:
+            f = np.array(base)
+            ys, xs = rng.integers(2, n_side - 2, hot), rng.integers(2, n_side - 2, hot)
+            f[:, ys, xs] *= np.exp(0.3 * rng.standard_normal((9, hot))).astype(np.float32)
+            ft = torch.from_numpy(f).cuda()
+            del f
+            times = []
+            for _ in range(reps):
+                lat.set_state(ft)
+                torch.cuda.synchronize()
+                lat.profile(True)
+                lat.step(1)
+                prof = lat.profile_read()
+                lat.profile(False)
+                times.append((prof["step"][1], prof["fixup"][1]))
+            st = lat.stats()
+            times.sort(key=lambda t: t[0] + t[1])
+            k_ms, f_ms = times[len(times) // 2]
+            rows.append({"hot_sites": hot, "screened": st["screened_last"], "candidates": st["candidates_last"],
+                         "limited": st["limited_total"], "step_kernel_ms": round(k_ms, 5),
+                         "followup_ms": round(f_ms, 5), "ms_per_step": round(k_ms + f_ms, 5),
+                         "mlups": round(n_side * n_side / ((k_ms + f_ms) * 1e-3) / 1e6, 1)})
+            del ft
+        out[coll] = rows
+        del lat
         torch.cuda.empty_cache()
-    out["H_fp64_per_site"] = ref[2] / (n_side * n_side)
-    out["note"] = ("rho_dev_rel_l2 is taken on rho - 1, the part that varies; H is near zero for a "
-                   "fluid mostly at rest, so its error is given per site, not relative")
+    return out
+
+
+GOLDEN_513 = os.path.join(ROOT, "tests", "golden", "cavity513_re10000.npz")
+
+
+def run_precision_error(n_side=None, steps=None):
+    """Storage-precision error of the bandwidth configuration against the
+    FP64 oracle, on the reduced 513 x 513 run that stands for it (the same
+    Re 10000 and U 0.05, 2000 steps from rest): each storage format's GPU
+    run against the oracle's fields stored by tests/golden/make_cavity513.py
+    (rho, u at every 8th site, totals of mass and H), for the Ehrenfest and
+    median limiters (plain LBGK diverges at this resolution): rel-L2
+    of rho - 1 and of u on the sampled sites, relative errors of the total
+    mass and of H."""
+    import torch
+    from paper_1110_0270_gb300 import lbm
+    from paper_1110_0270_gb300 import workloads as WL
+    g = np.load(GOLDEN_513)
+    n, re, u0, steps, stride = int(g["n"]), float(g["re"]), float(g["u"]), int(g["steps"]), int(g["stride"])
+    out = {"reference": "FP64 oracle (tests/golden/cavity513_re10000.npz)", "lattice": f"{n}x{n}", "re": re,
+           "u": u0, "steps": steps, "sample_stride": stride}
+    nrm = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    for coll in ["ehrenfest", "median"]:  # plain LBGK diverges at 513^2, Re 10000
+        extra = {"ehrenfest": dict(topk=64, delta=1e-3), "median": dict(delta=1e-3)}[coll]
+        rows = {}
+        for precision in ["fp64", "fp32", "fp16_dev", "bf16_dev"]:
+            cfg, init = WL.cavity(n, re, u0)
+            cfg.update(collision=coll, precision=precision, **extra)
+            lat = lbm.Lattice(cfg)
+            lat.init(init["rho"], init["ux"], init["uy"])
+            lat.step(steps)
+            rho, u = lat.macros(torch.float64)
+            rho, u = rho.cpu().numpy(), u.cpu().numpy()
+            f = lat.get_state(torch.float64)
+            sub = np.s_[::stride, ::stride]
+            H = lat.entropy()
+            rows[precision] = {
+                "rho_dev_rel_l2": nrm(rho[sub] - 1.0, g[f"{coll}_rho"] - 1.0),
+                "u_rel_l2": nrm(np.stack([u[0][sub], u[1][sub]]), np.stack([g[f"{coll}_ux"], g[f"{coll}_uy"]])),
+                "mass_rel": abs(float(f.sum()) - float(g[f"{coll}_mass"])) / float(g[f"{coll}_mass"]),
+                "H_rel": abs(H - float(g[f"{coll}_H"])) / abs(float(g[f"{coll}_H"]))}
+            del lat, f
+        out[coll] = rows
     return out
 
 
@@ -314,36 +375,71 @@ def batched_configs(precision="fp32", seed=0, n=512):
     return out
 
 
-def run_batched(steps, warmup, fp64_mlups=None, separate=True):
-    """Aggregate MLUPS of the batched form against the same instances run as
-    separate single-lattice contexts (one lbm_step per instance per step)."""
+def run_batched(steps, warmup, fp64_mlups=None, separate=True, tune=True):
+    """The batched configuration (512 cavities, FP32): aggregate MLUPS of the
+    persistent batched kernels with the default launch options and with the
+    options the library's autotuner picks (its sweep recorded), the time and
+    HBM fraction of each collision group advanced alone, and the same
+    instances run as separate single-lattice contexts (one lbm_step per
+    instance per step)."""
     import torch
     from paper_1110_0270_gb300 import lbm
     hbm, _ = peaks()
     cfgs = batched_configs()
     sites = sum(c["nx"] * c["ny"] for c in cfgs)
-    b = lbm.Batch(cfgs)
-    b.init_uniform(1.0, 0.0, 0.0)
-    b.step(warmup)
-    torch.cuda.synchronize()
     s = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(s)
-    b.step(steps)
-    e1.record(s)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
+
+    def timed(opts):
+        b = lbm.Batch(cfgs, opts=opts)
+        b.init_uniform(1.0, 0.0, 0.0)
+        b.step(warmup)
+        torch.cuda.synchronize()
+        e0.record(s)
+        b.step(steps)
+        e1.record(s)
+        torch.cuda.synchronize()
+        return b, e0.elapsed_time(e1) / steps
+
+    b, ms = timed(None)
     status = b.step(0, status=True)
+    group_sites = {}
+    for c in cfgs:
+        group_sites[c["collision"]] = group_sites.get(c["collision"], 0) + c["nx"] * c["ny"]
+    gt = b.group_times(steps)
+    groups = {}
+    for k, t in gt.items():
+        per = t / steps
+        groups[k] = {"instances": sum(1 for c in cfgs if c["collision"] == k), "sites": group_sites[k],
+                     "ms_per_step": round(per, 4), "mlups": round(group_sites[k] / (per * 1e-3) / 1e6, 1),
+                     "hbm_frac": round(72 * group_sites[k] / (per * 1e-3) / 1e9 / hbm, 4)}
     out = {"instances": len(cfgs), "sites": sites, "steps": steps, "ms_per_step": round(ms, 4),
            "mlups": round(sites / (ms * 1e-3) / 1e6, 1),
            "hbm_frac_if_all_streaming": round(72 * sites / (ms * 1e-3) / 1e9 / hbm, 4),
            "diverged_instances": sum(1 for v in status if v != "LBM_OK"),
-           "groups": {k: sum(1 for c in cfgs if c["collision"] == k) for k in
-                      ["lbgk", "elbm", "ehrenfest", "median"]},
-           "note": "one CUDA graph of two steps per replay; collision groups are parallel "
-                   "branches; ELBM instances dominate (FP64 root finder)"}
+           "opts": b.opts, "groups": groups,
+           "note": "persistent kernels (HBM-bound collisions; ELBM) on parallel branches of a CUDA graph; "
+                   "groups: each collision's instances alone, HBM fraction at 72 B per site update"}
     del b
     torch.cuda.empty_cache()
+    def tuned():
+        t0 = time.perf_counter()
+        opts, sweep = lbm.tune_batch(cfgs, steps=2)
+        tb, tms = timed(opts)
+        tg = tb.group_times(steps)
+        del tb
+        torch.cuda.empty_cache()
+        return {"opts": opts, "ms_per_step": round(tms, 4), "mlups": round(sites / (tms * 1e-3) / 1e6, 1),
+                "tune_s": round(time.perf_counter() - t0, 2),
+                "groups_hbm_frac": {k: round(72 * group_sites[k] / (t / steps * 1e-3) / 1e9 / hbm, 4)
+                                    for k, t in tg.items()},
+                "sweep": [[o["tile_x"], o["tile_rows"], o["ctas_per_sm"], o["chunk"], o["order"], round(m, 4),
+                           round(r, 4)] for o, m, r in sweep],
+                "sweep_columns": ["tile_x", "tile_rows", "ctas_per_sm", "chunk", "order",
+                                  "groups_ms_per_step_summed", "objective_mean_relative_group_time"]}
+
+    if tune:
+        guarded(out, "tuned", tuned)
     if separate:
         lats = []
         for c in cfgs:
@@ -673,8 +769,10 @@ def run_sections(args, result, init):
                 lambda: run_variants(args.side, args.variant_steps, 3, r.get("dfma_flops", 0) / 2 or None))
     if not args.no_small:
         guarded(result, "small_configs", run_small_configs)
-    if args.precision_steps > 0:
-        guarded(result, "precision_error", lambda: run_precision_error(args.side, args.precision_steps))
+    if not args.no_variants:
+        guarded(result, "loaded_selection", lambda: run_loaded_selection(args.side))
+    if args.precision_steps > 0 and os.path.exists(GOLDEN_513):
+        guarded(result, "precision_error", run_precision_error)
     if not args.no_small:
         guarded(result, "shear_decay", run_shear_decay)
     if args.adjoint_steps > 0:
@@ -735,13 +833,14 @@ def main():
     ap.add_argument("--side", type=int, default=N_SIDE)
     ap.add_argument("--collision", default="ehrenfest",
                     choices=["lbgk", "elbm", "ehrenfest", "positivity", "median", "mrt", "smooth",
-                             "double_monotonic", "ensemble", "threshold", "mrt2", "mrt_limiter"])
+                             "double_monotonic", "ensemble", "ensemble_lagged", "threshold", "mrt2",
+                             "mrt_limiter"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16_dev", "bf16_dev"])
     ap.add_argument("--variant-steps", type=int, default=100)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-small", action="store_true", help="skip the tube and 257^2 runs")
-    ap.add_argument("--precision-steps", type=int, default=200,
-                    help="steps of the storage-precision comparison (0 skips it)")
+    ap.add_argument("--precision-steps", type=int, default=1,
+                    help="0 skips the storage-precision comparison against the oracle's 513^2 fields")
     ap.add_argument("--adjoint-steps", type=int, default=4000,
                     help="T of the adjoint run (0 skips it)")
     ap.add_argument("--batch-steps", type=int, default=20,

@@ -93,8 +93,14 @@ enum { LBM_LBGK = 0, LBM_ELBM = 1, LBM_EHRENFEST = 2, LBM_POSITIVITY = 3,
         * every moment but the two shear moments relaxes to equilibrium,
         * those at s_nu = 2 beta */
        LBM_MRT2 = 10,            /* F = f - A_2 (f - f*) at every site */
-       LBM_MRT_LIMITER = 11 };   /* LBGK; the Ehrenfest selection (topk, delta)
+       LBM_MRT_LIMITER = 11,     /* LBGK; the Ehrenfest selection (topk, delta)
                                     gets A_2 instead of f* */
+       LBM_ENSEMBLE_LAGGED = 12 }; /* LBM_ENSEMBLE with E(Delta S) the mean over
+                                    the previous step's pre-collision state
+                                    (accumulated by that step; the first step
+                                    after lbm_init / lbm_set_state uses its
+                                    own, computed there): no pass over the
+                                    state before each step */
 /* Equilibria: product of the 1D polynomial equilibria of Section 6 (the
  * paper's D2Q9 choice, Section 8), product of the 1D entropic equilibria
  * (always used by ELBM), or the textbook W_i rho (1 + 3cu + 9/2 (cu)^2 - 3/2 u^2). */
@@ -121,7 +127,7 @@ enum { LBM_DTYPE_F64 = 0, LBM_DTYPE_F32 = 1 };
 typedef struct {
     int lattice;     /* LBM_D1Q3 | LBM_D2Q9 */
     int nx, ny;      /* sites; ny = 1 for D1Q3.  nx, ny >= 1 */
-    int collision;   /* LBM_LBGK ... LBM_MRT_LIMITER */
+    int collision;   /* LBM_LBGK ... LBM_ENSEMBLE_LAGGED */
     int equilibrium; /* LBM_EQ_*; ignored by LBM_ELBM (always entropic) */
     int precision;   /* LBM_FP64 | LBM_FP32 | LBM_BF16_DEV | LBM_FP16_DEV */
     int bc;          /* LBM_BC_* */
@@ -271,35 +277,116 @@ lbm_status lbm_stats_get(lbm_ctx* ctx, lbm_stats* out, void* stream);
 lbm_status lbm_last_candidates(lbm_ctx* ctx, double* ds, int32_t* site, int32_t* selected,
                                int cap, int* count, void* stream);
 
-/* ---- Batched form: many independent D2Q9 lattices in one context --------
- * All instances share the lattice (D2Q9) and the precision of cfgs[0]; size,
- * boundary, collision, beta, lid, limiter and MRT/ELBM parameters are per
- * instance.  One launch per collision kind covers every instance of that
- * kind (a CTA per 128 x 2 tile); two steps are captured once, at creation,
- * into a CUDA graph whose collision groups are independent branches, and
- * lbm_batch_step replays it.  Memory: one caller device allocation of
- * lbm_batch_required_bytes (populations, limiter scratch, descriptors and
- * work lists); nothing is allocated afterwards. */
+/* ---- Batched form: many independent lattices in one context -------------
+ * Instances: D2Q9 cavities, channels or periodic boxes and D1Q3 tubes (ends)
+ * or rings, of any size, mixed in one batch; they share the precision of
+ * cfgs[0]; size, lattice, boundary, collision (LBM_LBGK ... LBM_MRT), beta,
+ * lid, limiter and MRT/ELBM parameters are per instance.
+ *
+ * Persistent launch: one kernel launch advances every instance of its group
+ * several steps.  Its CTAs claim work items - (step, instance, tile) in step
+ * order - from a device queue until the queue is drained; an item waits until
+ * its instance has completed the previous step (a per-instance step
+ * generation), so instances advance independently, without a barrier
+ * between steps, and the CTA that completes an instance's step runs that
+ * instance's limiter fix-up (Ehrenfest selection, median filter) before
+ * publishing it.  Three kernels, on parallel stream branches: the streaming
+ * collisions (LBGK, positivity, MRT), the limiters (Ehrenfest, median) and
+ * ELBM (its FP64 root finder needs far more registers).
+ * graph_steps steps of both are captured once, at creation, into a CUDA
+ * graph that lbm_batch_step replays.  Every wait is bounded (wait_ms): one
+ * that runs out stops the launch and the next status check returns
+ * LBM_ERR_TIMEOUT (the states are then undefined until re-initialised).
+ *
+ * Memory: one caller device allocation of lbm_batch_required_bytes(_ex)
+ * (populations, limiter scratch, descriptors, work queues and step
+ * generations); nothing is allocated afterwards. */
 typedef struct lbm_batch lbm_batch; /* opaque, owned by the library */
+
+/* Launch shape and schedule of a batch (the autotuner's knobs). */
+enum { LBM_BATCH_ORDER_INSTANCE = 0,     /* an instance's tiles one after another */
+       LBM_BATCH_ORDER_INTERLEAVED = 1 }; /* tile j of every instance, then j + 1 */
+typedef struct {
+    int tile_x;       /* D2Q9 tile width in sites: 16, 32, 64, 128 or 256; the
+                         tile is tile_x x (256 / tile_x) sites, one per thread
+                         (D1Q3 tiles are 256 sites of the line) */
+    int ctas_per_sm;  /* CTAs per SM of each kernel, 0 = as many as fit */
+    int chunk;        /* work items claimed per queue access (1 ... 1024) */
+    int order;        /* LBM_BATCH_ORDER_* within a step */
+    int graph_steps;  /* steps per launch in the replayed graph (1 ... 4096) */
+    double wait_ms;   /* limit of one wait for an instance's previous step */
+    int tile_rows;    /* tiles per work item, stacked along y (D1Q3: along the
+                         line), 1 ... 64 */
+} lbm_batch_opts;
+/* Defaults: tile 128 x 2, 4 tiles per item, as many CTAs as fit, chunk 4,
+ * instance order, 16 steps per graph launch, 1000 ms waits. */
+lbm_status lbm_batch_opts_default(lbm_batch_opts* opts);
+
 lbm_status lbm_batch_required_bytes(const lbm_config* cfgs, int n, size_t* bytes);
-/* Creates the batch over dev_mem (256-byte aligned) on the current device;
- * copies the descriptors and builds the graph (synchronous). */
+/* The same for explicit options (NULL: defaults); LBM_ERR_ARG for an invalid
+ * batch or option. */
+lbm_status lbm_batch_required_bytes_ex(const lbm_config* cfgs, int n, const lbm_batch_opts* opts,
+                                       size_t* bytes);
+/* Creates the batch over dev_mem (256-byte aligned) on the current device
+ * with the default options; copies the descriptors and queues and builds
+ * the graph (synchronous). */
 lbm_status lbm_batch_create(const lbm_config* cfgs, int n, void* dev_mem, size_t bytes,
                             lbm_batch** out);
+lbm_status lbm_batch_create_ex(const lbm_config* cfgs, int n, const lbm_batch_opts* opts, void* dev_mem,
+                               size_t bytes, lbm_batch** out);
+lbm_status lbm_batch_get_opts(const lbm_batch* b, lbm_batch_opts* opts);
 void lbm_batch_destroy(lbm_batch* b);
 /* Every instance to the equilibrium of a uniform (rho, u) (entropic for ELBM
- * instances, the configured one otherwise); resets the step counter. */
+ * instances, the configured one otherwise; u_y ignored for D1Q3); resets the
+ * step counter. */
 lbm_status lbm_batch_init_uniform(lbm_batch* b, double rho, double ux, double uy, void* stream);
-/* Per-instance state transfer, dense DEVICE f[9][ny][nx] as in
+/* Per-instance state transfer, dense DEVICE f[Q][ny][nx] as in
  * lbm_set_state / lbm_get_state.  set_state needs an even step count. */
 lbm_status lbm_batch_set_state(lbm_batch* b, int instance, const void* f, int dtype, void* stream);
 lbm_status lbm_batch_get_state(lbm_batch* b, int instance, void* f, int dtype, void* stream);
-/* Advances every instance nsteps steps.  If status is not NULL it receives,
- * per instance, LBM_OK or LBM_ERR_DIVERGED (a non-finite or non-positive
- * density seen since creation or the last init), which synchronises `stream`. */
+/* Advances every instance nsteps steps (graph replays, the remainder as
+ * direct launches).  If status is not NULL it receives, per instance,
+ * LBM_OK or LBM_ERR_DIVERGED (a non-finite or non-positive density seen
+ * since creation or the last init); this synchronises `stream` and returns
+ * LBM_ERR_TIMEOUT if a bounded wait ran out since the last check. */
 lbm_status lbm_batch_step(lbm_batch* b, int nsteps, int* status, void* stream);
+/* Per-collision-group timing: for each collision k = LBM_LBGK ... LBM_MRT,
+ * the instances of that collision alone advance nsteps steps in one
+ * persistent launch timed with CUDA events on `stream`; ms[k] receives its
+ * time in milliseconds (0 for a collision without instances).  Every
+ * instance ends nsteps steps further, as after lbm_batch_step.
+ * Synchronises `stream`; LBM_ERR_TIMEOUT as lbm_batch_step. */
+lbm_status lbm_batch_group_times(lbm_batch* b, int nsteps, double* ms, void* stream);
 lbm_status lbm_batch_stats(lbm_batch* b, int instance, lbm_stats* out, void* stream);
 const char* lbm_batch_last_error(const lbm_batch* b);
+
+/* Autotuner.  Sweeps one knob at a time from *best (tile width 32, 64, 128,
+ * 256; tiles per item 1, 2, 4, 8, 16; CTAs per SM 0, 6, 4, 2; chunk 1, 4, 16;
+ * both orders), keeping each value that lowers the objective, and writes the
+ * winner to *best and its objective to *best_obj.  Each candidate is a batch
+ * of cfgs created over dev_mem (at least lbm_batch_tune_bytes; it is
+ * overwritten), started from rest, two steps of warm-up, then `steps` steps
+ * of each collision group alone (lbm_batch_group_times) on `stream`
+ * (synchronised).  The objective is the mean over the groups of each
+ * group's time relative to its time with the starting options (1 = the
+ * start), so that every group weighs alike.  Up to cap candidates (options,
+ * summed group time per step in ms, objective) go to records (may be NULL)
+ * and *nrec receives how many were timed. */
+typedef struct {
+    lbm_batch_opts opts;
+    double ms_per_step;
+    double objective;
+} lbm_batch_tune_record;
+lbm_status lbm_batch_tune_bytes(const lbm_config* cfgs, int n, size_t* bytes);
+lbm_status lbm_batch_tune(const lbm_config* cfgs, int n, void* dev_mem, size_t bytes, int steps,
+                          lbm_batch_opts* best, lbm_batch_tune_record* records, int cap, int* nrec,
+                          double* best_obj, void* stream);
+
+/* Testing support for the bounded waits: sets the step generation of
+ * `instance` one step behind the batch, so that the instance's next step
+ * waits for a step that is never published and runs into wait_ms
+ * (synchronous; LBM_ERR_STATE before the first step). */
+lbm_status lbm_batch_debug_hold(lbm_batch* b, int instance, void* stream);
 
 /* ---- Adjoint: reverse-mode gradient ---------------------------------------
  * For the LBGK, Ehrenfest, median-filter and positivity collisions (no

@@ -31,7 +31,7 @@ const char* check_config(const lbm_config* c) {
     if (c->ny > 65535LL * kBlockY) return "ny too large for the launch grid";
     if ((long long)(c->lattice == LBM_D1Q3 ? 3 : 9) * c->ny * ((c->nx + 31) / 32 * 32) >= 0x7fffffffLL)
         return "Q * ny * pitch must be below 2^31 elements";
-    if (c->collision < LBM_LBGK || c->collision > LBM_MRT_LIMITER) return "unknown collision";
+    if (c->collision < LBM_LBGK || c->collision > LBM_ENSEMBLE_LAGGED) return "unknown collision";
     if ((c->collision == LBM_MRT2 || c->collision == LBM_MRT_LIMITER) && c->lattice != LBM_D2Q9)
         return "LBM_MRT2 and LBM_MRT_LIMITER need D2Q9";
     if (c->equilibrium < LBM_EQ_POLY_PRODUCT || c->equilibrium > LBM_EQ_POLY_STD) return "unknown equilibrium";
@@ -45,10 +45,11 @@ const char* check_config(const lbm_config* c) {
     if (!std::isfinite(c->lid_u)) return "lid_u must be finite";
     if (c->topk < 0) return "topk must be >= 0";
     if (!(c->delta >= 0.0)) return "delta must be >= 0";
-    if (c->collision == LBM_SMOOTH || c->collision == LBM_ENSEMBLE) {
+    const bool ensemble = c->collision == LBM_ENSEMBLE || c->collision == LBM_ENSEMBLE_LAGGED;
+    if (c->collision == LBM_SMOOTH || ensemble) {
         if (!(c->lim_alpha > 0.0 && std::isfinite(c->lim_alpha))) return "lim_alpha must be > 0";
     }
-    if (c->collision == LBM_SMOOTH || c->collision == LBM_ENSEMBLE || c->collision == LBM_DOUBLE_MONOTONIC) {
+    if (c->collision == LBM_SMOOTH || ensemble || c->collision == LBM_DOUBLE_MONOTONIC) {
         if (!(c->lim_k > 0.0 && std::isfinite(c->lim_k))) return "lim_k must be > 0";
     }
     if (c->collision == LBM_DOUBLE_MONOTONIC && !(c->lim_dst > 0.0)) return "lim_dst must be > 0";
@@ -139,7 +140,7 @@ bool limiter(int coll) {
     return coll == LBM_EHRENFEST || coll == LBM_MEDIAN || coll == LBM_THRESHOLD || coll == LBM_MRT_LIMITER;
 }
 // collisions that reduce over the lattice each step
-bool reduces(int coll) { return coll == LBM_ENSEMBLE || coll == LBM_THRESHOLD; }
+bool reduces(int coll) { return coll == LBM_ENSEMBLE || coll == LBM_THRESHOLD || coll == LBM_ENSEMBLE_LAGGED; }
 
 struct Layout {
     int Q, pitch;
@@ -275,6 +276,17 @@ lbm_status reset_counters(lbm_ctx* ctx, cudaStream_t s) {
     return LBM_OK;
 }
 
+// The lagged ensemble limiter's E(Delta S) for the first step of a new
+// state: the mean over that state itself (the unlagged limiter's pre-pass).
+lbm_status initial_mean(lbm_ctx* ctx, cudaStream_t s) {
+    if (ctx->cfg.collision != LBM_ENSEMBLE_LAGGED) return LBM_OK;
+    Params q = ctx->p;
+    q.pdl = 0;
+    LBM_CK(ctx, dispatch(ctx->cfg.precision,
+                         [&](auto L) { return decltype(L)::prepass(ctx->Q, LBM_ENSEMBLE, false, q, s); }));
+    return LBM_OK;
+}
+
 }  // namespace
 
 namespace {
@@ -298,7 +310,7 @@ cudaError_t enqueue_one_step(lbm_ctx* ctx, bool odd, int cslot, cudaStream_t s) 
         });
     if (e == cudaSuccess && q.diffusive)  // the wall sites of the same step
         e = dispatch(ctx->cfg.precision, [&](auto L) { return decltype(L)::walls(odd, q, s); });
-    if (e == cudaSuccess && limiter(coll))
+    if (e == cudaSuccess && (limiter(coll) || coll == LBM_ENSEMBLE_LAGGED))
         e = traced(ctx, LBM_KERNEL_FIXUP, s, [&] {
             return dispatch(ctx->cfg.precision,
                             [&](auto L) { return decltype(L)::fixup(ctx->Q, coll, odd, q, s, ctx->nsm); });
@@ -507,7 +519,7 @@ lbm_status lbm_init_device(lbm_ctx* ctx, const double* rho, const double* ux, co
            }));
     ctx->parity = 0;
     ctx->t = 0;
-    return LBM_OK;
+    return initial_mean(ctx, S(stream));
 }
 
 lbm_status lbm_init(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy, void* stream) {
@@ -534,7 +546,7 @@ lbm_status lbm_set_state(lbm_ctx* ctx, const void* f, int dtype, void* stream) {
            }));
     ctx->parity = 0;
     ctx->t = 0;
-    return LBM_OK;
+    return initial_mean(ctx, S(stream));
 }
 
 lbm_status lbm_get_state(lbm_ctx* ctx, void* f, int dtype, void* stream) {

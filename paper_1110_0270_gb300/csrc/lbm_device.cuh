@@ -329,7 +329,7 @@ __device__ __forceinline__ bool slack_reaches(float v, float q, float rho, float
 
 // Ehrenfest: g(x) <= x^2 for |x| < 1/2, and with m = min_i f*_i > 0 and
 // s2 = sum d^2, max |x| <= max |d| / m <= sqrt(s2) / m, so s2 < m^2 / 4 gives
-// Delta S <= sum d^2 / f* <= s2 / m.  One reciprocal per site and no
+// Delta S <= sum d^2 / f* <= s2 / m.  One approximate division per site and no
 // per-population division; the looseness (up to ~30x near equilibrium) only
 // lets more sites through to the exact test.  A negative population fails
 // the first test (|d_i| > f*_i >= m).
@@ -343,7 +343,7 @@ __device__ __forceinline__ bool maybe_above_loose(const float* f, const float* f
         m = fminf(m, feq[i]);
     }
     if (!(m > 0.f) || !(s2 < 0.25f * m * m)) return true;  // also NaN
-    const float q = s2 * __frcp_rn(m);
+    const float q = __fdividef(s2, m);  // approximate (2 ulp), far inside the slack
     return slack_reaches(q, q, rho, delta);
 }
 
@@ -597,7 +597,11 @@ __device__ __forceinline__ void elbm_eval(const double* feq, const double* D, co
                                           double& s2) {
     const double ax = fabs(a - 1.0) * amax_d;  // max |x_i| at this alpha
     float c;
-    if (ax < 0.015625)
+    if (ax < 0x1p-20)
+        elbm_sum<Q, 2, 2>(feq, D, R, gm, Df, gf, a, s0, s1, c);
+    else if (ax < 0x1p-10)
+        elbm_sum<Q, 5, 5>(feq, D, R, gm, Df, gf, a, s0, s1, c);
+    else if (ax < 0.015625)
         elbm_sum<Q, 8, 9>(feq, D, R, gm, Df, gf, a, s0, s1, c);
     else if (ax < 0.125)
         elbm_sum<Q, 16, 18>(feq, D, R, gm, Df, gf, a, s0, s1, c);
@@ -606,6 +610,55 @@ __device__ __forceinline__ void elbm_eval(const double* feq, const double* D, co
     else
         elbm_sum<Q, 0, 0>(feq, D, R, gm, Df, gf, a, s0, s1, c);
     s2 = (double)c;
+}
+
+// FP32 evaluation of S_f, S_f', S_f'' (the same cancellation-free form),
+// for the iterations that bring alpha near the root before the FP64 ones.
+// Series tiers for FP32 (first omitted term below 2^-24 of the leading one).
+template <int K>
+__device__ __forceinline__ float lpoly_f(float x) {
+    float p = ((K & 1) ? -1.0f : 1.0f) / (float)(K + 1);
+#pragma unroll
+    for (int k = K - 1; k >= 0; --k) p = fmaf(p, x, ((k & 1) ? -1.0f : 1.0f) / (float)(k + 1));
+    return p;
+}
+
+template <int Q, int K>
+__device__ __forceinline__ void elbm_sum_f(const float* fe, const float* Df, const float* Rf, const float* gmf,
+                                           const float* gf, float a, float& s0, float& s1, float& s2) {
+    float A = 0.f, B = 0.f, C = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float x = (a - 1.f) * Rf[i];
+        float g, l;
+        if (K > 0) {
+            g = x * x * gpoly_f<K>(x);
+            l = x * lpoly_f<K>(x);
+        } else {
+            const float xc = x < -1.f ? -1.f : x;
+            l = log1pf(xc);
+            g = xc <= -1.f ? 1.f : (1.f + xc) * l - xc;
+        }
+        A = fmaf(fe[i], gmf[i] - g, A);
+        B = fmaf(-Df[i], l, B);
+        C -= Df[i] * Df[i] / fmaxf(gf[i] + a * Df[i], 1e-37f);
+    }
+    s0 = A;
+    s1 = B;
+    s2 = C;
+}
+
+template <int Q>
+__device__ __forceinline__ void elbm_eval_f(const float* fe, const float* Df, const float* Rf, const float* gmf,
+                                            const float* gf, float amax_d, float a, float& s0, float& s1,
+                                            float& s2) {
+    const float ax = fabsf(a - 1.f) * amax_d;
+    if (ax < 0.015625f)
+        elbm_sum_f<Q, 4>(fe, Df, Rf, gmf, gf, a, s0, s1, s2);
+    else if (ax < 0.25f)
+        elbm_sum_f<Q, 11>(fe, Df, Rf, gmf, gf, a, s0, s1, s2);
+    else
+        elbm_sum_f<Q, 0>(fe, Df, Rf, gmf, gf, a, s0, s1, s2);
 }
 
 struct ElbmOut {
@@ -617,7 +670,9 @@ struct ElbmOut {
 // Root finder of Section 3.3: start at the LBGK value alpha = 2, step to the
 // greater root of the local second-order Taylor parabola, stop when
 // |S_f / S_f'| ||f* - f|| < eps (Eqs. Stopping, ConvergenceTwo), and take the
-// double Newton step back if the estimate ended above the root.  Sites with
+// double Newton step back if the estimate ended above the root.  The first
+// steps run in FP32, the rest - and every decision - in FP64 (the reported
+// iteration count is that of the FP64 steps).  Sites with
 // Delta S < 1e-15 take the LBGK step (in FP32 or 16-bit storage: below
 // 1e-15 + 2^-48 rho, the floor the storage rounding alone produces).  Where
 // the paper is silent: iterates are
@@ -662,6 +717,43 @@ __device__ ElbmOut elbm_alpha(const double* f, const double* feq, double rho, co
     if (p.elbm_norm != LBM_NORM_L1) nrm = sqrt(nrm);
     double lo = 1.0, hi = amax;
     double a = (2.0 < amax) ? 2.0 : 0.5 * (1.0 + amax);
+    {
+        // FP32 parabola iterations from the same start: they bring alpha to
+        // about 1e-6 of the root (their S_f carries ~1e-6 of Delta S in
+        // rounding), so that the FP64 iterations below - which decide the
+        // root's existence, take the steps to the stopping test and the final
+        // correction - start next to it and mostly need one step.  FP64
+        // evaluations are the cost of this solve on GB300.
+        float fe32[Q], R32[Q], gm32[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            fe32[i] = (float)feq[i];
+            R32[i] = (float)R[i];
+            gm32[i] = (float)gm[i];
+        }
+        const float amf = (float)amax, dmf = (float)dmax;
+        float af = (float)a, lof = 1.f, hif = amf;
+        for (int k = 0; k < 8; ++k) {
+            float t0, t1, t2;
+            elbm_eval_f<Q>(fe32, Df, R32, gm32, gf, dmf, af, t0, t1, t2);
+            if (t0 > 0.f)
+                lof = af;
+            else
+                hif = af;
+            const float disc = t1 * t1 - 2.f * t0 * t2;
+            float next = __int_as_float(0x7fc00000);
+            if (disc >= 0.f) {
+                const float q = -0.5f * (t1 + copysignf(sqrtf(disc), t1));
+                next = af + fmaxf(q / (0.5f * t2), t0 / q);
+            }
+            if (!(next > lof && next < hif)) next = 0.5f * (lof + hif);
+            const bool done = fabsf(next - af) <= 1e-6f * af;
+            af = next;
+            if (done) break;
+        }
+        const double ad = (double)af;
+        if (ad > 1.0 && ad < amax) a = ad;
+    }
     double s0, s1, s2;
     elbm_eval<Q>(feq, D, R, gm, Df, gf, dmax, a, s0, s1, s2);
     if (s0 > 0.0) {
@@ -748,29 +840,32 @@ __device__ __forceinline__ int interior_offset(const Params& p, int o, int i) {
     return ODD ? L::opp(i) * p.plane32 + o - L::cy(i) * p.pitch - L::cx(i) : i * p.plane32 + o;
 }
 
-template <int Q, class ST, bool ODD>
+// DEV: move the stored deviation f_i - W_i itself (16-bit formats; the
+// lid term is additive, so it applies to the deviation unchanged).
+template <int Q, class ST, bool ODD, bool DEV = false>
 __device__ __forceinline__ void load_interior(const Params& p, int o, typename ST::T* f) {
     using T = typename ST::T;
     using L = Lat<Q>;
     const typename ST::S* base = (const typename ST::S*)p.f;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = ST::ld(base + interior_offset<Q, ST, ODD>(p, o, i), T(L::w(i)));
+    for (int i = 0; i < Q; ++i)
+        f[i] = ST::ld(base + interior_offset<Q, ST, ODD>(p, o, i), DEV ? T(0) : T(L::w(i)));
 }
 
-template <int Q, class ST, bool ODD>
+template <int Q, class ST, bool ODD, bool DEV = false>
 __device__ __forceinline__ void store_interior(const Params& p, int o, const typename ST::T* F) {
     using T = typename ST::T;
     using L = Lat<Q>;
     typename ST::S* base = (typename ST::S*)p.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i)
-        ST::st(base + interior_offset<Q, ST, ODD>(p, o, i), F[L::opp(i)], T(L::w(i)));
+        ST::st(base + interior_offset<Q, ST, ODD>(p, o, i), F[L::opp(i)], DEV ? T(0) : T(L::w(i)));
 }
 
 // Boundary (or any) site: the general addressing with wrap-around and walls,
 // one direction at a time so that no address array stays live.
 // (W_i = W_opp(i), so the deviation formats need no slot bookkeeping.)
-template <int Q, class ST, bool ODD>
+template <int Q, class ST, bool ODD, bool DEV = false>
 __device__ __forceinline__ void load_general(const Params& p, int x, int y, typename ST::T* f) {
     using T = typename ST::T;
     using L = Lat<Q>;
@@ -779,11 +874,11 @@ __device__ __forceinline__ void load_general(const Params& p, int x, int y, type
     for (int i = 0; i < Q; ++i) {
         T lidc;
         const int64_t r = aa_address<Q, T>(p, x, y, i, ODD, lidc);
-        f[i] = ST::ld(base + r, T(L::w(i))) - lidc;
+        f[i] = ST::ld(base + r, DEV ? T(0) : T(L::w(i))) - lidc;
     }
 }
 
-template <int Q, class ST, bool ODD>
+template <int Q, class ST, bool ODD, bool DEV = false>
 __device__ __forceinline__ void store_general(const Params& p, int x, int y,
                                               const typename ST::T* F) {
     using T = typename ST::T;
@@ -793,7 +888,7 @@ __device__ __forceinline__ void store_general(const Params& p, int x, int y,
     for (int i = 0; i < Q; ++i) {
         T lidc;
         const int64_t r = aa_address<Q, T>(p, x, y, i, ODD, lidc);
-        ST::st(base + r, F[L::opp(i)] - lidc, T(L::w(i)));
+        ST::st(base + r, F[L::opp(i)] - lidc, DEV ? T(0) : T(L::w(i)));
     }
 }
 

@@ -144,7 +144,7 @@ __device__ __forceinline__ void collide_site(const Params& p, int x, int y, cons
         const double ab = out.alpha * p.beta;
 #pragma unroll
         for (int i = 0; i < Q; ++i) F[i] = (T)(fd[i] + ab * (fe[i] - fd[i]));
-    } else if (COLL >= LBM_SMOOTH && COLL <= LBM_THRESHOLD) {
+    } else if ((COLL >= LBM_SMOOTH && COLL <= LBM_THRESHOLD) || COLL == LBM_ENSEMBLE_LAGGED) {
         // Sections 4.2-4.4: f -> f* + phi(Delta S) (f - f*), then LBGK, i.e.
         // F = f* + (1 - 2 beta) phi (f - f*); the threshold limiter's phi is
         // decided after the step (the sites above Delta S_t are rewritten)
@@ -152,6 +152,10 @@ __device__ __forceinline__ void collide_site(const Params& p, int x, int y, cons
         equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
         const T ds = delta_s_and_q<Q, T>(f, feq, q);
         T phi = T(1);
+        if (COLL == LBM_ENSEMBLE_LAGGED && isfinite(ds)) {
+            acc += ds;  // the next step's E: this step's sum and count
+            e_code = 1;
+        }
         if (COLL == LBM_THRESHOLD) {
             if (isfinite(ds)) acc += ds;  // the step's sum of Delta S
             if (median_maybe_above((float)ds, (float)q, (float)rho, p.delta_f)) record_candidate<Q, T>(p, x, y, f);
@@ -165,7 +169,7 @@ __device__ __forceinline__ void collide_site(const Params& p, int x, int y, cons
             } else if (COLL == LBM_DOUBLE_MONOTONIC) {
                 const T z = d ? ds / T(p.lim_dst) : ds * T(p.lim_f[2]);
                 phi = pow_lim(T(1) + pow_lim(z, k), d ? T(-0.5) / k : T(p.lim_f[3]));
-            } else {  // LBM_ENSEMBLE, E from this step's pre-pass
+            } else {  // LBM_ENSEMBLE (E from this step's pre-pass), LBM_ENSEMBLE_LAGGED (the previous step's)
                 const T E = d ? T(*p.lim_E) : T(*p.lim_E_f);
                 if (E > T(0)) {
                     const T yv = ds / (alpha * E);
@@ -193,6 +197,117 @@ __device__ __forceinline__ void collide_site(const Params& p, int x, int y, cons
         }
     }
     conserve_mass<Q, T>(rho, F);
+}
+
+// The same collision in deviation form for the 16-bit formats, whose stored
+// value is the deviation d_i = f_i - W_i: with sum_i W_i = 1 and
+// sum_i W_i v_i = 0, rho = 1 + sum_i d_i and rho u = sum_i v_i d_i; the
+// equilibrium enters as d*_i = f*_i - W_i, and LBGK, MRT and A_2 only use
+// differences f - f* = d - d*, so the post-collision deviation
+// D_i = F_i - W_i comes out directly (no W_i added on load or subtracted on
+// store).  The Ehrenfest screen and the positivity rule form absolute values
+// where they need them.  D2Q9; the collisions of the paired kernel.
+// Also returns a lower bound of min_i f*_i for the limiter screen: for the
+// product equilibria the minimum of the products rho a_x a_y is the product
+// of the minima when every factor is positive (else 0, which passes every
+// site to the exact test).
+template <class T>
+__device__ __forceinline__ T equilibrium_dev9(int kind, T drho, T rho, T ux, T uy, T* ds) {
+    using L = Lat<9>;
+    if (kind == LBM_EQ_POLY_STD) {
+        const T uu = ux * ux + uy * uy;
+        T rest = drho, m = T(1);
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const T cu = T(L::cx(i)) * ux + T(L::cy(i)) * uy;
+            ds[i] = T(L::w(i)) * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
+            rest -= ds[i];
+            m = fminf(m, T(L::w(i)) + ds[i]);
+        }
+        ds[0] = rest;
+        return fminf(m, T(L::w(0)) + rest);
+    }
+    T ax[3], ay[3];
+    if (kind == LBM_EQ_ENTROPIC) {
+        eq1d_entropic<T>(ux, ax[0], ax[1], ax[2]);
+        eq1d_entropic<T>(uy, ay[0], ay[1], ay[2]);
+    } else {
+        eq1d_poly<T>(ux, ax[0], ax[1], ax[2]);
+        eq1d_poly<T>(uy, ay[0], ay[1], ay[2]);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ax[k] *= rho;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) ds[i] = fmaf(ax[L::cx(i) + 1], ay[L::cy(i) + 1], -T(L::w(i)));
+    const T mx = fminf(fminf(ax[0], ax[1]), ax[2]), my = fminf(fminf(ay[0], ay[1]), ay[2]);
+    return (mx > T(0) && my > T(0)) ? mx * my : T(0);
+}
+
+template <class ST, int COLL>
+__device__ __forceinline__ void collide_site_dev(const Params& p, int x, int y, const float* d, float* D) {
+    using L = Lat<9>;
+    using T = float;
+    T drho = T(0), jx = T(0), jy = T(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        drho += d[i];
+        if (L::cx(i) > 0) jx += d[i];
+        if (L::cx(i) < 0) jx -= d[i];
+        if (L::cy(i) > 0) jy += d[i];
+        if (L::cy(i) < 0) jy -= d[i];
+    }
+    const T rho = T(1) + drho;
+    const T inv = T(1) / rho;
+    const T ux = jx * inv, uy = jy * inv;
+    if (!(rho > T(0)) || !(fabsf(ux) < T(1e30)) || !(fabsf(uy) < T(1e30)))
+        if (*(volatile unsigned*)&p.counters[CNT_DIVERGED] == 0u) atomicExch(&p.counters[CNT_DIVERGED], 1u);
+    T ds[9];
+    const T m = equilibrium_dev9<T>(p.eq, drho, rho, ux, uy, ds);
+    if (COLL == LBM_EHRENFEST || COLL == LBM_MRT_LIMITER) {
+        // the screen of maybe_above_loose on f - f* = d - d* with m a lower
+        // bound of min f* (the bound's argument holds for any positive one)
+        float s2 = 0.f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float e = d[i] - ds[i];
+            s2 = fmaf(e, e, s2);
+        }
+        bool maybe = true;
+        if (m > 0.f && s2 < 0.25f * m * m) {
+            const float q = __fdividef(s2, m);  // approximate (2 ulp), far inside the slack
+            maybe = slack_reaches(q, q, rho, p.delta_f);
+        }
+        if (maybe) {
+            T f[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i] = T(L::w(i)) + d[i];
+            record_candidate<9, T>(p, x, y, f);
+        }
+    }
+    if (COLL == LBM_MRT) {
+        mrt_d2q9<T>(d, ds, p.mrt, p.mrt_f, D);
+    } else if (COLL == LBM_MRT2) {
+        mrt2_d2q9<T>(d, ds, T(2) * T(p.beta_f), D);
+    } else {
+        lbgk<9, T>(d, ds, T(p.beta_f), D);
+    }
+    if (COLL == LBM_POSITIVITY) {
+        bool neg = false;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) neg |= D[i] < -T(L::w(i));
+        if (neg) {
+            T fe[9], F[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                fe[i] = T(L::w(i)) + ds[i];
+                F[i] = T(L::w(i)) + D[i];
+            }
+            if (positivity<9, T>(fe, F)) atomicAdd(&p.stats[ST_LIMITED], 1ull);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) D[i] = F[i] - T(L::w(i));
+        }
+    }
+    conserve_mass<9, T>(drho, D);
 }
 
 // Section 8's diffusive Maxwell rule at wall site (x, y) (bc DIFFUSIVE), on
@@ -238,26 +353,37 @@ __device__ __forceinline__ void diffusive_rule(const Params& p, int x, int y, T*
 
 // The whole step for the site (x, y): load (streaming in odd steps),
 // collision, store.
+// The 16-bit D2Q9 collisions that run in deviation form (collide_site_dev),
+// at every site so that every kernel computes a site alike.
+template <int Q, class ST, int COLL>
+constexpr bool kDeviationForm = Q == 9 && sizeof(typename ST::S) == 2 &&
+                                (COLL == LBM_LBGK || COLL == LBM_EHRENFEST || COLL == LBM_POSITIVITY ||
+                                 COLL == LBM_MRT || COLL == LBM_MRT2 || COLL == LBM_MRT_LIMITER);
+
 template <int Q, class ST, int COLL, bool ODD>
 __device__ __forceinline__ void site_update(const Params& p, int x, int y, int& e_code,
                                             int& e_iters, typename ST::T& acc) {
     using T = typename ST::T;
+    constexpr bool DEV = kDeviationForm<Q, ST, COLL>;
     T f[Q], F[Q];
     const bool interior = x > 0 && x < p.nx - 1 && (Q == 3 || (y > 0 && y < p.ny - 1));
     const int o = y * p.pitch + x;
     if (interior) {
-        load_interior<Q, ST, ODD>(p, o, f);
+        load_interior<Q, ST, ODD, DEV>(p, o, f);
     } else {
         // diffusive walls: wall sites are updated by diffusive_wall_kernel
         // (each site owns its addresses, so the two kernels of a step commute)
         if (Q == 9 && p.diffusive) return;
-        load_general<Q, ST, ODD>(p, x, y, f);
+        load_general<Q, ST, ODD, DEV>(p, x, y, f);
     }
-    collide_site<Q, ST, COLL>(p, x, y, f, F, e_code, e_iters, acc);
-    if (interior)
-        store_interior<Q, ST, ODD>(p, o, F);
+    if constexpr (DEV)
+        collide_site_dev<ST, COLL>(p, x, y, f, F);
     else
-        store_general<Q, ST, ODD>(p, x, y, F);
+        collide_site<Q, ST, COLL>(p, x, y, f, F, e_code, e_iters, acc);
+    if (interior)
+        store_interior<Q, ST, ODD, DEV>(p, o, F);
+    else
+        store_general<Q, ST, ODD, DEV>(p, x, y, F);
 }
 
 // Warp-aggregated ELBM counters (all 32 lanes of the warp call this).
@@ -326,7 +452,9 @@ constexpr int kMinBlocks =
         ? 0
         : (COLL == LBM_EHRENFEST || COLL == LBM_POSITIVITY || COLL == LBM_MRT_LIMITER)
               ? 8
-              : (COLL == LBM_MEDIAN || (COLL >= LBM_SMOOTH && COLL <= LBM_THRESHOLD)) ? 6 : 0;
+              : (COLL == LBM_MEDIAN || (COLL >= LBM_SMOOTH && COLL <= LBM_THRESHOLD) || COLL == LBM_ENSEMBLE_LAGGED)
+                    ? 6
+                    : 0;
 
 template <int Q, class ST, int COLL, bool ODD>
 __global__ void __launch_bounds__(kBlockX* kBlockY, kMinBlocks<ST, COLL>) step_kernel(Params p) {
@@ -344,6 +472,8 @@ __global__ void __launch_bounds__(kBlockX* kBlockY, kMinBlocks<ST, COLL>) step_k
     if (x < p.nx && y < p.ny) site_update<Q, ST, COLL, ODD>(p, x, y, e_code, e_iters, acc);
     if (COLL == LBM_ELBM) elbm_stats(p, e_code, e_iters);
     if (COLL == LBM_THRESHOLD) block_sum_to_slots<typename ST::T>(p, acc, 0, false);
+    if (COLL == LBM_ENSEMBLE_LAGGED)
+        block_sum_to_slots<typename ST::T>(p, acc, e_code == 1 ? typename ST::T(1) : typename ST::T(0), true);
 }
 
 // Two sites per thread (x0 = 2t, x0 + 1): every population plane moves with
@@ -360,13 +490,18 @@ __global__ void __launch_bounds__(kBlockX* kBlockY, kMinBlocks<ST, COLL>) step_k
 // Used for the 16-bit formats, whose per-site instruction count (packed
 // conversions, addressing) otherwise limits them below the HBM roofline;
 // with FP32 storage the one-site kernel is as fast or faster.  Compiled for
-// six resident CTAs (40 registers): 2-7% faster than five or no cap.
+// six resident CTAs (40 registers) where that leaves no or few spills, five
+// (48 registers) for the collisions with the Ehrenfest screen or the
+// positivity rule.
 constexpr int kVecX = 64;
 constexpr int kVecY = 4;
 template <class ST, int COLL>
 constexpr bool kPairedSites = sizeof(typename ST::S) == 2 &&
                               (COLL == LBM_LBGK || COLL == LBM_EHRENFEST || COLL == LBM_POSITIVITY ||
                                COLL == LBM_MRT || COLL == LBM_MRT2 || COLL == LBM_MRT_LIMITER);
+template <int COLL>
+constexpr int kPairedMinBlocks =
+    (COLL == LBM_EHRENFEST || COLL == LBM_MRT_LIMITER || COLL == LBM_POSITIVITY) ? 5 : 6;
 
 __device__ __forceinline__ uint32_t ld_word(const void* base, int off) {
     return *reinterpret_cast<const uint32_t*>(reinterpret_cast<const uint16_t*>(base) + off);
@@ -379,7 +514,7 @@ __device__ __forceinline__ void st_half(void* base, int off, uint32_t v16) {
 }
 
 template <int Q, class ST, int COLL, bool ODD>
-__global__ void __launch_bounds__(kVecX* kVecY, 6) step_kernel_v2(Params p) {
+__global__ void __launch_bounds__(kVecX* kVecY, kPairedMinBlocks<COLL>) step_kernel_v2(Params p) {
     pdl_enter();
     using T = typename ST::T;
     using L = Lat<Q>;
@@ -405,37 +540,42 @@ __global__ void __launch_bounds__(kVecX* kVecY, 6) step_kernel_v2(Params p) {
     const int lane = threadIdx.x & 31;
     const int o = y * p.pitch + x0;  // even: every word access is 4-byte aligned
     void* base = p.f;
+    // every load first - the words of the lanes' own pairs and the one
+    // extra word a warp-edge lane needs per shifted plane - so that their
+    // latencies overlap; then the shifted pairs are assembled
+    uint32_t W[Q], E[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int k = ODD ? L::opp(i) : i;
+        const int off = k * p.plane32 + o - (ODD ? L::cy(i) * p.pitch : 0);
+        W[i] = ld_word(base, off);  // elements x0, x0 + 1 of the plane row
+        E[i] = 0u;
+        if (ODD && L::cx(i) > 0) E[i] = lane == 0 ? ld_word(base, off - 2) : 0u;   // x0 >= 2 here
+        if (ODD && L::cx(i) < 0) E[i] = lane == 31 ? ld_word(base, off + 2) : 0u;  // x0 + 2 < nx here
+    }
     T fa[Q], fb[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const int k = ODD ? L::opp(i) : i;
-        const int off = k * p.plane32 + o - (ODD ? L::cy(i) * p.pitch : 0);
-        const T w = T(L::w(i));
-        const uint32_t W = ld_word(base, off);  // elements x0, x0 + 1 of the plane row
-        uint32_t pair = W;
+        uint32_t pair = W[i];
         if (ODD && L::cx(i) > 0) {  // sources x0 - 1, x0: the lane below's high half, our low half
-            uint32_t Wp = __shfl_up_sync(full, W, 1);
-            if (lane == 0) Wp = ld_word(base, off - 2);  // x0 >= 2 here
-            pair = __byte_perm(Wp, W, 0x5432);
+            const uint32_t Wp = __shfl_up_sync(full, W[i], 1);
+            pair = __byte_perm(lane == 0 ? E[i] : Wp, W[i], 0x5432);
         } else if (ODD && L::cx(i) < 0) {  // sources x0 + 1, x0 + 2: our high half, the lane above's low
-            uint32_t Wn = __shfl_down_sync(full, W, 1);
-            if (lane == 31) Wn = ld_word(base, off + 2);  // x0 + 2 < nx here
-            pair = __byte_perm(W, Wn, 0x5432);
+            const uint32_t Wn = __shfl_down_sync(full, W[i], 1);
+            pair = __byte_perm(W[i], lane == 31 ? E[i] : Wn, 0x5432);
         }
-        const float2 v = ST::unpack(pair);
-        fa[i] = w + v.x;
-        fb[i] = w + v.y;
+        const float2 v = ST::unpack(pair);  // deviations f - W of the two sites
+        fa[i] = v.x;
+        fb[i] = v.y;
     }
-    T Fa[Q], Fb[Q];
-    T acc = 0;
-    collide_site<Q, ST, COLL>(p, x0, y, fa, Fa, e_code, e_iters, acc);
-    collide_site<Q, ST, COLL>(p, x0 + 1, y, fb, Fb, e_code, e_iters, acc);
+    T Fa[Q], Fb[Q];  // post-collision deviations F - W
+    collide_site_dev<ST, COLL>(p, x0, y, fa, Fa);
+    collide_site_dev<ST, COLL>(p, x0 + 1, y, fb, Fb);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int k = ODD ? L::opp(i) : i;
         const int off = k * p.plane32 + o - (ODD ? L::cy(i) * p.pitch : 0);
-        const T w = T(L::w(i));
-        const uint32_t P = ST::pack(Fa[L::opp(i)] - w, Fb[L::opp(i)] - w);  // (a, b)
+        const uint32_t P = ST::pack(Fa[L::opp(i)], Fb[L::opp(i)]);  // (a, b)
         if (!ODD || L::cx(i) == 0) {
             st_word(base, off, P);
         } else if (L::cx(i) > 0) {
@@ -1210,6 +1350,28 @@ __global__ void __launch_bounds__(256) ensemble_mean(Params p) {
     }
 }
 
+// Lagged ensemble limiter, after its step: E(Delta S) for the next step from
+// the step's partial sums and counts of the finite Delta S (one CTA), the
+// slots cleared.
+template <class ST>
+__global__ void __launch_bounds__(256) ensemble_finalize(Params p) {
+    pdl_enter();
+    const int t = threadIdx.x;
+    double S = 0.0, N = 0.0;
+    for (int k = t; k < kRedSlots; k += blockDim.x) {
+        S += p.red[k];
+        N += p.red[kRedSlots + k];
+        p.red[k] = 0.0;
+        p.red[kRedSlots + k] = 0.0;
+    }
+    S = block_sum(S);
+    N = block_sum(N);
+    if (t == 0) {
+        *p.lim_E = N > 0.0 ? S / N : 0.0;
+        *p.lim_E_f = (float)*p.lim_E;
+    }
+}
+
 // Median entropy filter (Section 4.4): lower median of Delta S over the site
 // and its neighbours (clipped at walls, wrapped where periodic); where the
 // median is below the site's Delta S the homothety with coefficient
@@ -1748,6 +1910,7 @@ cudaError_t launch_step_c(int coll, bool odd, const Params& p, cudaStream_t s) {
         case LBM_THRESHOLD: return launch_step_q<Q, ST, LBM_THRESHOLD>(odd, p, s);
         case LBM_MRT2: return launch_step_q<Q, ST, LBM_MRT2>(odd, p, s);
         case LBM_MRT_LIMITER: return launch_step_q<Q, ST, LBM_MRT_LIMITER>(odd, p, s);
+        case LBM_ENSEMBLE_LAGGED: return launch_step_q<Q, ST, LBM_ENSEMBLE_LAGGED>(odd, p, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -1759,8 +1922,12 @@ cudaError_t launch_fixup_q(int coll, bool odd, const Params& p, cudaStream_t s, 
     if (coll == LBM_EHRENFEST)
         return launch_p(odd ? ehrenfest_eval_select<Q, ST, true> : ehrenfest_eval_select<Q, ST, false>, nsm,
                         256, s, p);
+    // the field-free median filter takes one candidate per CTA and round:
+    // four CTAs per SM, so that thousands of candidates overlap their FP64
+    // window evaluations (with few, the CTAs without one exit at once)
     if (coll == LBM_MEDIAN && p.median_inv != 0.0)
-        return launch_p(odd ? median_recon_fixup<Q, ST, true> : median_recon_fixup<Q, ST, false>, nsm, 256, s, p);
+        return launch_p(odd ? median_recon_fixup<Q, ST, true> : median_recon_fixup<Q, ST, false>, 4 * nsm, 256,
+                        s, p);
     if (coll == LBM_MEDIAN)
         return launch_p(odd ? median_fixup<Q, ST, true> : median_fixup<Q, ST, false>, nsm, 256, s, p);
     if (coll == LBM_THRESHOLD)
@@ -1769,6 +1936,7 @@ cudaError_t launch_fixup_q(int coll, bool odd, const Params& p, cudaStream_t s, 
     if (coll == LBM_MRT_LIMITER)
         return launch_p(odd ? mrt_limiter_eval_select<Q, ST, true> : mrt_limiter_eval_select<Q, ST, false>, nsm,
                         256, s, p);
+    if (coll == LBM_ENSEMBLE_LAGGED) return launch_p(ensemble_finalize<ST>, 1, 256, s, p);
     return cudaSuccess;
 }
 

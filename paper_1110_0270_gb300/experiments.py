@@ -19,13 +19,15 @@ the line's zero locates it (the paper reports Re = 7135 on this grid).
 Readings: the box has n sites a side, the wall sites on its edges, and
 L = n - 1 is the distance between opposite walls (Re = u0 L / nu); the
 control point is the site nearest (L/16, 13L/16) from the bottom-left
-corner; 5000 L / u0 steps.
+corner; 5000 L / u0 steps.  The alternative placement (walls="outside")
+reads "100 x 100" as the fluid sites: the lattice has n + 2 sites a side,
+the wall sites around the n x n fluid, and L = n + 1.
 
 Stability readings: L = n - 1 = 128 (Re = u_wall L / nu), Ehrenfest and
 MRT-limiter threshold delta = 1e-3, survival = no non-finite or
 non-positive density seen (checked every `check` steps).
 
-    python -m paper_1110_0270_gb300.experiments hopf --re 7000 7250 7500 7750 8000
+    python -m paper_1110_0270_gb300.experiments hopf --re 7000 7250 7500 7750 8000 [--walls outside]
     python -m paper_1110_0270_gb300.experiments stability --re 1000 2500 5000 7500 10000
 """
 from __future__ import annotations
@@ -39,12 +41,18 @@ from .analysis import dominant_frequency, fit_onset, hopf_energy, stream_functio
 
 
 def hopf_sweep(res, n: int = 100, u0: float = 0.1, steps: int | None = None, precision: str = "fp64",
-               delta: float = 1e-3, frac: float = 0.01, chunk: int = 6400) -> dict:
+               delta: float = 1e-3, frac: float = 0.01, chunk: int = 6400, walls: str = "edge") -> dict:
     """One lattice per Reynolds number, each on its own CUDA stream so that
     the small, latency-bound lattices run concurrently; the probe keeps the
-    last `frac` of the signal of the control point."""
+    last `frac` of the signal of the control point.  walls: "edge" (n sites
+    a side including the wall sites) or "outside" (n x n fluid sites inside
+    the wall sites)."""
     import numpy as np
     import torch
+    if walls not in ("edge", "outside"):
+        raise ValueError(f"walls must be 'edge' or 'outside', not {walls!r}")
+    fluid = n
+    n = n + 2 if walls == "outside" else n
     L = n - 1
     steps = int(steps if steps is not None else 5000 * L / u0)
     keep = max(2, int(frac * steps))
@@ -79,7 +87,8 @@ def hopf_sweep(res, n: int = 100, u0: float = 0.1, steps: int | None = None, pre
                        "u_mean": float(sig[:, 0].mean()), "v_mean": float(sig[:, 1].mean()),
                        "diverged": int(st["diverged"]), "limited_total": int(st["limited_total"])})
     fit = fit_onset([p["re"] for p in points], [p["E_u2"] for p in points])
-    return {"n": n, "L": L, "u0": u0, "steps": steps, "control_point": [xp, yp], "precision": precision,
+    return {"n": n, "fluid_sites": fluid if walls == "outside" else n - 2, "walls": walls, "L": L, "u0": u0,
+            "steps": steps, "control_point": [xp, yp], "precision": precision,
             "seconds": round(seconds, 1), "points": points, "fit": fit}
 
 
@@ -171,6 +180,8 @@ def main(argv=None):
     h.add_argument("--n", type=int, default=100)
     h.add_argument("--steps", type=int, default=None, help="default 5000 L / u0")
     h.add_argument("--precision", default="fp64")
+    h.add_argument("--walls", choices=["edge", "outside"], default="edge",
+                   help="n sites a side with the walls on the edges, or n x n fluid sites inside them")
     s = sub.add_parser("stability", help="survival of six methods (129 x 129, bounce-back)")
     s.add_argument("--re", type=float, nargs="+", required=True)
     s.add_argument("--methods", nargs="+", default=list(STABILITY_METHODS))
@@ -179,7 +190,7 @@ def main(argv=None):
     s.add_argument("--precision", default="fp64")
     args = ap.parse_args(argv)
     if args.study == "hopf":
-        out = hopf_sweep(args.re, n=args.n, steps=args.steps, precision=args.precision)
+        out = hopf_sweep(args.re, n=args.n, steps=args.steps, precision=args.precision, walls=args.walls)
     else:
         out = stability_sweep(args.re, methods=args.methods, n=args.n, steps=args.steps,
                               precision=args.precision)

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblbm.so")
 LATTICES = {"D1Q3": 1, "D2Q9": 2}
 COLLISIONS = {"lbgk": 0, "elbm": 1, "ehrenfest": 2, "positivity": 3, "median": 4, "mrt": 5,
               "smooth": 6, "double_monotonic": 7, "ensemble": 8, "threshold": 9, "mrt2": 10,
-              "mrt_limiter": 11}
+              "mrt_limiter": 11, "ensemble_lagged": 12}
 EQUILIBRIA = {"poly": 0, "entropic": 1, "poly_std": 2}
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16_dev": 2, "fp16_dev": 3}
 BCS = {"cavity": 0, "ends": 1, "periodic": 2, "channel": 3, "diffusive": 4}
@@ -40,7 +40,9 @@ EXPORTS = ["lbm_config_default", "lbm_required_bytes", "lbm_create", "lbm_destro
            "lbm_batch_get_state", "lbm_batch_step", "lbm_batch_stats", "lbm_batch_last_error",
            "lbm_adjoint_required_bytes", "lbm_adjoint_forward", "lbm_adjoint_backward",
            "lbm_fp64_rates", "lbm_enstrophy", "lbm_probe_set", "lbm_probe_count",
-           "lbm_mrt_preset"]
+           "lbm_mrt_preset", "lbm_batch_opts_default", "lbm_batch_required_bytes_ex",
+           "lbm_batch_create_ex", "lbm_batch_get_opts", "lbm_batch_group_times", "lbm_batch_tune_bytes",
+           "lbm_batch_tune", "lbm_batch_debug_hold"]
 
 
 class lbm_config(C.Structure):
@@ -62,6 +64,21 @@ class lbm_stats(C.Structure):
         "steps", "candidates_last", "limited_total", "elbm_solved", "elbm_skipped",
         "elbm_fallbacks", "elbm_iters_total", "elbm_iters_max", "diverged", "overflow",
         "screened_last")]
+
+
+class lbm_batch_opts(C.Structure):
+    _fields_ = [("tile_x", C.c_int), ("ctas_per_sm", C.c_int), ("chunk", C.c_int), ("order", C.c_int),
+                ("graph_steps", C.c_int), ("wait_ms", C.c_double), ("tile_rows", C.c_int)]
+
+    def as_dict(self) -> dict:
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class lbm_batch_tune_record(C.Structure):
+    _fields_ = [("opts", lbm_batch_opts), ("ms_per_step", C.c_double), ("objective", C.c_double)]
+
+
+BATCH_KINDS = ["lbgk", "elbm", "ehrenfest", "positivity", "median", "mrt"]  # LBM_LBGK ... LBM_MRT
 
 
 class LBMError(RuntimeError):
@@ -108,6 +125,17 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "lbm_batch_step": (i, [p, i, C.POINTER(i), p]),
         "lbm_batch_stats": (i, [p, i, C.POINTER(lbm_stats), p]),
         "lbm_batch_last_error": (C.c_char_p, [p]),
+        "lbm_batch_opts_default": (i, [C.POINTER(lbm_batch_opts)]),
+        "lbm_batch_required_bytes_ex": (i, [C.POINTER(lbm_config), i, C.POINTER(lbm_batch_opts),
+                                            C.POINTER(sz)]),
+        "lbm_batch_create_ex": (i, [C.POINTER(lbm_config), i, C.POINTER(lbm_batch_opts), p, sz,
+                                    C.POINTER(p)]),
+        "lbm_batch_get_opts": (i, [p, C.POINTER(lbm_batch_opts)]),
+        "lbm_batch_group_times": (i, [p, i, C.POINTER(C.c_double), p]),
+        "lbm_batch_tune_bytes": (i, [C.POINTER(lbm_config), i, C.POINTER(sz)]),
+        "lbm_batch_tune": (i, [C.POINTER(lbm_config), i, p, sz, i, C.POINTER(lbm_batch_opts),
+                               C.POINTER(lbm_batch_tune_record), i, C.POINTER(i), C.POINTER(C.c_double), p]),
+        "lbm_batch_debug_hold": (i, [p, i, p]),
         "lbm_adjoint_required_bytes": (i, [C.POINTER(lbm_config), i, i, C.POINTER(sz)]),
         "lbm_adjoint_forward": (i, [p, i, i, p, sz, C.POINTER(C.c_double), p]),
         "lbm_adjoint_backward": (i, [p, i, i, p, i, p, i, C.POINTER(C.c_double),
@@ -405,31 +433,101 @@ def fp64_rates(stream=None) -> dict:
     return {"dfma_flops": fl.value, "log_per_s": lg.value}
 
 
-def batch_required_bytes(cfgs) -> int:
+def batch_opts(**kw) -> lbm_batch_opts:
+    """lbm_batch_opts with the library's defaults, overridden by kw."""
+    o = lbm_batch_opts()
+    lib().lbm_batch_opts_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _configs(cfgs):
     cs = [c if isinstance(c, LBMConfig) else LBMConfig.from_dict(c) for c in cfgs]
-    arr = (lbm_config * len(cs))(*[c.to_c() for c in cs])
+    return cs, (lbm_config * len(cs))(*[c.to_c() for c in cs])
+
+
+def batch_required_bytes(cfgs, opts=None) -> int:
+    cs, arr = _configs(cfgs)
     n = C.c_size_t()
-    rc = lib().lbm_batch_required_bytes(arr, len(cs), C.byref(n))
+    rc = lib().lbm_batch_required_bytes_ex(arr, len(cs), C.byref(opts) if opts is not None else None,
+                                           C.byref(n))
     if rc != 0:
         raise LBMError(f"lbm_batch_required_bytes: {STATUS.get(rc, rc)}")
     return n.value
 
 
-class Batch:
-    """Many independent D2Q9 lattices advanced together (lbm_batch_*)."""
+def _tune_key(cs) -> str:
+    """The tuner's cache key: precision, lattice x collision mix, and the
+    size class (log2 of the total and of the largest instance's sites)."""
+    import math
+    mix = sorted({f"{c.lattice}/{c.collision}" for c in cs})
+    sites = [c.nx * c.ny for c in cs]
+    return "|".join([cs[0].precision, ",".join(mix), f"total2^{int(math.log2(sum(sites)))}",
+                     f"max2^{int(math.log2(max(sites)))}", f"n{len(cs)}"])
 
-    def __init__(self, cfgs, device=None):
+
+def tune_batch(cfgs, steps: int = 4, cache: str | None = None, device=None) -> tuple[dict, list]:
+    """The library's autotuner (lbm_batch_tune) for this batch: returns the
+    chosen options and the timed sweep [(opts, summed group ms per step,
+    objective)].  With a cache
+    path the choice is read from / stored in a JSON file keyed by
+    precision, lattice and collision mix and size class."""
+    import json
+    import torch
+    cs, arr = _configs(cfgs)
+    key = _tune_key(cs)
+    if cache and os.path.exists(cache):
+        with open(cache) as fh:
+            data = json.load(fh)
+        if key in data:
+            return data[key]["opts"], data[key]["sweep"]
+    n = C.c_size_t()
+    rc = lib().lbm_batch_tune_bytes(arr, len(cs), C.byref(n))
+    if rc != 0:
+        raise LBMError(f"lbm_batch_tune_bytes: {STATUS.get(rc, rc)}")
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    mem = torch.empty(n.value, dtype=torch.uint8, device=dev)
+    best = batch_opts()
+    recs = (lbm_batch_tune_record * 64)()
+    nrec, best_ms = C.c_int(), C.c_double()
+    with torch.cuda.device(dev):
+        rc = lib().lbm_batch_tune(arr, len(cs), _ptr(mem), n.value, int(steps), C.byref(best), recs, 64,
+                                  C.byref(nrec), C.byref(best_ms), _stream(None))
+    if rc != 0:
+        raise LBMError(f"lbm_batch_tune: {STATUS.get(rc, rc)}")
+    sweep = [(recs[k].opts.as_dict(), recs[k].ms_per_step, recs[k].objective) for k in range(min(nrec.value, 64))]
+    out = best.as_dict()
+    if cache:
+        data = {}
+        if os.path.exists(cache):
+            with open(cache) as fh:
+                data = json.load(fh)
+        data[key] = {"opts": out, "objective": best_ms.value, "sweep": sweep}
+        os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
+        with open(cache, "w") as fh:
+            json.dump(data, fh, indent=1)
+    return out, sweep
+
+
+class Batch:
+    """Many independent lattices (D2Q9 and D1Q3) advanced together by the
+    library's persistent batched kernels (lbm_batch_*).  `opts`: a dict of
+    lbm_batch_opts fields (None: the library's defaults)."""
+
+    def __init__(self, cfgs, device=None, opts=None):
         import torch
-        self.cfgs = [c if isinstance(c, LBMConfig) else LBMConfig.from_dict(c) for c in cfgs]
+        self.cfgs, self._arr = _configs(cfgs)
         self.n = len(self.cfgs)
         self.device = torch.device(device) if device is not None else torch.device(
             "cuda", torch.cuda.current_device())
-        self._arr = (lbm_config * self.n)(*[c.to_c() for c in self.cfgs])
-        self.nbytes = batch_required_bytes(self.cfgs)
+        self._opts = batch_opts(**(opts or {}))
+        self.nbytes = batch_required_bytes(self.cfgs, self._opts)
         self.mem = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
         h = C.c_void_p()
         with torch.cuda.device(self.device):
-            rc = lib().lbm_batch_create(self._arr, self.n, _ptr(self.mem), self.nbytes, C.byref(h))
+            rc = lib().lbm_batch_create_ex(self._arr, self.n, C.byref(self._opts), _ptr(self.mem), self.nbytes,
+                                           C.byref(h))
         if rc != 0:
             raise LBMError(f"lbm_batch_create: {STATUS.get(rc, rc)}")
         self._h = h
@@ -445,8 +543,14 @@ class Batch:
             msg = lib().lbm_batch_last_error(self._h)
             raise LBMError(f"{what}: {STATUS.get(rc, rc)}: {msg.decode() if msg else ''}")
 
+    @property
+    def opts(self) -> dict:
+        o = lbm_batch_opts()
+        self._check(lib().lbm_batch_get_opts(self._h, C.byref(o)), "lbm_batch_get_opts")
+        return o.as_dict()
+
     def shape(self, i):
-        return (9, self.cfgs[i].ny, self.cfgs[i].nx)
+        return (self.cfgs[i].Q, self.cfgs[i].ny, self.cfgs[i].nx)
 
     def init_uniform(self, rho=1.0, ux=0.0, uy=0.0, stream=None):
         self._check(lib().lbm_batch_init_uniform(self._h, rho, ux, uy, _stream(stream)),
@@ -472,6 +576,20 @@ class Batch:
         st = (C.c_int * self.n)() if status else None
         self._check(lib().lbm_batch_step(self._h, int(n), st, _stream(stream)), "lbm_batch_step")
         return [STATUS[v] for v in st] if status else None
+
+    def step_status(self, n=1, stream=None) -> int:
+        """lbm_batch_step with status; returns the raw lbm_status code."""
+        st = (C.c_int * self.n)()
+        return lib().lbm_batch_step(self._h, int(n), st, _stream(stream))
+
+    def group_times(self, n: int, stream=None) -> dict:
+        """{collision: ms} of each collision group advanced alone n steps."""
+        ms = (C.c_double * 6)()
+        self._check(lib().lbm_batch_group_times(self._h, int(n), ms, _stream(stream)), "lbm_batch_group_times")
+        return {k: ms[j] for j, k in enumerate(BATCH_KINDS) if ms[j] > 0.0}
+
+    def debug_hold(self, i: int, stream=None):
+        self._check(lib().lbm_batch_debug_hold(self._h, int(i), _stream(stream)), "lbm_batch_debug_hold")
 
     def stats(self, i, stream=None) -> dict:
         st = lbm_stats()

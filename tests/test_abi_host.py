@@ -105,7 +105,7 @@ def test_limiter_config_defaults_and_validation(lib):
         assert lib.lbm_required_bytes(C.byref(c2), C.byref(n)) == 0, coll
         setattr(c2, field, bad)
         assert lib.lbm_required_bytes(C.byref(c2), C.byref(n)) == 1, (coll, field)
-    c.collision = 12
+    c.collision = 13
     assert lib.lbm_required_bytes(C.byref(c), C.byref(n)) == 1
     # Section 5's A_2 collisions exist for D2Q9 only
     for coll in (10, 11):

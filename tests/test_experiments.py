@@ -100,3 +100,18 @@ def test_hopf_runner_matches_oracle():
     assert p["samples"] == sig.size and p["diverged"] == 0
     assert p["E_u"] == pytest.approx(hopf_energy(sig, L, 0.1), rel=1e-8)
     assert p["f_dom"] == pytest.approx(dominant_frequency(sig, L, 0.1)["f"], rel=1e-12)
+
+
+@pytest.mark.gpu
+def test_hopf_outside_walls_is_the_box_two_sites_larger():
+    """walls="outside" reads n as the fluid sites: 18 x 18 fluid sites inside
+    the wall sites is the 20-site box of the edge reading (L = 19, the same
+    control point), so both give the same signal."""
+    a = X.hopf_sweep([300.0], n=18, steps=400, frac=0.5, chunk=256, walls="outside")
+    b = X.hopf_sweep([300.0], n=20, steps=400, frac=0.5, chunk=256)
+    assert (a["n"], a["L"], a["fluid_sites"], a["walls"]) == (20, 19, 18, "outside")
+    assert (b["fluid_sites"], b["walls"]) == (18, "edge")
+    assert a["control_point"] == b["control_point"]
+    assert a["points"][0]["E_u"] == b["points"][0]["E_u"]
+    with pytest.raises(ValueError):
+        X.hopf_sweep([300.0], n=18, steps=10, walls="inside")

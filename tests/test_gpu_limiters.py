@@ -1,6 +1,7 @@
 """GPU-vs-oracle parity of the Section 4.2-4.4 limiters through the C ABI:
 smooth (Eq. smoothReg), double monotonic (Eq. DoublMonSpec), ensemble
-dependent (Eq. phiExamp, the lattice mean of Delta S from a pre-pass) and
+dependent (Eq. phiExamp, the lattice mean of Delta S from a pre-pass, or
+lagged: the previous step's mean, accumulated by that step) and
 the threshold limiter (Eqs. EntThresh, entrHom: step-wide sum of Delta S,
 then Delta S_t from the candidates).  FP64 storage within 1e-12 rel-L2,
 FP32 within 1e-5; the threshold limiter's corrected-site count is exact in
@@ -29,6 +30,8 @@ PARAMS = {
     "smooth": dict(lim_alpha=40.0, lim_k=1.0, beta=0.95),
     "double_monotonic": dict(lim_dst=2e-3, lim_k=1.5, beta=0.95),
     "ensemble": dict(lim_alpha=1.0, lim_k=1.0, beta=0.8),
+    # E(Delta S) of the previous step (accumulated by the step kernel)
+    "ensemble_lagged": dict(lim_alpha=1.0, lim_k=1.0, beta=0.8),
     "threshold": dict(lim_delta0=0.05, delta=1e-4, beta=0.95),
 }
 
