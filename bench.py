@@ -53,9 +53,9 @@ LIMITER_PARAMS = {"smooth": dict(lim_alpha=40.0, lim_k=1.0), "double_monotonic":
                   "threshold": dict(lim_delta0=0.01)}
 
 
-# DRAM bytes per launch of the headline step kernel from the full-size ncu
-# launch list (profiles/step_kernel_d2q9_fp32_ehrenfest_4097.md), valid only
-# for the kernel sources it was taken on.
+# DRAM bytes (read + written) per launch of the headline step kernel, from a
+# one-pass ncu launch list of the full-size workload; valid only for the
+# kernel sources it was taken on (their hash).
 TRAFFIC_CAPTURE = {"sources_sha256_16": "0ffa72a8912f6606", "collision": "ehrenfest",
                    "precision": "fp32", "side": 4097, "bytes_per_launch": 1160.9e6}
 TRAFFIC_SOURCES = ["lbm_device.cuh", "lbm_kernels.cuh", "lbm_params.h", "lbm_kernels_f32.cu"]
@@ -102,7 +102,7 @@ class ClockSampler:
         try:
             self._proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self._proc = None
@@ -123,8 +123,13 @@ class ClockSampler:
                 self._proc.kill()
 
     def summary(self, t0: float, t1: float) -> dict:
+        """Median SM clock and the throttle reasons seen during [t0, t1]; a
+        timed window shorter than the sampling period may hold no sample,
+        and then the samples within 0.3 s of it (warm-up and the per-kernel
+        pass right after, the same kernels) stand in ("samples_near")."""
         inside = [r for t, r in self.rows if t0 <= t <= t1]
-        pool = inside if inside else [r for _, r in self.rows]
+        near = [r for t, r in self.rows if t0 - 0.3 <= t <= t1 + 0.3]
+        pool = inside or near or [r for _, r in self.rows]
         if not pool:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
                     "samples": 0}
@@ -134,7 +139,7 @@ class ClockSampler:
         reasons = sorted({n for r in pool for n, v in zip(names, r[5:9]) if v == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(inside), "window_s": round(t1 - t0, 3)}
+                "samples": len(inside), "samples_near": len(near), "window_s": round(t1 - t0, 3)}
 
 
 # --------------------------------------------------------------------------- GPU arm
@@ -224,8 +229,58 @@ def run_variants(n_side, steps, warmup, fma_per_s=None):
                 out[f"{coll}/{precision}"]["fixup_ms"] = round(prof["fixup"][1] / prof["fixup"][0], 5)
             if fma_per_s and (coll == "elbm" or precision == "fp64"):
                 out[f"{coll}/{precision}"]["fp64_fma_slots_per_site"] = round(fma_per_s / (mlups * 1e6), 1)
+            if coll == "elbm":
+                # the root finder's work: FP64 parabola steps per solved site
+                # (after the FP32 pre-iterations) and the share of each outcome
+                st = lat.stats()
+                tot = max(1, st["elbm_solved"] + st["elbm_skipped"] + st["elbm_fallbacks"])
+                out[f"{coll}/{precision}"]["elbm"] = {
+                    "fp64_steps_per_solved": round(st["elbm_iters_total"] / max(1, st["elbm_solved"]), 4),
+                    "fp64_steps_max": st["elbm_iters_max"], "solved_frac": round(st["elbm_solved"] / tot, 4),
+                    "skipped_frac": round(st["elbm_skipped"] / tot, 4),
+                    "fallback_frac": round(st["elbm_fallbacks"] / tot, 6)}
             del lat
             torch.cuda.empty_cache()
+    return out
+
+
+def random_start(n, seed=7):
+    """Equilibrium at a seeded random density and velocity field (rho
+    1 +- 0.02, u components uniform in +-0.05): after the first streaming
+    every site is out of equilibrium, so the per-site work the rest state
+    skips (the ELBM root solve, the limiters' candidates) runs everywhere."""
+    from paper_1110_0270_gb300 import workloads as WL
+    return WL.random_fields(n, n, seed, 0.02, 0.05)
+
+
+def run_elbm_loaded(n_side, steps=5):
+    """ELBM with every site solved: the 4097^2 cavity started from the random
+    velocity field of random_start (the variants table starts from rest,
+    where the near-equilibrium skip takes most sites), FP32 and FP64 storage:
+    MLUPS, FP64 parabola steps per solved site (after the FP32
+    pre-iterations) and the share of solved / skipped / fallback sites."""
+    import torch
+    from paper_1110_0270_gb300 import lbm
+    out = {}
+    init = random_start(n_side)
+    for precision in ["fp32", "fp64"]:
+        cfg, _ = workload_cfg("elbm", precision, n_side)
+        lat = lbm.Lattice(cfg)
+        lat.init(init["rho"], init["ux"], init["uy"])
+        lat.step(2)
+        st0 = lat.stats()
+        ms, _, _ = time_steps(lat, steps, 1)
+        st = lat.stats()
+        d = {k: st[k] - st0[k] for k in ("elbm_solved", "elbm_skipped", "elbm_fallbacks", "elbm_iters_total")}
+        tot = max(1, d["elbm_solved"] + d["elbm_skipped"] + d["elbm_fallbacks"])
+        out[precision] = {"mlups": round(n_side * n_side * steps / (ms * 1e-3) / 1e6, 1),
+                          "ms_per_step": round(ms / steps, 3),
+                          "fp64_steps_per_solved": round(d["elbm_iters_total"] / max(1, d["elbm_solved"]), 4),
+                          "solved_frac": round(d["elbm_solved"] / tot, 4),
+                          "skipped_frac": round(d["elbm_skipped"] / tot, 4),
+                          "fallback_frac": round(d["elbm_fallbacks"] / tot, 6)}
+        del lat
+        torch.cuda.empty_cache()
     return out
 
 
@@ -277,47 +332,74 @@ def run_loaded_selection(n_side, hots=(300, 3000, 30000), reps=5):
     return out
 
 
-GOLDEN_513 = os.path.join(ROOT, "tests", "golden", "cavity513_re10000.npz")
+GOLDEN_513 = os.path.join(ROOT, "tests", "golden", "cavity513.npz")
 
 
-def run_precision_error(n_side=None, steps=None):
+PRECISION_RUNS = {"ehrenfest_re10000": ("ehrenfest", dict(topk=64, delta=1e-3)),
+                  "median_re10000": ("median", dict(delta=1e-3)), "lbgk_re1000": ("lbgk", {})}
+
+
+def run_precision_error():
     """Storage-precision error of the bandwidth configuration against the
-    FP64 oracle, on the reduced 513 x 513 run that stands for it (the same
-    Re 10000 and U 0.05, 2000 steps from rest): each storage format's GPU
-    run against the oracle's fields stored by tests/golden/make_cavity513.py
-    (rho, u at every 8th site, totals of mass and H), for the Ehrenfest and
-    median limiters (plain LBGK diverges at this resolution): rel-L2
-    of rho - 1 and of u on the sampled sites, relative errors of the total
-    mass and of H."""
+    FP64 oracle, on the reduced 513 x 513 run that stands for it (U 0.05,
+    2000 steps from rest): each storage format's GPU run against the
+    oracle's fields stored by tests/golden/make_cavity513.py (rho, u at every
+    8th site, totals of mass and H), for Re 10000 with the Ehrenfest and
+    median limiters (plain LBGK diverges there) and for plain LBGK at Re
+    1000: rel-L2 of rho - 1 and of u on the sampled sites, relative errors of
+    the total mass, of H = sum f ln(f / W) and of its Kullback form
+    H_K = sum (f ln(f / W) - f + W) = H - (mass - N), which leaves out the
+    mass term (the oracle's own FP64 mass rounding dominates H's error in
+    FP64 storage).
+
+    The rows "fp64_perturbed_<eps>" run FP64 storage from the same rest state
+    with every initial population multiplied by (1 + eps z), z ~ N(0, 1)
+    (seeded), eps = 1e-12 and 6e-8 (FP32's relative rounding): how the flow
+    answers one small perturbation.  Under the Ehrenfest step at Re 10000 any
+    perturbation changes the fields at O(1): the symmetric start has exact
+    ties in Delta S, broken by site index, and a perturbation breaks them
+    differently."""
     import torch
     from paper_1110_0270_gb300 import lbm
     from paper_1110_0270_gb300 import workloads as WL
     g = np.load(GOLDEN_513)
-    n, re, u0, steps, stride = int(g["n"]), float(g["re"]), float(g["u"]), int(g["steps"]), int(g["stride"])
-    out = {"reference": "FP64 oracle (tests/golden/cavity513_re10000.npz)", "lattice": f"{n}x{n}", "re": re,
-           "u": u0, "steps": steps, "sample_stride": stride}
+    n, u0, steps, stride = int(g["n"]), float(g["u"]), int(g["steps"]), int(g["stride"])
+    out = {"reference": "FP64 oracle (tests/golden/cavity513.npz)", "lattice": f"{n}x{n}", "u": u0,
+           "steps": steps, "sample_stride": stride}
     nrm = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
-    for coll in ["ehrenfest", "median"]:  # plain LBGK diverges at 513^2, Re 10000
-        extra = {"ehrenfest": dict(topk=64, delta=1e-3), "median": dict(delta=1e-3)}[coll]
-        rows = {}
-        for precision in ["fp64", "fp32", "fp16_dev", "bf16_dev"]:
+    sub = np.s_[::stride, ::stride]
+    variants = [(p, None) for p in ["fp64", "fp32", "fp16_dev", "bf16_dev"]]
+    variants += [("fp64", eps) for eps in (1e-12, 6e-8)]
+    for run, (coll, extra) in PRECISION_RUNS.items():
+        re = float(g[f"{run}_re"])
+        m_ref, H_ref = float(g[f"{run}_mass"]), float(g[f"{run}_H"])
+        HK_ref = H_ref - (m_ref - n * n)
+        rows = {"re": re, "collision": coll}
+        for precision, eps in variants:
             cfg, init = WL.cavity(n, re, u0)
             cfg.update(collision=coll, precision=precision, **extra)
             lat = lbm.Lattice(cfg)
             lat.init(init["rho"], init["ux"], init["uy"])
+            if eps is not None:
+                f0 = lat.get_state(torch.float64)
+                z = torch.from_numpy(WL.normal_noise(tuple(f0.shape), 2024, 1.0)).to(f0.device)
+                lat.set_state(f0 * (1.0 + eps * z))
             lat.step(steps)
             rho, u = lat.macros(torch.float64)
             rho, u = rho.cpu().numpy(), u.cpu().numpy()
-            f = lat.get_state(torch.float64)
-            sub = np.s_[::stride, ::stride]
+            mass = float(lat.get_state(torch.float64).sum())
             H = lat.entropy()
-            rows[precision] = {
-                "rho_dev_rel_l2": nrm(rho[sub] - 1.0, g[f"{coll}_rho"] - 1.0),
-                "u_rel_l2": nrm(np.stack([u[0][sub], u[1][sub]]), np.stack([g[f"{coll}_ux"], g[f"{coll}_uy"]])),
-                "mass_rel": abs(float(f.sum()) - float(g[f"{coll}_mass"])) / float(g[f"{coll}_mass"]),
-                "H_rel": abs(H - float(g[f"{coll}_H"])) / abs(float(g[f"{coll}_H"]))}
-            del lat, f
-        out[coll] = rows
+            HK = H - (mass - n * n)
+            key = precision if eps is None else f"fp64_perturbed_{eps:g}"
+            rows[key] = {
+                "rho_dev_rel_l2": nrm(rho[sub] - 1.0, g[f"{run}_rho"] - 1.0),
+                "u_rel_l2": nrm(np.stack([u[0][sub], u[1][sub]]), np.stack([g[f"{run}_ux"], g[f"{run}_uy"]])),
+                "mass_rel": abs(mass - m_ref) / m_ref,
+                "H_rel": abs(H - H_ref) / abs(H_ref),
+                "HK_rel": abs(HK - HK_ref) / abs(HK_ref),
+                "limited_total": lat.stats()["limited_total"]}
+            del lat
+        out[run] = rows
     return out
 
 
@@ -691,6 +773,8 @@ def gpu_arm(args):
     if dist is not None:
         dist.barrier()
     cfg, init = workload_cfg(args.collision, args.precision, args.side)
+    if args.init == "random":
+        init = random_start(args.side)
     N = args.side * args.side
     lat = lbm.Lattice(cfg)
     lat.init(init["rho"], init["ux"], init["uy"])
@@ -723,7 +807,8 @@ def gpu_arm(args):
         "data": "synthetic",
         "config": {"workload": f"D2Q9 lid-driven cavity {args.side}x{args.side}, Re {RE:g}, "
                                f"U {LID_U}, {args.precision} populations, collision {args.collision}"
-                               f" (Ehrenfest/median: k={TOPK}, delta={DELTA:g}), started from rest",
+                               f" (Ehrenfest/median: k={TOPK}, delta={DELTA:g}), started "
+                               + ("from rest" if args.init == "rest" else "from a random velocity field"),
                    "sites": N, "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "inputs larger than L2 (state 604 MB in FP32), no flush",
                    "limiter_sites_total": st["limited_total"],
@@ -771,6 +856,7 @@ def run_sections(args, result, init):
         guarded(result, "small_configs", run_small_configs)
     if not args.no_variants:
         guarded(result, "loaded_selection", lambda: run_loaded_selection(args.side))
+        guarded(result, "elbm_loaded", lambda: run_elbm_loaded(args.side))
     if args.precision_steps > 0 and os.path.exists(GOLDEN_513):
         guarded(result, "precision_error", run_precision_error)
     if not args.no_small:
@@ -836,6 +922,8 @@ def main():
                              "double_monotonic", "ensemble", "ensemble_lagged", "threshold", "mrt2",
                              "mrt_limiter"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16_dev", "bf16_dev"])
+    ap.add_argument("--init", default="rest", choices=["rest", "random"],
+                    help="start the timed lattice from rest (the workload) or from random_start (profiling)")
     ap.add_argument("--variant-steps", type=int, default=100)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-small", action="store_true", help="skip the tube and 257^2 runs")
