@@ -320,8 +320,6 @@ cudaError_t enqueue_one_step(lbm_ctx* ctx, bool odd, int cslot, cudaStream_t s) 
     return e;
 }
 
-// Captures the two steps of one A-A period (even with counter slot 0, odd
-// with slot 1) into a graph on a private stream; lbm_step replays it.
 // Captures `periods` A-A periods (even step with counter slot 0, odd with
 // slot 1, repeated) into *graph / *exec on a private stream.
 cudaError_t capture_periods(lbm_ctx* ctx, int periods, cudaGraph_t* graph, cudaGraphExec_t* exec) {

@@ -129,26 +129,80 @@ lbm_status backward_t(lbm_ctx* ctx, int T_, int K, const void* seed, int seed_dt
     } else {
         ACK(ctx, AdjLaunch<float>::convert((const float*)seed, lam[0], Q * N, s));
     }
+    // One segment: the recomputation of its len pre-collision states and
+    // branches from the context's state (just set from the checkpoint:
+    // t = 0, even parity), then len adjoint steps from lambda buffer c0.
+    auto enqueue_segment = [&](int len, int c0, cudaStream_t st) -> lbm_status {
+        if (branches) ACK(ctx, cudaMemsetAsync(aux, 0xff, (size_t)len * N * sizeof(int), st));  // AUX_LBGK
+        for (int k = 0; k < len; ++k) {
+            const T* fk = (const T*)(w + L.seg + (size_t)k * L.dense);
+            AST(lbm_get_state(ctx, (void*)fk, dtype_of(ctx), st));
+            AST(lbm_step(ctx, 1, st));
+            if (branches)
+                ACK(ctx, AdjLaunch<T>::record(Q, ctx->p, coll, (int)((ctx->t - 1) & 1), fk, aux + (size_t)k * N,
+                                              ctx->nsm, st));
+        }
+        int c = c0;
+        for (int k = len - 1; k >= 0; --k) {
+            ACK(ctx, AdjLaunch<T>::step(Q, g, (const T*)(w + L.seg + (size_t)k * L.dense),
+                                        branches ? aux + (size_t)k * N : nullptr, lam[c], lam[c ^ 1], acc, wbuf,
+                                        coll == LBM_MEDIAN, st));
+            c ^= 1;
+        }
+        return LBM_OK;
+    };
+    // Full segments replay a graph of that sequence (about 5 K kernels of a
+    // few microseconds each, where separate launches would set the pace),
+    // captured on a private stream once per starting lambda buffer; every
+    // segment starts from t = 0, so the captured kernels (parities, counter
+    // slots) are those of every full segment.  Without a graph (capture not
+    // possible) the kernels are launched one by one.
+    struct Execs {
+        cudaGraphExec_t e[2] = {nullptr, nullptr};
+        ~Execs() {
+            for (auto x : e)
+                if (x) cudaGraphExecDestroy(x);
+        }
+    } seg_exec;
+    auto capture_segment = [&](int c0) -> cudaGraphExec_t {
+        cudaStream_t cap;
+        if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+        cudaGraphExec_t exec = nullptr;
+        const uint64_t t0 = ctx->t;
+        const int par0 = ctx->parity;
+        ctx->t = 0;
+        ctx->parity = 0;
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const lbm_status st = enqueue_segment(K, c0, cap);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(cap, &graph);
+            if (st == LBM_OK && e == cudaSuccess && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+                exec = nullptr;
+            if (graph) cudaGraphDestroy(graph);
+        }
+        cudaGetLastError();  // a failed capture leaves the direct launches
+        cudaStreamDestroy(cap);
+        ctx->t = t0;
+        ctx->parity = par0;
+        return exec;
+    };
     int cur = 0;
     for (int sg = L.nseg - 1; sg >= 0; --sg) {
         const int len = std::min(K, T_ - sg * K);
-        // recompute the segment: its pre-collision states and branches
         AST(lbm_set_state(ctx, w + L.ckpt + (size_t)sg * L.dense, dtype_of(ctx), s));
-        if (branches) ACK(ctx, cudaMemsetAsync(aux, 0xff, (size_t)len * N * sizeof(int), s));  // AUX_LBGK
-        for (int k = 0; k < len; ++k) {
-            const T* fk = (const T*)(w + L.seg + (size_t)k * L.dense);
-            AST(lbm_get_state(ctx, (void*)fk, dtype_of(ctx), s));
-            AST(lbm_step(ctx, 1, s));
-            if (branches)
-                ACK(ctx, AdjLaunch<T>::record(Q, ctx->p, coll, (int)((ctx->t - 1) & 1), fk, aux + (size_t)k * N,
-                                              ctx->nsm, s));
+        cudaGraphExec_t exec = nullptr;
+        if (len == K && K > 1) {
+            if (!seg_exec.e[cur]) seg_exec.e[cur] = capture_segment(cur);
+            exec = seg_exec.e[cur];
         }
-        for (int k = len - 1; k >= 0; --k) {
-            ACK(ctx, AdjLaunch<T>::step(Q, g, (const T*)(w + L.seg + (size_t)k * L.dense),
-                                        branches ? aux + (size_t)k * N : nullptr, lam[cur], lam[cur ^ 1], acc,
-                                        wbuf, coll == LBM_MEDIAN, s));
-            cur ^= 1;
+        if (exec) {
+            ACK(ctx, cudaGraphLaunch(exec, s));
+            ctx->t = len;
+            ctx->parity = len & 1;
+        } else {
+            AST(enqueue_segment(len, cur, s));
         }
+        if (len & 1) cur ^= 1;
     }
     // the context ends where the forward pass left it
     AST(lbm_set_state(ctx, fT, dtype_of(ctx), s));
