@@ -131,6 +131,62 @@ struct StF16 {
 };
 
 // ---------------------------------------------------------------------------
+// FP32 arithmetic on one site (float) or on two sites at once (F2: two FP32
+// values in one 64-bit register pair, the packed add / sub / mul / fma
+// .rn.f32x2 instructions of sm_100-class GPUs: one instruction, both sites).
+// The one-site forms are the same correctly rounded operations (explicit
+// _rn intrinsics, which the compiler neither contracts nor reorders), so a
+// site computes to the same bits in either form.
+// ---------------------------------------------------------------------------
+struct F2 {
+    uint64_t v;
+};
+template <class V> struct VLanes;
+template <> struct VLanes<float> { static constexpr int n = 1; };
+template <> struct VLanes<F2> { static constexpr int n = 2; };
+
+__device__ __forceinline__ float vsplat(float a, float) { return a; }
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float vlane(float a, int) { return a; }
+template <class V> __device__ __forceinline__ V vmake(float a, float b);
+template <> __device__ __forceinline__ float vmake<float>(float a, float) { return a; }
+
+template <> __device__ __forceinline__ F2 vmake<F2>(float a, float b) {
+    F2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ F2 vsplat(float a, F2) { return vmake<F2>(a, a); }
+__device__ __forceinline__ float vlane(F2 a, int k) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+    return k ? hi : lo;
+}
+__device__ __forceinline__ F2 vadd(F2 a, F2 b) {
+    F2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 vsub(F2 a, F2 b) {
+    F2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 vmul(F2 a, F2 b) {
+    F2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 vfma(F2 a, F2 b, F2 c) {
+    F2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+
+// ---------------------------------------------------------------------------
 // Equilibria.  1D polynomial and entropic equilibria of Section 6 per unit
 // density (order -, 0, +); the D2Q9 quasi-equilibrium is their product
 // (Section 8).  The textbook polynomial is an option.

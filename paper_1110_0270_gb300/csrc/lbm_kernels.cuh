@@ -206,108 +206,191 @@ __device__ __forceinline__ void collide_site(const Params& p, int x, int y, cons
 // differences f - f* = d - d*, so the post-collision deviation
 // D_i = F_i - W_i comes out directly (no W_i added on load or subtracted on
 // store).  The Ehrenfest screen and the positivity rule form absolute values
-// where they need them.  D2Q9; the collisions of the paired kernel.
-// Also returns a lower bound of min_i f*_i for the limiter screen: for the
-// product equilibria the minimum of the products rho a_x a_y is the product
-// of the minima when every factor is positive (else 0, which passes every
-// site to the exact test).
-template <class T>
-__device__ __forceinline__ T equilibrium_dev9(int kind, T drho, T rho, T ux, T uy, T* ds) {
+// where they need them.  D2Q9, the collisions of the paired kernel, for one
+// site (V = float) or two adjacent sites at once (V = F2, the pair kernel):
+// the same operations in the same order, so either form gives the same bits.
+// The per-lane parts (the division by rho, the tests, the rare candidate
+// record and positivity fix-up) run on each lane's value.
+//
+// Equilibrium d*_i; with MIN also a lower bound of min_i f*_i per lane for
+// the limiter screen: for the product equilibria the product of the 1D
+// minima when every factor is positive (else 0, which passes every site to
+// the exact test).
+template <class V, bool MIN>
+__device__ __forceinline__ void equilibrium_dev9(int kind, V drho, V rho, V ux, V uy, V* ds, float* m) {
     using L = Lat<9>;
+    constexpr int NL = VLanes<V>::n;
+    const V one = vsplat(1.f, rho);
     if (kind == LBM_EQ_POLY_STD) {
-        const T uu = ux * ux + uy * uy;
-        T rest = drho, m = T(1);
+        // textbook form: d*_i = W_i (drho + rho (3 cu + 4.5 cu^2 - 1.5 u^2))
+        const V nuu = vmul(vsplat(-1.5f, rho), vfma(ux, ux, vmul(uy, uy)));
+        V rest = drho;
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
-            const T cu = T(L::cx(i)) * ux + T(L::cy(i)) * uy;
-            ds[i] = T(L::w(i)) * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
-            rest -= ds[i];
-            m = fminf(m, T(L::w(i)) + ds[i]);
+            const V cu = vfma(vsplat(float(L::cx(i)), rho), ux, vmul(vsplat(float(L::cy(i)), rho), uy));
+            const V a = vfma(vmul(vsplat(4.5f, rho), cu), cu, vfma(vsplat(3.f, rho), cu, nuu));
+            ds[i] = vmul(vsplat(float(L::w(i)), rho), vfma(rho, a, drho));
+            rest = vsub(rest, ds[i]);
         }
         ds[0] = rest;
-        return fminf(m, T(L::w(0)) + rest);
+        if (MIN) {
+#pragma unroll
+            for (int k = 0; k < NL; ++k) {
+                float mk = float(L::w(0)) + vlane(rest, k);
+#pragma unroll
+                for (int i = 1; i < 9; ++i) mk = fminf(mk, float(L::w(i)) + vlane(ds[i], k));
+                m[k] = mk;
+            }
+        }
+        return;
     }
-    T ax[3], ay[3];
-    if (kind == LBM_EQ_ENTROPIC) {
-        eq1d_entropic<T>(ux, ax[0], ax[1], ax[2]);
-        eq1d_entropic<T>(uy, ay[0], ay[1], ay[2]);
-    } else {
-        eq1d_poly<T>(ux, ax[0], ax[1], ax[2]);
-        eq1d_poly<T>(uy, ay[0], ay[1], ay[2]);
+    // product of the 1D factors a_-, a_0, a_+ = a - u/2, 1 - 2a, a + u/2
+    V ax[3], ay[3];
+    const V uv[2] = {ux, uy};
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const V u = uv[c];
+        const V t = vfma(vmul(vsplat(3.f, rho), u), u, one);  // 1 + 3 u^2
+        V a;
+        if (kind == LBM_EQ_ENTROPIC) {
+            float sq[NL];
+#pragma unroll
+            for (int k = 0; k < NL; ++k) sq[k] = __fsqrt_rn(vlane(t, k));
+            a = vmul(vfma(vsplat(2.f, rho), vmake<V>(sq[0], sq[NL - 1]), vsplat(-1.f, rho)), vsplat(1.f / 6.f, rho));
+        } else {
+            a = vmul(t, vsplat(1.f / 6.f, rho));
+        }
+        const V h = vmul(vsplat(0.5f, rho), u);
+        V* f1 = c == 0 ? ax : ay;
+        f1[0] = vsub(a, h);
+        f1[1] = vfma(vsplat(-2.f, rho), a, one);
+        f1[2] = vadd(a, h);
     }
 #pragma unroll
-    for (int k = 0; k < 3; ++k) ax[k] *= rho;
+    for (int k = 0; k < 3; ++k) ax[k] = vmul(ax[k], rho);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) ds[i] = fmaf(ax[L::cx(i) + 1], ay[L::cy(i) + 1], -T(L::w(i)));
-    const T mx = fminf(fminf(ax[0], ax[1]), ax[2]), my = fminf(fminf(ay[0], ay[1]), ay[2]);
-    return (mx > T(0) && my > T(0)) ? mx * my : T(0);
+    for (int i = 0; i < 9; ++i) ds[i] = vfma(ax[L::cx(i) + 1], ay[L::cy(i) + 1], vsplat(-float(L::w(i)), rho));
+    if (MIN) {
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            const float mx = fminf(fminf(vlane(ax[0], k), vlane(ax[1], k)), vlane(ax[2], k));
+            const float my = fminf(fminf(vlane(ay[0], k), vlane(ay[1], k)), vlane(ay[2], k));
+            m[k] = (mx > 0.f && my > 0.f) ? mx * my : 0.f;
+        }
+    }
 }
 
-template <class ST, int COLL>
-__device__ __forceinline__ void collide_site_dev(const Params& p, int x, int y, const float* d, float* D) {
+template <class V, class ST, int COLL>
+__device__ __forceinline__ void collide_dev(const Params& p, int x, int y, const V* d, V* D) {
     using L = Lat<9>;
-    using T = float;
-    T drho = T(0), jx = T(0), jy = T(0);
+    constexpr int NL = VLanes<V>::n;
+    constexpr bool kScreen = COLL == LBM_EHRENFEST || COLL == LBM_MRT_LIMITER;
+    static_assert(L::cx(1) == 1 && L::cx(2) == 1 && L::cx(8) == 1 && L::cx(4) == -1 && L::cx(5) == -1 &&
+                      L::cx(6) == -1 && L::cy(6) == 1 && L::cy(7) == 1 && L::cy(8) == 1 && L::cy(2) == -1 &&
+                      L::cy(3) == -1 && L::cy(4) == -1,
+                  "D2Q9 numbering of Lat<9>");
+    V drho = d[0];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        drho += d[i];
-        if (L::cx(i) > 0) jx += d[i];
-        if (L::cx(i) < 0) jx -= d[i];
-        if (L::cy(i) > 0) jy += d[i];
-        if (L::cy(i) < 0) jy -= d[i];
-    }
-    const T rho = T(1) + drho;
-    const T inv = T(1) / rho;
-    const T ux = jx * inv, uy = jy * inv;
-    if (!(rho > T(0)) || !(fabsf(ux) < T(1e30)) || !(fabsf(uy) < T(1e30)))
+    for (int i = 1; i < 9; ++i) drho = vadd(drho, d[i]);
+    const V jx = vsub(vadd(vadd(d[1], d[2]), d[8]), vadd(vadd(d[4], d[5]), d[6]));
+    const V jy = vsub(vadd(vadd(d[6], d[7]), d[8]), vadd(vadd(d[2], d[3]), d[4]));
+    const V rho = vadd(vsplat(1.f, drho), drho);
+    float inv[NL];
+#pragma unroll
+    for (int k = 0; k < NL; ++k) inv[k] = __fdiv_rn(1.f, vlane(rho, k));
+    const V vinv = vmake<V>(inv[0], inv[NL - 1]);
+    const V ux = vmul(jx, vinv), uy = vmul(jy, vinv);
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < NL; ++k)
+        bad |= !(vlane(rho, k) > 0.f) || !(fabsf(vlane(ux, k)) < 1e30f) || !(fabsf(vlane(uy, k)) < 1e30f);
+    if (bad)
         if (*(volatile unsigned*)&p.counters[CNT_DIVERGED] == 0u) atomicExch(&p.counters[CNT_DIVERGED], 1u);
-    T ds[9];
-    const T m = equilibrium_dev9<T>(p.eq, drho, rho, ux, uy, ds);
-    if (COLL == LBM_EHRENFEST || COLL == LBM_MRT_LIMITER) {
-        // the screen of maybe_above_loose on f - f* = d - d* with m a lower
-        // bound of min f* (the bound's argument holds for any positive one)
-        float s2 = 0.f;
+    V ds[9], e[9];
+    float m[NL];
+    equilibrium_dev9<V, kScreen>(p.eq, drho, rho, ux, uy, ds, m);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const float e = d[i] - ds[i];
-            s2 = fmaf(e, e, s2);
-        }
-        bool maybe = true;
-        if (m > 0.f && s2 < 0.25f * m * m) {
-            const float q = __fdividef(s2, m);  // approximate (2 ulp), far inside the slack
-            maybe = slack_reaches(q, q, rho, p.delta_f);
-        }
-        if (maybe) {
-            T f[9];
+    for (int i = 0; i < 9; ++i) e[i] = vsub(d[i], ds[i]);  // f - f*
+    if (kScreen) {
+        // the screen of maybe_above_loose on f - f* with m a lower bound of
+        // min f* (the bound's argument holds for any positive one)
+        V s2 = vmul(e[0], e[0]);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) f[i] = T(L::w(i)) + d[i];
-            record_candidate<9, T>(p, x, y, f);
+        for (int i = 1; i < 9; ++i) s2 = vfma(e[i], e[i], s2);
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            const float s2k = vlane(s2, k), mk = m[k];
+            bool maybe = true;
+            if (mk > 0.f && s2k < 0.25f * mk * mk) {
+                const float q = __fdividef(s2k, mk);  // approximate (2 ulp), far inside the slack
+                maybe = slack_reaches(q, q, vlane(rho, k), p.delta_f);
+            }
+            if (maybe) {
+                float f[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) f[i] = float(L::w(i)) + vlane(d[i], k);
+                record_candidate<9, float>(p, x + k, y, f);
+            }
         }
     }
+    const float om = 2.f * p.beta_f;
     if (COLL == LBM_MRT) {
-        mrt_d2q9<T>(d, ds, p.mrt, p.mrt_f, D);
-    } else if (COLL == LBM_MRT2) {
-        mrt2_d2q9<T>(d, ds, T(2) * T(p.beta_f), D);
-    } else {
-        lbgk<9, T>(d, ds, T(p.beta_f), D);
-    }
-    if (COLL == LBM_POSITIVITY) {
-        bool neg = false;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) neg |= D[i] < -T(L::w(i));
-        if (neg) {
-            T fe[9], F[9];
+        for (int k = 0; k < NL; ++k) {
+            float dl[9], sl[9], Dl[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                fe[i] = T(L::w(i)) + ds[i];
-                F[i] = T(L::w(i)) + D[i];
+                dl[i] = vlane(d[i], k);
+                sl[i] = vlane(ds[i], k);
             }
-            if (positivity<9, T>(fe, F)) atomicAdd(&p.stats[ST_LIMITED], 1ull);
+            mrt_d2q9<float>(dl, sl, p.mrt, p.mrt_f, Dl);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) D[i] = F[i] - T(L::w(i));
+            for (int i = 0; i < 9; ++i) D[i] = k == 0 ? vmake<V>(Dl[i], Dl[i]) : vmake<V>(vlane(D[i], 0), Dl[i]);
+        }
+    } else if (COLL == LBM_MRT2) {
+        // A_2: D = d* + (1 - s_nu)/4 (m4 r4 + m5 r5), m = r . (f - f*)
+        const V c = vsplat((1.f - om) * 0.25f, rho);
+        const V m4 = vmul(vsub(vadd(e[1], e[5]), vadd(e[3], e[7])), c);
+        const V m5 = vmul(vsub(vadd(e[4], e[8]), vadd(e[2], e[6])), c);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int r4 = L::cx(i) * L::cx(i) - L::cy(i) * L::cy(i), r5 = L::cx(i) * L::cy(i);
+            D[i] = r4 > 0 ? vadd(ds[i], m4) : r4 < 0 ? vsub(ds[i], m4) : r5 > 0 ? vadd(ds[i], m5)
+                                                     : r5 < 0 ? vsub(ds[i], m5) : ds[i];
+        }
+    } else {
+        // LBGK: F = f - 2 beta (f - f*)
+        const V nom = vsplat(-om, rho);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) D[i] = vfma(nom, e[i], d[i]);
+    }
+    if (COLL == LBM_POSITIVITY) {
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            bool neg = false;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) neg |= vlane(D[i], k) < -float(L::w(i));
+            if (neg) {
+                float fe[9], F[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    fe[i] = float(L::w(i)) + vlane(ds[i], k);
+                    F[i] = float(L::w(i)) + vlane(D[i], k);
+                }
+                if (positivity<9, float>(fe, F)) atomicAdd(&p.stats[ST_LIMITED], 1ull);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const float v = F[i] - float(L::w(i));
+                    D[i] = vmake<V>(k == 0 ? v : vlane(D[i], 0), k == 0 ? vlane(D[i], NL - 1) : v);
+                }
+            }
         }
     }
-    conserve_mass<9, T>(drho, D);
+    // every collision conserves mass: the rest population as rho minus the others
+    V sD = D[1];
+#pragma unroll
+    for (int i = 2; i < 9; ++i) sD = vadd(sD, D[i]);
+    D[0] = vsub(drho, sD);
 }
 
 // Section 8's diffusive Maxwell rule at wall site (x, y) (bc DIFFUSIVE), on
@@ -353,7 +436,7 @@ __device__ __forceinline__ void diffusive_rule(const Params& p, int x, int y, T*
 
 // The whole step for the site (x, y): load (streaming in odd steps),
 // collision, store.
-// The 16-bit D2Q9 collisions that run in deviation form (collide_site_dev),
+// The 16-bit D2Q9 collisions that run in deviation form (collide_dev),
 // at every site so that every kernel computes a site alike.
 template <int Q, class ST, int COLL>
 constexpr bool kDeviationForm = Q == 9 && sizeof(typename ST::S) == 2 &&
@@ -377,7 +460,7 @@ __device__ __forceinline__ void site_update(const Params& p, int x, int y, int& 
         load_general<Q, ST, ODD, DEV>(p, x, y, f);
     }
     if constexpr (DEV)
-        collide_site_dev<ST, COLL>(p, x, y, f, F);
+        collide_dev<float, ST, COLL>(p, x, y, f, F);
     else
         collide_site<Q, ST, COLL>(p, x, y, f, F, e_code, e_iters, acc);
     if (interior)
@@ -487,21 +570,19 @@ __global__ void __launch_bounds__(kBlockX* kBlockY, kMinBlocks<ST, COLL>) step_k
 // screened collisions, 3% on LBGK.  Each element is written only by the
 // thread of the site that owns it.  Warps that touch a wall, the domain edge
 // or a ragged end take the per-site path.
-// Used for the 16-bit formats, whose per-site instruction count (packed
-// conversions, addressing) otherwise limits them below the HBM roofline;
-// with FP32 storage the one-site kernel is as fast or faster.  Compiled for
-// six resident CTAs (40 registers) where that leaves no or few spills, five
-// (48 registers) for the collisions with the Ehrenfest screen or the
-// positivity rule.
+// The collision runs on both sites at once with the packed FP32 pair
+// instructions (collide_dev<F2>).  Used for the 16-bit formats, whose
+// per-site instruction count (conversions, addressing) otherwise limits
+// them below the HBM roofline; with FP32 storage the one-site kernel is as
+// fast or faster.  Compiled for five resident CTAs (48 registers; the
+// register pairs of the packed form need more than the one-site form's 40).
 constexpr int kVecX = 64;
 constexpr int kVecY = 4;
 template <class ST, int COLL>
 constexpr bool kPairedSites = sizeof(typename ST::S) == 2 &&
                               (COLL == LBM_LBGK || COLL == LBM_EHRENFEST || COLL == LBM_POSITIVITY ||
                                COLL == LBM_MRT || COLL == LBM_MRT2 || COLL == LBM_MRT_LIMITER);
-template <int COLL>
-constexpr int kPairedMinBlocks =
-    (COLL == LBM_EHRENFEST || COLL == LBM_MRT_LIMITER || COLL == LBM_POSITIVITY) ? 5 : 6;
+constexpr int kPairedMinBlocks = 5;
 
 __device__ __forceinline__ uint32_t ld_word(const void* base, int off) {
     return *reinterpret_cast<const uint32_t*>(reinterpret_cast<const uint16_t*>(base) + off);
@@ -511,7 +592,7 @@ __device__ __forceinline__ void st_word(void* base, int off, uint32_t v) {
 }
 
 template <int Q, class ST, int COLL, bool ODD>
-__global__ void __launch_bounds__(kVecX* kVecY, kPairedMinBlocks<COLL>) step_kernel_v2(Params p) {
+__global__ void __launch_bounds__(kVecX* kVecY, kPairedMinBlocks) step_kernel_v2(Params p) {
     pdl_enter();
     using T = typename ST::T;
     using L = Lat<Q>;
@@ -554,30 +635,28 @@ __global__ void __launch_bounds__(kVecX* kVecY, kPairedMinBlocks<COLL>) step_ker
             B[i] = reinterpret_cast<const S*>(base)[off + 1 - L::cx(i)];
         }
     }
-    T fa[Q], fb[Q];  // deviations f - W of the two sites
+    F2 dv[Q];  // deviations f - W of the two sites
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (!ODD || L::cx(i) == 0) {
             const float2 v = ST::unpack(W[i]);
-            fa[i] = v.x;
-            fb[i] = v.y;
+            dv[i] = vmake<F2>(v.x, v.y);
         } else {
-            fa[i] = ST::dec(A[i]);
-            fb[i] = ST::dec(B[i]);
+            dv[i] = vmake<F2>(ST::dec(A[i]), ST::dec(B[i]));
         }
     }
-    T Fa[Q], Fb[Q];  // post-collision deviations F - W
-    collide_site_dev<ST, COLL>(p, x0, y, fa, Fa);
-    collide_site_dev<ST, COLL>(p, x0 + 1, y, fb, Fb);
+    F2 Dv[Q];  // post-collision deviations F - W of both sites
+    collide_dev<F2, ST, COLL>(p, x0, y, dv, Dv);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int k = ODD ? L::opp(i) : i;
         const int off = k * p.plane32 + o - (ODD ? L::cy(i) * p.pitch : 0);
+        const float Fa = vlane(Dv[L::opp(i)], 0), Fb = vlane(Dv[L::opp(i)], 1);
         if (!ODD || L::cx(i) == 0) {
-            st_word(base, off, ST::pack(Fa[L::opp(i)], Fb[L::opp(i)]));
+            st_word(base, off, ST::pack(Fa, Fb));
         } else {  // a -> x0 - v_x, b -> x0 + 1 - v_x
-            reinterpret_cast<S*>(base)[off - L::cx(i)] = ST::enc(Fa[L::opp(i)]);
-            reinterpret_cast<S*>(base)[off + 1 - L::cx(i)] = ST::enc(Fb[L::opp(i)]);
+            reinterpret_cast<S*>(base)[off - L::cx(i)] = ST::enc(Fa);
+            reinterpret_cast<S*>(base)[off + 1 - L::cx(i)] = ST::enc(Fb);
         }
     }
 }
