@@ -136,6 +136,13 @@ __global__ void __launch_bounds__(256) adj_seed_ke(AdjGeo g, const T* __restrict
     block_add2(e, 0.0, J, nullptr);
 }
 
+// The adjoint kernels hold the rare FP64 branch work (median Delta S
+// gradients) in out-of-line functions and are compiled for four resident
+// CTAs per SM (two in FP64): the rare work spills instead of setting every site's
+// register allocation (without the cap a kernel takes over 200 registers).
+template <class T>
+constexpr int kAdjMinBlocks = sizeof(T) == 8 ? 2 : 4;
+
 // Branch of a site in one step (the int recorded per site and step).
 enum { AUX_LBGK = -1, AUX_FSTAR = -2, AUX_POS0 = -3 };  // AUX_POS0 - k; m >= 0: median
 
@@ -143,7 +150,7 @@ enum { AUX_LBGK = -1, AUX_FSTAR = -2, AUX_POS0 = -3 };  // AUX_POS0 - k; m >= 0:
 // its gradient dDelta S/df_j = ln(f_j/f*_j) + 1 - sum_i (f_i/f*_i) df*_i/df_j.
 // +inf (gradient 0) with a non-positive population.
 template <int Q>
-__device__ double delta_s_grad(int eqkind, const double* f, double* grad) {
+__device__ __noinline__ double delta_s_grad(int eqkind, const double* f, double* grad) {
     using L = Lat<Q>;
     double rho, ux, uy, feq[Q], dr[Q], dx[Q], dy[Q];
     moments<Q, double>(f, rho, ux, uy);
@@ -155,14 +162,19 @@ __device__ double delta_s_grad(int eqkind, const double* f, double* grad) {
         neg |= !(f[i] > 0.0) || !(feq[i] > 0.0);
         ds += feq[i] * gfun_d((f[i] - feq[i]) / feq[i]);
     }
+    // sum_i (f_i / f*_i) df*_i/df_j = S0 + (v_jx - u_x) Sx / rho + (v_jy - u_y) Sy / rho
+    double r[Q], S0 = 0.0, Sx = 0.0, Sy = 0.0;
 #pragma unroll
-    for (int j = 0; j < Q; ++j) {
-        double s = 0.0;
-#pragma unroll
-        for (int i = 0; i < Q; ++i)
-            s += f[i] / feq[i] * (dr[i] + dx[i] * (L::cx(j) - ux) / rho + dy[i] * (L::cy(j) - uy) / rho);
-        grad[j] = neg ? 0.0 : log(f[j] / feq[j]) + 1.0 - s;
+    for (int i = 0; i < Q; ++i) {
+        r[i] = f[i] / feq[i];
+        S0 += r[i] * dr[i];
+        Sx += r[i] * dx[i];
+        Sy += r[i] * dy[i];
     }
+    const double ir = 1.0 / rho;
+#pragma unroll
+    for (int j = 0; j < Q; ++j)
+        grad[j] = neg ? 0.0 : log(r[j]) + 1.0 - (S0 + (L::cx(j) - ux) * ir * Sx + (L::cy(j) - uy) * ir * Sy);
     return neg ? __longlong_as_double(0x7ff0000000000000ULL) : ds;
 }
 
@@ -179,7 +191,7 @@ __device__ __forceinline__ void dense_site_d(const T* a, int64_t N, int64_t s, d
 // same precision, so the same decision).  The median's window site m: the
 // lower median of the clipped window's FP64 Delta S, ties by site index.
 template <int Q, class T>
-__global__ void __launch_bounds__(256) adj_record(Params p, int coll, int cslot, const T* __restrict__ f,
+__global__ void __launch_bounds__(256, kAdjMinBlocks<T>) adj_record(Params p, int coll, int cslot, const T* __restrict__ f,
                                                  int* __restrict__ aux) {
     const int64_t N = (int64_t)p.nx * p.ny;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
@@ -208,40 +220,118 @@ __global__ void __launch_bounds__(256) adj_record(Params p, int coll, int cslot,
     }
     unsigned M = p.counters[cslot];
     if (M > (unsigned)p.cand_cap) M = (unsigned)p.cand_cap;
-    for (int64_t j = tid; j < (int64_t)M; j += nt) {
-        if (!p.cand_sel[j]) continue;
+    if (coll == LBM_EHRENFEST) {
+        for (int64_t j = tid; j < (int64_t)M; j += nt)
+            if (p.cand_sel[j] && p.cand_ds[j] > p.delta) aux[p.cand_site[j]] = AUX_FSTAR;
+        return;
+    }
+    // median: one warp per selected candidate, one lane per window site
+    // (lane l: offset (l % 3 - 1, l / 3 - ry), the window's scan order);
+    // the first lane sorts the values and keeps the window site of the
+    // lower median
+    const int lane = threadIdx.x & 31;
+    const int ry = Q == 9 ? 1 : 0;
+    for (int64_t j = tid >> 5; j < (int64_t)M; j += nt >> 5) {
+        if (!p.cand_sel[j]) continue;  // the same j on every lane
         const int site = p.cand_site[j];
-        if (coll == LBM_EHRENFEST) {
-            if (p.cand_ds[j] > p.delta) aux[site] = AUX_FSTAR;
-            continue;
-        }
-        // median: the window site of the lower median
         const int x = site % p.nx, y = site / p.nx;
-        const int ry = Q == 9 ? 1 : 0;
+        int q = -1;
+        double d = 0.0;
+        if (lane < 3 * (2 * ry + 1)) {
+            int xx = x + lane % 3 - 1, yy = y + lane / 3 - ry;
+            if (p.periodic_x) xx = xx < 0 ? xx + p.nx : (xx >= p.nx ? xx - p.nx : xx);
+            if (p.periodic_y) yy = yy < 0 ? yy + p.ny : (yy >= p.ny ? yy - p.ny : yy);
+            if (xx >= 0 && xx < p.nx && yy >= 0 && yy < p.ny) {
+                q = yy * p.nx + xx;
+                double fq[Q], g[Q];
+                dense_site_d<Q, T>(f, N, q, fq);
+                d = delta_s_grad<Q>(p.eq, fq, g);
+            }
+        }
         int w[9];
         double v[9];
         int n = 0;
-        for (int dy = -ry; dy <= ry; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                int xx = x + dx, yy = y + dy;
-                if (p.periodic_x) xx = xx < 0 ? xx + p.nx : (xx >= p.nx ? xx - p.nx : xx);
-                if (p.periodic_y) yy = yy < 0 ? yy + p.ny : (yy >= p.ny ? yy - p.ny : yy);
-                if (xx < 0 || xx >= p.nx || yy < 0 || yy >= p.ny) continue;
-                const int q = yy * p.nx + xx;
-                double fq[Q], g[Q];
-                dense_site_d<Q, T>(f, N, q, fq);
-                const double d = delta_s_grad<Q>(p.eq, fq, g);
-                int k = n++;
-                while (k > 0 && (v[k - 1] > d || (v[k - 1] == d && w[k - 1] > q))) {  // ascending
-                    v[k] = v[k - 1];
-                    w[k] = w[k - 1];
-                    --k;
-                }
-                v[k] = d;
-                w[k] = q;
+#pragma unroll
+        for (int l = 0; l < 3 * (2 * ry + 1); ++l) {
+            const int ql = __shfl_sync(0xffffffffu, q, l);
+            const double dl = __shfl_sync(0xffffffffu, d, l);
+            if (ql < 0) continue;
+            int k = n++;
+            while (k > 0 && (v[k - 1] > dl || (v[k - 1] == dl && w[k - 1] > ql))) {  // ascending
+                v[k] = v[k - 1];
+                w[k] = w[k - 1];
+                --k;
             }
-        aux[site] = w[(n - 1) / 2];
+            v[k] = dl;
+            w[k] = ql;
+        }
+        if (lane == 0) aux[site] = w[(n - 1) / 2];
     }
+}
+
+// The positivity and median branches of the adjoint step at site s (psi,
+// dpsi/dbeta, dpsi/df_j and the median's cross-term coefficient w), out of
+// line: they are rare, and the median's FP64 Delta S gradients would
+// otherwise set the register allocation of every site's adjoint step.
+template <int Q, class T>
+struct AdjBranch {
+    T psi, dpsi_db, dpsi[Q];
+    double w;
+};
+
+template <int Q, class T>
+__device__ __noinline__ AdjBranch<Q, T> adj_branch(AdjGeo g, const T* __restrict__ f, int64_t N, int64_t s,
+                                                   int br, T gs) {
+    using L = Lat<Q>;
+    AdjBranch<Q, T> b;
+    T fs[Q], feq[Q], dr[Q], dx[Q], dy[Q], rho, ux, uy;
+    dense_site<Q, T>(f, N, s, fs);
+    moments<Q, T>(fs, rho, ux, uy);
+    eq_partials<Q, T>(g.eq, rho, ux, uy, feq, dr, dx, dy);
+    const T inv = T(1) / rho;
+    const T c = T(1) - T(2) * T(g.beta);
+    b.w = 0.0;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) b.dpsi[j] = T(0);
+    if (br <= AUX_POS0) {
+        // psi = f*_k / (f*_k - f_k), independent of beta
+        const int k = AUX_POS0 - br;
+        T fk = T(0), ek = T(0), drk = T(0), dxk = T(0), dyk = T(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            if (i == k) {
+                fk = fs[i];
+                ek = feq[i];
+                drk = dr[i];
+                dxk = dx[i];
+                dyk = dy[i];
+            }
+        const T D = ek - fk;
+        b.psi = ek / D;
+        b.dpsi_db = T(0);
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const T dfk = drk + dxk * (T(L::cx(j)) - ux) * inv + dyk * (T(L::cy(j)) - uy) * inv;
+            b.dpsi[j] = (-fk * dfk + (j == k ? ek : T(0))) / (D * D);
+        }
+        return b;
+    }
+    // psi = c sqrt(M / C): C and its gradient here, M at window site br (FP64)
+    double fd[Q], gC[Q], fm[Q], gM[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) fd[i] = (double)fs[i];
+    const double C = delta_s_grad<Q>(g.eq, fd, gC);
+    dense_site_d<Q, T>(f, N, br, fm);
+    const double Mv = delta_s_grad<Q>(g.eq, fm, gM);
+    const double phi = isinf(C) ? 0.0 : sqrt(Mv / C);
+    b.psi = T(c * T(phi));
+    b.dpsi_db = T(-2.0 * phi);
+    if (!isinf(C) && Mv > 0.0) {
+#pragma unroll
+        for (int j = 0; j < Q; ++j) b.dpsi[j] = T(-(double)c * phi / (2.0 * C) * gC[j]);
+        b.w = (double)gs * (double)c * phi / (2.0 * Mv);
+    }
+    return b;
 }
 
 // lambda_t from lambda_{t+1} (see the header), with dJ/dU in acc[0] and
@@ -249,7 +339,7 @@ __global__ void __launch_bounds__(256) adj_record(Params p, int coll, int cslot,
 // For a median site the coefficient w = g (1 - 2 beta) sqrt(M / C) / (2 M) of
 // its cross term goes to wbuf[s] (adj_median_cross adds it at m).
 template <int Q, class T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, kAdjMinBlocks<T>)
     adj_step(AdjGeo g, const T* __restrict__ f, const int* __restrict__ aux, const T* __restrict__ lam_in,
              T* __restrict__ lam_out, double* acc, double* __restrict__ wbuf) {
     using L = Lat<Q>;
@@ -257,7 +347,7 @@ __global__ void __launch_bounds__(256)
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double dU = 0.0, dB = 0.0;
     if (s < N) {
-        const int x = (int)(s % g.nx), y = (int)(s / g.nx);
+        const int x = (int)s % g.nx, y = (int)s / g.nx;  // N < 2^31
         T Lam[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
@@ -285,52 +375,19 @@ __global__ void __launch_bounds__(256)
         }
         const T inv = T(1) / rho;
         const int br = aux ? aux[s] : AUX_LBGK;
-        const T c = T(1) - T(2) * T(g.beta);
-        T psi = c, dpsi_db = T(-2), dpsi[Q];
+        T psi = T(1) - T(2) * T(g.beta), dpsi_db = T(-2), dpsi[Q];
 #pragma unroll
         for (int j = 0; j < Q; ++j) dpsi[j] = T(0);
         if (br == AUX_FSTAR) {
             psi = T(0);
             dpsi_db = T(0);
-        } else if (br <= AUX_POS0) {
-            // psi = f*_k / (f*_k - f_k), independent of beta
-            const int k = AUX_POS0 - br;
-            T fk = T(0), ek = T(0), drk = T(0), dxk = T(0), dyk = T(0);
+        } else if (br != AUX_LBGK) {
+            const AdjBranch<Q, T> b = adj_branch<Q, T>(g, f, N, s, br, gs);
+            psi = b.psi;
+            dpsi_db = b.dpsi_db;
 #pragma unroll
-            for (int i = 0; i < Q; ++i)
-                if (i == k) {
-                    fk = fs[i];
-                    ek = feq[i];
-                    drk = dr[i];
-                    dxk = dx[i];
-                    dyk = dy[i];
-                }
-            const T D = ek - fk;
-            psi = ek / D;
-            dpsi_db = T(0);
-#pragma unroll
-            for (int j = 0; j < Q; ++j) {
-                const T dfk = drk + dxk * (T(L::cx(j)) - ux) * inv + dyk * (T(L::cy(j)) - uy) * inv;
-                dpsi[j] = (-fk * dfk + (j == k ? ek : T(0))) / (D * D);
-            }
-        } else if (br >= 0) {
-            // psi = c sqrt(M / C): C and its gradient here, M at site br (FP64)
-            double fd[Q], gC[Q], fm[Q], gM[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) fd[i] = (double)fs[i];
-            const double C = delta_s_grad<Q>(g.eq, fd, gC);
-            dense_site_d<Q, T>(f, N, br, fm);
-            const double Mv = delta_s_grad<Q>(g.eq, fm, gM);
-            const double phi = isinf(C) ? 0.0 : sqrt(Mv / C);
-            psi = T(c * T(phi));
-            dpsi_db = T(-2.0 * phi);
-            double w = 0.0;
-            if (!isinf(C) && Mv > 0.0) {
-#pragma unroll
-                for (int j = 0; j < Q; ++j) dpsi[j] = T(-(double)c * phi / (2.0 * C) * gC[j]);
-                w = (double)gs * (double)c * phi / (2.0 * Mv);
-            }
-            wbuf[s] = w;
+            for (int j = 0; j < Q; ++j) dpsi[j] = b.dpsi[j];
+            if (br >= 0) wbuf[s] = b.w;
         }
 #pragma unroll
         for (int j = 0; j < Q; ++j) {
@@ -345,20 +402,25 @@ __global__ void __launch_bounds__(256)
 // The median's cross term: a selected site s with window site m = aux[s]
 // adds wbuf[s] dM/df(m) to lambda_t(m) (after adj_step has written it).
 template <int Q, class T>
-__global__ void __launch_bounds__(256) adj_median_cross(AdjGeo g, const T* __restrict__ f,
+__device__ __noinline__ void adj_cross_site(AdjGeo g, const T* __restrict__ f, int64_t N, int m, double w,
+                                            T* lam_out) {
+    double fm[Q], gM[Q];
+    dense_site_d<Q, T>(f, N, m, fm);
+    delta_s_grad<Q>(g.eq, fm, gM);
+#pragma unroll
+    for (int j = 0; j < Q; ++j) atomicAdd(&lam_out[(int64_t)j * N + m], T(w * gM[j]));
+}
+
+template <int Q, class T>
+__global__ void __launch_bounds__(256, kAdjMinBlocks<T>) adj_median_cross(AdjGeo g, const T* __restrict__ f,
                                                        const int* __restrict__ aux,
                                                        const double* __restrict__ wbuf, T* lam_out) {
-    const int64_t N = (int64_t)g.nx * g.ny;
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+    const int N = g.nx * g.ny;  // < 2^31
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
         const int m = aux[s];
         if (m < 0) continue;
         const double w = wbuf[s];
-        if (w == 0.0) continue;
-        double fm[Q], gM[Q];
-        dense_site_d<Q, T>(f, N, m, fm);
-        delta_s_grad<Q>(g.eq, fm, gM);
-#pragma unroll
-        for (int j = 0; j < Q; ++j) atomicAdd(&lam_out[(int64_t)j * N + m], T(w * gM[j]));
+        if (w != 0.0) adj_cross_site<Q, T>(g, f, N, m, w, lam_out);
     }
 }
 
