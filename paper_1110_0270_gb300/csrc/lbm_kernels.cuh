@@ -393,6 +393,236 @@ __device__ __forceinline__ void collide_dev(const Params& p, int x, int y, const
     D[0] = vsub(drho, sD);
 }
 
+// ---------------------------------------------------------------------------
+// The Section 4.2-4.4 limiters on D2Q9 in FP32 arithmetic (FP32 and 16-bit
+// storage): moments, the equilibrium and Delta S as explicit correctly
+// rounded operations (nothing left to contraction) with one approximate
+// reciprocal per population, then phi per site.  The kernels run it on one
+// site per thread (V = float).  Written for either value type: on packed
+// pairs (V = F2, both lanes in the same series tier evaluated at once) the
+// step needs ~116 registers, two CTAs per SM, and measured slower.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float rcp_approx(float a) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+
+// rho, u and f* (absolute) of D2Q9 populations f
+template <class V>
+__device__ __forceinline__ void lim_state(int kind, const V* f, V& rho, V& ux, V& uy, V* feq) {
+    using L = Lat<9>;
+    constexpr int NL = VLanes<V>::n;
+    rho = f[0];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) rho = vadd(rho, f[i]);
+    const V jx = vsub(vadd(vadd(f[1], f[2]), f[8]), vadd(vadd(f[4], f[5]), f[6]));
+    const V jy = vsub(vadd(vadd(f[6], f[7]), f[8]), vadd(vadd(f[2], f[3]), f[4]));
+    float inv[NL];
+#pragma unroll
+    for (int k = 0; k < NL; ++k) inv[k] = __fdiv_rn(1.f, vlane(rho, k));
+    const V vinv = vmake<V>(inv[0], inv[NL - 1]);
+    ux = vmul(jx, vinv);
+    uy = vmul(jy, vinv);
+    const V one = vsplat(1.f, rho);
+    if (kind == LBM_EQ_POLY_STD) {
+        const V nuu = vmul(vsplat(-1.5f, rho), vfma(ux, ux, vmul(uy, uy)));
+        V rest = rho;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const V cu = vfma(vsplat(float(L::cx(i)), rho), ux, vmul(vsplat(float(L::cy(i)), rho), uy));
+            const V a = vfma(vmul(vsplat(4.5f, rho), cu), cu, vfma(vsplat(3.f, rho), cu, nuu));
+            feq[i] = vmul(vsplat(float(L::w(i)), rho), vfma(rho, a, rho));
+            rest = vsub(rest, feq[i]);
+        }
+        feq[0] = rest;
+        return;
+    }
+    V ax[3], ay[3];
+    const V uv[2] = {ux, uy};
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const V u = uv[c];
+        const V t = vfma(vmul(vsplat(3.f, rho), u), u, one);  // 1 + 3 u^2
+        V a;
+        if (kind == LBM_EQ_ENTROPIC) {
+            float sq[NL];
+#pragma unroll
+            for (int k = 0; k < NL; ++k) sq[k] = __fsqrt_rn(vlane(t, k));
+            a = vmul(vfma(vsplat(2.f, rho), vmake<V>(sq[0], sq[NL - 1]), vsplat(-1.f, rho)), vsplat(1.f / 6.f, rho));
+        } else {
+            a = vmul(t, vsplat(1.f / 6.f, rho));
+        }
+        const V h = vmul(vsplat(0.5f, rho), u);
+        V* f1 = c == 0 ? ax : ay;
+        f1[0] = vsub(a, h);
+        f1[1] = vfma(vsplat(-2.f, rho), a, one);
+        f1[2] = vadd(a, h);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ax[k] = vmul(ax[k], rho);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) feq[i] = vmul(ax[L::cx(i) + 1], ay[L::cy(i) + 1]);
+}
+
+// sum_i dx_i P_K(x_i), P_K the series of g(x) / x^2 (gpoly_f's coefficients)
+template <int K, class V>
+__device__ __forceinline__ V lim_series(const V* dx, const V* x) {
+    V s;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        V pk = vsplat(((K & 1) ? -1.0f : 1.0f) / (float)((K + 1) * (K + 2)), x[i]);
+#pragma unroll
+        for (int k = K - 1; k >= 0; --k)
+            pk = vfma(pk, x[i], vsplat(((k & 1) ? -1.0f : 1.0f) / (float)((k + 1) * (k + 2)), x[i]));
+        s = i == 0 ? vmul(dx[0], pk) : vfma(dx[i], pk, s);
+    }
+    return s;
+}
+
+// Tier of the series by max |x| (the tiers of delta_s_and_q<9, float>):
+// -1 a non-positive f*, 0/1/2 series of length 1/4/11, 3 the closed form.
+__device__ __forceinline__ int lim_tier(float amax, float emin) {
+    return !(emin > 0.f) ? -1 : amax < 0x1p-12f ? 0 : amax < 0.03125f ? 1 : amax < 0.25f ? 2 : 3;
+}
+
+template <class V>
+__device__ __forceinline__ float lim_tier_sum(int tier, const V* dx, const V* x, int lane) {
+    return vlane(tier == 0 ? lim_series<1, V>(dx, x) : tier == 1 ? lim_series<4, V>(dx, x) : lim_series<11, V>(dx, x),
+                 lane);
+}
+
+// Delta S (Eq. DelS, the FP32 screen evaluation) and q = sum (f - f*)^2 / f*
+// per lane.  Both lanes in the same series tier: one packed evaluation;
+// otherwise each lane on its own, with the same operations.
+template <class V>
+__device__ __forceinline__ void delta_s_v(const V* f, const V* feq, float* ds, float* q) {
+    constexpr int NL = VLanes<V>::n;
+    V d[9], x[9], dx[9];
+    float amax[NL], emin[NL];
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+        amax[k] = 0.f;
+        emin[k] = vlane(feq[0], k);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        d[i] = vsub(f[i], feq[i]);
+        float r[NL];
+#pragma unroll
+        for (int k = 0; k < NL; ++k) r[k] = rcp_approx(vlane(feq[i], k));
+        x[i] = vmul(d[i], vmake<V>(r[0], r[NL - 1]));
+        dx[i] = vmul(d[i], x[i]);
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            amax[k] = fmaxf(amax[k], fabsf(vlane(x[i], k)));
+            emin[k] = fminf(emin[k], vlane(feq[i], k));
+        }
+    }
+    V qv = dx[0];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) qv = vadd(qv, dx[i]);
+    int tier[NL];
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+        q[k] = vlane(qv, k);
+        tier[k] = lim_tier(amax[k], emin[k]);
+    }
+    if (NL == 2 && tier[0] == tier[NL - 1] && tier[0] >= 0 && tier[0] <= 2) {
+        const V sv = tier[0] == 0 ? lim_series<1, V>(dx, x) : tier[0] == 1 ? lim_series<4, V>(dx, x)
+                                                                            : lim_series<11, V>(dx, x);
+#pragma unroll
+        for (int k = 0; k < NL; ++k) ds[k] = vlane(sv, k);
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+        float dxl[9], xl[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            dxl[i] = vlane(dx[i], k);
+            xl[i] = vlane(x[i], k);
+        }
+        if (tier[k] < 0) {
+            ds[k] = INFINITY;
+        } else if (tier[k] <= 2) {
+            ds[k] = lim_tier_sum<float>(tier[k], dxl, xl, 0);
+        } else {
+            // the closed form g(x) = (1 + x) ln(1 + x) - x; a negative population: +inf
+            float sk = 0.f;
+            bool neg = false;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                neg |= vlane(f[i], k) < 0.f;
+                sk = fmaf(vlane(feq[i], k), gfun_f(xl[i]), sk);
+            }
+            ds[k] = neg ? INFINITY : sk;
+        }
+    }
+}
+
+// The collision: F = f* + (1 - 2 beta) phi (f - f*) (c27), phi per lane from
+// the site's Delta S; the threshold limiter keeps phi = 1 here and screens
+// candidates, its rewrite follows the step; the threshold and lagged-ensemble
+// limiters add each finite Delta S to acc (cnt counts them).
+template <class V, int COLL>
+__device__ __forceinline__ void collide_lim(const Params& p, int x, int y, const V* f, V* F, float& acc, int& cnt) {
+    using L = Lat<9>;
+    constexpr int NL = VLanes<V>::n;
+    V rho, ux, uy, feq[9];
+    lim_state<V>(p.eq, f, rho, ux, uy, feq);
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < NL; ++k)
+        bad |= !(vlane(rho, k) > 0.f) || !(fabsf(vlane(ux, k)) < 1e30f) || !(fabsf(vlane(uy, k)) < 1e30f);
+    if (bad)
+        if (*(volatile unsigned*)&p.counters[CNT_DIVERGED] == 0u) atomicExch(&p.counters[CNT_DIVERGED], 1u);
+    float ds[NL], q[NL], c[NL];
+    delta_s_v<V>(f, feq, ds, q);
+    const float om1 = 1.f - 2.f * p.beta_f;
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+        const float dk = ds[k];
+        float phi = 1.f;
+        if ((COLL == LBM_ENSEMBLE_LAGGED || COLL == LBM_THRESHOLD) && isfinite(dk)) {
+            acc += dk;
+            ++cnt;
+        }
+        if (COLL == LBM_THRESHOLD) {
+            if (median_maybe_above(dk, q[k], vlane(rho, k), p.delta_f)) {
+                float fl[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) fl[i] = vlane(f[i], k);
+                record_candidate<9, float>(p, x + k, y, fl);
+            }
+        } else if (!(dk < INFINITY)) {
+            phi = 0.f;  // a negative population: the state goes to f*
+        } else {
+            const float alpha = p.lim_f[0], kk = p.lim_f[1];
+            if (COLL == LBM_SMOOTH) {
+                phi = 1.f / (1.f + alpha * pow_lim(dk, kk));
+            } else if (COLL == LBM_DOUBLE_MONOTONIC) {
+                phi = pow_lim(1.f + pow_lim(dk * p.lim_f[2], kk), p.lim_f[3]);
+            } else {  // LBM_ENSEMBLE, LBM_ENSEMBLE_LAGGED
+                const float E = *p.lim_E_f;
+                if (E > 0.f) {
+                    const float yv = dk / (alpha * E);
+                    phi = (1.f + pow_lim(yv, kk - 0.5f)) / (1.f + pow_lim(yv, kk));
+                }
+            }
+        }
+        c[k] = om1 * phi;
+    }
+    const V cv = vmake<V>(c[0], c[NL - 1]);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) F[i] = vfma(cv, vsub(f[i], feq[i]), feq[i]);
+    // every collision conserves mass: the rest population as rho minus the others
+    V sF = F[1];
+#pragma unroll
+    for (int i = 2; i < 9; ++i) sF = vadd(sF, F[i]);
+    F[0] = vsub(rho, sF);
+}
+
 // Section 8's diffusive Maxwell rule at wall site (x, y) (bc DIFFUSIVE), on
 // its pre-collision populations: at a site of one wall (outward normal n)
 // the populations with v . n < 0 become gamma f*_i(u_wall), f* at unit
@@ -443,6 +673,14 @@ constexpr bool kDeviationForm = Q == 9 && sizeof(typename ST::S) == 2 &&
                                 (COLL == LBM_LBGK || COLL == LBM_EHRENFEST || COLL == LBM_POSITIVITY ||
                                  COLL == LBM_MRT || COLL == LBM_MRT2 || COLL == LBM_MRT_LIMITER);
 
+// The D2Q9 Section 4.2-4.4 limiters in FP32 arithmetic (FP32 and 16-bit
+// storage) that run collide_lim, at every site so that every kernel computes
+// a site alike.
+template <int Q, class ST, int COLL>
+constexpr bool kLimForm = Q == 9 && sizeof(typename ST::T) == 4 &&
+                          (COLL == LBM_SMOOTH || COLL == LBM_DOUBLE_MONOTONIC || COLL == LBM_ENSEMBLE ||
+                           COLL == LBM_THRESHOLD || COLL == LBM_ENSEMBLE_LAGGED);
+
 template <int Q, class ST, int COLL, bool ODD>
 __device__ __forceinline__ void site_update(const Params& p, int x, int y, int& e_code,
                                             int& e_iters, typename ST::T& acc) {
@@ -459,10 +697,17 @@ __device__ __forceinline__ void site_update(const Params& p, int x, int y, int& 
         if (Q == 9 && p.diffusive) return;
         load_general<Q, ST, ODD, DEV>(p, x, y, f);
     }
-    if constexpr (DEV)
+    if constexpr (DEV) {
         collide_dev<float, ST, COLL>(p, x, y, f, F);
-    else
+    } else if constexpr (kLimForm<Q, ST, COLL>) {
+        float a = 0.f;
+        int cnt = 0;
+        collide_lim<float, COLL>(p, x, y, f, F, a, cnt);
+        acc += a;
+        if (cnt) e_code = 1;
+    } else {
         collide_site<Q, ST, COLL>(p, x, y, f, F, e_code, e_iters, acc);
+    }
     if (interior)
         store_interior<Q, ST, ODD, DEV>(p, o, F);
     else
@@ -579,9 +824,7 @@ __global__ void __launch_bounds__(kBlockX* kBlockY, kMinBlocks<ST, COLL>) step_k
 constexpr int kVecX = 64;
 constexpr int kVecY = 4;
 template <class ST, int COLL>
-constexpr bool kPairedSites = sizeof(typename ST::S) == 2 &&
-                              (COLL == LBM_LBGK || COLL == LBM_EHRENFEST || COLL == LBM_POSITIVITY ||
-                               COLL == LBM_MRT || COLL == LBM_MRT2 || COLL == LBM_MRT_LIMITER);
+constexpr bool kPairedSites = kDeviationForm<9, ST, COLL>;
 constexpr int kPairedMinBlocks = 5;
 
 __device__ __forceinline__ uint32_t ld_word(const void* base, int off) {
@@ -1384,9 +1627,18 @@ __global__ void __launch_bounds__(256) ensemble_mean(Params p) {
             load_interior<Q, ST, ODD>(p, y * p.pitch + x, f);
         else
             load_general<Q, ST, ODD>(p, x, y, f);
-        moments<Q, T>(f, rho, ux, uy);
-        equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
-        const T ds = delta_s_and_q<Q, T>(f, feq, q);
+        T ds;
+        if constexpr (kLimForm<Q, ST, LBM_ENSEMBLE>) {
+            // the Delta S the step's collision computes (collide_lim)
+            float fq[Q], dsl[1], ql[1];
+            lim_state<float>(p.eq, f, rho, ux, uy, fq);
+            delta_s_v<float>(f, fq, dsl, ql);
+            ds = dsl[0];
+        } else {
+            moments<Q, T>(f, rho, ux, uy);
+            equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
+            ds = delta_s_and_q<Q, T>(f, feq, q);
+        }
         if (isfinite(ds)) {
             sum += ds;
             cnt += T(1);
