@@ -35,10 +35,10 @@ RUNS = {"ehrenfest_re10000": ("ehrenfest", dict(topk=64, delta=1e-3)),
 
 # bounds on (rel-L2 of rho - 1, rel-L2 of u, relative error of H_K) at the
 # sampled sites after 2000 steps.  Measured on a GB300 (fp64 / fp32 /
-# fp16_dev / bf16_dev): Ehrenfest Re 10000 rho 3.8e-10 / 0.086 / 0.12 / 0.31,
-# u 1.9e-12 / 0.014 / 0.031 / 0.13; median Re 10000 rho 7.0e-10 / 0.053 /
-# 0.080 / 0.27, u 1.6e-12 / 0.0037 / 0.024 / 0.12; LBGK Re 1000 rho 4.1e-10 /
-# 6.2e-4 / 6.5e-3 / 0.070, u 9.8e-13 / 7.0e-5 / 6.7e-4 / 0.015.  Under the
+# fp16_dev / bf16_dev): Ehrenfest Re 10000 rho 3.8e-10 / 0.086 / 0.092 / 0.27,
+# u 1.9e-12 / 0.014 / 0.040 / 0.14; median Re 10000 rho 7.0e-10 / 0.053 /
+# 0.077 / 0.26, u 1.6e-12 / 0.0037 / 0.023 / 0.12; LBGK Re 1000 rho 4.1e-10 /
+# 6.2e-4 / 6.8e-3 / 0.069, u 9.8e-13 / 7.0e-5 / 6.6e-4 / 0.014.  Under the
 # Ehrenfest step FP32 and FP16 sit below the level of fully decorrelated
 # selections (FP64 from a 1e-12 perturbation: rho 0.40, u 0.12, H_K 0.11), which caps
 # their bounds there; the smooth LBGK flow bounds every format tightly.
