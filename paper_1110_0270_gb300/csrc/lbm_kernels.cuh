@@ -395,12 +395,11 @@ __device__ __forceinline__ void collide_dev(const Params& p, int x, int y, const
 
 // ---------------------------------------------------------------------------
 // The Section 4.2-4.4 limiters on D2Q9 in FP32 arithmetic (FP32 and 16-bit
-// storage): moments, the equilibrium and Delta S as explicit correctly
-// rounded operations (nothing left to contraction) with one approximate
-// reciprocal per population, then phi per site.  The kernels run it on one
-// site per thread (V = float).  Written for either value type: on packed
-// pairs (V = F2, both lanes in the same series tier evaluated at once) the
-// step needs ~116 registers, two CTAs per SM, and measured slower.
+// storage), one site per thread: moments, the equilibrium and Delta S as
+// explicit correctly rounded operations (nothing left to contraction) with
+// one approximate reciprocal per population, then phi per site.  (On packed
+// pairs, two sites per thread, the step needs ~116 registers, two CTAs per
+// SM, and measured slower.)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float rcp_approx(float a) {
     float r;
@@ -409,218 +408,142 @@ __device__ __forceinline__ float rcp_approx(float a) {
 }
 
 // rho, u and f* (absolute) of D2Q9 populations f
-template <class V>
-__device__ __forceinline__ void lim_state(int kind, const V* f, V& rho, V& ux, V& uy, V* feq) {
+__device__ __forceinline__ void lim_state(int kind, const float* f, float& rho, float& ux, float& uy,
+                                          float* feq) {
     using L = Lat<9>;
-    constexpr int NL = VLanes<V>::n;
+    static_assert(L::cx(1) == 1 && L::cx(2) == 1 && L::cx(8) == 1 && L::cx(4) == -1 && L::cx(5) == -1 &&
+                      L::cx(6) == -1 && L::cy(6) == 1 && L::cy(7) == 1 && L::cy(8) == 1 && L::cy(2) == -1 &&
+                      L::cy(3) == -1 && L::cy(4) == -1,
+                  "D2Q9 numbering of Lat<9>");
     rho = f[0];
 #pragma unroll
-    for (int i = 1; i < 9; ++i) rho = vadd(rho, f[i]);
-    const V jx = vsub(vadd(vadd(f[1], f[2]), f[8]), vadd(vadd(f[4], f[5]), f[6]));
-    const V jy = vsub(vadd(vadd(f[6], f[7]), f[8]), vadd(vadd(f[2], f[3]), f[4]));
-    float inv[NL];
-#pragma unroll
-    for (int k = 0; k < NL; ++k) inv[k] = __fdiv_rn(1.f, vlane(rho, k));
-    const V vinv = vmake<V>(inv[0], inv[NL - 1]);
-    ux = vmul(jx, vinv);
-    uy = vmul(jy, vinv);
-    const V one = vsplat(1.f, rho);
+    for (int i = 1; i < 9; ++i) rho = __fadd_rn(rho, f[i]);
+    const float jx = __fsub_rn(__fadd_rn(__fadd_rn(f[1], f[2]), f[8]), __fadd_rn(__fadd_rn(f[4], f[5]), f[6]));
+    const float jy = __fsub_rn(__fadd_rn(__fadd_rn(f[6], f[7]), f[8]), __fadd_rn(__fadd_rn(f[2], f[3]), f[4]));
+    const float inv = __fdiv_rn(1.f, rho);
+    ux = __fmul_rn(jx, inv);
+    uy = __fmul_rn(jy, inv);
     if (kind == LBM_EQ_POLY_STD) {
-        const V nuu = vmul(vsplat(-1.5f, rho), vfma(ux, ux, vmul(uy, uy)));
-        V rest = rho;
+        const float nuu = __fmul_rn(-1.5f, __fmaf_rn(ux, ux, __fmul_rn(uy, uy)));
+        float rest = rho;
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
-            const V cu = vfma(vsplat(float(L::cx(i)), rho), ux, vmul(vsplat(float(L::cy(i)), rho), uy));
-            const V a = vfma(vmul(vsplat(4.5f, rho), cu), cu, vfma(vsplat(3.f, rho), cu, nuu));
-            feq[i] = vmul(vsplat(float(L::w(i)), rho), vfma(rho, a, rho));
-            rest = vsub(rest, feq[i]);
+            const float cu = __fmaf_rn(float(L::cx(i)), ux, __fmul_rn(float(L::cy(i)), uy));
+            const float a = __fmaf_rn(__fmul_rn(4.5f, cu), cu, __fmaf_rn(3.f, cu, nuu));
+            feq[i] = __fmul_rn(float(L::w(i)), __fmaf_rn(rho, a, rho));
+            rest = __fsub_rn(rest, feq[i]);
         }
         feq[0] = rest;
         return;
     }
-    V ax[3], ay[3];
-    const V uv[2] = {ux, uy};
+    // product of the 1D factors a_-, a_0, a_+ = a - u/2, 1 - 2a, a + u/2
+    float ax[3], ay[3];
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-        const V u = uv[c];
-        const V t = vfma(vmul(vsplat(3.f, rho), u), u, one);  // 1 + 3 u^2
-        V a;
-        if (kind == LBM_EQ_ENTROPIC) {
-            float sq[NL];
-#pragma unroll
-            for (int k = 0; k < NL; ++k) sq[k] = __fsqrt_rn(vlane(t, k));
-            a = vmul(vfma(vsplat(2.f, rho), vmake<V>(sq[0], sq[NL - 1]), vsplat(-1.f, rho)), vsplat(1.f / 6.f, rho));
-        } else {
-            a = vmul(t, vsplat(1.f / 6.f, rho));
-        }
-        const V h = vmul(vsplat(0.5f, rho), u);
-        V* f1 = c == 0 ? ax : ay;
-        f1[0] = vsub(a, h);
-        f1[1] = vfma(vsplat(-2.f, rho), a, one);
-        f1[2] = vadd(a, h);
+        const float u = c == 0 ? ux : uy;
+        const float t = __fmaf_rn(__fmul_rn(3.f, u), u, 1.f);  // 1 + 3 u^2
+        const float a = kind == LBM_EQ_ENTROPIC ? __fmul_rn(__fmaf_rn(2.f, __fsqrt_rn(t), -1.f), 1.f / 6.f)
+                                                : __fmul_rn(t, 1.f / 6.f);
+        const float h = __fmul_rn(0.5f, u);
+        float* f1 = c == 0 ? ax : ay;
+        f1[0] = __fsub_rn(a, h);
+        f1[1] = __fmaf_rn(-2.f, a, 1.f);
+        f1[2] = __fadd_rn(a, h);
     }
 #pragma unroll
-    for (int k = 0; k < 3; ++k) ax[k] = vmul(ax[k], rho);
+    for (int k = 0; k < 3; ++k) ax[k] = __fmul_rn(ax[k], rho);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) feq[i] = vmul(ax[L::cx(i) + 1], ay[L::cy(i) + 1]);
+    for (int i = 0; i < 9; ++i) feq[i] = __fmul_rn(ax[L::cx(i) + 1], ay[L::cy(i) + 1]);
 }
 
 // sum_i dx_i P_K(x_i), P_K the series of g(x) / x^2 (gpoly_f's coefficients)
-template <int K, class V>
-__device__ __forceinline__ V lim_series(const V* dx, const V* x) {
-    V s;
+template <int K>
+__device__ __forceinline__ float lim_series(const float* dx, const float* x) {
+    float s = 0.f;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        V pk = vsplat(((K & 1) ? -1.0f : 1.0f) / (float)((K + 1) * (K + 2)), x[i]);
+        float pk = ((K & 1) ? -1.0f : 1.0f) / (float)((K + 1) * (K + 2));
 #pragma unroll
-        for (int k = K - 1; k >= 0; --k)
-            pk = vfma(pk, x[i], vsplat(((k & 1) ? -1.0f : 1.0f) / (float)((k + 1) * (k + 2)), x[i]));
-        s = i == 0 ? vmul(dx[0], pk) : vfma(dx[i], pk, s);
+        for (int k = K - 1; k >= 0; --k) pk = __fmaf_rn(pk, x[i], ((k & 1) ? -1.0f : 1.0f) / (float)((k + 1) * (k + 2)));
+        s = i == 0 ? __fmul_rn(dx[0], pk) : __fmaf_rn(dx[i], pk, s);
     }
     return s;
 }
 
-// Tier of the series by max |x| (the tiers of delta_s_and_q<9, float>):
-// -1 a non-positive f*, 0/1/2 series of length 1/4/11, 3 the closed form.
-__device__ __forceinline__ int lim_tier(float amax, float emin) {
-    return !(emin > 0.f) ? -1 : amax < 0x1p-12f ? 0 : amax < 0.03125f ? 1 : amax < 0.25f ? 2 : 3;
-}
-
-template <class V>
-__device__ __forceinline__ float lim_tier_sum(int tier, const V* dx, const V* x, int lane) {
-    return vlane(tier == 0 ? lim_series<1, V>(dx, x) : tier == 1 ? lim_series<4, V>(dx, x) : lim_series<11, V>(dx, x),
-                 lane);
-}
-
-// Delta S (Eq. DelS, the FP32 screen evaluation) and q = sum (f - f*)^2 / f*
-// per lane.  Both lanes in the same series tier: one packed evaluation;
-// otherwise each lane on its own, with the same operations.
-template <class V>
-__device__ __forceinline__ void delta_s_v(const V* f, const V* feq, float* ds, float* q) {
-    constexpr int NL = VLanes<V>::n;
-    V d[9], x[9], dx[9];
-    float amax[NL], emin[NL];
-#pragma unroll
-    for (int k = 0; k < NL; ++k) {
-        amax[k] = 0.f;
-        emin[k] = vlane(feq[0], k);
-    }
+// Delta S (Eq. DelS, the FP32 screen evaluation) and q = sum (f - f*)^2 / f*:
+// one series length per site, chosen by max |x| (the tiers of
+// delta_s_and_q<9, float>), the closed form g(x) = (1 + x) ln(1 + x) - x
+// beyond 1/4; +inf with a non-positive f* or population.
+__device__ __forceinline__ float delta_s_lim(const float* f, const float* feq, float& q) {
+    float x[9], dx[9], amax = 0.f, emin = feq[0];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        d[i] = vsub(f[i], feq[i]);
-        float r[NL];
-#pragma unroll
-        for (int k = 0; k < NL; ++k) r[k] = rcp_approx(vlane(feq[i], k));
-        x[i] = vmul(d[i], vmake<V>(r[0], r[NL - 1]));
-        dx[i] = vmul(d[i], x[i]);
-#pragma unroll
-        for (int k = 0; k < NL; ++k) {
-            amax[k] = fmaxf(amax[k], fabsf(vlane(x[i], k)));
-            emin[k] = fminf(emin[k], vlane(feq[i], k));
-        }
+        const float d = __fsub_rn(f[i], feq[i]);
+        x[i] = __fmul_rn(d, rcp_approx(feq[i]));
+        dx[i] = __fmul_rn(d, x[i]);
+        amax = fmaxf(amax, fabsf(x[i]));
+        emin = fminf(emin, feq[i]);
     }
-    V qv = dx[0];
+    q = dx[0];
 #pragma unroll
-    for (int i = 1; i < 9; ++i) qv = vadd(qv, dx[i]);
-    int tier[NL];
+    for (int i = 1; i < 9; ++i) q = __fadd_rn(q, dx[i]);
+    if (!(emin > 0.f)) return INFINITY;
+    if (amax < 0x1p-12f) return lim_series<1>(dx, x);
+    if (amax < 0.03125f) return lim_series<4>(dx, x);
+    if (amax < 0.25f) return lim_series<11>(dx, x);
+    float s = 0.f;
+    bool neg = false;
 #pragma unroll
-    for (int k = 0; k < NL; ++k) {
-        q[k] = vlane(qv, k);
-        tier[k] = lim_tier(amax[k], emin[k]);
+    for (int i = 0; i < 9; ++i) {
+        neg |= f[i] < 0.f;
+        s = fmaf(feq[i], gfun_f(x[i]), s);
     }
-    if (NL == 2 && tier[0] == tier[NL - 1] && tier[0] >= 0 && tier[0] <= 2) {
-        const V sv = tier[0] == 0 ? lim_series<1, V>(dx, x) : tier[0] == 1 ? lim_series<4, V>(dx, x)
-                                                                            : lim_series<11, V>(dx, x);
-#pragma unroll
-        for (int k = 0; k < NL; ++k) ds[k] = vlane(sv, k);
-        return;
-    }
-#pragma unroll
-    for (int k = 0; k < NL; ++k) {
-        float dxl[9], xl[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            dxl[i] = vlane(dx[i], k);
-            xl[i] = vlane(x[i], k);
-        }
-        if (tier[k] < 0) {
-            ds[k] = INFINITY;
-        } else if (tier[k] <= 2) {
-            ds[k] = lim_tier_sum<float>(tier[k], dxl, xl, 0);
-        } else {
-            // the closed form g(x) = (1 + x) ln(1 + x) - x; a negative population: +inf
-            float sk = 0.f;
-            bool neg = false;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                neg |= vlane(f[i], k) < 0.f;
-                sk = fmaf(vlane(feq[i], k), gfun_f(xl[i]), sk);
-            }
-            ds[k] = neg ? INFINITY : sk;
-        }
-    }
+    return neg ? INFINITY : s;
 }
 
-// The collision: F = f* + (1 - 2 beta) phi (f - f*) (c27), phi per lane from
-// the site's Delta S; the threshold limiter keeps phi = 1 here and screens
+// The collision: F = f* + (1 - 2 beta) phi (f - f*) (c27), phi from the
+// site's Delta S; the threshold limiter keeps phi = 1 here and screens
 // candidates, its rewrite follows the step; the threshold and lagged-ensemble
-// limiters add each finite Delta S to acc (cnt counts them).
-template <class V, int COLL>
-__device__ __forceinline__ void collide_lim(const Params& p, int x, int y, const V* f, V* F, float& acc, int& cnt) {
-    using L = Lat<9>;
-    constexpr int NL = VLanes<V>::n;
-    V rho, ux, uy, feq[9];
-    lim_state<V>(p.eq, f, rho, ux, uy, feq);
-    bool bad = false;
-#pragma unroll
-    for (int k = 0; k < NL; ++k)
-        bad |= !(vlane(rho, k) > 0.f) || !(fabsf(vlane(ux, k)) < 1e30f) || !(fabsf(vlane(uy, k)) < 1e30f);
-    if (bad)
+// limiters add a finite Delta S to acc (cnt counts it).
+template <int COLL>
+__device__ __forceinline__ void collide_lim(const Params& p, int x, int y, const float* f, float* F, float& acc,
+                                            int& cnt) {
+    float rho, ux, uy, feq[9], q;
+    lim_state(p.eq, f, rho, ux, uy, feq);
+    if (!(rho > 0.f) || !(fabsf(ux) < 1e30f) || !(fabsf(uy) < 1e30f))
         if (*(volatile unsigned*)&p.counters[CNT_DIVERGED] == 0u) atomicExch(&p.counters[CNT_DIVERGED], 1u);
-    float ds[NL], q[NL], c[NL];
-    delta_s_v<V>(f, feq, ds, q);
-    const float om1 = 1.f - 2.f * p.beta_f;
-#pragma unroll
-    for (int k = 0; k < NL; ++k) {
-        const float dk = ds[k];
-        float phi = 1.f;
-        if ((COLL == LBM_ENSEMBLE_LAGGED || COLL == LBM_THRESHOLD) && isfinite(dk)) {
-            acc += dk;
-            ++cnt;
-        }
-        if (COLL == LBM_THRESHOLD) {
-            if (median_maybe_above(dk, q[k], vlane(rho, k), p.delta_f)) {
-                float fl[9];
-#pragma unroll
-                for (int i = 0; i < 9; ++i) fl[i] = vlane(f[i], k);
-                record_candidate<9, float>(p, x + k, y, fl);
-            }
-        } else if (!(dk < INFINITY)) {
-            phi = 0.f;  // a negative population: the state goes to f*
-        } else {
-            const float alpha = p.lim_f[0], kk = p.lim_f[1];
-            if (COLL == LBM_SMOOTH) {
-                phi = 1.f / (1.f + alpha * pow_lim(dk, kk));
-            } else if (COLL == LBM_DOUBLE_MONOTONIC) {
-                phi = pow_lim(1.f + pow_lim(dk * p.lim_f[2], kk), p.lim_f[3]);
-            } else {  // LBM_ENSEMBLE, LBM_ENSEMBLE_LAGGED
-                const float E = *p.lim_E_f;
-                if (E > 0.f) {
-                    const float yv = dk / (alpha * E);
-                    phi = (1.f + pow_lim(yv, kk - 0.5f)) / (1.f + pow_lim(yv, kk));
-                }
-            }
-        }
-        c[k] = om1 * phi;
+    const float ds = delta_s_lim(f, feq, q);
+    float phi = 1.f;
+    if ((COLL == LBM_ENSEMBLE_LAGGED || COLL == LBM_THRESHOLD) && isfinite(ds)) {
+        acc += ds;
+        ++cnt;
     }
-    const V cv = vmake<V>(c[0], c[NL - 1]);
+    if (COLL == LBM_THRESHOLD) {
+        if (median_maybe_above(ds, q, rho, p.delta_f)) record_candidate<9, float>(p, x, y, f);
+    } else if (!(ds < INFINITY)) {
+        phi = 0.f;  // a negative population: the state goes to f*
+    } else {
+        const float alpha = p.lim_f[0], k = p.lim_f[1];
+        if (COLL == LBM_SMOOTH) {
+            phi = 1.f / (1.f + alpha * pow_lim(ds, k));
+        } else if (COLL == LBM_DOUBLE_MONOTONIC) {
+            phi = pow_lim(1.f + pow_lim(ds * p.lim_f[2], k), p.lim_f[3]);
+        } else {  // LBM_ENSEMBLE, LBM_ENSEMBLE_LAGGED
+            const float E = *p.lim_E_f;
+            if (E > 0.f) {
+                const float yv = ds / (alpha * E);
+                phi = (1.f + pow_lim(yv, k - 0.5f)) / (1.f + pow_lim(yv, k));
+            }
+        }
+    }
+    const float c = (1.f - 2.f * p.beta_f) * phi;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) F[i] = vfma(cv, vsub(f[i], feq[i]), feq[i]);
+    for (int i = 0; i < 9; ++i) F[i] = __fmaf_rn(c, __fsub_rn(f[i], feq[i]), feq[i]);
     // every collision conserves mass: the rest population as rho minus the others
-    V sF = F[1];
+    float sF = F[1];
 #pragma unroll
-    for (int i = 2; i < 9; ++i) sF = vadd(sF, F[i]);
-    F[0] = vsub(rho, sF);
+    for (int i = 2; i < 9; ++i) sF = __fadd_rn(sF, F[i]);
+    F[0] = __fsub_rn(rho, sF);
 }
 
 // Section 8's diffusive Maxwell rule at wall site (x, y) (bc DIFFUSIVE), on
@@ -702,7 +625,7 @@ __device__ __forceinline__ void site_update(const Params& p, int x, int y, int& 
     } else if constexpr (kLimForm<Q, ST, COLL>) {
         float a = 0.f;
         int cnt = 0;
-        collide_lim<float, COLL>(p, x, y, f, F, a, cnt);
+        collide_lim<COLL>(p, x, y, f, F, a, cnt);
         acc += a;
         if (cnt) e_code = 1;
     } else {
@@ -1630,10 +1553,8 @@ __global__ void __launch_bounds__(256) ensemble_mean(Params p) {
         T ds;
         if constexpr (kLimForm<Q, ST, LBM_ENSEMBLE>) {
             // the Delta S the step's collision computes (collide_lim)
-            float fq[Q], dsl[1], ql[1];
-            lim_state<float>(p.eq, f, rho, ux, uy, fq);
-            delta_s_v<float>(f, fq, dsl, ql);
-            ds = dsl[0];
+            lim_state(p.eq, f, rho, ux, uy, feq);
+            ds = delta_s_lim(f, feq, q);
         } else {
             moments<Q, T>(f, rho, ux, uy);
             equilibrium<Q, T>(p.eq, rho, ux, uy, feq);
