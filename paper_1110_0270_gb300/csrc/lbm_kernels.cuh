@@ -523,16 +523,17 @@ __device__ __forceinline__ void collide_lim(const Params& p, int x, int y, const
     } else if (!(ds < INFINITY)) {
         phi = 0.f;  // a negative population: the state goes to f*
     } else {
+        // approximate divisions (2 ulp): phi only scales the non-equilibrium part
         const float alpha = p.lim_f[0], k = p.lim_f[1];
         if (COLL == LBM_SMOOTH) {
-            phi = 1.f / (1.f + alpha * pow_lim(ds, k));
+            phi = __fdividef(1.f, 1.f + alpha * pow_lim(ds, k));
         } else if (COLL == LBM_DOUBLE_MONOTONIC) {
             phi = pow_lim(1.f + pow_lim(ds * p.lim_f[2], k), p.lim_f[3]);
         } else {  // LBM_ENSEMBLE, LBM_ENSEMBLE_LAGGED
             const float E = *p.lim_E_f;
             if (E > 0.f) {
-                const float yv = ds / (alpha * E);
-                phi = (1.f + pow_lim(yv, k - 0.5f)) / (1.f + pow_lim(yv, k));
+                const float yv = __fdividef(ds, alpha * E);
+                phi = __fdividef(1.f + pow_lim(yv, k - 0.5f), 1.f + pow_lim(yv, k));
             }
         }
     }
