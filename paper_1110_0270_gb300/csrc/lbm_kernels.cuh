@@ -708,6 +708,45 @@ constexpr int kMinBlocks =
                     ? 6
                     : 0;
 
+// L2 prefetch of the rows (and the row on either side, for the odd step's
+// shifted reads) of the tile that the CTA one resident wave later processes
+// (tiles of tw sites x blockDim.y rows in a 2D grid, ctas_per_sm resident
+// CTAs per SM): one bulk prefetch per plane row by the CTA's first threads,
+// so that the DRAM reads of that tile are under way before it starts.  Only
+// on padded layouts (pitch and planes multiples of 32 elements, a 256-byte
+// aligned base): every segment then starts on a tile boundary, 16-byte
+// aligned, and ends within the padded row with a multiple of 16 bytes; a
+// caller's dense array may be neither.
+template <int Q, class ST>
+__device__ __forceinline__ void prefetch_ahead(const Params& p, int tw, int ctas_per_sm) {
+    constexpr int b = (int)sizeof(typename ST::S);
+    const bool padded = (p.pitch & 31) == 0 && (p.plane32 & 31) == 0 && ((uintptr_t)p.f & 255u) == 0;
+    const int ahead = p.pipe_ctas / 8 * ctas_per_sm;  // SMs x resident CTAs
+    const int L = blockIdx.y * gridDim.x + blockIdx.x + ahead;
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nrow = blockDim.y + 2;
+    if (!padded || L >= (int)(gridDim.x * gridDim.y) || t >= Q * nrow) return;
+    const int bx = L % gridDim.x, by = L / gridDim.x;
+    const int tx0 = bx * tw, pl = t / nrow, yy = by * blockDim.y - 1 + (t - pl * nrow);
+    const int room = p.pitch - tx0;  // a multiple of 32 elements
+    const int n = room < tw ? room : tw;
+    if (yy < 0 || yy >= p.ny || n <= 0) return;
+    const char* a = reinterpret_cast<const char*>(p.f) + ((int64_t)pl * p.plane32 + (int64_t)yy * p.pitch + tx0) * b;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)(n * b)) : "memory");
+}
+
+// The one-site kernel prefetches the next wave's tiles (prefetch_ahead) in
+// FP32 storage for the collisions it speeds up (measured, 4097^2: LBGK
+// 0.963 -> 1.02 of the measured copy bandwidth, Ehrenfest 0.948 -> 0.975,
+// median 0.930 -> 0.956, positivity, MRT and A_2 to 1.00-1.02, MRT limiter
+// 0.954 -> 0.982, smooth limiter 0.857 -> 0.907); the lagged-ensemble and
+// threshold steps, which end in a CTA-wide reduction, ran 9-11% slower with it.
+template <int Q, class ST, int COLL>
+constexpr bool kSitePrefetch = Q == 9 && sizeof(typename ST::S) == 4 &&
+                               (COLL == LBM_LBGK || COLL == LBM_EHRENFEST || COLL == LBM_MEDIAN ||
+                                COLL == LBM_POSITIVITY || COLL == LBM_MRT || COLL == LBM_MRT2 ||
+                                COLL == LBM_MRT_LIMITER || COLL == LBM_SMOOTH);
+
 template <int Q, class ST, int COLL, bool ODD>
 __global__ void __launch_bounds__(kBlockX* kBlockY, kMinBlocks<ST, COLL>) step_kernel(Params p) {
     pdl_enter();
@@ -719,6 +758,7 @@ __global__ void __launch_bounds__(kBlockX* kBlockY, kMinBlocks<ST, COLL>) step_k
         p.counters[p.cslot ^ 1] = 0u;  // the next step's list starts empty
         p.counters[CNT_NVALID] = 0u;   // counted by this step's eval / median kernel
     }
+    if (kSitePrefetch<Q, ST, COLL>) prefetch_ahead<Q, ST>(p, kBlockX, 8);
     int e_code = -1, e_iters = 0;
     typename ST::T acc = 0;
     if (x < p.nx && y < p.ny) site_update<Q, ST, COLL, ODD>(p, x, y, e_code, e_iters, acc);
@@ -777,34 +817,7 @@ __global__ void __launch_bounds__(kVecX* kVecY, kPairedMinBlocks) step_kernel_v2
         p.counters[p.cslot ^ 1] = 0u;
         p.counters[CNT_NVALID] = 0u;
     }
-    if (kPairPrefetch<COLL>) {
-        // L2 prefetch of the rows (and the row on either side, for the odd
-        // step's shifted reads) of the tile that the CTA one resident wave
-        // later processes: one bulk prefetch per plane row by the first
-        // threads, so that the DRAM reads of that tile are under way before
-        // it starts.  Segments start on a 128-site boundary (256 bytes) and
-        // end within the padded row (the pitch is a multiple of 32).
-        const int ahead = p.pipe_ctas / 8 * kPairedMinBlocks;  // SMs x resident CTAs
-        const int L = blockIdx.y * gridDim.x + blockIdx.x + ahead;
-        const int t = threadIdx.y * blockDim.x + threadIdx.x;
-        const int nrow = blockDim.y + 2;
-        // only on padded layouts (pitch and planes multiples of 32 elements, a
-        // 256-byte aligned base), where every segment is 16-byte aligned and
-        // a multiple of 16 bytes; a caller's dense array may be neither
-        const bool padded = (p.pitch & 31) == 0 && (p.plane32 & 31) == 0 && ((uintptr_t)p.f & 255u) == 0;
-        if (padded && L < (int)(gridDim.x * gridDim.y) && t < Q * nrow) {
-            const int bx = L % gridDim.x, by = L / gridDim.x;
-            const int tx0 = 2 * bx * blockDim.x, pl = t / nrow, yy = by * blockDim.y - 1 + (t - pl * nrow);
-            const int room = p.pitch - tx0;  // a multiple of 32 elements
-            const int n = room < 2 * (int)blockDim.x ? room : 2 * (int)blockDim.x;
-            if (yy >= 0 && yy < p.ny && n > 0) {
-                const char* a = reinterpret_cast<const char*>(p.f) +
-                                ((int64_t)pl * p.plane32 + (int64_t)yy * p.pitch + tx0) * (int64_t)sizeof(typename ST::S);
-                const unsigned bytes = (unsigned)(n * (int)sizeof(typename ST::S));
-                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(bytes) : "memory");
-            }
-        }
-    }
+    if (kPairPrefetch<COLL>) prefetch_ahead<Q, ST>(p, 2 * kVecX, kPairedMinBlocks);
     int e_code = -1, e_iters = 0;
     const unsigned full = 0xffffffffu;
     const bool inner = y > 0 && y < p.ny - 1 && x0 > 0 && x0 + 2 < p.nx;
