@@ -280,6 +280,37 @@ __device__ __forceinline__ void equilibrium_dev9(int kind, V drho, V rho, V ux, 
     }
 }
 
+// MRT of Section 5 (mrt_d2q9: M1's orthogonal rows, rest, E, SE, S, SW, W,
+// NW, N, NE numbering) in deviation form on e = f - f*: the non-conserved
+// moments of e scaled by C1 N^-1 (rates), then D = d - M1^T m.  Explicit
+// operations for one site or a pair (the same bits either way).
+template <class V>
+__device__ __forceinline__ void mrt_dev(const V* d, const V* e, const MrtRatesF& r, V* D) {
+    const V se = vadd(vadd(e[2], e[4]), vadd(e[6], e[8]));  // diagonals
+    const V ax = vadd(vadd(e[1], e[3]), vadd(e[5], e[7]));  // axis
+    const V two = vsplat(2.f, se), four = vsplat(4.f, se), mtwo = vsplat(-2.f, se);
+    // e_m = -4 e0 - ax + 2 se, eps_m = 4 e0 - 2 ax + se
+    const V em = vmul(vsub(vfma(two, se, vmul(vsplat(-4.f, se), e[0])), ax), vsplat(r.e, se));
+    const V ep = vmul(vadd(vfma(mtwo, ax, vmul(four, e[0])), se), vsplat(r.eps, se));
+    // q_x = -2 e1 + e2 - e4 + 2 e5 - e6 + e8, q_y = -e2 + 2 e3 - e4 + e6 - 2 e7 + e8
+    const V qx = vmul(vfma(two, vsub(e[5], e[1]), vadd(vsub(e[2], e[4]), vsub(e[8], e[6]))), vsplat(r.q, se));
+    const V qy = vmul(vfma(two, vsub(e[3], e[7]), vadd(vsub(e[6], e[2]), vsub(e[8], e[4]))), vsplat(r.q, se));
+    // p_xx = e1 - e3 + e5 - e7, p_xy = -e2 + e4 - e6 + e8
+    const V pxx = vmul(vsub(vadd(e[1], e[5]), vadd(e[3], e[7])), vsplat(r.nu, se));
+    const V pxy = vmul(vsub(vadd(e[4], e[8]), vadd(e[2], e[6])), vsplat(r.nu, se));
+    const V a = vfma(mtwo, ep, vsub(vsplat(0.f, se), em));  // -e - 2 eps (axis rows)
+    const V b = vfma(two, em, ep);                           // 2 e + eps (diagonal rows)
+    D[0] = vsub(d[0], vmul(four, vsub(ep, em)));
+    D[1] = vsub(d[1], vadd(vfma(mtwo, qx, a), pxx));
+    D[2] = vsub(d[2], vsub(vadd(b, vsub(qx, qy)), pxy));
+    D[3] = vsub(d[3], vsub(vfma(two, qy, a), pxx));
+    D[4] = vsub(d[4], vadd(vsub(b, vadd(qx, qy)), pxy));
+    D[5] = vsub(d[5], vadd(vfma(two, qx, a), pxx));
+    D[6] = vsub(d[6], vsub(vadd(b, vsub(qy, qx)), pxy));
+    D[7] = vsub(d[7], vsub(vfma(mtwo, qy, a), pxx));
+    D[8] = vsub(d[8], vadd(vadd(b, vadd(qx, qy)), pxy));
+}
+
 template <class V, class ST, int COLL>
 __device__ __forceinline__ void collide_dev(const Params& p, int x, int y, const V* d, V* D) {
     using L = Lat<9>;
@@ -335,18 +366,7 @@ __device__ __forceinline__ void collide_dev(const Params& p, int x, int y, const
     }
     const float om = 2.f * p.beta_f;
     if (COLL == LBM_MRT) {
-#pragma unroll
-        for (int k = 0; k < NL; ++k) {
-            float dl[9], sl[9], Dl[9];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                dl[i] = vlane(d[i], k);
-                sl[i] = vlane(ds[i], k);
-            }
-            mrt_d2q9<float>(dl, sl, p.mrt, p.mrt_f, Dl);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) D[i] = k == 0 ? vmake<V>(Dl[i], Dl[i]) : vmake<V>(vlane(D[i], 0), Dl[i]);
-        }
+        mrt_dev<V>(d, e, p.mrt_f, D);
     } else if (COLL == LBM_MRT2) {
         // A_2: D = d* + (1 - s_nu)/4 (m4 r4 + m5 r5), m = r . (f - f*)
         const V c = vsplat((1.f - om) * 0.25f, rho);
