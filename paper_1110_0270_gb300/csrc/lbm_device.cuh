@@ -735,12 +735,13 @@ struct ElbmOut {
 // error, inside the factor 1 + 1e-5.  A site this clears takes the LBGK step
 // that the FP64 test would also give it; every other site goes to that test.
 template <int Q>
-__device__ __forceinline__ bool elbm_skip_certain(const double* f, const double* feq, double thr) {
+__device__ __forceinline__ bool elbm_skip_certain(const double* f, const double* feq, const double* Dd,
+                                                  double thr) {
     float q = 0.f, amax = 0.f;
     bool pos = true;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const float D = (float)(feq[i] - f[i]);
+        const float D = (float)Dd[i];
         const float e = (float)feq[i];
         pos &= f[i] > 0.0 && e > 0.f;
         const float x = __fdividef(D, e);
@@ -750,7 +751,8 @@ __device__ __forceinline__ bool elbm_skip_certain(const double* f, const double*
     return pos && amax <= 0.5f && 0.5f * q * (1.f + amax) * 1.00001f < (float)thr;
 }
 
-// Root finder of Section 3.3: start at the LBGK value alpha = 2, step to the
+// Root finder of Section 3.3 (Dd = f* - f, formed by the caller): start at
+// the LBGK value alpha = 2, step to the
 // greater root of the local second-order Taylor parabola, stop when
 // |S_f / S_f'| ||f* - f|| < eps (Eqs. Stopping, ConvergenceTwo), and take the
 // double Newton step back if the estimate ended above the root.  The first
@@ -763,10 +765,10 @@ __device__ __forceinline__ bool elbm_skip_certain(const double* f, const double*
 // of a non-trivial root is decided by the sign of S_f(alpha_max); without a
 // root the configured rule of Section 3.2 applies.
 template <int Q>
-__device__ ElbmOut elbm_alpha(const double* f, const double* feq, double rho, const Params& p) {
+__device__ ElbmOut elbm_alpha(const double* f, const double* feq, const double* Dd, double rho, const Params& p) {
     ElbmOut o;
     o.iters = 0;
-    if (elbm_skip_certain<Q>(f, feq, 1e-15 + p.elbm_skip_rel * rho)) {
+    if (elbm_skip_certain<Q>(f, feq, Dd, 1e-15 + p.elbm_skip_rel * rho)) {
         o.alpha = 2.0;
         o.code = 1;
         return o;
@@ -777,7 +779,7 @@ __device__ ElbmOut elbm_alpha(const double* f, const double* feq, double rho, co
     bool neg = false;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        D[i] = feq[i] - f[i];
+        D[i] = Dd[i];
         const double d = D[i] / feq[i];
         R[i] = d;
         dmax = fmax(dmax, fabs(d));

@@ -133,17 +133,27 @@ __device__ __forceinline__ void collide_site(const Params& p, int x, int y, cons
     if (!(rho > T(0)) || !(fabs(ux) < T(1e30)) || !(fabs(uy) < T(1e30)))
         if (*(volatile unsigned*)&p.counters[CNT_DIVERGED] == 0u) atomicExch(&p.counters[CNT_DIVERGED], 1u);
     if (COLL == LBM_ELBM) {
-        double fd[Q], fe[Q], r, a, b;
+        double fd[Q], fe[Q], Dd[Q], r, a, b;
 #pragma unroll
         for (int i = 0; i < Q; ++i) fd[i] = (double)f[i];
         moments<Q, double>(fd, r, a, b);
         equilibrium<Q, double>(LBM_EQ_ENTROPIC, r, a, b, fe);
-        ElbmOut out = elbm_alpha<Q>(fd, fe, r, p);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Dd[i] = fe[i] - fd[i];
+        ElbmOut out = elbm_alpha<Q>(fd, fe, Dd, r, p);
         e_code = out.code;
         e_iters = out.iters;
         const double ab = out.alpha * p.beta;
+        if constexpr (sizeof(T) == 8) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) F[i] = (T)(fd[i] + ab * (fe[i] - fd[i]));
+            for (int i = 0; i < Q; ++i) F[i] = fd[i] + ab * Dd[i];
+        } else {
+            // F = f + alpha beta (f* - f) rounds to FP32 (or 16 bits) anyway:
+            // the product in FP32 on the FP64 difference, no FP64 update
+            const float abf = (float)ab;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) F[i] = fmaf(abf, (float)Dd[i], f[i]);
+        }
     } else if ((COLL >= LBM_SMOOTH && COLL <= LBM_THRESHOLD) || COLL == LBM_ENSEMBLE_LAGGED) {
         // Sections 4.2-4.4: f -> f* + phi(Delta S) (f - f*), then LBGK, i.e.
         // F = f* + (1 - 2 beta) phi (f - f*); the threshold limiter's phi is
