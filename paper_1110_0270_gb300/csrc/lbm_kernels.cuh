@@ -244,12 +244,13 @@ __device__ __forceinline__ void equilibrium_dev9(int kind, V drho, V rho, V ux, 
         }
         ds[0] = rest;
         if (MIN) {
+            // min f*, 0 when not positive
 #pragma unroll
             for (int k = 0; k < NL; ++k) {
                 float mk = float(L::w(0)) + vlane(rest, k);
 #pragma unroll
                 for (int i = 1; i < 9; ++i) mk = fminf(mk, float(L::w(i)) + vlane(ds[i], k));
-                m[k] = mk;
+                m[k] = fmaxf(mk, 0.f);
             }
         }
         return;
@@ -278,16 +279,21 @@ __device__ __forceinline__ void equilibrium_dev9(int kind, V drho, V rho, V ux, 
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) ax[k] = vmul(ax[k], rho);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) ds[i] = vfma(ax[L::cx(i) + 1], ay[L::cy(i) + 1], vsplat(-float(L::w(i)), rho));
     if (MIN) {
+        // min f* = (min of the rho-scaled x factors) (min of the y factors),
+        // 0 when either is not positive
+        float mx[NL], my[NL];
 #pragma unroll
         for (int k = 0; k < NL; ++k) {
-            const float mx = fminf(fminf(vlane(ax[0], k), vlane(ax[1], k)), vlane(ax[2], k));
-            const float my = fminf(fminf(vlane(ay[0], k), vlane(ay[1], k)), vlane(ay[2], k));
-            m[k] = (mx > 0.f && my > 0.f) ? mx * my : 0.f;
+            mx[k] = fmaxf(fminf(fminf(vlane(ax[0], k), vlane(ax[1], k)), vlane(ax[2], k)), 0.f);
+            my[k] = fmaxf(fminf(fminf(vlane(ay[0], k), vlane(ay[1], k)), vlane(ay[2], k)), 0.f);
         }
+        const V mv = vmul(vmake<V>(mx[0], mx[NL - 1]), vmake<V>(my[0], my[NL - 1]));
+#pragma unroll
+        for (int k = 0; k < NL; ++k) m[k] = vlane(mv, k);
     }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) ds[i] = vfma(ax[L::cx(i) + 1], ay[L::cy(i) + 1], vsplat(-float(L::w(i)), rho));
 }
 
 // MRT of Section 5 (mrt_d2q9: M1's orthogonal rows, rest, E, SE, S, SW, W,
@@ -321,8 +327,15 @@ __device__ __forceinline__ void mrt_dev(const V* d, const V* e, const MrtRatesF&
     D[8] = vsub(d[8], vadd(vadd(b, vadd(qx, qy)), pxy));
 }
 
+// One site (V = float): a screened site is recorded as a candidate.  Two
+// sites (V = F2): nothing is recorded; bit k of *scr is set when site k
+// needs the record, and the caller runs both sites again through the
+// one-site form (the same operations, so the same result), which records.
+// (Keeping the pre-collision state live for the rare record would hold 18
+// more registers through the collision.)
 template <class V, class ST, int COLL>
-__device__ __forceinline__ void collide_dev(const Params& p, int x, int y, const V* d, V* D) {
+__device__ __forceinline__ void collide_dev(const Params& p, int x, int y, const V* d, V* D,
+                                            unsigned* scr = nullptr) {
     using L = Lat<9>;
     constexpr int NL = VLanes<V>::n;
     constexpr bool kScreen = COLL == LBM_EHRENFEST || COLL == LBM_MRT_LIMITER;
@@ -350,28 +363,58 @@ __device__ __forceinline__ void collide_dev(const Params& p, int x, int y, const
     V ds[9], e[9];
     float m[NL];
     equilibrium_dev9<V, kScreen>(p.eq, drho, rho, ux, uy, ds, m);
+    V s2;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) e[i] = vsub(d[i], ds[i]);  // f - f*
+    for (int i = 0; i < 9; ++i) {
+        e[i] = vsub(d[i], ds[i]);  // f - f*
+        if (kScreen) s2 = i == 0 ? vmul(e[0], e[0]) : vfma(e[i], e[i], s2);
+        if (COLL == LBM_EHRENFEST || COLL == LBM_MRT_LIMITER) D[i] = vfma(vsplat(-2.f * p.beta_f, rho), e[i], d[i]);
+    }
     if (kScreen) {
-        // the screen of maybe_above_loose on f - f* with m a lower bound of
-        // min f* (the bound's argument holds for any positive one)
-        V s2 = vmul(e[0], e[0]);
+        // The screen of maybe_above_loose on f - f* with m a lower bound of
+        // min f* (the bound's argument holds for any positive one), first as
+        // one product test without the division: a site is quiet when
+        // s2 < m min(m / 4, 0.998 delta) and rho < 1e6 delta.  Then
+        // Delta S <= s2 / m < 0.998 delta, and the FP32 rounding of f* and
+        // d (at most 2e-6 q + 3e-7 sqrt(q rho)) stays inside the 0.2% margin
+        // for rho < 4e7 delta.
+        const float dq = 0.998f * p.delta_f, rq = 1e6f * p.delta_f;
+        // (m = 0 when f* has a non-positive population: bound 0, never quiet)
+        const V mv = vmake<V>(m[0], m[NL - 1]);
+        const V m4 = vmul(mv, vsplat(0.25f, mv));
+        float lim[NL];
 #pragma unroll
-        for (int i = 1; i < 9; ++i) s2 = vfma(e[i], e[i], s2);
+        for (int k = 0; k < NL; ++k) lim[k] = fminf(vlane(m4, k), dq);
+        const V bound = vmul(mv, vmake<V>(lim[0], lim[NL - 1]));
+        unsigned mask = 0u;
 #pragma unroll
-        for (int k = 0; k < NL; ++k) {
-            const float s2k = vlane(s2, k), mk = m[k];
-            bool maybe = true;
-            if (mk > 0.f && s2k < 0.25f * mk * mk) {
-                const float q = __fdividef(s2k, mk);  // approximate (2 ulp), far inside the slack
-                maybe = slack_reaches(q, q, vlane(rho, k), p.delta_f);
+        for (int k = 0; k < NL; ++k)
+            if (!(vlane(s2, k) < vlane(bound, k) && vlane(rho, k) < rq)) mask |= 1u << k;
+        if (mask) {
+            // not certified quiet (near delta, a tiny delta, or not finite):
+            // the division form of the same screen decides
+#pragma unroll
+            for (int k = 0; k < NL; ++k) {
+                const float s2k = vlane(s2, k), mk = m[k];
+                if ((mask >> k & 1u) && mk > 0.f && s2k < 0.25f * mk * mk &&
+                    !slack_reaches(__fdividef(s2k, mk), __fdividef(s2k, mk), vlane(rho, k), p.delta_f))
+                    mask &= ~(1u << k);
             }
-            if (maybe) {
-                float f[9];
+        }
+        if constexpr (NL == 1) {
+            if (mask) {
+                const unsigned pos = atomicAdd(&p.counters[p.cslot], 1u);
+                if (pos < (unsigned)p.cand_cap) {
+                    float* cf = (float*)p.cand_f + pos;
 #pragma unroll
-                for (int i = 0; i < 9; ++i) f[i] = float(L::w(i)) + vlane(d[i], k);
-                record_candidate<9, float>(p, x + k, y, f);
+                    for (int i = 0; i < 9; ++i) cf[(int64_t)i * p.cand_cap] = float(L::w(i)) + vlane(d[i], 0);
+                    p.cand_site[pos] = y * p.nx + x;
+                } else {
+                    atomicExch(&p.counters[CNT_OVERFLOW], 1u);
+                }
             }
+        } else {
+            *scr = mask;
         }
     }
     const float om = 2.f * p.beta_f;
@@ -388,13 +431,25 @@ __device__ __forceinline__ void collide_dev(const Params& p, int x, int y, const
             D[i] = r4 > 0 ? vadd(ds[i], m4) : r4 < 0 ? vsub(ds[i], m4) : r5 > 0 ? vadd(ds[i], m5)
                                                      : r5 < 0 ? vsub(ds[i], m5) : ds[i];
         }
-    } else {
+    } else if (COLL != LBM_EHRENFEST && COLL != LBM_MRT_LIMITER) {
         // LBGK: F = f - 2 beta (f - f*)
         const V nom = vsplat(-om, rho);
 #pragma unroll
         for (int i = 0; i < 9; ++i) D[i] = vfma(nom, e[i], d[i]);
     }
-    if (COLL == LBM_POSITIVITY) {
+    if (COLL == LBM_POSITIVITY && NL > 1) {
+        // a negative population (rare): the caller runs both sites again
+        // through the one-site form, which applies the rule
+        unsigned mask = 0u;
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            bool neg = false;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) neg |= vlane(D[i], k) < -float(L::w(i));
+            if (neg) mask |= 1u << k;
+        }
+        *scr = mask;
+    } else if (COLL == LBM_POSITIVITY) {
 #pragma unroll
         for (int k = 0; k < NL; ++k) {
             bool neg = false;
@@ -834,6 +889,16 @@ __device__ __forceinline__ void st_word(void* base, int off, uint32_t v) {
     *reinterpret_cast<uint32_t*>(reinterpret_cast<uint16_t*>(base) + off) = v;
 }
 
+// Both sites of a pair through the one-site step (out of line: the call is
+// rare and nothing of the pair's collision is live across it).
+template <int Q, class ST, int COLL, bool ODD>
+__device__ __noinline__ void pair_again(const Params& p, int x0, int y) {
+    int e_code = -1, e_iters = 0;
+    typename ST::T acc = 0;
+    site_update<Q, ST, COLL, ODD>(p, x0, y, e_code, e_iters, acc);
+    site_update<Q, ST, COLL, ODD>(p, x0 + 1, y, e_code, e_iters, acc);
+}
+
 template <int Q, class ST, int COLL, bool ODD>
 __global__ void __launch_bounds__(kVecX* kVecY, kPairedMinBlocks) step_kernel_v2(Params p) {
     pdl_enter();
@@ -890,7 +955,15 @@ __global__ void __launch_bounds__(kVecX* kVecY, kPairedMinBlocks) step_kernel_v2
         }
     }
     F2 Dv[Q];  // post-collision deviations F - W of both sites
-    collide_dev<F2, ST, COLL>(p, x0, y, dv, Dv);
+    unsigned scr = 0u;
+    collide_dev<F2, ST, COLL>(p, x0, y, dv, Dv, &scr);
+    if (scr) {
+        // a screened site (rare): nothing is stored yet, so both sites run
+        // again from the unchanged state through the one-site form, which
+        // records the candidate
+        pair_again<Q, ST, COLL, ODD>(p, x0, y);
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int k = ODD ? L::opp(i) : i;
