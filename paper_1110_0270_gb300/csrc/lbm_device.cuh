@@ -402,6 +402,10 @@ __device__ __forceinline__ bool maybe_above_loose(const float* f, const float* f
         s2 = fmaf(d, d, s2);
         m = fminf(m, feq[i]);
     }
+    // quiet without the division: s2 < m min(m / 4, 0.998 delta) and
+    // rho < 1e6 delta give Delta S <= s2 / m < 0.998 delta, the FP32
+    // rounding inside the 0.2% margin (for rho < 4e7 delta)
+    if (m > 0.f && s2 < m * fminf(0.25f * m, 0.998f * delta) && rho < 1e6f * delta) return false;
     if (!(m > 0.f) || !(s2 < 0.25f * m * m)) return true;  // also NaN
     const float q = __fdividef(s2, m);  // approximate (2 ulp), far inside the slack
     return slack_reaches(q, q, rho, delta);
