@@ -608,20 +608,23 @@ __device__ __forceinline__ void mrt_d2q9(const T* f, const T* feq, const MrtRate
 // S(y) = S(f*) - DeltaS(y): with d_i = Delta_i / f*_i and x_i = (alpha-1) d_i,
 //   S_f = sum f*_i [g(-d_i) - g(x_i)],  S_f' = -sum Delta_i ln(1 + x_i),
 //   S_f'' = -sum Delta_i^2 / (f_i + alpha Delta_i).
-// g(x) and ln(1+x) from two Taylor series of the same length (one tier per
-// evaluation, chosen from max |x| so that the lanes of a site stay together):
-// ln(1+x) = x sum_k (-1)^k x^k / (k+1); the first omitted terms are below
-// 2^-54 of the leading ones in every tier.
+// g(x) and ln(1+x) from one Taylor series (one tier per evaluation, chosen
+// from max |x| so that the lanes of a site stay together):
+// ln(1+x) = x (1 + m(x)) with m(x) = sum_{k=1..K} (-1)^k x^k / (k+1), and
+// g(x) = (1+x) ln(1+x) - x = x (x + (1+x) m(x)), which has no cancellation
+// (x + (1+x) m = x/2 - x^2/6 + ...).  With K = max(KL, KG + 1) the first
+// omitted term is below 2^-54 of the leading one for both (KG, KL: the
+// lengths two separate series of g / x^2 and ln(1+x) / x would need).
 template <int KG, int KL>
 __device__ __forceinline__ void gl_series(double x, double& g, double& l) {
-    double pg = ((KG & 1) ? -1.0 : 1.0) / (double)((KG + 1) * (KG + 2));
+    constexpr int K = KL > KG + 1 ? KL : KG + 1;
+    // m / x = sum_{j=0..K-1} (-1)^(j+1) x^j / (j+2)
+    double p = ((K & 1) ? -1.0 : 1.0) / (double)(K + 1);
 #pragma unroll
-    for (int k = KG - 1; k >= 0; --k) pg = fma(pg, x, ((k & 1) ? -1.0 : 1.0) / (double)((k + 1) * (k + 2)));
-    double pl = ((KL & 1) ? -1.0 : 1.0) / (double)(KL + 1);
-#pragma unroll
-    for (int k = KL - 1; k >= 0; --k) pl = fma(pl, x, ((k & 1) ? -1.0 : 1.0) / (double)(k + 1));
-    g = x * x * pg;
-    l = x * pl;
+    for (int j = K - 2; j >= 0; --j) p = fma(p, x, ((j & 1) ? 1.0 : -1.0) / (double)(j + 2));
+    const double m = x * p;
+    l = fma(x, m, x);
+    g = x * fma(m, 1.0 + x, x);
 }
 
 template <int Q, int KG, int KL>
@@ -807,7 +810,7 @@ __device__ ElbmOut elbm_alpha(const double* f, const double* feq, const double* 
     }
     double nrm = 0.0;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) nrm += p.elbm_norm == LBM_NORM_L1 ? fabs(D[i]) : D[i] * D[i] / feq[i];
+    for (int i = 0; i < Q; ++i) nrm += p.elbm_norm == LBM_NORM_L1 ? fabs(D[i]) : D[i] * R[i];  // D^2 / f*
     if (p.elbm_norm != LBM_NORM_L1) nrm = sqrt(nrm);
     double lo = 1.0, hi = amax;
     double a = (2.0 < amax) ? 2.0 : 0.5 * (1.0 + amax);

@@ -785,7 +785,9 @@ __device__ __forceinline__ void block_sum_to_slots(const Params& p, T a, T b, bo
 // capped).
 template <class ST, int COLL>
 constexpr int kMinBlocks =
-    sizeof(typename ST::T) != 4
+    (COLL == LBM_ELBM && sizeof(typename ST::T) == 8)
+        ? 2  // 128 registers: two CTAs per SM also near rest, where the step streams
+        : sizeof(typename ST::T) != 4
         ? 0
         : (COLL == LBM_EHRENFEST || COLL == LBM_POSITIVITY || COLL == LBM_MRT_LIMITER)
               ? 8
