@@ -782,7 +782,7 @@ __device__ ElbmOut elbm_alpha(const double* f, const double* feq, const double* 
     }
     double D[Q], R[Q], gm[Q];
     float Df[Q], gf[Q];
-    double dS = 0.0, amax = __longlong_as_double(0x7ff0000000000000ULL), dmax = 0.0;
+    double dS = 0.0, rneg = 0.0, dmax = 0.0;
     bool neg = false;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -793,10 +793,13 @@ __device__ ElbmOut elbm_alpha(const double* f, const double* feq, const double* 
         gm[i] = gfun_d(-d);
         dS += feq[i] * gm[i];
         neg |= f[i] < 0.0;
-        if (D[i] < 0.0) amax = fmin(amax, -f[i] / D[i]);
+        rneg = fmax(rneg, -d);
         Df[i] = (float)D[i];
         gf[i] = (float)f[i];
     }
+    // alpha_max = min over Delta_i < 0 of -f_i / Delta_i = 1 - f*_i / Delta_i
+    // (f = f* - Delta) = 1 + 1 / max(-Delta_i / f*_i): one division
+    const double amax = rneg > 0.0 ? 1.0 + 1.0 / rneg : __longlong_as_double(0x7ff0000000000000ULL);
     if (!neg && dS < 1e-15 + p.elbm_skip_rel * rho) {
         o.alpha = 2.0;
         o.code = 1;
