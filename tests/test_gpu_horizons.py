@@ -176,6 +176,46 @@ BOUND16 = {
 }
 
 
+def far_state(precision):
+    """A periodic box whose sites lie at every distance from equilibrium:
+    lognormal noise on every population with a per-site width from 1e-3 to
+    0.4 (geometric, shuffled by a seeded permutation)."""
+    ny, nx = 17, 33
+    cfg = dict(lattice="D2Q9", nx=nx, ny=ny, bc="periodic", collision="elbm", precision=precision,
+               beta=0.95)
+    fields = WL.random_fields(ny, nx, 21, 0.05, 0.05)
+    f0 = O.init_equilibrium(dict(cfg, collision="lbgk"), fields["rho"], fields["ux"], fields["uy"])
+    width = np.random.default_rng(23).permutation(np.geomspace(1e-3, 0.4, ny * nx)).reshape(ny, nx)
+    f0 = f0 * WL.lognormal_factors(f0.shape, 22, 1.0) ** width[None]
+    return cfg, as_stored(cfg, f0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_elbm_one_step_at_every_distance_from_equilibrium(precision):
+    """ELBM (Section 3.3) one step from a state whose sites span every
+    series length of the FP64 evaluation of S_f and S_f' (max |x| below
+    1/64, up to 1/8, up to 1/4 and beyond, where ln(1 + x) is used in
+    closed form): x_i = (f_i - f*_i) / f*_i is measured on the start state
+    with the oracle's entropic equilibrium (at the LBGK value alpha = 2 the
+    evaluation's |x| is exactly this)."""
+    cfg, f0 = far_state(precision)
+    ny, nx = cfg["ny"], cfg["nx"]
+    xmax = np.empty((ny, nx))
+    for y in range(ny):
+        for x in range(nx):
+            f = f0[:, y, x]
+            fe = O.equilibrium("D2Q9", "entropic", *O.moments("D2Q9", f))
+            xmax[y, x] = np.abs((f - fe) / fe).max()
+    for lo, hi in [(1e-4, 1 / 64), (1 / 64, 1 / 8), (1 / 8, 1 / 4), (1 / 4, np.inf)]:
+        assert ((xmax >= lo) & (xmax < hi)).sum() >= 5, (lo, hi)
+    g, lat = gpu_run(cfg, f0, 1)
+    f, st = O.step(cfg, f0, 1, stats=True)
+    assert rel(g, f) < TOL[precision], rel(g, f)
+    gs = lat.stats()
+    assert gs["diverged"] == 0 and gs["elbm_solved"] > 100
+    assert gs["elbm_solved"] == st["elbm_solved"]
+
+
 @functools.lru_cache(maxsize=None)
 def cavity_oracle_fp64(collision):
     cfg, f0 = cavity_corners(collision, "fp64")
