@@ -2028,12 +2028,15 @@ __global__ void init_kernel(Params p, const double* rho, const double* ux, const
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= p.nx || y >= p.ny) return;
     const int64_t s = (int64_t)y * p.nx + x;
-    double feq[Q];
-    equilibrium<Q, double>(eqkind, rho[s], ux[s], uy ? uy[s] : 0.0, feq);
+    // in the arithmetic type: FP32 (and 16-bit) storage keeps f* to a few
+    // units of its last place either way, and the FP64 form is FP64-pipe
+    // bound on GB300 (7x the time of the bytes it moves)
+    T feq[Q];
+    equilibrium<Q, T>(eqkind, (T)rho[s], (T)ux[s], uy ? (T)uy[s] : T(0), feq);
     typename ST::S* f = (typename ST::S*)p.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i)
-        ST::st(f + (int64_t)i * p.plane + (int64_t)y * p.pitch + x, (T)feq[i], T(L::w(i)));
+        ST::st(f + (int64_t)i * p.plane + (int64_t)y * p.pitch + x, feq[i], T(L::w(i)));
 }
 
 // f = f*(rho, u) with the same rho, u at every site.
@@ -2145,10 +2148,34 @@ __global__ void macros_kernel(Params p, Out* rho, Out* u, int odd) {
     if (x >= p.nx || y >= p.ny) return;
     T f[Q];
     read_state<Q, ST>(p, x, y, odd != 0, f);
-    double fd[Q], r, a, b;
+    double r, a, b;
+    if constexpr (sizeof(Out) == 4 && sizeof(T) == 4) {
+        // FP32 output from FP32 arithmetic: opposite populations are
+        // subtracted first (exactly, while they lie within a factor 2 of
+        // each other), so rho u keeps its own relative precision however
+        // small u is; the FP64 form is FP64-pipe bound on GB300
+        using L = Lat<Q>;
+        float rf = f[0], jx = 0.f, jy = 0.f;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) fd[i] = (double)f[i];
-    moments<Q, double>(fd, r, a, b);
+        for (int i = 1; i < Q; ++i) rf += f[i];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (L::opp(i) <= i) continue;
+            const float d = f[i] - f[L::opp(i)];
+            if (L::cx(i) > 0) jx += d;
+            if (L::cx(i) < 0) jx -= d;
+            if (L::cy(i) > 0) jy += d;
+            if (L::cy(i) < 0) jy -= d;
+        }
+        r = rf;
+        a = jx / rf;
+        b = jy / rf;
+    } else {
+        double fd[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) fd[i] = (double)f[i];
+        moments<Q, double>(fd, r, a, b);
+    }
     const int64_t N = (int64_t)p.nx * p.ny, s = (int64_t)y * p.nx + x;
     if (rho) rho[s] = (Out)r;
     if (u) {
