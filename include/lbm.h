@@ -208,9 +208,11 @@ void lbm_destroy(lbm_ctx* ctx);
 
 /* f = f*(rho, u) at every site from HOST arrays rho, ux, uy of nx*ny
  * doubles, row-major [y][x] (uy may be NULL for D1Q3).  The equilibrium is
- * the configured one (entropic for ELBM).  Copies the inputs to device
- * scratch first; synchronises `stream` (the host arrays may be reused on
- * return).  Resets the step counter and statistics. */
+ * the configured one (entropic for ELBM), evaluated in the storage's
+ * arithmetic type (FP64 for FP64 storage, FP32 otherwise) from the inputs
+ * rounded to it.  Copies the inputs to device scratch first; synchronises
+ * `stream` (the host arrays may be reused on return).  Resets the step
+ * counter and statistics. */
 lbm_status lbm_init(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy,
                     void* stream);
 
@@ -234,7 +236,10 @@ lbm_status lbm_step(lbm_ctx* ctx, int nsteps, void* stream);
 
 /* Density rho[ny][nx] and velocity u[2][ny][nx] (u_x plane then u_y plane;
  * D1Q3 writes only u_x) of the current state into caller-owned DEVICE
- * buffers of the given dtype. */
+ * buffers of the given dtype.  LBM_DTYPE_F64 outputs are formed in FP64;
+ * LBM_DTYPE_F32 outputs of FP32 or 16-bit storage in FP32, with opposite
+ * populations subtracted before the sum (exact while they lie within a
+ * factor 2 of each other), so that rho u keeps its relative precision. */
 lbm_status lbm_macros(lbm_ctx* ctx, void* rho, void* u, int dtype, void* stream);
 
 /* H = sum_x sum_i f_i ln(f_i / W_i) (minus the perfect-mixture entropy of
