@@ -199,6 +199,37 @@ def test_median_window_sources_match_oracle(precision, beta):
         assert lat.stats()["limited_total"] == st["limited_sites"]
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp16_dev"])
+def test_fp32_init_and_macros(precision):
+    """lbm_init evaluates f* in the storage's arithmetic type and lbm_macros
+    forms FP32 outputs in FP32 (opposite populations subtracted first): from
+    random rho and u the initial state is the oracle's f*(rho, u) to a few
+    FP32 units (plus the 16-bit rounding of f - W), and after 300 steps of a
+    65^2 cavity from rest (speeds from ~1e-9 near the bottom to 0.1 at the
+    lid) the FP32 rho and u of the GPU's own state equal the oracle's
+    moments of that state to 1e-6 of their largest magnitude."""
+    cfg, init = WL.cavity(65, 400.0, 0.1)
+    cfg.update(collision="lbgk", precision=precision)
+    lat = lbm.Lattice(cfg)
+    fields = WL.random_fields(65, 65, 41, 0.05, 0.05)
+    lat.init(fields["rho"], fields["ux"], fields["uy"])
+    g = lat.get_state(torch.float64).cpu().numpy()
+    f = O.init_equilibrium(cfg, fields["rho"], fields["ux"], fields["uy"])
+    _, _, w = O.lattice("D2Q9")
+    slack = 1e-6 * np.abs(f) if precision == "fp32" else np.spacing(
+        np.abs(f - np.asarray(w)[:, None, None]).astype(np.float16)).astype(np.float64) + 1e-7
+    assert (np.abs(g - f) <= slack).all(), float((np.abs(g - f) / slack).max())
+    lat.init(init["rho"], init["ux"], init["uy"])
+    lat.step(300)
+    g = lat.get_state(torch.float64).cpu().numpy()
+    rho, u = lat.macros(torch.float32)
+    r0, ux0, uy0 = O.macros(cfg, g)
+    assert np.abs(rho.double().cpu().numpy() - r0).max() < 1e-6 * np.abs(r0).max()
+    umax = max(np.abs(ux0).max(), np.abs(uy0).max())
+    assert np.abs(u[0].double().cpu().numpy() - ux0).max() < 1e-6 * umax
+    assert np.abs(u[1].double().cpu().numpy() - uy0).max() < 1e-6 * umax
+
+
 def test_cavity_from_rest_fp64_1000_steps_and_macros():
     cfg, init = WL.cavity(41, 400.0, 0.1)
     cfg.update(collision="lbgk", precision="fp64")
